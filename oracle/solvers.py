@@ -1,0 +1,201 @@
+"""Objective, duality-gap certificate, FISTA and pdNCG (oracle side).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* Objective f_tau(x) = tau ||x||_1 + 1/2 ||A x - b||^2, Eq. (prob1).
+* Certificate.  The paper stops its comparison solvers at pdNCG's objective and gives no
+  gap; this project certifies with the Lagrange dual of Eq. (prob1),
+  max_theta b^T theta - 1/2 ||theta||^2 s.t. ||A^T theta||_inf <= tau, at the feasible
+  point theta = s r with r = b - A y and s = min(1, tau / ||A^T r||_inf).  By weak
+  duality P(x) - D(theta) >= P(x) - P(x*) for any x and any such y; at the optimum with
+  y = x = x* it is zero (Sec. 3.1: A^T e = tau g).  rel_gap = gap / max(P, tiny).
+* FISTA (Sec. 8.1; Beck & Teboulle): x_k = S_{tau/L}(y_k - A^T(A y_k - b) / L),
+  t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, y_{k+1} = x_k + ((t_k - 1)/t_{k+1})(x_k - x_{k-1}),
+  y_1 = x_0, t_1 = 1, L an upper bound of lambda_max(A^T A) (fixed, not TFOCS' dynamic L).
+  Iteration k evaluates A x_{k-1} (which certifies x_{k-1} through P(x_{k-1})) and
+  A^T r at y_k (which supplies a dual point); x_{k-1} is returned as soon as
+  P(x_{k-1}) - max_{j<=k} D(y_j) is within the tolerance.  A y_k is formed by linearity
+  from A x_{k-1} and A x_{k-2}.
+* pdNCG (Sec. 8.1 and 8.3): Newton-CG on f^mu_tau(x) = tau psi_mu(x) + 1/2||Ax - b||^2 with
+  the pseudo-Huber psi_mu of Eq. (pseudoHuber), mu = 1e-5.  The Newton system of the model
+  (bd4) is solved by PCG with the inverse diagonal of its matrix as preconditioner, stopped
+  at relative residual 0.1; then a backtracking (halving) Armijo line search with at most
+  50 trials, accepting the last trial when none passes.
+  Readings (the paper defers the details of its primal-dual method to its reference):
+  - primal-dual direction: Newton's method on the pair of conditions
+    tau g + A^T(Ax - b) = 0 and g_i sqrt(mu^2 + x_i^2) = x_i, linearised in (x, g) and with
+    dx eliminated for, gives [A^T A + tau diag((1 - g_i x_i / w_i) / w_i)] dx = -grad f^mu(x)
+    (w_i = sqrt(mu^2 + x_i^2)); with g = x / w this is exactly the Newton system of (bd4).
+    The dual estimate is updated by the full Newton step dg = (x + (1 - g x / w) dx) / w - g
+    and projected onto [-1, 1]^n.  (The purely primal system stalls on these instances:
+    its curvature mu^2 / w^3 spans ~15 decades and steps shrink to ~1e-4.)
+  - Armijo constant 1e-4; psi_mu evaluated as x^2 / (sqrt(mu^2 + x^2) + mu) and the line
+    search through per-coordinate differences, the same quantities without cancellation.
+  - mu-continuation: the smoothed minimiser carries an O(mu) bias in the l1 certificate
+    (about 0.2 tau mu per zero of x*), so when a full Newton step (alpha = 1) fails to halve
+    the gap, mu <- max(mu / 10, mu_min).
+"""
+
+import math
+
+import numpy as np
+
+TINY = 1e-300
+
+STATUS_OK = 0
+STATUS_NOCONV = 6
+
+
+def objective(A, b, tau, x):
+    """f_tau(x), Eq. (prob1)."""
+    r = A @ x - b
+    return tau * np.abs(x).sum() + 0.5 * float(r @ r)
+
+
+def dual_value(b, r, atr, tau):
+    """D(theta) at theta = s r, s = min(1, tau/||A^T r||_inf)."""
+    amax = float(np.abs(atr).max()) if len(atr) else 0.0
+    s = 1.0 if amax <= tau else tau / amax
+    return s * float(b @ r) - 0.5 * s * s * float(r @ r)
+
+
+def certificate(A, b, tau, x):
+    """(P, D, gap, rel_gap) at x with the dual point built from r = b - A x."""
+    r = b - A @ x
+    atr = A.T @ r
+    P = tau * np.abs(x).sum() + 0.5 * float(r @ r)
+    D = dual_value(b, r, atr, tau)
+    gap = P - D
+    return P, D, gap, gap / max(abs(P), TINY)
+
+
+def soft_threshold(v, t):
+    """Shrinkage S_t(v) = sign(v) max(|v| - t, 0), the exact minimiser of the separable
+    model (bd1) with H = L I (Sec. 2)."""
+    return np.sign(v) * np.maximum(np.abs(v) - t, 0.0)
+
+
+def fista(A, b, tau, L, tol, max_iter, x0=None):
+    """FISTA with the certificate above.  Returns dict(x, iters, products, P, D, gap, rel_gap, status)."""
+    n = A.shape[1]
+    x_cur = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)   # x_{k-1}
+    x_old = x_cur.copy()                                                              # x_{k-2}
+    Ax_old = A @ x_old
+    products = 1
+    t = 1.0
+    beta = 0.0
+    best_D = -math.inf
+    k = 1
+    while True:
+        u = A @ x_cur                                   # A x_{k-1}
+        P = tau * np.abs(x_cur).sum() + 0.5 * float((u - b) @ (u - b))
+        y = x_cur + beta * (x_cur - x_old)              # y_k
+        Ay = u + beta * (u - Ax_old)
+        r = b - Ay
+        g = A.T @ r                                     # -grad of the smooth part at y_k
+        products += 2
+        best_D = max(best_D, dual_value(b, r, g, tau))
+        gap = P - best_D
+        rel = gap / max(abs(P), TINY)
+        if rel <= tol or k - 1 >= max_iter:
+            return dict(x=x_cur, iters=k - 1, products=products, P=P, D=best_D, gap=gap,
+                        rel_gap=rel, status=STATUS_OK if rel <= tol else STATUS_NOCONV)
+        x_new = soft_threshold(y + g / L, tau / L)
+        t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
+        beta = (t - 1.0) / t_new
+        t = t_new
+        x_old, x_cur = x_cur, x_new
+        Ax_old = u
+        k += 1
+
+
+def psi_terms(x, mu):
+    """Per-coordinate sqrt(mu^2 + x^2) - mu of Eq. (pseudoHuber), cancellation-free."""
+    return x * x / (np.sqrt(mu * mu + x * x) + mu)
+
+
+def psi_diff_terms(x, d, alpha, mu):
+    """Per-coordinate psi(x + alpha d) - psi(x), cancellation-free."""
+    xt = x + alpha * d
+    return (alpha * d) * (x + xt) / (np.sqrt(mu * mu + xt * xt) + np.sqrt(mu * mu + x * x))
+
+
+def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, pcg_max=1000,
+          ls_max=50, armijo=1e-4, stall=0.5, x0=None):
+    """Primal-dual Newton-CG with the certificate above.
+
+    Returns dict(x, iters, products, cg_iters, ls_trials, P, D, gap, rel_gap, mu, status).
+    """
+    m, n = A.shape
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    gd = np.zeros(n)                                                # dual estimate g
+    mu = mu0
+    colnorm2 = np.asarray(A.multiply(A).sum(axis=0)).ravel()       # diag(A^T A)
+    products = 0
+    cg_total = 0
+    ls_total = 0
+    it = 0
+    prev_gap = math.inf
+    prev_full = False
+    while True:
+        Ax = A @ x
+        r = b - Ax
+        atr = A.T @ r
+        products += 2
+        P = tau * np.abs(x).sum() + 0.5 * float(r @ r)
+        D = dual_value(b, r, atr, tau)
+        gap = P - D
+        rel = gap / max(abs(P), TINY)
+        if rel <= tol or it >= max_newton:
+            return dict(x=x, iters=it, products=products, cg_iters=cg_total, ls_trials=ls_total,
+                        P=P, D=D, gap=gap, rel_gap=rel, mu=mu,
+                        status=STATUS_OK if rel <= tol else STATUS_NOCONV)
+        if prev_full and gap > stall * prev_gap:
+            mu = max(mu * 0.1, mu_min)
+        prev_gap = gap
+        w = np.sqrt(mu * mu + x * x)
+        grad = tau * x / w - atr                                    # grad f^mu
+        hdiag = tau * (1.0 - gd * x / w) / w                        # primal-dual psi curvature
+        minv = 1.0 / (hdiag + colnorm2)
+        gnorm = math.sqrt(float(grad @ grad))
+        # PCG on (diag(hdiag) + A^T A) d = -grad from d = 0.
+        d = np.zeros(n)
+        res = -grad
+        z = minv * res
+        p = z.copy()
+        rz = float(res @ z)
+        for _ in range(pcg_max):
+            Ap = A @ p
+            Hp = hdiag * p + A.T @ Ap
+            products += 2
+            cg_total += 1
+            pHp = float(p @ Hp)
+            if pHp <= 0.0:
+                break
+            alpha = rz / pHp
+            d += alpha * p
+            res -= alpha * Hp
+            if math.sqrt(float(res @ res)) <= pcg_rtol * gnorm:
+                break
+            z = minv * res
+            rz_new = float(res @ z)
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        # Backtracking Armijo line search on f^mu.
+        Ad = A @ d
+        products += 1
+        slope = float(grad @ d)
+        rAd = float(r @ Ad)
+        AdAd = float(Ad @ Ad)
+        step = 1.0
+        for trial in range(ls_max):
+            ls_total += 1
+            df = tau * float(psi_diff_terms(x, d, step, mu).sum()) - step * rAd + 0.5 * step * step * AdAd
+            if df <= armijo * step * slope or trial == ls_max - 1:
+                break                                               # the last trial is accepted
+            step *= 0.5
+        dg = (x + (1.0 - gd * x / w) * d) / w - gd
+        x = x + step * d
+        gd = np.clip(gd + dg, -1.0, 1.0)
+        prev_full = step == 1.0
+        it += 1

@@ -1,0 +1,128 @@
+"""Pins of the oracle's objective, certificate, FISTA and pdNCG.
+
+Closed forms (shrinkage for orthogonal A, Sec. 2), the generator's known optimum (IGen,
+Sec. 3.1; unique because A has rank n), weak duality, and brute-force support
+enumeration (Eq. bd9) for tiny n.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import solvers
+from oracle.brute import brute_force
+from oracle.generator import GenParams, generate
+
+
+def _small(seed=0, kappa=20.0, tau=1.0, m=16, n=8, right=1, frac=0.25):
+    return generate(GenParams(m=m, n=n, seed=seed, kappa=kappa, tau=tau, right_stages=right,
+                              xstar_frac=frac))
+
+
+def test_soft_threshold_definition():
+    v = np.array([-3.0, -0.5, 0.0, 0.2, 2.5])
+    assert np.array_equal(solvers.soft_threshold(v, 1.0), np.array([-2.0, -0.0, 0.0, 0.0, 1.5]))
+
+
+@pytest.mark.parametrize("tau", [0.3, 1.0, 4.0])
+def test_orthogonal_A_closed_form(tau):
+    """A^T A = I: the minimiser is S_tau(A^T b); FISTA with L = 1 reaches it in one step."""
+    inst = generate(GenParams(m=64, n=32, seed=1, kappa=1.0, right_stages=2, tau=1.0, xstar_frac=0.2))
+    A, b = inst.A, inst.b
+    x_cf = solvers.soft_threshold(A.T @ b, tau)
+    r = solvers.fista(A, b, tau, 1.0, 1e-12, 10)
+    assert r["iters"] == 1
+    assert np.allclose(r["x"], x_cf, atol=1e-13)
+    q = solvers.pdncg(A, b, tau, 1e-10)
+    assert q["status"] == 0
+    assert np.allclose(q["x"], x_cf, atol=1e-5)
+
+
+def test_certificate_zero_at_generated_optimum_and_weak_duality():
+    inst = generate(GenParams(m=256, n=128, seed=2, kappa=100.0, right_stages=2))
+    A, b, tau = inst.A, inst.b, 1.0
+    assert abs(solvers.certificate(A, b, tau, inst.xstar)[3]) < 1e-13
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        x = inst.xstar + rng.standard_normal(128)
+        y = rng.standard_normal(128)
+        r = b - A @ y
+        D = solvers.dual_value(b, r, A.T @ r, tau)
+        assert solvers.objective(A, b, tau, x) >= D
+        assert D <= inst.f_star * (1 + 1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fista_and_pdncg_reach_the_generated_optimum(seed):
+    inst = generate(GenParams(m=512, n=256, seed=seed, kappa=100.0, right_stages=2, xstar_frac=0.05))
+    A, b = inst.A, inst.b
+    smin = inst.sigma.min()
+    for res in (solvers.fista(A, b, 1.0, inst.lipschitz, 1e-8, 100000), solvers.pdncg(A, b, 1.0, 1e-8)):
+        assert res["status"] == 0
+        assert res["rel_gap"] <= 1e-8
+        # strong convexity: ||x - x*||^2 <= 2 gap / sigma_min^2
+        err2 = float(np.sum((res["x"] - inst.xstar) ** 2))
+        assert err2 <= 2.0 * res["gap"] / smin ** 2 + 1e-20
+        assert res["P"] >= inst.f_star * (1 - 1e-14)
+
+
+@pytest.mark.parametrize("tau_factor", [1.0, 0.4, 2.5])
+@pytest.mark.parametrize("right", [1, 2])
+def test_brute_force_agrees(tau_factor, right):
+    inst = _small(seed=3, right=right, tau=1.0)
+    A, b = inst.A, inst.b
+    tau = tau_factor
+    xb, fb = brute_force(A, b, tau)
+    if tau_factor == 1.0:
+        assert np.allclose(xb, inst.xstar, atol=1e-10)
+    f = solvers.fista(A, b, tau, inst.lipschitz, 1e-12, 200000)
+    q = solvers.pdncg(A, b, tau, 1e-12)
+    for res in (f, q):
+        assert res["status"] == 0
+        assert np.allclose(res["x"], xb, atol=1e-4)
+        assert math.isclose(res["P"], fb, rel_tol=1e-11)
+
+
+def test_fista_warm_start_at_optimum_needs_no_iteration():
+    inst = _small(seed=4)
+    r = solvers.fista(inst.A, inst.b, 1.0, inst.lipschitz, 1e-12, 100, x0=inst.xstar)
+    assert r["iters"] == 0
+
+
+def test_fista_is_beck_teboulle_on_a_tiny_case():
+    """Three iterations written out by hand from the FISTA recursion."""
+    inst = _small(seed=5, kappa=5.0)
+    A, b, L, tau = inst.A.toarray(), inst.b, inst.lipschitz, 0.6
+    x_prev = np.zeros(8)
+    y = x_prev.copy()
+    t = 1.0
+    for _ in range(3):
+        x = solvers.soft_threshold(y - A.T @ (A @ y - b) / L, tau / L)
+        t_new = (1 + math.sqrt(1 + 4 * t * t)) / 2
+        y = x + ((t - 1) / t_new) * (x - x_prev)
+        x_prev, t = x, t_new
+    r = solvers.fista(inst.A, b, tau, L, 0.0, 3)
+    assert r["iters"] == 3
+    assert np.allclose(r["x"], x_prev, atol=1e-14)
+
+
+def test_pdncg_newton_count_is_small_on_c1_shape():
+    """The paper reports at most 30 pdNCG iterations on its Sec. 8.4 instances."""
+    inst = generate(GenParams(m=2048, n=1024, seed=0, kappa=100.0, xstar_frac=0.05))
+    r = solvers.pdncg(inst.A, inst.b, 1.0, 1e-8)
+    assert r["status"] == 0 and r["iters"] <= 30
+
+
+def test_planted_dual_scaling_error_is_caught(monkeypatch):
+    """Dropping the scaling s of the dual point breaks weak duality at a random point."""
+    inst = generate(GenParams(m=64, n=32, seed=1, kappa=10.0))
+    A, b = inst.A, inst.b
+
+    def bad_dual(b_, r, atr, tau):
+        return float(b_ @ r) - 0.5 * float(r @ r)
+
+    monkeypatch.setattr(solvers, "dual_value", bad_dual)
+    y = np.zeros(32)
+    r = b - A @ y
+    assert solvers.dual_value(b, r, A.T @ r, 1.0) > inst.f_star
