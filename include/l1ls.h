@@ -1,0 +1,199 @@
+/*
+ * l1ls -- l1-regularised least squares on one GB300: the instance generator, the products
+ * A x and A^T y, FISTA and primal-dual Newton-CG, behind a plain C ABI.
+ *
+ * Problem (Eq. prob1 of Fountoulakis & Gondzio, "Performance of First- and Second-Order
+ * Methods for l1-Regularized Least Squares Problems"):
+ *
+ *     minimise  f_tau(x) = tau ||x||_1 + 1/2 ||A x - b||_2^2,   A in R^{m x n}.
+ *
+ * Conventions for every entry point
+ *  - Status: every function returns an l1ls_status; on anything but L1LS_OK a message for
+ *    the calling thread is available from l1ls_last_error().  No entry point aborts, exits
+ *    or traps; a CUDA error is reported as L1LS_ECUDA.
+ *  - Ownership: a context owns all device memory it allocates (instances, work buffers).
+ *    Buffers passed in by the caller stay owned by the caller.
+ *  - Pointers: vector arguments may point to device memory (any pointer CUDA reports as
+ *    device or managed memory) or to host memory.  Device pointers are used in place and
+ *    the work is only enqueued on `stream` (the caller synchronises).  Host pointers are
+ *    staged through context buffers and the call returns after the result has been copied
+ *    back (it synchronises `stream`).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  It must belong to the device the context was created on.
+ *  - Threads: one thread at a time per context, except l1ls_submit / l1ls_poll /
+ *    l1ls_cancel, which may be called from any thread.
+ *  - Row order: the library stores P1^T A (rows relabelled by the generator's row
+ *    permutation, so the two rows mixed by one left rotation are adjacent).  Every entry
+ *    point that takes or returns an m-vector (b, y of l1ls_matvec / l1ls_rmatvec, exports)
+ *    uses the ORIGINAL row order of A.
+ */
+#ifndef L1LS_H
+#define L1LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct l1ls_ctx l1ls_ctx;     /* one GPU: streams, work buffers, memory budget      */
+typedef struct l1ls_inst l1ls_inst;   /* a generated instance resident in device memory     */
+
+typedef enum {
+    L1LS_OK = 0,
+    L1LS_EINVAL = 1,      /* an argument is out of range or inconsistent                    */
+    L1LS_ENOMEM = 2,      /* device or host allocation failed, or the budget is exceeded    */
+    L1LS_ECUDA = 3,       /* a CUDA call failed; the context may be unusable                */
+    L1LS_ETIMEOUT = 4,    /* time limit reached before convergence (result still filled)    */
+    L1LS_ENOCONV = 5,     /* iteration limit reached before convergence (result filled)      */
+    L1LS_ENUMERIC = 6,    /* a NaN or Inf appeared in the iteration                          */
+    L1LS_EBUSY = 7,       /* the request does not fit the memory budget right now            */
+    L1LS_ENOTFOUND = 8,   /* unknown ticket                                                   */
+    L1LS_ECANCELLED = 9   /* the request was cancelled                                        */
+} l1ls_status;
+
+typedef enum { L1LS_F64 = 0, L1LS_F32 = 1, L1LS_BF16 = 2 } l1ls_dtype;
+
+/*
+ * Generator parameters: Procedure IGen (Sec. 3.1) for m >= n, IGen2 (Sec. 3.2) for m < n,
+ * matrix A = (P1 G~ P2) Sigma G^T of Eq. (bd8) with the Givens stages of Sec. 4.1-4.2 and
+ * x* from Procedure OsGen (Sec. 6).
+ *   right_stages  w >= 1 stages in the right factor R = T_w ... T_1, T_1 on planes
+ *                 (0,1),(2,3),... and T_2 on planes (1,2),(3,4),..., alternating.
+ *   left_stages   0 (L = I, the A = Sigma G^T of the experiments of Sec. 8) or 1
+ *                 (L = P G~ P of Sec. 4.1; m must then be even).
+ *   kappa         kappa(A) = sigma_max / sigma_min >= 1; sigma_i = kappa^(-rank_i/(n-1)).
+ *   tau           the tau of IGen; x* is the unique minimiser of f_tau for this tau.
+ *   xstar_frac    s = floor(frac * n + 0.5) nonzeros (clamped to [1, min(m, n)]) with
+ *                 magnitudes U[xstar_lo, xstar_hi] and random signs.
+ *   theta,        rotation angles of the right and left stages (vartheta NaN: = theta).
+ *   vartheta
+ *   value_dtype   l1ls_dtype in which the nonzeros of A are stored (rounded from FP64).
+ *   g_offsupport  0: g_i ~ U(-1,1) off the support of x*; 1: g_i = 0 there.
+ *   n_nnz_per_col IGen2 only: nonzeros per column of N.
+ *   seed          all random draws are SplitMix64 streams of this seed.
+ */
+typedef struct {
+    uint64_t m, n, seed;
+    double kappa;
+    double tau;
+    double xstar_frac, xstar_lo, xstar_hi;
+    double theta, vartheta;
+    int32_t right_stages;
+    int32_t left_stages;
+    int32_t value_dtype;
+    int32_t g_offsupport;
+    int32_t n_nnz_per_col;
+    int32_t reserved;
+} l1ls_gen_params;
+
+/* Fill p with the defaults: m = 2048, n = 1024, seed 0, kappa 100, tau 1, frac 0.05,
+ * magnitudes [1, 10], w = 1, one left stage, theta = vartheta = 2 pi / 10, FP64 values. */
+void l1ls_gen_params_default(l1ls_gen_params* p);
+
+typedef struct {
+    uint64_t m, n, nnz, s;
+    double f_star;        /* f_tau(x*) at tau = tau_gen                                       */
+    double lipschitz;     /* upper bound of lambda_max(A^T A) used by FISTA                    */
+    double lam_max;       /* ||A^T b||_inf: every tau >= lam_max has minimiser 0               */
+    double tau_gen;
+    int32_t value_dtype, right_stages, left_stages, igen2;
+    uint64_t device_bytes;/* device memory held by the instance                                */
+} l1ls_inst_info;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
+ * context may hold for instances and solver state (0 = 90% of the free memory at creation).
+ * Errors: EINVAL (bad device), ECUDA. */
+l1ls_status l1ls_create(int device, size_t hbm_budget_bytes, l1ls_ctx** out);
+
+/* Destroy a context: waits for its serving thread, frees every instance it still owns. */
+l1ls_status l1ls_destroy(l1ls_ctx* ctx);
+
+/* Generate an instance on the device (Procedures IGen / IGen2, Eq. bd8, OsGen): random keys
+ * and permutations, singular values, x*, g, e and b by the matrix-free route of Sec. 4
+ * (two products with the right factor and a diagonal scaling), and CSR(P1^T A) and
+ * CSR(A^T P1) with FP64 values rounded once to value_dtype.  The integer structure is
+ * fully determined by the parameters.  Enqueued on `stream`; returns after completion.
+ * Errors: EINVAL (sizes, stages, kappa < 1, nnz >= 2^31), ENOMEM (budget), ECUDA. */
+l1ls_status l1ls_generate(l1ls_ctx* ctx, const l1ls_gen_params* p, void* stream, l1ls_inst** out);
+
+l1ls_status l1ls_inst_free(l1ls_inst* inst);
+l1ls_status l1ls_inst_get_info(const l1ls_inst* inst, l1ls_inst_info* info);
+
+/* Copy an instance to host buffers (any may be NULL).  A is returned in CSR with the
+ * ORIGINAL row order and ascending column indices within each row; values converted to
+ * double from the stored dtype.  row_ptr: m+1, col_idx/vals: nnz, b: m, xstar/sigma: n
+ * (sigma: the singular values of the square factor, length min(m, n)), perm: m (the row
+ * permutation P, (P v)_i = v_{perm[i]}; identity when left_stages = 0).  Synchronous. */
+l1ls_status l1ls_inst_export(const l1ls_inst* inst, int64_t* row_ptr, int32_t* col_idx, double* vals,
+                             double* b, double* xstar, double* sigma, int64_t* perm);
+
+/* Copy CSR(A^T) (= CSC of A) to host: col_ptr n+1, row_idx/vals nnz, row indices in the
+ * ORIGINAL row order, ascending within each column.  Synchronous. */
+l1ls_status l1ls_inst_export_t(const l1ls_inst* inst, int64_t* col_ptr, int32_t* row_idx, double* vals);
+
+/* y = A x (Algorithm MvPA computes the same product matrix-free).  x: n entries, y: m
+ * entries, both of type vec_dtype (L1LS_F64 or L1LS_F32).  Accumulation is in FP64 for
+ * FP64 values and FP32 otherwise.  Errors: EINVAL, ECUDA. */
+l1ls_status l1ls_matvec(const l1ls_inst* inst, const void* x, l1ls_dtype vec_dtype, void* y, void* stream);
+
+/* x = A^T y (Algorithm MvPAt).  y: m entries, x: n entries, as for l1ls_matvec. */
+l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream);
+
+/* Solver options.  Defaults (l1ls_solve_opts_default): tau 1, rel_gap_tol 1e-6,
+ * max_iter 100000 (FISTA iterations; Newton steps for pdNCG: 200), no time limit, mu 1e-5,
+ * mu_min 1e-14, pcg_rtol 0.1, pcg_max 1000, ls_max 50, armijo 1e-4, check_every 32. */
+typedef struct {
+    double tau;
+    double rel_gap_tol;
+    int64_t max_iter;
+    double time_limit_s;      /* <= 0: none */
+    double mu, mu_min, pcg_rtol, armijo;
+    int32_t ls_max, pcg_max;
+    int32_t check_every;      /* iterations per graph launch between host checks          */
+    int32_t reserved;
+} l1ls_solve_opts;
+
+void l1ls_solve_opts_default(l1ls_solve_opts* o);
+
+typedef struct {
+    int64_t iters;            /* FISTA iterations / Newton steps performed                  */
+    int64_t products;         /* products with A or A^T                                      */
+    int64_t cg_iters, ls_trials;
+    double f;                 /* primal objective f_tau at the returned x                    */
+    double dual;              /* dual objective of the certifying dual point                  */
+    double gap, rel_gap;      /* f - dual and (f - dual) / f                                  */
+    double seconds;           /* wall time of the call                                        */
+    double mu;                /* final smoothing parameter (pdNCG)                            */
+    int32_t status;           /* l1ls_status of the solve                                     */
+    int32_t reserved;
+} l1ls_result;
+
+/* FISTA (Sec. 8.1; Beck & Teboulle) with fixed L = info.lipschitz from x0 (NULL: 0).  Stops
+ * when the duality-gap certificate P(x_k) - max_j D(theta(y_j)) is at most rel_gap_tol * P(x_k),
+ * where theta(y) = s (b - A y), s = min(1, tau / ||A^T (b - A y)||_inf).  x0 and x_out are
+ * n doubles (device or host; x_out may be NULL).  Returns ENOCONV / ETIMEOUT with `res`
+ * filled when a limit is hit, ENUMERIC on NaN/Inf.  Blocking. */
+l1ls_status l1ls_solve_fista(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
+                             l1ls_result* res, void* stream);
+
+/* pdNCG (Sec. 8.1, parameters of Sec. 8.3): primal-dual Newton-CG on the pseudo-Huber
+ * smoothing (Eqs. pseudoHuber, prob2, bd4) with diagonal-preconditioned CG stopped at
+ * relative residual pcg_rtol, a halving Armijo line search of at most ls_max trials, and
+ * mu reduced tenfold when a full Newton step fails to halve the gap.  Certified with the
+ * same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista. */
+l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
+                             l1ls_result* res, void* stream);
+
+/* Thread-local message describing the last non-OK status returned on this thread. */
+const char* l1ls_last_error(void);
+
+/* Library version string. */
+const char* l1ls_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* L1LS_H */

@@ -339,3 +339,42 @@ def _generate_igen2(p: GenParams) -> Instance:
     lipschitz = float(sigma.max() ** 2) + bound
     return Instance(p, A, b, xstar, g, e, sigma, perm, S, R, L, f_star, lam_max, lipschitz,
                     extra={"B": B, "N": Ntil, "xi": xi})
+
+
+@dataclass
+class Factors:
+    """The ingredients of Eq. (bd8) and of x*, without assembling A (m >= n only)."""
+    params: GenParams
+    sigma: np.ndarray
+    perm: np.ndarray
+    xstar: np.ndarray
+    support: np.ndarray
+    g: np.ndarray
+
+
+def make_factors(p: GenParams) -> Factors:
+    if p.m < p.n:
+        raise ValueError("make_factors covers IGen (m >= n)")
+    sigma = singular_values(p.seed, p.n, p.kappa)
+    perm = row_permutation(p.seed, p.m) if p.left_stages > 0 else None
+    xstar, S = optimal_solution(p, p.n)
+    g = subgradient(p, xstar, p.n)
+    return Factors(p, sigma, perm, xstar, S, g)
+
+
+def igen_matrix_free(f: Factors):
+    """(b, e) of Procedure IGen through Algorithm MvPA, the route the paper proposes when A is
+    not stored (Sec. 4): e = tau A G (Sigma^T Sigma)^{-1} G^T g, b = A x* + e."""
+    from .operators import rotate, rotate_t   # local import: operators imports this module
+    p = f.params
+    c, s, _, _ = angles(p)
+    v = np.array(f.g, dtype=np.float64, copy=True)
+    for k in range(p.right_stages, 0, -1):      # G^T g
+        rotate_t(v, stage_first(k), c, s)
+    v = v / (f.sigma * f.sigma)
+    for k in range(1, p.right_stages + 1):      # G (...)
+        rotate(v, stage_first(k), c, s)
+    from .operators import mvpa
+    e = p.tau * mvpa(f, v)
+    b = mvpa(f, f.xstar) + e
+    return b, e

@@ -36,6 +36,7 @@ def rotate_t(v, first, c, s):
 
 
 def _square_dims(inst):
+    """Works for an Instance or a Factors object (both carry params, sigma and perm)."""
     p = inst.params
     size = p.n if p.m >= p.n else p.m
     return size, p.m

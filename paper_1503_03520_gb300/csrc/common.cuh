@@ -1,0 +1,135 @@
+// Device helpers shared by the l1ls kernels: SplitMix64 streams, value conversions,
+// deterministic block reductions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace l1ls {
+
+// ---- SplitMix64 (Steele, Lea & Flood 2014) as counter-based streams ------------------------
+// The i-th output (0-based) of SplitMix64 started at state s0 is mix64(s0 + (i+1) * gamma);
+// stream `tag` of `seed` starts at output `tag` of the generator seeded with `seed`.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm_output(uint64_t s0, uint64_t i) {
+    return mix64(s0 + (i + 1ull) * kGamma);
+}
+__host__ __device__ __forceinline__ uint64_t sm_stream(uint64_t seed, uint64_t tag) {
+    return sm_output(seed, tag);
+}
+// uniform double in [0, 1) from the top 53 bits
+__host__ __device__ __forceinline__ double u01(uint64_t u) {
+    return (double)(u >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// stream tags (one stream per random quantity of the generator)
+enum : uint64_t {
+    kTagSigma = 1, kTagPerm = 2, kTagSupport = 3, kTagXVal = 4, kTagXSign = 5, kTagGOff = 6,
+    kTagNRow = 7, kTagNVal = 8, kTagXi = 9
+};
+
+// ---- conversions ------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<double>(double v) { return (float)v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class Acc, class T> __device__ __forceinline__ Acc to_acc(T v);
+template <> __device__ __forceinline__ double to_acc<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_acc<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_acc<float, double>(double v) { return (float)v; }
+
+template <class T> __device__ __forceinline__ T from_double(double v);
+template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
+    return __double2bfloat16(v);
+}
+
+// ---- reductions ---------------------------------------------------------------------------
+template <bool IS_MAX> __device__ __forceinline__ double red_op(double a, double b) {
+    if constexpr (IS_MAX) return fmax(a, b);
+    else return a + b;
+}
+
+template <bool IS_MAX> __device__ __forceinline__ double warp_reduce(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = red_op<IS_MAX>(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block reduction of NP values; `maxmask` bit i selects max instead of sum for value i.
+// Fixed order: lanes by shuffle tree, warps in index order.  Result valid in thread 0.
+template <int BLOCK, int NP>
+__device__ __forceinline__ void block_reduce(double (&v)[NP], unsigned maxmask, double* smem /*[NP*32]*/) {
+    constexpr int NW = BLOCK / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        v[i] = ((maxmask >> i) & 1) ? warp_reduce<true>(v[i]) : warp_reduce<false>(v[i]);
+        if (lane == 0) smem[i * 32 + wid] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            double a = smem[i * 32];
+            for (int w = 1; w < NW; ++w) a = ((maxmask >> i) & 1) ? fmax(a, smem[i * 32 + w]) : a + smem[i * 32 + w];
+            v[i] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide deterministic reduction through per-block partials and a "last block" step.
+// Every block calls it with its block totals (valid in thread 0).  The block that arrives
+// last reduces all partials in a fixed order and returns true with the totals in `tot`
+// (valid in thread 0).  `counter` must be zero on entry to the launch; it is reset here.
+template <int BLOCK, int NP>
+__device__ __forceinline__ bool grid_reduce_last(const double (&blk)[NP], unsigned maxmask, double* partials,
+                                                 unsigned* counter, double (&tot)[NP], double* smem) {
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) partials[(size_t)blockIdx.x * NP + i] = blk[i];
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double v[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) v[i] = ((maxmask >> i) & 1) ? -INFINITY : 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += BLOCK) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            double p = __ldcg(&partials[(size_t)b * NP + i]);
+            v[i] = ((maxmask >> i) & 1) ? fmax(v[i], p) : v[i] + p;
+        }
+    }
+    block_reduce<BLOCK, NP>(v, maxmask, smem);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) tot[i] = v[i];
+        *counter = 0u;
+    }
+    return true;
+}
+
+__device__ __forceinline__ double soft_threshold(double v, double t) {
+    double a = fabs(v) - t;
+    return a > 0.0 ? copysign(a, v) : 0.0;
+}
+
+}  // namespace l1ls

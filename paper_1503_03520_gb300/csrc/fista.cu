@@ -1,0 +1,419 @@
+// FISTA (Sec. 8.1; Beck & Teboulle) with fused epilogues and a duality-gap certificate.
+//
+// Iteration k (k = 1, 2, ...) runs two kernels, each streaming one copy of A once:
+//   K1  u = A x_{k-1};  A y_k = u + beta_k (u - A x_{k-2});  r_k = b - A y_k
+//       writes u over A x_{k-2} and r_k; partial sums (u - b)^2, b.r_k, r_k^2  [FP64]
+//   K2  g = A^T r_k;  y_k = x_{k-1} + beta_k (x_{k-1} - x_{k-2});
+//       x_k = S_{tau/L}(y_k + g / L) written over x_{k-2}; partials max|g|, sum|x_k|
+//       the last CTA certifies x_{k-1}: P = tau ||x_{k-1}||_1 + 1/2 ||u - b||^2,
+//       D_k = s b.r_k - s^2/2 ||r_k||^2 with s = min(1, tau / ||g||_inf), gap = P - max_j D_j,
+//       and either stops (flag in device memory) or advances t, beta.
+// Every kernel returns at once when the stop flag is set, so chunks of iterations are
+// captured in one CUDA graph and launched without host round trips.  x_{k-1} and x_{k-2}
+// alternate between two buffers; a chunk holds an even number of iterations.
+// FP64 values: all vectors FP64.  FP32 / BF16 values: products, residuals and A x in FP32
+// (FP32 accumulation), iterates and every reduction in FP64, FP32 shadow of x for gathers.
+#include <chrono>
+#include <cmath>
+
+#include "internal.h"
+#include <cstring>
+#include "spmv.cuh"
+
+namespace l1ls {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct FistaState {
+    double tau, L, tol;
+    int64_t max_iter;
+    double t, beta, best_d, l1_cur;
+    double k1[3];
+    int64_t iter, cert_iter, products;
+    double P, D, gap, rel;
+    int32_t stop, status;
+    unsigned cnt1, cnt2;
+};
+
+template <class V, class Vec>
+struct K1Args {
+    const int32_t* ptr;
+    const int32_t* col;
+    const V* val;
+    const Vec* x;        // x_{k-1} (gather source)
+    Vec* ax;             // in: A x_{k-2}; out: A x_{k-1}
+    Vec* res;            // out: r_k = b - A y_k
+    const Vec* b;
+    double* partials;
+    FistaState* st;
+    int64_t m;
+};
+
+template <class V, class Vec>
+struct K2Args {
+    const int32_t* ptr;
+    const int32_t* col;
+    const V* val;
+    const Vec* res;
+    const double* xc;    // x_{k-1}
+    double* xo;          // in: x_{k-2}; out: x_k
+    float* xo32;         // FP32 shadow of x_k (nullptr for FP64 values)
+    double* partials;
+    FistaState* st;
+    int64_t n;
+};
+
+template <class V> constexpr int cap_of() { return sizeof(V) == 8 ? 2048 : 4096; }
+
+template <class V, class Vec>
+__global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
+    using Acc = Vec;
+    constexpr int CAP = cap_of<V>();
+    __shared__ CsrSmem<kBlock, CAP, Acc> sm;
+    __shared__ double red[3 * 32];
+    if (*(volatile int32_t*)&a.st->stop) return;
+    const Vec beta = (Vec)a.st->beta;
+    double p[3] = {0.0, 0.0, 0.0};
+    const int64_t ntiles = (a.m + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, a.m - r0);
+        const Acc u = csr_tile<kBlock, CAP, V, Vec, Acc>(a.ptr, a.col, a.val, a.x, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t r = r0 + threadIdx.x;
+            const Vec axo = a.ax[r];
+            const Vec bb = a.b[r];
+            const Vec ay = u + beta * (u - axo);
+            const Vec rr = bb - ay;
+            a.ax[r] = u;
+            a.res[r] = rr;
+            const double du = (double)u - (double)bb;
+            p[0] += du * du;
+            p[1] += (double)bb * (double)rr;
+            p[2] += (double)rr * (double)rr;
+        }
+    }
+    block_reduce<kBlock, 3>(p, 0u, red);
+    double tot[3];
+    if (grid_reduce_last<kBlock, 3>(p, 0u, a.partials, &a.st->cnt1, tot, red) && threadIdx.x == 0) {
+        a.st->k1[0] = tot[0];
+        a.st->k1[1] = tot[1];
+        a.st->k1[2] = tot[2];
+    }
+}
+
+__device__ void fista_finalize(FistaState* st, double amax, double l1_new) {
+    const double tau = st->tau;
+    const double P = __dadd_rn(__dmul_rn(tau, st->l1_cur), __dmul_rn(0.5, st->k1[0]));
+    const double s = amax <= tau ? 1.0 : tau / amax;
+    const double D = __dadd_rn(__dmul_rn(s, st->k1[1]), -__dmul_rn(__dmul_rn(__dmul_rn(0.5, s), s), st->k1[2]));
+    st->best_d = fmax(st->best_d, D);
+    const double gap = P - st->best_d;
+    const double rel = gap / fmax(fabs(P), 1e-300);
+    st->cert_iter = st->iter - 1;
+    st->P = P;
+    st->D = st->best_d;
+    st->gap = gap;
+    st->rel = rel;
+    st->products += 2;
+    if (!isfinite(P) || !isfinite(D)) {
+        st->status = L1LS_ENUMERIC;
+        st->stop = 1;
+    } else if (rel <= st->tol) {
+        st->status = L1LS_OK;
+        st->stop = 1;
+    } else if (st->iter - 1 >= st->max_iter) {
+        st->status = L1LS_ENOCONV;
+        st->stop = 1;
+    } else {
+        const double t = st->t;
+        const double tn = __dmul_rn(0.5, __dadd_rn(1.0, sqrt(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
+        st->beta = (t - 1.0) / tn;
+        st->t = tn;
+        st->l1_cur = l1_new;
+        st->iter += 1;
+    }
+}
+
+template <class V, class Vec>
+__global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
+    using Acc = Vec;
+    constexpr int CAP = cap_of<V>();
+    __shared__ CsrSmem<kBlock, CAP, Acc> sm;
+    __shared__ double red[2 * 32];
+    if (*(volatile int32_t*)&a.st->stop) return;
+    const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
+    const double invL = 1.0 / L, thr = tau / L;
+    double p[2] = {0.0, 0.0};
+    const int64_t ntiles = (a.n + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, a.n - r0);
+        const Acc gacc = csr_tile<kBlock, CAP, V, Vec, Acc>(a.ptr, a.col, a.val, a.res, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t j = r0 + threadIdx.x;
+            const double g = (double)gacc;
+            const double x1 = a.xc[j], x0 = a.xo[j];
+            const double y = x1 + beta * (x1 - x0);
+            const double xn = soft_threshold(y + g * invL, thr);
+            a.xo[j] = xn;
+            if (a.xo32) a.xo32[j] = __double2float_rn(xn);
+            p[0] = fmax(p[0], fabs(g));
+            p[1] += fabs(xn);
+        }
+    }
+    block_reduce<kBlock, 2>(p, 1u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(p, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
+        fista_finalize(a.st, tot[0], tot[1]);
+}
+
+__global__ void k_abs_sum(const double* __restrict__ x, int64_t n, double* __restrict__ partials,
+                          unsigned* __restrict__ counter, double* __restrict__ out) {
+    __shared__ double red[32];
+    double v[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[0] += fabs(x[i]);
+    block_reduce<kBlock, 1>(v, 0u, red);
+    double tot[1];
+    if (grid_reduce_last<kBlock, 1>(v, 0u, partials, counter, tot, red) && threadIdx.x == 0) *out = tot[0];
+}
+
+__global__ void k_d2f(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __double2float_rn(in[i]);
+}
+
+template <class K>
+int grid_of(const Inst* I, K kernel, int64_t rows) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ntiles = (rows + kBlock - 1) / kBlock;
+    const int64_t g = (int64_t)I->ctx->num_sms * per_sm;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, g));
+}
+
+// Per-instance FISTA work space and cached graph.
+struct FistaWork {
+    double* X[2] = {nullptr, nullptr};
+    float* X32[2] = {nullptr, nullptr};
+    void* ax = nullptr;
+    void* res = nullptr;
+    double* part1 = nullptr;
+    double* part2 = nullptr;
+    FistaState* st = nullptr;
+    FistaState* host_st = nullptr;   // pinned
+    int grid1 = 0, grid2 = 0;
+    cudaGraphExec_t exec = nullptr;
+    int exec_chunk = 0;
+    cudaStream_t exec_stream = nullptr;
+    ~FistaWork() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (host_st) cudaFreeHost(host_st);
+    }
+};
+
+template <class V, class Vec>
+l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
+    // parity 0: iteration k odd (x_{k-1} in X[0]); parity 1: k even (x_{k-1} in X[1])
+    const int c = parity, o = 1 - parity;
+    K1Args<V, Vec> a1;
+    a1.ptr = I->csr_ptr;
+    a1.col = I->csr_col;
+    a1.val = static_cast<const V*>(I->csr_val);
+    if constexpr (sizeof(Vec) == 8) a1.x = reinterpret_cast<const Vec*>(w->X[c]);
+    else a1.x = reinterpret_cast<const Vec*>(w->X32[c]);
+    a1.ax = static_cast<Vec*>(w->ax);
+    a1.res = static_cast<Vec*>(w->res);
+    if constexpr (sizeof(Vec) == 8) a1.b = reinterpret_cast<const Vec*>(I->bhat);
+    else a1.b = reinterpret_cast<const Vec*>(I->bhat32);
+    a1.partials = w->part1;
+    a1.st = w->st;
+    a1.m = I->m;
+    k_fista_k1<V, Vec><<<w->grid1, kBlock, 0, st>>>(a1);
+    K2Args<V, Vec> a2;
+    a2.ptr = I->csc_ptr;
+    a2.col = I->csc_row;
+    a2.val = static_cast<const V*>(I->csc_val);
+    a2.res = static_cast<const Vec*>(w->res);
+    a2.xc = w->X[c];
+    a2.xo = w->X[o];
+    a2.xo32 = sizeof(Vec) == 8 ? nullptr : w->X32[o];
+    a2.partials = w->part2;
+    a2.st = w->st;
+    a2.n = I->n;
+    k_fista_k2<V, Vec><<<w->grid2, kBlock, 0, st>>>(a2);
+    return L1LS_OK;
+}
+
+template <class V, class Vec>
+l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t m = I->m, n = I->n;
+    FistaWork* w = static_cast<FistaWork*>(I->fista_work);
+    if (!w) {
+        w = new FistaWork();
+        I->fista_work = w;
+        I->fista_work_free = [](void* p) { delete static_cast<FistaWork*>(p); };
+        L1LS_TRY(I->alloc_n(&w->X[0], n));
+        L1LS_TRY(I->alloc_n(&w->X[1], n));
+        if (sizeof(Vec) == 4) {
+            L1LS_TRY(I->alloc_n(&w->X32[0], n));
+            L1LS_TRY(I->alloc_n(&w->X32[1], n));
+        }
+        L1LS_TRY(I->alloc(&w->ax, sizeof(Vec) * m));
+        L1LS_TRY(I->alloc(&w->res, sizeof(Vec) * m));
+        w->grid1 = grid_of(I, k_fista_k1<V, Vec>, m);
+        w->grid2 = grid_of(I, k_fista_k2<V, Vec>, n);
+        L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
+        L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 2 + 1024));
+        L1LS_TRY(I->alloc_n(&w->st, 1));
+        L1LS_CUDA(cudaMallocHost((void**)&w->host_st, sizeof(FistaState)));
+    }
+    // initial point
+    FistaState h{};
+    h.tau = o->tau;
+    h.L = I->lipschitz;
+    h.tol = o->rel_gap_tol;
+    h.max_iter = o->max_iter;
+    h.t = 1.0;
+    h.beta = 0.0;
+    h.best_d = -INFINITY;
+    h.iter = 1;
+    h.cert_iter = 0;
+    h.stop = 0;
+    h.status = L1LS_OK;
+    if (x0) {
+        L1LS_CUDA(cudaMemcpyAsync(w->X[0], x0, sizeof(double) * n, cudaMemcpyDefault, st));
+        L1LS_CUDA(cudaMemcpyAsync(w->X[1], w->X[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        unsigned nb = (unsigned)((n + 255) / 256);
+        if (sizeof(Vec) == 4) {
+            k_d2f<<<nb, 256, 0, st>>>(w->X[0], n, w->X32[0]);
+            k_d2f<<<nb, 256, 0, st>>>(w->X[0], n, w->X32[1]);
+        }
+        // ||x0||_1 into the state, A x0 into ax (relabelled rows)
+        L1LS_CUDA(cudaMemsetAsync(&w->st->cnt1, 0, sizeof(unsigned), st));
+        k_abs_sum<<<256, kBlock, 0, st>>>(w->X[0], n, w->part2, &w->st->cnt1, &w->st->l1_cur);
+        L1LS_CUDA(cudaGetLastError());
+        const void* xsrc = sizeof(Vec) == 8 ? (const void*)w->X[0] : (const void*)w->X32[0];
+        L1LS_TRY(spmv_plain(I, false, xsrc, sizeof(Vec) == 8 ? L1LS_F64 : L1LS_F32, w->ax, false, st));
+        h.products = 1;
+    } else {
+        L1LS_CUDA(cudaMemsetAsync(w->X[0], 0, sizeof(double) * n, st));
+        L1LS_CUDA(cudaMemsetAsync(w->X[1], 0, sizeof(double) * n, st));
+        if (sizeof(Vec) == 4) {
+            L1LS_CUDA(cudaMemsetAsync(w->X32[0], 0, sizeof(float) * n, st));
+            L1LS_CUDA(cudaMemsetAsync(w->X32[1], 0, sizeof(float) * n, st));
+        }
+        L1LS_CUDA(cudaMemsetAsync(w->ax, 0, sizeof(Vec) * m, st));
+        h.products = 0;
+        h.l1_cur = 0.0;
+    }
+    // upload the scalar state without clobbering l1_cur when it was computed on the device
+    if (x0) {
+        L1LS_CUDA(cudaStreamSynchronize(st));
+        double l1 = 0.0;
+        L1LS_CUDA(cudaMemcpy(&l1, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost));
+        h.l1_cur = l1;
+    }
+    h.cnt1 = h.cnt2 = 0;
+    *w->host_st = h;
+    L1LS_CUDA(cudaMemcpyAsync(w->st, w->host_st, sizeof(FistaState), cudaMemcpyHostToDevice, st));
+
+    int chunk = o->check_every > 0 ? o->check_every : 32;
+    if (chunk & 1) ++chunk;
+    if (!w->exec || w->exec_chunk != chunk) {
+        if (w->exec) {
+            cudaGraphExecDestroy(w->exec);
+            w->exec = nullptr;
+        }
+        cudaStream_t cap;
+        L1LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        L1LS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < chunk; ++i) enqueue_iteration<V, Vec>(I, w, i & 1, cap);
+        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+        }
+        L1LS_CUDA(cudaGraphInstantiate(&w->exec, graph, 0));
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        w->exec_chunk = chunk;
+    }
+    l1ls_status final_status = L1LS_OK;
+    // the device stops by itself at max_iter; the host cap only guards against a stuck flag
+    const int64_t max_launches = o->max_iter / chunk + 3;
+    for (int64_t launch = 0;; ++launch) {
+        if (launch >= max_launches) {
+            final_status = L1LS_ECUDA;
+            set_error(L1LS_ECUDA, "internal: FISTA did not raise its stop flag");
+            break;
+        }
+        L1LS_CUDA(cudaGraphLaunch(w->exec, st));
+        L1LS_CUDA(cudaMemcpyAsync(w->host_st, w->st, sizeof(FistaState), cudaMemcpyDeviceToHost, st));
+        L1LS_CUDA(cudaStreamSynchronize(st));
+        if (w->host_st->stop) {
+            final_status = (l1ls_status)w->host_st->status;
+            break;
+        }
+        if (o->time_limit_s > 0) {
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > o->time_limit_s) {
+                final_status = L1LS_ETIMEOUT;
+                break;
+            }
+        }
+    }
+    const FistaState& f = *w->host_st;
+    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X[f.cert_iter & 1], sizeof(double) * n, cudaMemcpyDefault, st));
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->iters = f.cert_iter;
+        res->products = f.products;
+        res->f = f.P;
+        res->dual = f.D;
+        res->gap = f.gap;
+        res->rel_gap = f.rel;
+        res->status = final_status;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (final_status != L1LS_OK) {
+        const char* why = final_status == L1LS_ENOCONV ? "iteration limit reached"
+                          : final_status == L1LS_ETIMEOUT ? "time limit reached"
+                                                          : "NaN or Inf in the iteration";
+        return set_error(final_status, "FISTA: %s (rel_gap %.3e)", why, f.rel);
+    }
+    return L1LS_OK;
+}
+
+}  // namespace
+
+l1ls_status fista_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                        cudaStream_t st) {
+    switch (I->dtype) {
+        case L1LS_F64: return run<double, double>(I, o, x0, x_out, res, st);
+        case L1LS_F32: return run<float, float>(I, o, x0, x_out, res, st);
+        default: return run<__nv_bfloat16, float>(I, o, x0, x_out, res, st);
+    }
+}
+
+}  // namespace l1ls
+
+using namespace l1ls;
+
+extern "C" l1ls_status l1ls_solve_fista(l1ls_inst* h, const l1ls_solve_opts* o, const double* x0, double* x_out,
+                                        l1ls_result* res, void* stream) {
+    if (!h || !o) return set_error(L1LS_EINVAL, "NULL argument");
+    if (!(o->tau > 0.0) || !(o->rel_gap_tol >= 0.0) || o->max_iter < 0)
+        return set_error(L1LS_EINVAL, "bad solver options");
+    Inst* I = reinterpret_cast<Inst*>(h);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    return fista_solve(I, o, x0, x_out, res, (cudaStream_t)stream);
+}

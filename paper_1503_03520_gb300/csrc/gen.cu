@@ -1,0 +1,580 @@
+// Instance generator on the device: Procedure IGen (Sec. 3.1) on the matrix of Eq. (bd8),
+// A = (P G~ P) Sigma R^T with the Givens stages of Sec. 4.1-4.2, x* from Procedure OsGen.
+//
+// The library stores Ahat = P1^T A = G~ P2 Sigma R^T, whose rows 2p and 2p+1 are the two
+// rows mixed by one left rotation and share one column support.  Both CSR(Ahat) and
+// CSR(Ahat^T) are produced directly from the structure:
+//   column j of Sigma R^T  : rows I_j = supp(R^T e_j), a contiguous interval (each stage
+//                            widens an interval by at most one on each side),
+//   row k of R^T           : columns J_k = supp(R e_k), also an interval,
+//   row q of P2 Sigma R^T  : row perm[q] of Sigma R^T (zero when perm[q] >= n),
+//   row 2p / 2p+1 of Ahat  : c~ X_2p - s~ X_2p+1  /  s~ X_2p + c~ X_2p+1.
+// Every entry value is computed once, column by column (R^T e_j by rotating a window, the
+// MvPA order), and CSR(Ahat) copies it from CSR(Ahat^T), so the two are exact transposes.
+// Products and sums use __dmul_rn / __dadd_rn so no contraction changes the rounding.
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace l1ls {
+
+l1ls_status exclusive_scan_i32(const int32_t* in, int64_t count, int32_t* out, int64_t* total, cudaStream_t st);
+l1ls_status radix_argsort_u64(const uint64_t* keys, int64_t count, uint32_t* order, cudaStream_t st);
+
+namespace {
+
+constexpr int kWMax = 8;                 // right stages supported
+constexpr int kWin = 2 * kWMax + 1;      // window of R^T e_j
+
+struct Geo {
+    int64_t m, n;      // rows of A, size of the square Givens part
+    int w;             // right stages
+    int left;          // left stages (0 / 1)
+    double c, s, ct, st;
+};
+
+__device__ __forceinline__ void expand(int64_t& lo, int64_t& hi, int first, int64_t n) {
+    const int64_t d = lo - first;
+    if (d >= 0 && (d & 1)) lo -= 1;                      // lo is the second of its plane
+    const int64_t e = hi - first;
+    if (e >= 0 && !(e & 1) && hi + 1 < n) hi += 1;       // hi is the first of its plane
+}
+// I_j = supp(R^T e_j): stages T_w^T first, T_1^T last
+__device__ __forceinline__ void col_interval(int64_t j, const Geo& g, int64_t& lo, int64_t& hi) {
+    lo = hi = j;
+    for (int k = g.w; k >= 1; --k) expand(lo, hi, (k - 1) & 1, g.n);
+}
+// J_k = supp(R e_k): stages T_1 first, T_w last
+__device__ __forceinline__ void row_interval(int64_t k, const Geo& g, int64_t& lo, int64_t& hi) {
+    lo = hi = k;
+    for (int q = 1; q <= g.w; ++q) expand(lo, hi, (q - 1) & 1, g.n);
+}
+// values of R^T e_j on the window [j - w, j + w]
+__device__ void col_values(int64_t j, const Geo& g, double* v) {
+    const int64_t base = j - g.w;
+    for (int t = 0; t < kWin; ++t) v[t] = 0.0;
+    v[g.w] = 1.0;
+    for (int k = g.w; k >= 1; --k) {
+        const int first = (k - 1) & 1;
+        int64_t i = base < first ? first : base;
+        if ((i - first) & 1) ++i;
+        for (; i + 1 <= base + 2 * g.w && i + 1 < g.n; i += 2) {
+            const double a = v[i - base], b = v[i + 1 - base];
+            v[i - base] = __dadd_rn(__dmul_rn(g.c, a), __dmul_rn(g.s, b));
+            v[i + 1 - base] = __dadd_rn(__dmul_rn(-g.s, a), __dmul_rn(g.c, b));
+        }
+    }
+}
+
+__global__ void k_keys(uint64_t seed, uint64_t tag, int64_t count, uint64_t* __restrict__ keys) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) keys[i] = sm_output(sm_stream(seed, tag), (uint64_t)i);
+}
+
+__global__ void k_sigma(const uint32_t* __restrict__ order, int64_t count, double logk, double* __restrict__ sigma) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    double v = 1.0;
+    if (count > 1) v = exp(-((double)r / (double)(count - 1)) * logk);
+    sigma[order[r]] = v;
+}
+
+__global__ void k_perm(const uint32_t* __restrict__ order, int64_t count, int32_t* __restrict__ perm,
+                       int32_t* __restrict__ perm_inv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    perm[i] = (int32_t)order[i];
+    perm_inv[order[i]] = (int32_t)i;
+}
+
+__global__ void k_identity_perm(int64_t count, int32_t* __restrict__ perm, int32_t* __restrict__ perm_inv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    perm[i] = (int32_t)i;
+    perm_inv[i] = (int32_t)i;
+}
+
+__global__ void k_support(const uint32_t* __restrict__ order, int64_t s, uint8_t* __restrict__ flag) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < s) flag[order[r]] = 1;
+}
+
+// OsGen with magnitudes U[lo, hi] and random signs; g of Eq. (bd6).
+__global__ void k_xstar_g(uint64_t seed, int64_t n, int64_t nsup, const uint8_t* __restrict__ flag, double lo,
+                          double hi, int goff_mode, double* __restrict__ xstar, double* __restrict__ g) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool on = i < nsup && flag[i];
+    double x = 0.0, gi;
+    if (on) {
+        const double u = u01(sm_output(sm_stream(seed, kTagXVal), (uint64_t)i));
+        const double mag = __dadd_rn(lo, __dmul_rn(hi - lo, u));
+        const bool neg = (sm_output(sm_stream(seed, kTagXSign), (uint64_t)i) >> 63) != 0;
+        x = neg ? -mag : mag;
+        gi = neg ? -1.0 : 1.0;
+    } else {
+        gi = goff_mode == 0 ? __dadd_rn(2.0 * u01(sm_output(sm_stream(seed, kTagGOff), (uint64_t)i)), -1.0) : 0.0;
+    }
+    xstar[i] = x;
+    if (i < nsup) g[i] = gi;
+}
+
+// one stage on a vector, in place: transpose ? T^T v : T v
+__global__ void k_stage(double* __restrict__ v, int64_t n, int first, double c, double s, int transpose) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = first + 2 * t;
+    if (i + 1 >= n) return;
+    const double a = v[i], b = v[i + 1];
+    if (transpose) {
+        v[i] = __dadd_rn(__dmul_rn(c, a), __dmul_rn(s, b));
+        v[i + 1] = __dadd_rn(__dmul_rn(-s, a), __dmul_rn(c, b));
+    } else {
+        v[i] = __dadd_rn(__dmul_rn(c, a), __dmul_rn(-s, b));
+        v[i + 1] = __dadd_rn(__dmul_rn(s, a), __dmul_rn(c, b));
+    }
+}
+
+// z = Sigma^{-1}-scaled vectors: ze = tau vg / sigma, zb = sigma vx + tau vg / sigma (length n)
+__global__ void k_scale(const double* __restrict__ vg, const double* __restrict__ vx, const double* __restrict__ sigma,
+                        int64_t n, double tau, double* __restrict__ ze, double* __restrict__ zb,
+                        double* __restrict__ u_lam) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double sg = sigma[k];
+    const double e = __dmul_rn(tau, vg[k]) / sg;
+    ze[k] = e;
+    zb[k] = __dadd_rn(__dmul_rn(sg, vx[k]), e);
+    // A^T b = R (Sigma^2 R^T x* + tau R^T g): the inner vector
+    u_lam[k] = __dadd_rn(__dmul_rn(__dmul_rn(sg, sg), vx[k]), __dmul_rn(tau, vg[k]));
+}
+
+// ehat = G~ P2 [ze; 0], bhat = G~ P2 [zb; 0] in the relabelled row order
+__global__ void k_left(const double* __restrict__ ze, const double* __restrict__ zb, const int32_t* __restrict__ perm,
+                       Geo g, double* __restrict__ ehat, double* __restrict__ bhat) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g.left == 0) {
+        if (t >= g.m) return;
+        ehat[t] = t < g.n ? ze[t] : 0.0;
+        bhat[t] = t < g.n ? zb[t] : 0.0;
+        return;
+    }
+    if (2 * t + 1 >= g.m) return;
+    const int64_t ke = perm[2 * t], ko = perm[2 * t + 1];
+    const double e0 = ke < g.n ? ze[ke] : 0.0, e1 = ko < g.n ? ze[ko] : 0.0;
+    const double b0 = ke < g.n ? zb[ke] : 0.0, b1 = ko < g.n ? zb[ko] : 0.0;
+    ehat[2 * t] = __dadd_rn(__dmul_rn(g.ct, e0), __dmul_rn(-g.st, e1));
+    ehat[2 * t + 1] = __dadd_rn(__dmul_rn(g.st, e0), __dmul_rn(g.ct, e1));
+    bhat[2 * t] = __dadd_rn(__dmul_rn(g.ct, b0), __dmul_rn(-g.st, b1));
+    bhat[2 * t + 1] = __dadd_rn(__dmul_rn(g.st, b0), __dmul_rn(g.ct, b1));
+}
+
+// deterministic grid reduction: out[0] = sum |a|, out[1] = sum b^2, out[2] = max |c|
+__global__ void k_reduce3(const double* __restrict__ a, int64_t na, const double* __restrict__ b, int64_t nb,
+                          const double* __restrict__ c, int64_t nc, double* __restrict__ partials,
+                          unsigned* __restrict__ counter, double* __restrict__ out) {
+    __shared__ double smem[3 * 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride) v[0] += fabs(a[i]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) v[1] += b[i] * b[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) v[2] = fmax(v[2], fabs(c[i]));
+    block_reduce<256, 3>(v, 4u, smem);
+    double tot[3];
+    if (grid_reduce_last<256, 3>(v, 4u, partials, counter, tot, smem) && threadIdx.x == 0) {
+        out[0] = tot[0];
+        out[1] = tot[1];
+        out[2] = tot[2];
+    }
+}
+
+// number of distinct left planes touched by column j (x2 rows); L = I: |I_j|
+__global__ void k_csc_count(Geo g, const int32_t* __restrict__ perm_inv, int32_t* __restrict__ cnt) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n) return;
+    int64_t lo, hi;
+    col_interval(j, g, lo, hi);
+    if (g.left == 0) {
+        cnt[j] = (int32_t)(hi - lo + 1);
+        return;
+    }
+    int32_t pl[2 * kWMax];
+    int np = 0;
+    for (int64_t k = lo; k <= hi; ++k) {
+        const int32_t p = perm_inv[k] >> 1;
+        bool seen = false;
+        for (int t = 0; t < np; ++t) seen |= (pl[t] == p);
+        if (!seen) pl[np++] = p;
+    }
+    cnt[j] = 2 * np;
+}
+
+__global__ void k_csc_fill(Geo g, const int32_t* __restrict__ perm_inv, const double* __restrict__ sigma,
+                           const int32_t* __restrict__ ptr, int32_t* __restrict__ rows, double* __restrict__ vals) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n) return;
+    int64_t lo, hi;
+    col_interval(j, g, lo, hi);
+    double v[kWin];
+    col_values(j, g, v);
+    const int64_t base = j - g.w;
+    int64_t o = ptr[j];
+    if (g.left == 0) {
+        for (int64_t k = lo; k <= hi; ++k) {
+            rows[o] = (int32_t)k;
+            vals[o] = __dmul_rn(sigma[k], v[k - base]);
+            ++o;
+        }
+        return;
+    }
+    // entries (q, t_k) with q = perm_inv[k], sorted by q
+    int32_t q[2 * kWMax];
+    double tv[2 * kWMax];
+    int ne = 0;
+    for (int64_t k = lo; k <= hi; ++k) {
+        const int32_t qq = perm_inv[k];
+        const double tt = __dmul_rn(sigma[k], v[k - base]);
+        int pos = ne++;
+        while (pos > 0 && q[pos - 1] > qq) {
+            q[pos] = q[pos - 1];
+            tv[pos] = tv[pos - 1];
+            --pos;
+        }
+        q[pos] = qq;
+        tv[pos] = tt;
+    }
+    for (int a = 0; a < ne;) {
+        const int32_t p = q[a] >> 1;
+        bool he = false, ho = false;
+        double te = 0.0, to = 0.0;
+        while (a < ne && (q[a] >> 1) == p) {
+            if (q[a] & 1) { ho = true; to = tv[a]; }
+            else { he = true; te = tv[a]; }
+            ++a;
+        }
+        double v0, v1;
+        if (he && ho) {
+            v0 = __dadd_rn(__dmul_rn(g.ct, te), __dmul_rn(-g.st, to));
+            v1 = __dadd_rn(__dmul_rn(g.st, te), __dmul_rn(g.ct, to));
+        } else if (he) {
+            v0 = __dmul_rn(g.ct, te);
+            v1 = __dmul_rn(g.st, te);
+        } else {
+            v0 = __dmul_rn(-g.st, to);
+            v1 = __dmul_rn(g.ct, to);
+        }
+        rows[o] = 2 * p;
+        vals[o] = v0;
+        rows[o + 1] = 2 * p + 1;
+        vals[o + 1] = v1;
+        o += 2;
+    }
+}
+
+// columns of row rho: J_{perm[2p]} U J_{perm[2p+1]} (those below n); L = I: J_rho
+__device__ __forceinline__ int row_support(int64_t rho, const Geo& g, const int32_t* __restrict__ perm, int64_t& a1,
+                                           int64_t& b1, int64_t& a2, int64_t& b2) {
+    if (g.left == 0) {
+        if (rho >= g.n) return 0;
+        row_interval(rho, g, a1, b1);
+        return 1;
+    }
+    const int64_t p = rho >> 1;
+    const int64_t ke = perm[2 * p], ko = perm[2 * p + 1];
+    int cnt = 0;
+    if (ke < g.n) { row_interval(ke, g, a1, b1); cnt = 1; }
+    if (ko < g.n) {
+        if (cnt == 0) { row_interval(ko, g, a1, b1); cnt = 1; }
+        else { row_interval(ko, g, a2, b2); cnt = 2; }
+    }
+    if (cnt == 2) {
+        if (a2 < a1) { int64_t t = a1; a1 = a2; a2 = t; t = b1; b1 = b2; b2 = t; }
+        if (a2 <= b1 + 1) {            // overlapping or touching: one interval
+            b1 = b1 > b2 ? b1 : b2;
+            cnt = 1;
+        }
+    }
+    return cnt;
+}
+
+__global__ void k_csr_count(Geo g, const int32_t* __restrict__ perm, int32_t* __restrict__ cnt) {
+    int64_t rho = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rho >= g.m) return;
+    int64_t a1 = 0, b1 = -1, a2 = 0, b2 = -1;
+    const int c = row_support(rho, g, perm, a1, b1, a2, b2);
+    cnt[rho] = c == 0 ? 0 : (int32_t)((b1 - a1 + 1) + (c == 2 ? (b2 - a2 + 1) : 0));
+}
+
+__global__ void k_csr_fill(Geo g, const int32_t* __restrict__ perm, const int32_t* __restrict__ csc_ptr,
+                           const int32_t* __restrict__ csc_row, const double* __restrict__ csc_val,
+                           const int32_t* __restrict__ ptr, int32_t* __restrict__ cols, double* __restrict__ vals,
+                           int* __restrict__ err) {
+    int64_t rho = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rho >= g.m) return;
+    int64_t a[2] = {0, 0}, b[2] = {-1, -1};
+    const int c = row_support(rho, g, perm, a[0], b[0], a[1], b[1]);
+    int64_t o = ptr[rho];
+    for (int iv = 0; iv < c; ++iv) {
+        for (int64_t j = a[iv]; j <= b[iv]; ++j) {
+            int32_t lo = csc_ptr[j], hi = csc_ptr[j + 1];
+            while (lo < hi) {                       // first position with row >= rho
+                const int32_t mid = (lo + hi) >> 1;
+                if (csc_row[mid] < rho) lo = mid + 1;
+                else hi = mid;
+            }
+            double val = 0.0;
+            if (lo < csc_ptr[j + 1] && csc_row[lo] == rho) val = csc_val[lo];
+            else atomicExch(err, 1);
+            cols[o] = (int32_t)j;
+            vals[o] = val;
+            ++o;
+        }
+    }
+}
+
+template <class V>
+__global__ void k_cast(const double* __restrict__ in, int64_t count, V* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = from_double<V>(in[i]);
+}
+
+__global__ void k_to_f32(const double* __restrict__ in, int64_t count, float* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = __double2float_rn(in[i]);
+}
+
+template <class V>
+__global__ void k_colnorm2(const int32_t* __restrict__ ptr, const V* __restrict__ vals, int64_t n,
+                           double* __restrict__ out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int32_t e = ptr[j]; e < ptr[j + 1]; ++e) {
+        double v;
+        if constexpr (sizeof(V) == 2) v = (double)__bfloat162float(vals[e]);
+        else v = (double)vals[e];
+        s += v * v;
+    }
+    out[j] = s;
+}
+
+inline unsigned nblk(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b); }
+
+struct TempList {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit TempList(cudaStream_t s) : st(s) {}
+    template <class T> l1ls_status get(T** p, int64_t count) {
+        cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * (size_t)(count > 0 ? count : 1), st);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(temp)", __FILE__, __LINE__);
+        ptrs.push_back(*p);
+        return L1LS_OK;
+    }
+    ~TempList() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+l1ls_status argsort_stream(uint64_t seed, uint64_t tag, int64_t count, uint32_t* order, TempList& tmp,
+                           cudaStream_t st) {
+    uint64_t* keys = nullptr;
+    L1LS_TRY(tmp.get(&keys, count));
+    k_keys<<<nblk(count), 256, 0, st>>>(seed, tag, count, keys);
+    L1LS_CUDA(cudaGetLastError());
+    return radix_argsort_u64(keys, count, order, st);
+}
+
+template <class V>
+l1ls_status cast_and_norms(Inst* I, const double* csc64, const double* csr64, cudaStream_t st) {
+    V* cv = nullptr;
+    V* rv = nullptr;
+    L1LS_TRY(I->alloc_n(&cv, I->nnz));
+    L1LS_TRY(I->alloc_n(&rv, I->nnz));
+    k_cast<V><<<nblk(I->nnz), 256, 0, st>>>(csc64, I->nnz, cv);
+    k_cast<V><<<nblk(I->nnz), 256, 0, st>>>(csr64, I->nnz, rv);
+    k_colnorm2<V><<<nblk(I->n), 256, 0, st>>>(I->csc_ptr, cv, I->n, I->colnorm2);
+    L1LS_CUDA(cudaGetLastError());
+    I->csc_val = cv;
+    I->csr_val = rv;
+    return L1LS_OK;
+}
+
+l1ls_status validate(const l1ls_gen_params* p) {
+    if (!p) return set_error(L1LS_EINVAL, "params is NULL");
+    if (p->m < 2 || p->n < 2) return set_error(L1LS_EINVAL, "m and n must be >= 2");
+    if (p->m > (uint64_t)INT32_MAX - 2 || p->n > (uint64_t)INT32_MAX - 2)
+        return set_error(L1LS_EINVAL, "m and n must be below 2^31 - 2");
+    if (p->m < p->n) return set_error(L1LS_EINVAL, "m < n (IGen2) is not supported by l1ls_generate yet");
+    if (!(p->kappa >= 1.0) || !std::isfinite(p->kappa)) return set_error(L1LS_EINVAL, "kappa must be >= 1");
+    if (!(p->tau > 0.0)) return set_error(L1LS_EINVAL, "tau must be > 0");
+    if (p->right_stages < 1 || p->right_stages > kWMax)
+        return set_error(L1LS_EINVAL, "right_stages must be in [1, %d]", kWMax);
+    if (p->left_stages != 0 && p->left_stages != 1) return set_error(L1LS_EINVAL, "left_stages must be 0 or 1");
+    if (p->left_stages == 1 && (p->m & 1)) return set_error(L1LS_EINVAL, "m must be even with a left stage");
+    if (p->value_dtype < L1LS_F64 || p->value_dtype > L1LS_BF16) return set_error(L1LS_EINVAL, "bad value_dtype");
+    if (!(p->xstar_lo >= 0.0) || !(p->xstar_hi >= p->xstar_lo)) return set_error(L1LS_EINVAL, "bad x* magnitudes");
+    if (!(p->xstar_frac >= 0.0) || !(p->xstar_frac <= 1.0)) return set_error(L1LS_EINVAL, "xstar_frac must be in [0, 1]");
+    return L1LS_OK;
+}
+
+}  // namespace
+
+l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out) {
+    L1LS_TRY(validate(p));
+    Inst* I = new Inst();
+    I->ctx = ctx;
+    I->p = *p;
+    I->m = (int64_t)p->m;
+    I->n = (int64_t)p->n;
+    I->nsq = I->n;
+    I->dtype = p->value_dtype;
+    int64_t s = (int64_t)std::floor(p->xstar_frac * (double)p->n + 0.5);
+    if (s < 1) s = 1;
+    if (s > I->m) s = I->m;
+    if (s > I->n) s = I->n;
+    I->s = s;
+    const int64_t m = I->m, n = I->n;
+    const double vt = std::isnan(p->vartheta) ? p->theta : p->vartheta;
+    Geo g{m, n, p->right_stages, p->left_stages, std::cos(p->theta), std::sin(p->theta), std::cos(vt), std::sin(vt)};
+
+    auto fail = [&](l1ls_status e) {
+        I->free_all();
+        delete I;
+        return e;
+    };
+#define GEN_TRY(x)                          \
+    do {                                    \
+        l1ls_status s__ = (x);              \
+        if (s__ != L1LS_OK) return fail(s__); \
+    } while (0)
+#define GEN_CUDA(x)                                                              \
+    do {                                                                         \
+        cudaError_t e__ = (x);                                                   \
+        if (e__ != cudaSuccess) return fail(cuda_error(e__, #x, __FILE__, __LINE__)); \
+    } while (0)
+
+    {
+        TempList tmp(st);
+        // persistent vectors
+        GEN_TRY(I->alloc_n(&I->sigma, n));
+        GEN_TRY(I->alloc_n(&I->xstar, n));
+        GEN_TRY(I->alloc_n(&I->bhat, m));
+        GEN_TRY(I->alloc_n(&I->perm, m));
+        GEN_TRY(I->alloc_n(&I->perm_inv, m));
+        GEN_TRY(I->alloc_n(&I->colnorm2, n));
+        if (I->dtype != L1LS_F64) GEN_TRY(I->alloc_n(&I->bhat32, m));
+
+        // singular values: sigma_i = kappa^(-rank_i/(n-1))
+        uint32_t* order_n = nullptr;
+        GEN_TRY(tmp.get(&order_n, n));
+        GEN_TRY(argsort_stream(p->seed, kTagSigma, n, order_n, tmp, st));
+        k_sigma<<<nblk(n), 256, 0, st>>>(order_n, n, std::log(p->kappa), I->sigma);
+        GEN_CUDA(cudaGetLastError());
+        // row permutation P (P1 = P2 = P)
+        if (p->left_stages == 1) {
+            uint32_t* order_m = nullptr;
+            GEN_TRY(tmp.get(&order_m, m));
+            GEN_TRY(argsort_stream(p->seed, kTagPerm, m, order_m, tmp, st));
+            k_perm<<<nblk(m), 256, 0, st>>>(order_m, m, I->perm, I->perm_inv);
+        } else {
+            k_identity_perm<<<nblk(m), 256, 0, st>>>(m, I->perm, I->perm_inv);
+        }
+        GEN_CUDA(cudaGetLastError());
+        // support of x*: the s smallest keys
+        GEN_TRY(argsort_stream(p->seed, kTagSupport, n, order_n, tmp, st));
+        uint8_t* flag = nullptr;
+        GEN_TRY(tmp.get(&flag, n));
+        GEN_CUDA(cudaMemsetAsync(flag, 0, n, st));
+        k_support<<<nblk(s), 256, 0, st>>>(order_n, s, flag);
+        double *gvec = nullptr, *vg = nullptr, *vx = nullptr, *ze = nullptr, *zb = nullptr, *ul = nullptr,
+               *ehat = nullptr;
+        GEN_TRY(tmp.get(&gvec, n));
+        GEN_TRY(tmp.get(&vg, n));
+        GEN_TRY(tmp.get(&vx, n));
+        GEN_TRY(tmp.get(&ze, n));
+        GEN_TRY(tmp.get(&zb, n));
+        GEN_TRY(tmp.get(&ul, n));
+        GEN_TRY(tmp.get(&ehat, m));
+        k_xstar_g<<<nblk(n), 256, 0, st>>>(p->seed, n, n, flag, p->xstar_lo, p->xstar_hi, p->g_offsupport, I->xstar,
+                                            gvec);
+        GEN_CUDA(cudaGetLastError());
+        // IGen step 3 by the route of Sec. 4: R^T g and R^T x* (T_w^T first)
+        GEN_CUDA(cudaMemcpyAsync(vg, gvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        GEN_CUDA(cudaMemcpyAsync(vx, I->xstar, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        for (int k = p->right_stages; k >= 1; --k) {
+            k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(vg, n, (k - 1) & 1, g.c, g.s, 1);
+            k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(vx, n, (k - 1) & 1, g.c, g.s, 1);
+        }
+        k_scale<<<nblk(n), 256, 0, st>>>(vg, vx, I->sigma, n, p->tau, ze, zb, ul);
+        k_left<<<nblk(m), 256, 0, st>>>(ze, zb, I->perm, g, ehat, I->bhat);
+        // A^T b = R u (T_1 first) for lambda_max
+        for (int k = 1; k <= p->right_stages; ++k)
+            k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(ul, n, (k - 1) & 1, g.c, g.s, 0);
+        GEN_CUDA(cudaGetLastError());
+        double* red = nullptr;
+        double* partials = nullptr;
+        unsigned* counter = nullptr;
+        GEN_TRY(tmp.get(&red, 3));
+        GEN_TRY(tmp.get(&partials, 3 * 512));
+        GEN_TRY(tmp.get(&counter, 1));
+        GEN_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+        k_reduce3<<<512, 256, 0, st>>>(I->xstar, n, ehat, m, ul, n, partials, counter, red);
+        GEN_CUDA(cudaGetLastError());
+        double hred[3];
+        GEN_CUDA(cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st));
+
+        // CSR(Ahat^T): counts, scan, fill (FP64 values)
+        int32_t* cnt = nullptr;
+        GEN_TRY(tmp.get(&cnt, (m > n ? m : n)));
+        GEN_TRY(I->alloc_n(&I->csc_ptr, n + 1));
+        k_csc_count<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, cnt);
+        GEN_CUDA(cudaGetLastError());
+        int64_t nnz = 0;
+        GEN_TRY(exclusive_scan_i32(cnt, n, I->csc_ptr, &nnz, st));
+        I->nnz = nnz;
+        double *csc64 = nullptr, *csr64 = nullptr;
+        GEN_TRY(I->alloc_n(&I->csc_row, nnz));
+        GEN_TRY(tmp.get(&csc64, nnz));
+        k_csc_fill<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, I->sigma, I->csc_ptr, I->csc_row, csc64);
+        GEN_CUDA(cudaGetLastError());
+        // CSR(Ahat): counts, scan, fill by lookup in CSR(Ahat^T)
+        GEN_TRY(I->alloc_n(&I->csr_ptr, m + 1));
+        k_csr_count<<<nblk(m), 256, 0, st>>>(g, I->perm, cnt);
+        GEN_CUDA(cudaGetLastError());
+        int64_t nnz_r = 0;
+        GEN_TRY(exclusive_scan_i32(cnt, m, I->csr_ptr, &nnz_r, st));
+        if (nnz_r != nnz)
+            return fail(set_error(L1LS_ECUDA, "internal: row and column structures disagree (%lld vs %lld)",
+                                  (long long)nnz_r, (long long)nnz));
+        int* err = nullptr;
+        GEN_TRY(tmp.get(&err, 1));
+        GEN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        GEN_TRY(I->alloc_n(&I->csr_col, nnz));
+        GEN_TRY(tmp.get(&csr64, nnz));
+        k_csr_fill<<<nblk(m), 256, 0, st>>>(g, I->perm, I->csc_ptr, I->csc_row, csc64, I->csr_ptr, I->csr_col, csr64,
+                                             err);
+        GEN_CUDA(cudaGetLastError());
+        switch (I->dtype) {
+            case L1LS_F64: GEN_TRY(cast_and_norms<double>(I, csc64, csr64, st)); break;
+            case L1LS_F32: GEN_TRY(cast_and_norms<float>(I, csc64, csr64, st)); break;
+            default: GEN_TRY(cast_and_norms<__nv_bfloat16>(I, csc64, csr64, st)); break;
+        }
+        if (I->bhat32) k_to_f32<<<nblk(m), 256, 0, st>>>(I->bhat, m, I->bhat32);
+        GEN_CUDA(cudaGetLastError());
+        int herr = 0;
+        GEN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GEN_CUDA(cudaStreamSynchronize(st));
+        if (herr) return fail(set_error(L1LS_ECUDA, "internal: an entry of CSR(A) was not found in CSR(A^T)"));
+        I->f_star = p->tau * hred[0] + 0.5 * hred[1];
+        I->lam_max = hred[2];
+        I->lipschitz = 1.0;   // sigma_max = kappa^0 = 1
+    }
+    GEN_CUDA(cudaStreamSynchronize(st));
+#undef GEN_TRY
+#undef GEN_CUDA
+    *out = I;
+    return L1LS_OK;
+}
+
+}  // namespace l1ls

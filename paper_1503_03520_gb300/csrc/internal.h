@@ -1,0 +1,112 @@
+// Internal structures of the l1ls library (host side).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/l1ls.h"
+
+namespace l1ls {
+
+// ---- error reporting -------------------------------------------------------------------
+l1ls_status set_error(l1ls_status st, const char* fmt, ...);
+l1ls_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define L1LS_CUDA(call)                                                          \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) return ::l1ls::cuda_error(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define L1LS_TRY(call)                                                           \
+    do {                                                                         \
+        l1ls_status s_ = (call);                                                 \
+        if (s_ != L1LS_OK) return s_;                                            \
+    } while (0)
+
+// ---- context ------------------------------------------------------------------------------
+struct Inst;
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;          // bytes the context may hold
+    size_t used = 0;            // bytes currently held
+    std::mutex mem_mu;
+    // staging buffers for host pointers passed to products / solvers, and scratch
+    static constexpr int kStages = 4;
+    void* stage[kStages] = {nullptr, nullptr, nullptr, nullptr};
+    size_t stage_bytes[kStages] = {0, 0, 0, 0};
+    std::vector<Inst*> insts;   // instances owned by the context
+    std::mutex inst_mu;
+
+    l1ls_status alloc(void** p, size_t bytes);
+    void release(void* p, size_t bytes);
+    l1ls_status staging(int which, size_t bytes, void** out);
+};
+
+// ---- instance -----------------------------------------------------------------------------
+struct Inst {
+    Ctx* ctx = nullptr;
+    l1ls_gen_params p{};
+    int64_t m = 0, n = 0, nnz = 0, s = 0;
+    int64_t nsq = 0;            // size of the square Givens part (n for IGen, m for IGen2)
+    bool igen2 = false;
+    int dtype = L1LS_F64;
+    // CSR of P1^T A (rows relabelled), m rows
+    int32_t* csr_ptr = nullptr;
+    int32_t* csr_col = nullptr;
+    void* csr_val = nullptr;
+    // CSR of A^T P1 (CSC of the relabelled matrix), n rows
+    int32_t* csc_ptr = nullptr;
+    int32_t* csc_row = nullptr;
+    void* csc_val = nullptr;
+    double* bhat = nullptr;     // P1^T b in FP64
+    float* bhat32 = nullptr;    // FP32 copy (products in FP32)
+    double* xstar = nullptr;
+    double* sigma = nullptr;
+    double* colnorm2 = nullptr; // diag(A^T A) from the stored values
+    int32_t* perm = nullptr;    // P: (P v)_i = v_{perm[i]}
+    int32_t* perm_inv = nullptr;
+    double f_star = 0, lipschitz = 1, lam_max = 0;
+    size_t bytes = 0;
+    // solver work spaces (allocated on first use, owned by the instance)
+    void* fista_work = nullptr;
+    void (*fista_work_free)(void*) = nullptr;
+    void* pd_work = nullptr;
+    void (*pd_work_free)(void*) = nullptr;
+    struct Alloc { void* p; size_t bytes; };
+    std::vector<Alloc> allocs;
+
+    l1ls_status alloc(void** p, size_t bytes);
+    template <class T> l1ls_status alloc_n(T** p, int64_t count) {
+        return alloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+    }
+    void free_all();
+};
+
+// value size of a stored dtype
+inline size_t dtype_size(int dt) { return dt == L1LS_F64 ? 8 : dt == L1LS_F32 ? 4 : 2; }
+
+// pointer classification: true when the pointer is device (or managed) memory
+bool is_device_pointer(const void* p);
+
+// ---- entry points implemented per file ------------------------------------------------
+l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out);
+
+// products on device buffers (relabelled row order), vec_dtype F64 or F32
+l1ls_status spmv_plain(const Inst* I, bool transpose, const void* x, int vec_dtype, void* y,
+                       bool unpermute_rows, cudaStream_t st);
+
+l1ls_status fista_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                        cudaStream_t st);
+l1ls_status pdncg_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                        cudaStream_t st);
+
+}  // namespace l1ls

@@ -1,0 +1,560 @@
+// pdNCG (Sec. 8.1, parameters of Sec. 8.3): primal-dual Newton-CG on the pseudo-Huber
+// smoothing f^mu(x) = tau psi_mu(x) + 1/2 ||A x - b||^2 (Eqs. pseudoHuber, prob2, bd4).
+//
+// Newton step (one host round trip per phase; all arithmetic in the kernels):
+//   N1  r = b - A x                               (partials ||r||^2, b.r)
+//   N2  a = A^T r                                 (partials max|a|, ||x||_1); last CTA: gap
+//       certificate at x, stop test, mu-continuation (mu /= 10 when a full Newton step
+//       failed to halve the gap)
+//   N3  w = sqrt(mu^2 + x^2), grad = tau x / w - a, h = tau (1 - g x / w) / w (primal-dual
+//       curvature with the dual estimate g), M^{-1} = 1 / (h + diag(A^T A)), PCG start
+//   PCG iteration (stopped at ||res|| <= pcg_rtol ||grad|| or pcg_max):
+//   C1  Ap = A p          C2  Hp = h p + A^T Ap, alpha = rz / p.Hp
+//   C3  d += alpha p, res -= alpha Hp, beta    C4  p = M^{-1} res + beta p
+//   L1  Ad = A d (r.Ad, ||Ad||^2);  LT  Armijo trials, four halvings per pass, per-coordinate
+//       psi differences;  L3  x += alpha d, g <- clip(g + dg, -1, 1)
+// Vectors of length n and every reduction are FP64; with FP32 / BF16 values the products
+// run in FP32 with FP32 shadows of x and p for the gathers.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "spmv.cuh"
+
+namespace l1ls {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kTrialsPerPass = 4;
+
+struct PdState {
+    double tau, tol, mu, mu_min, pcg_rtol, armijo, stall;
+    int64_t max_newton, pcg_max, ls_max;
+    double P, D, gap, rel, prev_gap;
+    int32_t prev_full, pad0;
+    double k1[2];
+    double gnorm2, rz, alpha, beta;
+    int32_t cg_done, pad1;
+    int64_t cg_it;
+    double rAd, AdAd, step;
+    int32_t ls_done, pad2;
+    int64_t ls_trial;
+    int32_t stop, status;
+    int64_t iter, products, cg_total, ls_total;
+    unsigned cnt[8];
+};
+
+template <class V> constexpr int cap_of() { return sizeof(V) == 8 ? 2048 : 4096; }
+
+__device__ __forceinline__ bool halted(const PdState* st) { return *(volatile const int32_t*)&st->stop != 0; }
+
+// ---- N1: r = b - A x --------------------------------------------------------------------
+template <class V, class Vec, class X>
+__global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                     const V* __restrict__ val, const X* __restrict__ x,
+                                                     const Vec* __restrict__ b, Vec* __restrict__ r, int64_t m,
+                                                     double* partials, PdState* st) {
+    using Acc = Vec;
+    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    double p[2] = {0.0, 0.0};
+    const int64_t ntiles = (m + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, m - r0);
+        const Acc u = csr_tile<kBlock, cap_of<V>(), V, X, Acc>(ptr, col, val, x, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t i = r0 + threadIdx.x;
+            const Vec bb = b[i];
+            const Vec rr = bb - u;
+            r[i] = rr;
+            p[0] += (double)rr * (double)rr;
+            p[1] += (double)bb * (double)rr;
+        }
+    }
+    block_reduce<kBlock, 2>(p, 0u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(p, 0u, partials, &st->cnt[0], tot, red) && threadIdx.x == 0) {
+        st->k1[0] = tot[0];
+        st->k1[1] = tot[1];
+    }
+}
+
+// ---- N2: a = A^T r, certificate ---------------------------------------------------------
+template <class V, class Vec>
+__global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                   const V* __restrict__ val, const Vec* __restrict__ r,
+                                                   const double* __restrict__ x, double* __restrict__ atr, int64_t n,
+                                                   double* partials, PdState* st) {
+    using Acc = Vec;
+    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    double p[2] = {0.0, 0.0};
+    const int64_t ntiles = (n + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, n - r0);
+        const Acc a = csr_tile<kBlock, cap_of<V>(), V, Vec, Acc>(ptr, col, val, r, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t j = r0 + threadIdx.x;
+            atr[j] = (double)a;
+            p[0] = fmax(p[0], fabs((double)a));
+            p[1] += fabs(x[j]);
+        }
+    }
+    block_reduce<kBlock, 2>(p, 1u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(p, 1u, partials, &st->cnt[1], tot, red) && threadIdx.x == 0) {
+        const double tau = st->tau;
+        const double P = __dadd_rn(__dmul_rn(tau, tot[1]), __dmul_rn(0.5, st->k1[0]));
+        const double s = tot[0] <= tau ? 1.0 : tau / tot[0];
+        const double D = __dadd_rn(__dmul_rn(s, st->k1[1]), -__dmul_rn(__dmul_rn(__dmul_rn(0.5, s), s), st->k1[0]));
+        const double gap = P - D;
+        const double rel = gap / fmax(fabs(P), 1e-300);
+        st->P = P;
+        st->D = D;
+        st->gap = gap;
+        st->rel = rel;
+        st->products += 2;
+        if (!isfinite(P) || !isfinite(D)) {
+            st->status = L1LS_ENUMERIC;
+            st->stop = 1;
+        } else if (rel <= st->tol) {
+            st->status = L1LS_OK;
+            st->stop = 1;
+        } else if (st->iter >= st->max_newton) {
+            st->status = L1LS_ENOCONV;
+            st->stop = 1;
+        } else {
+            if (st->prev_full && gap > st->stall * st->prev_gap) st->mu = fmax(st->mu * 0.1, st->mu_min);
+            st->prev_gap = gap;
+        }
+    }
+}
+
+// ---- N3: gradient, primal-dual curvature, preconditioner, PCG start --------------------
+template <class PX>
+__global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x, const double* __restrict__ gd,
+                                                    const double* __restrict__ atr, const double* __restrict__ cn2,
+                                                    double* __restrict__ grad, double* __restrict__ hd,
+                                                    double* __restrict__ minv, double* __restrict__ rcg,
+                                                    double* __restrict__ p, PX* __restrict__ p_g, double* __restrict__ d,
+                                                    int64_t n, double* partials, PdState* st) {
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    const double mu = st->mu, tau = st->tau;
+    double q[2] = {0.0, 0.0};
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const double xj = x[j];
+        const double w = sqrt(mu * mu + xj * xj);
+        const double gr = tau * xj / w - atr[j];
+        const double h = tau * (1.0 - gd[j] * xj / w) / w;
+        const double mi = 1.0 / (h + cn2[j]);
+        const double rc = -gr;
+        const double z = mi * rc;
+        grad[j] = gr;
+        hd[j] = h;
+        minv[j] = mi;
+        rcg[j] = rc;
+        p[j] = z;
+        if (p_g) p_g[j] = (PX)z;
+        d[j] = 0.0;
+        q[0] += gr * gr;
+        q[1] += rc * z;
+    }
+    block_reduce<kBlock, 2>(q, 0u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(q, 0u, partials, &st->cnt[2], tot, red) && threadIdx.x == 0) {
+        st->gnorm2 = tot[0];
+        st->rz = tot[1];
+        st->cg_done = 0;
+        st->cg_it = 0;
+    }
+}
+
+// ---- C1: Ap = A p (also L1: Ad = A d with partials) -------------------------------------
+template <class V, class Vec, class X, bool LS>
+__global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                  const V* __restrict__ val, const X* __restrict__ x,
+                                                  Vec* __restrict__ out, const Vec* __restrict__ r, int64_t m,
+                                                  double* partials, PdState* st) {
+    using Acc = Vec;
+    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    if (!LS && *(volatile int32_t*)&st->cg_done) return;
+    double p[2] = {0.0, 0.0};
+    const int64_t ntiles = (m + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, m - r0);
+        const Acc u = csr_tile<kBlock, cap_of<V>(), V, X, Acc>(ptr, col, val, x, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t i = r0 + threadIdx.x;
+            out[i] = u;
+            if (LS) {
+                p[0] += (double)r[i] * (double)u;
+                p[1] += (double)u * (double)u;
+            }
+        }
+    }
+    if (!LS) return;
+    block_reduce<kBlock, 2>(p, 0u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(p, 0u, partials, &st->cnt[3], tot, red) && threadIdx.x == 0) {
+        st->rAd = tot[0];
+        st->AdAd = tot[1];
+        st->products += 1;
+        st->ls_done = 0;
+        st->ls_trial = 0;
+        st->step = 1.0;
+    }
+}
+
+// ---- C2: Hp = h p + A^T Ap, alpha ------------------------------------------------------
+template <class V, class Vec>
+__global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                  const V* __restrict__ val, const Vec* __restrict__ ap,
+                                                  const double* __restrict__ hd, const double* __restrict__ p,
+                                                  double* __restrict__ hp, int64_t n, double* partials, PdState* st) {
+    using Acc = Vec;
+    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ double red[32];
+    if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
+    double q[1] = {0.0};
+    const int64_t ntiles = (n + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, n - r0);
+        const Acc a = csr_tile<kBlock, cap_of<V>(), V, Vec, Acc>(ptr, col, val, ap, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t j = r0 + threadIdx.x;
+            const double pj = p[j];
+            const double h = hd[j] * pj + (double)a;
+            hp[j] = h;
+            q[0] += pj * h;
+        }
+    }
+    block_reduce<kBlock, 1>(q, 0u, red);
+    double tot[1];
+    if (grid_reduce_last<kBlock, 1>(q, 0u, partials, &st->cnt[4], tot, red) && threadIdx.x == 0) {
+        st->products += 2;
+        st->cg_total += 1;
+        if (tot[0] <= 0.0) {
+            st->cg_done = 1;
+            st->alpha = 0.0;
+        } else {
+            st->alpha = st->rz / tot[0];
+        }
+    }
+}
+
+// ---- C3: d += alpha p, res -= alpha Hp ------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_pd_cgupd(double* __restrict__ d, double* __restrict__ rcg,
+                                                     const double* __restrict__ p, const double* __restrict__ hp,
+                                                     const double* __restrict__ minv, int64_t n, double* partials,
+                                                     PdState* st) {
+    __shared__ double red[2 * 32];
+    if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
+    const double alpha = st->alpha;
+    double q[2] = {0.0, 0.0};
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        d[j] += alpha * p[j];
+        const double rc = rcg[j] - alpha * hp[j];
+        rcg[j] = rc;
+        q[0] += rc * rc;
+        q[1] += rc * (minv[j] * rc);
+    }
+    block_reduce<kBlock, 2>(q, 0u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(q, 0u, partials, &st->cnt[5], tot, red) && threadIdx.x == 0) {
+        st->cg_it += 1;
+        if (sqrt(tot[0]) <= st->pcg_rtol * sqrt(st->gnorm2) || st->cg_it >= st->pcg_max) {
+            st->cg_done = 1;
+        } else {
+            st->beta = tot[1] / st->rz;
+            st->rz = tot[1];
+        }
+    }
+}
+
+// ---- C4: p = M^{-1} res + beta p --------------------------------------------------------
+template <class PX>
+__global__ void __launch_bounds__(kBlock) k_pd_pupd(double* __restrict__ p, PX* __restrict__ p_g,
+                                                    const double* __restrict__ rcg, const double* __restrict__ minv,
+                                                    int64_t n, const PdState* st) {
+    if (halted(st) || *(volatile const int32_t*)&st->cg_done) return;
+    const double beta = st->beta;
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const double v = minv[j] * rcg[j] + beta * p[j];
+        p[j] = v;
+        if (p_g) p_g[j] = (PX)v;
+    }
+}
+
+// ---- LT: Armijo trials -------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ x, const double* __restrict__ d,
+                                                     const double* __restrict__ grad, int64_t n, double* partials,
+                                                     PdState* st) {
+    __shared__ double red[(kTrialsPerPass + 1) * 32];
+    if (halted(st) || *(volatile int32_t*)&st->ls_done) return;
+    const double mu = st->mu, step0 = st->step;
+    double q[kTrialsPerPass + 1];
+#pragma unroll
+    for (int t = 0; t <= kTrialsPerPass; ++t) q[t] = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const double xj = x[j], dj = d[j];
+        const double w0 = sqrt(mu * mu + xj * xj);
+        double a = step0;
+#pragma unroll
+        for (int t = 0; t < kTrialsPerPass; ++t) {
+            const double xt = xj + a * dj;
+            q[t] += (a * dj) * (xj + xt) / (sqrt(mu * mu + xt * xt) + w0);
+            a *= 0.5;
+        }
+        q[kTrialsPerPass] += grad[j] * dj;
+    }
+    block_reduce<kBlock, kTrialsPerPass + 1>(q, 0u, red);
+    double tot[kTrialsPerPass + 1];
+    if (grid_reduce_last<kBlock, kTrialsPerPass + 1>(q, 0u, partials, &st->cnt[6], tot, red) && threadIdx.x == 0) {
+        const double slope = tot[kTrialsPerPass];
+        double a = step0;
+        for (int t = 0; t < kTrialsPerPass; ++t) {
+            const int64_t trial = st->ls_trial + t;
+            const double df = st->tau * tot[t] - a * st->rAd + 0.5 * a * a * st->AdAd;
+            if (df <= st->armijo * a * slope || trial >= st->ls_max - 1) {
+                st->step = a;
+                st->ls_done = 1;
+                st->ls_total += trial + 1;
+                return;
+            }
+            a *= 0.5;
+        }
+        st->step = a;
+        st->ls_trial += kTrialsPerPass;
+    }
+}
+
+// ---- L3: x += step d, dual estimate update -----------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, double* __restrict__ gd,
+                                                     const double* __restrict__ d, int64_t n, PdState* st) {
+    if (halted(st)) return;
+    const double mu = st->mu, step = st->step;
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const double xj = x[j], dj = d[j], gj = gd[j];
+        const double w = sqrt(mu * mu + xj * xj);
+        const double dg = (xj + (1.0 - gj * xj / w) * dj) / w - gj;
+        const double xn = xj + step * dj;
+        x[j] = xn;
+        gd[j] = fmin(1.0, fmax(-1.0, gj + dg));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->prev_full = step == 1.0 ? 1 : 0;
+        st->iter += 1;
+    }
+}
+
+template <class K>
+int grid_for(const Inst* I, K kernel, int64_t rows) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ntiles = (rows + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)I->ctx->num_sms * per_sm));
+}
+
+struct PdWork {
+    double *X = nullptr, *gd = nullptr, *atr = nullptr, *grad = nullptr, *hd = nullptr, *minv = nullptr,
+           *rcg = nullptr, *p = nullptr, *hp = nullptr, *d = nullptr;
+    float* p32 = nullptr;   // FP32 shadow of p for the gathers of C1
+    void *r = nullptr, *ap = nullptr, *ad = nullptr;
+    double* part = nullptr;
+    PdState* st = nullptr;
+    PdState* host = nullptr;
+    int gm = 0, gn = 0, gv = 0;
+    cudaGraphExec_t cg_exec = nullptr;
+    int cg_chunk = 0;
+    ~PdWork() {
+        if (cg_exec) cudaGraphExecDestroy(cg_exec);
+        if (host) cudaFreeHost(host);
+    }
+};
+
+template <class V, class Vec>
+void enqueue_cg(Inst* I, PdWork* w, cudaStream_t s) {
+    const V* rv = static_cast<const V*>(I->csr_val);
+    const V* cv = static_cast<const V*>(I->csc_val);
+    if constexpr (sizeof(Vec) == 8)
+        k_pd_ax<V, Vec, double, false><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->p, (Vec*)w->ap,
+                                                                nullptr, I->m, w->part, w->st);
+    else
+        k_pd_ax<V, Vec, float, false><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->p32, (Vec*)w->ap,
+                                                               nullptr, I->m, w->part, w->st);
+    k_pd_hp<V, Vec><<<w->gn, kBlock, 0, s>>>(I->csc_ptr, I->csc_row, cv, (const Vec*)w->ap, w->hd, w->p, w->hp, I->n,
+                                             w->part, w->st);
+    k_pd_cgupd<<<w->gv, kBlock, 0, s>>>(w->d, w->rcg, w->p, w->hp, w->minv, I->n, w->part, w->st);
+    k_pd_pupd<float><<<w->gv, kBlock, 0, s>>>(w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->rcg, w->minv, I->n, w->st);
+}
+
+template <class V, class Vec>
+l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res, cudaStream_t s) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t m = I->m, n = I->n;
+    PdWork* w = static_cast<PdWork*>(I->pd_work);
+    if (!w) {
+        w = new PdWork();
+        I->pd_work = w;
+        I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
+        for (double** v : {&w->X, &w->gd, &w->atr, &w->grad, &w->hd, &w->minv, &w->rcg, &w->p, &w->hp, &w->d})
+            L1LS_TRY(I->alloc_n(v, n));
+        if (sizeof(Vec) == 4) L1LS_TRY(I->alloc_n(&w->p32, n));
+        L1LS_TRY(I->alloc(&w->r, sizeof(Vec) * m));
+        L1LS_TRY(I->alloc(&w->ap, sizeof(Vec) * m));
+        L1LS_TRY(I->alloc(&w->ad, sizeof(Vec) * m));
+        w->gm = grid_for(I, k_pd_resid<V, Vec, double>, m);
+        w->gn = grid_for(I, k_pd_atr<V, Vec>, n);
+        w->gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)I->ctx->num_sms * 8));
+        const int gmax = std::max(w->gm, std::max(w->gn, w->gv));
+        L1LS_TRY(I->alloc_n(&w->part, (int64_t)gmax * (kTrialsPerPass + 1)));
+        L1LS_TRY(I->alloc_n(&w->st, 1));
+        L1LS_CUDA(cudaMallocHost((void**)&w->host, sizeof(PdState)));
+    }
+    if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
+    else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
+    L1LS_CUDA(cudaMemsetAsync(w->gd, 0, sizeof(double) * n, s));
+    PdState h;
+    memset(&h, 0, sizeof(h));
+    h.tau = o->tau;
+    h.tol = o->rel_gap_tol;
+    h.mu = o->mu;
+    h.mu_min = o->mu_min;
+    h.pcg_rtol = o->pcg_rtol;
+    h.armijo = o->armijo;
+    h.stall = 0.5;
+    h.max_newton = o->max_iter;
+    h.pcg_max = o->pcg_max;
+    h.ls_max = o->ls_max;
+    h.prev_gap = INFINITY;
+    *w->host = h;
+    L1LS_CUDA(cudaMemcpyAsync(w->st, w->host, sizeof(PdState), cudaMemcpyHostToDevice, s));
+    const V* rv = static_cast<const V*>(I->csr_val);
+    const V* cv = static_cast<const V*>(I->csc_val);
+    const Vec* bvec = sizeof(Vec) == 8 ? (const Vec*)I->bhat : (const Vec*)I->bhat32;
+    l1ls_status final_status = L1LS_OK;
+    int chunk = o->check_every > 0 ? std::min(o->check_every, 16) : 8;
+    if (!w->cg_exec || w->cg_chunk != chunk) {
+        if (w->cg_exec) {
+            cudaGraphExecDestroy(w->cg_exec);
+            w->cg_exec = nullptr;
+        }
+        cudaStream_t cap;
+        L1LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        L1LS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < chunk; ++i) enqueue_cg<V, Vec>(I, w, cap);
+        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+        }
+        L1LS_CUDA(cudaGraphInstantiate(&w->cg_exec, graph, 0));
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        w->cg_chunk = chunk;
+    }
+    const int ls_passes = (o->ls_max + kTrialsPerPass - 1) / kTrialsPerPass;
+    for (;;) {
+        // N1 gathers the FP64 iterate (once per Newton step)
+        k_pd_resid<V, Vec, double><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->X, bvec, (Vec*)w->r, m,
+                                                            w->part, w->st);
+        k_pd_atr<V, Vec><<<w->gn, kBlock, 0, s>>>(I->csc_ptr, I->csc_row, cv, (const Vec*)w->r, w->X, w->atr, n,
+                                                  w->part, w->st);
+        L1LS_CUDA(cudaGetLastError());
+        L1LS_CUDA(cudaMemcpyAsync(w->host, w->st, sizeof(PdState), cudaMemcpyDeviceToHost, s));
+        L1LS_CUDA(cudaStreamSynchronize(s));
+        if (w->host->stop) {
+            final_status = (l1ls_status)w->host->status;
+            break;
+        }
+        if (o->time_limit_s > 0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > o->time_limit_s) {
+            final_status = L1LS_ETIMEOUT;
+            break;
+        }
+        k_pd_init<float><<<w->gv, kBlock, 0, s>>>(w->X, w->gd, w->atr, I->colnorm2, w->grad, w->hd, w->minv, w->rcg,
+                                                  w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->d, n, w->part, w->st);
+        L1LS_CUDA(cudaGetLastError());
+        const int64_t max_cg_launches = o->pcg_max / chunk + 3;
+        for (int64_t launch = 0;; ++launch) {
+            if (launch >= max_cg_launches) {
+                final_status = set_error(L1LS_ECUDA, "internal: PCG did not raise its stop flag");
+                break;
+            }
+            L1LS_CUDA(cudaGraphLaunch(w->cg_exec, s));
+            L1LS_CUDA(cudaMemcpyAsync(&w->host->cg_done, &w->st->cg_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            L1LS_CUDA(cudaStreamSynchronize(s));
+            if (w->host->cg_done) break;
+        }
+        if (final_status != L1LS_OK) break;
+        k_pd_ax<V, Vec, double, true><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->d, (Vec*)w->ad,
+                                                               (const Vec*)w->r, m, w->part, w->st);
+        for (int t = 0; t < ls_passes; ++t)
+            k_pd_trial<<<w->gv, kBlock, 0, s>>>(w->X, w->d, w->grad, n, w->part, w->st);
+        k_pd_apply<<<w->gv, kBlock, 0, s>>>(w->X, w->gd, w->d, n, w->st);
+        L1LS_CUDA(cudaGetLastError());
+    }
+    const PdState& f = *w->host;
+    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X, sizeof(double) * n, cudaMemcpyDefault, s));
+    L1LS_CUDA(cudaStreamSynchronize(s));
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->iters = f.iter;
+        res->products = f.products;
+        res->cg_iters = f.cg_total;
+        res->ls_trials = f.ls_total;
+        res->f = f.P;
+        res->dual = f.D;
+        res->gap = f.gap;
+        res->rel_gap = f.rel;
+        res->mu = f.mu;
+        res->status = final_status;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (final_status != L1LS_OK) {
+        const char* why = final_status == L1LS_ENOCONV ? "Newton iteration limit reached"
+                          : final_status == L1LS_ETIMEOUT ? "time limit reached"
+                                                          : "NaN or Inf in the iteration";
+        return set_error(final_status, "pdNCG: %s (rel_gap %.3e)", why, f.rel);
+    }
+    return L1LS_OK;
+}
+
+}  // namespace
+
+l1ls_status pdncg_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                        cudaStream_t st) {
+    switch (I->dtype) {
+        case L1LS_F64: return run<double, double>(I, o, x0, x_out, res, st);
+        case L1LS_F32: return run<float, float>(I, o, x0, x_out, res, st);
+        default: return run<__nv_bfloat16, float>(I, o, x0, x_out, res, st);
+    }
+}
+
+}  // namespace l1ls
+
+using namespace l1ls;
+
+extern "C" l1ls_status l1ls_solve_pdncg(l1ls_inst* h, const l1ls_solve_opts* o, const double* x0, double* x_out,
+                                        l1ls_result* res, void* stream) {
+    if (!h || !o) return set_error(L1LS_EINVAL, "NULL argument");
+    if (!(o->tau > 0.0) || !(o->rel_gap_tol >= 0.0) || o->max_iter < 0 || o->ls_max < 1 || o->pcg_max < 1 ||
+        !(o->mu > 0.0))
+        return set_error(L1LS_EINVAL, "bad solver options");
+    Inst* I = reinterpret_cast<Inst*>(h);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    return pdncg_solve(I, o, x0, x_out, res, (cudaStream_t)stream);
+}

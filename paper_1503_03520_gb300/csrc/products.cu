@@ -1,0 +1,130 @@
+// Plain products y = A x and x = A^T y (Algorithms MvPA / MvPAt compute the same products
+// matrix-free; here A is stored).  A is held as P1^T A, so
+//   A x   = P1 (P1^T A) x          : row rho of P1^T A lands in y[perm_inv[rho]],
+//   A^T y = (P1^T A)^T (P1^T y)    : (P1^T y)[rho] = y[perm_inv[rho]], gathered first.
+#include "internal.h"
+#include "spmv.cuh"
+
+namespace l1ls {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <class V, class Acc>
+constexpr int cap_for() { return sizeof(Acc) == 8 ? 2048 : 4096; }
+
+template <class V, class X, class Acc>
+__global__ void __launch_bounds__(kBlock) k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                 const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
+                                                 const int32_t* __restrict__ out_perm, X* __restrict__ y) {
+    constexpr int CAP = cap_for<V, Acc>();
+    __shared__ CsrSmem<kBlock, CAP, Acc> sm;
+    const int64_t ntiles = (nrows + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kBlock;
+        const int nr = (int)min((int64_t)kBlock, nrows - r0);
+        const Acc acc = csr_tile<kBlock, CAP, V, X, Acc>(ptr, col, val, x, r0, nr, sm);
+        if ((int)threadIdx.x < nr) {
+            const int64_t r = r0 + threadIdx.x;
+            const int64_t dst = out_perm ? out_perm[r] : r;
+            y[dst] = (X)acc;
+        }
+    }
+}
+
+template <class X>
+__global__ void k_gather(const X* __restrict__ y, const int32_t* __restrict__ idx, int64_t count, X* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = y[idx[i]];
+}
+
+int grid_for(const Inst* I, int64_t nrows) {
+    int64_t ntiles = (nrows + kBlock - 1) / kBlock;
+    int64_t g = (int64_t)I->ctx->num_sms * 8;
+    return (int)(ntiles < g ? (ntiles > 0 ? ntiles : 1) : g);
+}
+
+template <class V, class X>
+l1ls_status launch_spmv(const Inst* I, bool transpose, const X* x, X* y, const int32_t* out_perm, cudaStream_t st) {
+    using Acc = typename std::conditional<std::is_same<V, double>::value, double, float>::type;
+    const int32_t* ptr = transpose ? I->csc_ptr : I->csr_ptr;
+    const int32_t* col = transpose ? I->csc_row : I->csr_col;
+    const V* val = static_cast<const V*>(transpose ? I->csc_val : I->csr_val);
+    const int64_t nrows = transpose ? I->n : I->m;
+    k_spmv<V, X, Acc><<<grid_for(I, nrows), kBlock, 0, st>>>(ptr, col, val, x, nrows, out_perm, y);
+    L1LS_CUDA(cudaGetLastError());
+    return L1LS_OK;
+}
+
+template <class X>
+l1ls_status dispatch(const Inst* I, bool transpose, const X* x, X* y, const int32_t* out_perm, cudaStream_t st) {
+    switch (I->dtype) {
+        case L1LS_F64: return launch_spmv<double, X>(I, transpose, x, y, out_perm, st);
+        case L1LS_F32: return launch_spmv<float, X>(I, transpose, x, y, out_perm, st);
+        default: return launch_spmv<__nv_bfloat16, X>(I, transpose, x, y, out_perm, st);
+    }
+}
+
+}  // namespace
+
+// Products on device buffers.  transpose = false: y = A x (rows unpermuted into the original
+// order when unpermute_rows, else left in the relabelled order).  transpose = true: x = A^T y
+// where y is in the original row order when unpermute_rows (gathered through scratch), else
+// already relabelled.
+l1ls_status spmv_plain(const Inst* I, bool transpose, const void* in, int vec_dtype, void* out, bool unpermute_rows,
+                       cudaStream_t st) {
+    const size_t es = vec_dtype == L1LS_F64 ? 8 : 4;
+    if (!transpose) {
+        const int32_t* op = unpermute_rows ? I->perm_inv : nullptr;
+        if (vec_dtype == L1LS_F64) return dispatch<double>(I, false, (const double*)in, (double*)out, op, st);
+        return dispatch<float>(I, false, (const float*)in, (float*)out, op, st);
+    }
+    const void* src = in;
+    if (unpermute_rows) {
+        void* scratch = nullptr;
+        L1LS_TRY(I->ctx->staging(2, es * (size_t)I->m, &scratch));
+        unsigned nb = (unsigned)((I->m + 255) / 256);
+        if (vec_dtype == L1LS_F64) k_gather<double><<<nb, 256, 0, st>>>((const double*)in, I->perm_inv, I->m, (double*)scratch);
+        else k_gather<float><<<nb, 256, 0, st>>>((const float*)in, I->perm_inv, I->m, (float*)scratch);
+        L1LS_CUDA(cudaGetLastError());
+        src = scratch;
+    }
+    if (vec_dtype == L1LS_F64) return dispatch<double>(I, true, (const double*)src, (double*)out, nullptr, st);
+    return dispatch<float>(I, true, (const float*)src, (float*)out, nullptr, st);
+}
+
+}  // namespace l1ls
+
+using namespace l1ls;
+
+static l1ls_status product_entry(const l1ls_inst* h, const void* in, l1ls_dtype vd, void* out, void* stream,
+                                 bool transpose) {
+    if (!h || !in || !out) return set_error(L1LS_EINVAL, "NULL argument");
+    if (vd != L1LS_F64 && vd != L1LS_F32) return set_error(L1LS_EINVAL, "vec_dtype must be L1LS_F64 or L1LS_F32");
+    const Inst* I = reinterpret_cast<const Inst*>(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    const size_t es = vd == L1LS_F64 ? 8 : 4;
+    const int64_t nin = transpose ? I->m : I->n, nout = transpose ? I->n : I->m;
+    const bool din = is_device_pointer(in), dout = is_device_pointer(out);
+    if (din && dout) return spmv_plain(I, transpose, in, vd, out, true, st);
+    void *dx = const_cast<void*>(in), *dy = out;
+    if (!din) {
+        L1LS_TRY(I->ctx->staging(0, es * nin, &dx));
+        L1LS_CUDA(cudaMemcpyAsync(dx, in, es * nin, cudaMemcpyHostToDevice, st));
+    }
+    if (!dout) L1LS_TRY(I->ctx->staging(1, es * nout, &dy));
+    L1LS_TRY(spmv_plain(I, transpose, dx, vd, dy, true, st));
+    if (!dout) L1LS_CUDA(cudaMemcpyAsync(out, dy, es * nout, cudaMemcpyDeviceToHost, st));
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    return L1LS_OK;
+}
+
+extern "C" l1ls_status l1ls_matvec(const l1ls_inst* inst, const void* x, l1ls_dtype vec_dtype, void* y, void* stream) {
+    return product_entry(inst, x, vec_dtype, y, stream, false);
+}
+
+extern "C" l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream) {
+    return product_entry(inst, y, vec_dtype, x, stream, true);
+}

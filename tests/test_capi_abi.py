@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every entry point of include/l1ls.h (no GPU needed),
+and the ctypes structures of the binding match the C layout compiled by gcc."""
+
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "l1ls.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(l1ls_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["l1ls_generate", "l1ls_matvec", "l1ls_rmatvec", "l1ls_solve_fista", "l1ls_solve_pdncg",
+                     "l1ls_create", "l1ls_destroy", "l1ls_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1503_03520_gb300 as l1
+    lib = ctypes.CDLL(l1.library_path)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header():
+    import paper_1503_03520_gb300 as l1
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "l1ls.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(l1ls_gen_params), sizeof(l1ls_inst_info), sizeof(l1ls_solve_opts),
+         sizeof(l1ls_result));
+  printf("%zu %zu %zu\n", offsetof(l1ls_gen_params, right_stages), offsetof(l1ls_solve_opts, ls_max),
+         offsetof(l1ls_result, status));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    sizes = [int(v) for v in out]
+    assert sizes[:4] == [ctypes.sizeof(l1.GenParams), ctypes.sizeof(l1.InstInfo), ctypes.sizeof(l1.SolveOpts),
+                         ctypes.sizeof(l1.Result)]
+    assert sizes[4] == l1.GenParams.right_stages.offset
+    assert sizes[5] == l1.SolveOpts.ls_max.offset
+    assert sizes[6] == l1.Result.status.offset
+
+
+def test_defaults_without_gpu():
+    import paper_1503_03520_gb300 as l1
+    p = l1.gen_params({"m": 64, "n": 32, "value_dtype": "f32"})
+    assert p.m == 64 and p.n == 32 and p.value_dtype == 1 and p.right_stages == 1 and p.left_stages == 1
+    o = l1.solve_opts(tol=1e-8)
+    assert o.rel_gap_tol == 1e-8 and o.mu == 1e-5 and o.ls_max == 50 and o.pcg_rtol == 0.1
+
+
+def test_create_fails_cleanly_without_device():
+    import torch
+    import paper_1503_03520_gb300 as l1
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(l1.L1LSError):
+        l1.Context(0)

@@ -1,0 +1,98 @@
+"""Device generator against the oracle: integer structure bit-exact, values within rounding.
+
+Procedures IGen / OsGen and Eq. (bd8) with the stages of Sec. 4.1-4.2; recipes with one and
+with no left stage; sizes that span several 256-row tiles with ragged tails."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import csr_from_export, oracle_instance, ulp
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(m=2048, n=1024, right_stages=1, left_stages=1, kappa=1e2, value_dtype="f64"),
+    dict(m=10010, n=5003, right_stages=2, left_stages=1, kappa=1e4, value_dtype="f64", seed=3),
+    dict(m=6000, n=3000, right_stages=4, left_stages=1, kappa=1e6, value_dtype="f32", seed=5, xstar_frac=0.02),
+    dict(m=4098, n=2049, right_stages=3, left_stages=0, kappa=1e3, value_dtype="f64", seed=7),
+    dict(m=3000, n=3000, right_stages=2, left_stages=1, kappa=50.0, value_dtype="bf16", seed=9),
+    dict(m=512, n=8, right_stages=1, left_stages=1, kappa=10.0, value_dtype="f64", seed=1, xstar_frac=0.25),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1503_03520_gb300 as l1
+    c = l1.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "m%d_n%d_w%d_l%d_%s" % (c["m"], c["n"], c["right_stages"],
+                                                                            c["left_stages"], c["value_dtype"]))
+def test_generator_matches_oracle(ctx, case):
+    params = W.params(**case)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        m, n = params["m"], params["n"]
+        assert inst.nnz == ref.A.nnz
+        ex = inst.export()
+        A = csr_from_export(ex, m, n)
+        # integer structure: bit-exact
+        assert np.array_equal(ex["indptr"], ref.A.indptr.astype(np.int64))
+        assert np.array_equal(ex["indices"], ref.A.indices.astype(np.int32))
+        if params["left_stages"]:
+            assert np.array_equal(ex["perm"], ref.perm)
+        assert np.array_equal(np.flatnonzero(ex["xstar"]), ref.support)
+        # x*: the same arithmetic on both sides
+        assert np.array_equal(ex["xstar"], ref.xstar)
+        # sigma: exp of the same argument (device and host exp may differ by an ulp)
+        assert np.allclose(ex["sigma"], ref.sigma, rtol=4e-16, atol=0)
+        # values: FP64 entries agree to rounding; stored types to one unit in the last place
+        dt = params["value_dtype"]
+        diff = np.abs(A.data - ref.A.data)
+        if dt == "f64":
+            assert diff.max() <= 1e-14 * np.abs(ref.A.data).max()
+        else:
+            assert np.all(diff <= ulp(ref.A.data, dt) * 1.0 + 1e-15)
+        # b: e by different but equivalent routes (Sec. 4); agreement to kappa * eps
+        scale = np.abs(ref.b).max()
+        assert np.abs(ex["b"] - ref.b).max() <= 50 * params["kappa"] * 2.2e-16 * scale
+        info = inst.info
+        assert info["f_star"] == pytest.approx(ref.f_star, rel=1e-12)
+        assert info["lam_max"] == pytest.approx(ref.lam_max, rel=1e-10)
+        # transposed storage: the same matrix
+        et = inst.export_t()
+        At = ref.A.tocsc()
+        At.sort_indices()
+        assert np.array_equal(et["indptr"], At.indptr.astype(np.int64))
+        assert np.array_equal(et["indices"], At.indices.astype(np.int32))
+        Ag = A.tocsc()
+        Ag.sort_indices()
+        assert np.array_equal(et["data"], Ag.data)        # exact transposes of each other
+    finally:
+        inst.free()
+
+
+def test_generation_is_deterministic(ctx):
+    params = W.params(m=4096, n=2048, right_stages=2, seed=11, value_dtype="f32")
+    a = ctx.generate(params)
+    b = ctx.generate(params)
+    try:
+        ea, eb = a.export(), b.export()
+        for k in ea:
+            assert np.array_equal(ea[k], eb[k]), k
+    finally:
+        a.free()
+        b.free()
+
+
+def test_invalid_parameters_are_rejected(ctx):
+    import paper_1503_03520_gb300 as l1
+    for bad in [dict(m=2047, n=1024), dict(m=2048, n=1024, kappa=0.5), dict(m=2048, n=1024, right_stages=9),
+                dict(m=2048, n=1024, left_stages=2), dict(m=2048, n=1024, tau=-1.0)]:
+        with pytest.raises(l1.L1LSError) as e:
+            ctx.generate(W.params(**bad))
+        assert e.value.status == 1

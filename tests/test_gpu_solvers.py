@@ -1,0 +1,125 @@
+"""FISTA and pdNCG on the device against the oracle (Sec. 8.1; IGen's known optimum)."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import oracle_instance, stored_values
+from oracle import solvers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1503_03520_gb300 as l1
+    c = l1.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def c1(ctx):
+    ref = oracle_instance(W.C1)
+    inst = ctx.generate(W.C1)
+    yield ref, inst
+    inst.free()
+
+
+def test_fista_c1_matches_oracle(c1):
+    ref, inst = c1
+    tol = W.C1_TOL
+    x, r = inst.solve_fista(tau=1.0, tol=tol, max_iter=200000)
+    assert r["status"] == 0 and r["rel_gap"] <= tol
+    o = solvers.fista(ref.A, ref.b, 1.0, ref.lipschitz, tol, 200000)
+    # same rule, same iteration count up to rounding-order effects at the threshold
+    assert abs(r["iters"] - o["iters"]) <= max(3, 0.01 * o["iters"])
+    # primal suboptimality by the oracle's objective against the known optimum
+    f = solvers.objective(ref.A, ref.b, 1.0, x)
+    assert f - ref.f_star <= 1.01 * tol * ref.f_star
+    assert np.sum((x - ref.xstar) ** 2) <= 2.0 * 1.01 * tol * ref.f_star / ref.sigma.min() ** 2
+
+
+def test_pdncg_c1_matches_oracle(c1):
+    ref, inst = c1
+    tol = W.C1_TOL
+    x, r = inst.solve_pdncg(tau=1.0, tol=tol, max_iter=200)
+    assert r["status"] == 0 and r["rel_gap"] <= tol
+    o = solvers.pdncg(ref.A, ref.b, 1.0, tol)
+    assert abs(r["iters"] - o["iters"]) <= 2
+    assert r["iters"] <= 30
+    f = solvers.objective(ref.A, ref.b, 1.0, x)
+    assert f - ref.f_star <= 1.01 * tol * ref.f_star
+
+
+@pytest.mark.parametrize("method", ["fista", "pdncg"])
+@pytest.mark.parametrize("tau", [0.5, 2.0])
+def test_tau_off_generator_matches_oracle_solution(ctx, method, tau):
+    """tau != tau_gen: no closed form; compare with the oracle's own solve."""
+    params = W.params(m=1024, n=512, right_stages=2, kappa=30.0, seed=4, xstar_frac=0.05)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        fn = inst.solve_fista if method == "fista" else inst.solve_pdncg
+        x, r = fn(tau=tau, tol=1e-10, max_iter=500000 if method == "fista" else 200)
+        assert r["status"] == 0
+        o = (solvers.fista(ref.A, ref.b, tau, 1.0, 1e-10, 500000) if method == "fista"
+             else solvers.pdncg(ref.A, ref.b, tau, 1e-10))
+        fo = solvers.objective(ref.A, ref.b, tau, o["x"])
+        fg = solvers.objective(ref.A, ref.b, tau, x)
+        assert abs(fg - fo) <= 2e-10 * fo
+    finally:
+        inst.free()
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+@pytest.mark.parametrize("method", ["fista", "pdncg"])
+def test_reduced_precision_certificate_holds_on_the_stored_problem(ctx, dt, method):
+    """FP32 / BF16 values define their own problem (A rounded once); the oracle re-checks the
+    device's answer on that problem with its own certificate."""
+    tol = 1e-6 if dt == "f32" else 1e-4
+    params = W.params(m=16384, n=8192, right_stages=2, kappa=1e3, seed=6, xstar_frac=0.01, value_dtype=dt)
+    ref = oracle_instance(params)
+    A = stored_values(ref.A, dt)
+    b = ref.b.astype(np.float32).astype(np.float64)
+    inst = ctx.generate(params)
+    try:
+        fn = inst.solve_fista if method == "fista" else inst.solve_pdncg
+        x, r = fn(tau=1.0, tol=tol, max_iter=200000 if method == "fista" else 200)
+        assert r["status"] == 0 and r["rel_gap"] <= tol
+        P, D, gap, rel = solvers.certificate(A, b, 1.0, x)
+        assert rel <= 20 * tol
+        # stated per result: relative error of f_tau against the FP64 optimum
+        f64 = solvers.objective(ref.A, ref.b, 1.0, x)
+        assert abs(f64 - ref.f_star) / ref.f_star <= 100 * tol
+    finally:
+        inst.free()
+
+
+def test_warm_start_at_optimum_certifies_immediately(c1):
+    ref, inst = c1
+    x, r = inst.solve_fista(x0=ref.xstar.copy(), tau=1.0, tol=1e-10, max_iter=10)
+    assert r["status"] == 0 and r["iters"] == 0
+    x, r = inst.solve_pdncg(x0=ref.xstar.copy(), tau=1.0, tol=1e-10, max_iter=10)
+    assert r["status"] == 0 and r["iters"] == 0
+
+
+def test_iteration_limit_reports_noconv(c1):
+    ref, inst = c1
+    x, r = inst.solve_fista(tau=1.0, tol=1e-14, max_iter=10)
+    assert r["status"] == 5 and r["iters"] == 10
+    o = solvers.fista(ref.A, ref.b, 1.0, 1.0, 0.0, 10)
+    assert np.allclose(x, o["x"], rtol=1e-12, atol=1e-12)
+
+
+def test_device_buffers_in_place(c1):
+    import torch
+    ref, inst = c1
+    x0 = torch.zeros(inst.n, dtype=torch.float64, device="cuda")
+    xo = torch.empty(inst.n, dtype=torch.float64, device="cuda")
+    xr, r = inst.solve_fista(x0=x0, x_out=xo, tau=1.0, tol=1e-8, max_iter=100000)
+    torch.cuda.synchronize()
+    assert r["status"] == 0
+    xh, rh = inst.solve_fista(tau=1.0, tol=1e-8, max_iter=100000)
+    assert np.array_equal(xo.cpu().numpy(), xh)      # deterministic reductions
+    assert rh["iters"] == r["iters"]
