@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the l1-LS hot path on one GB300 (or N replicas under torchrun).
+
+Workload: the large single instance (m = 2^25, n = 2^24, about 8 nonzeros per column, FP32
+values, int32 indices, kappa(A) = 1e4, x* 1% nonzeros, tau = 1).  One step is one fused FISTA
+iteration: K1 (A x with the momentum / residual epilogue and FP64 gap partials) and K2 (A^T r
+with the shrinkage / momentum epilogue and the FP64 certificate), i.e. both products.
+
+value   = algorithmic bytes of the two products with their fused vector traffic per
+          iteration / device time per iteration (CUDA events on the launching stream),
+          summed over ranks (weak scaling: one instance per GPU).
+e2e     = the same quantity through l1ls_solve_fista with HOST buffers: every step is a
+          warm-started 32-iteration solve from a pinned host x0 to a pinned host x_out.
+roofline: the dominant kernel (K1 or K2) against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference: the FP64 oracle (numpy + scipy) on a sample of the same
+          recipe, timed on the host cores, in the same unit.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ax/ATy HBM GB/s (fused FISTA iteration)"
+UNIT = "GB/s"
+FALLBACK_HBM = 6800.0
+E2E_ITERS = 32
+KERNEL_SOURCES = ["spmv.cuh", "fista.cu", "common.cuh"]
+
+
+def bytes_per_iteration(m, n, nnz, value_bytes=4, vec_bytes=4):
+    """Algorithmic bytes of K1 and K2 for FP32 values and FP32 products (FP64 iterates).
+
+    K1: nnz (value + int32 index) + (m+1) row pointers + x gathered once (n FP32)
+        + A x_{k-2} read, b read, A x_{k-1} written, r written (4 m-vectors).
+    K2: nnz (value + index) + (n+1) pointers + r gathered once (m FP32) + x_{k-1}, x_{k-2}
+        read and x_k written (FP64) + FP32 shadow of x_k written.
+    """
+    k1 = nnz * (value_bytes + 4) + (m + 1) * 4 + n * vec_bytes + 4 * m * vec_bytes
+    k2 = nnz * (value_bytes + 4) + (n + 1) * 4 + m * vec_bytes + 3 * n * 8 + n * 4
+    return k1, k2
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1503_03520_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it still matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("bytes_per_launch", {}).get(kernel)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_iterations(log2n, warmup, steps, budget_s):
+    """Time oracle FISTA iterations in a fresh single-threaded Python process."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+import workloads as W
+from oracle.generator import GenParams, generate
+from oracle import solvers
+p = W.c2_scaled(%d)
+t0 = time.time()
+inst = generate(GenParams.from_dict(p))
+tgen = time.time() - t0
+A, b = inst.A, inst.b
+solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, %d)
+steps = %d
+if steps <= 0:
+    t = time.time(); solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, 2); one = (time.time() - t) / 2
+    steps = max(3, int(%f / max(one, 1e-6)))
+t = time.time()
+r = solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, steps)
+el = time.time() - t
+print(json.dumps(dict(m=A.shape[0], n=A.shape[1], nnz=int(A.nnz), steps=steps, seconds=el, gen_seconds=tgen)))
+""" % (ROOT, log2n, max(warmup, 1), steps, budget_s)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + out.stderr[-2000:])
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    k1, k2 = bytes_per_iteration(d["m"], d["n"], d["nnz"])
+    per_iter = d["seconds"] / d["steps"]
+    d["value"] = (k1 + k2) / per_iter / 1e9
+    d["ms_per_step"] = per_iter * 1e3
+    return d
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    log2n = 22
+    d = cpu_oracle_iterations(log2n, args.warmup, args.steps, 0.0)
+    sample = "one oracle FISTA iteration (numpy + scipy.sparse, FP64) per step on the n=2^%d, m=2^%d instance " \
+             "of the same recipe; %d timed steps after %d warm-up" % (log2n, log2n + 1, d["steps"], args.warmup)
+    line = {"metric": METRIC, "value": d["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": d["steps"],
+            "warmup": args.warmup, "ms_per_step": d["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (generator of Sec. 3-6)",
+            "impl": "reference",
+            "config": {"workload": "c2: m=2^25, n=2^24, ~8 nnz/col, FP32 values, kappa(A)=1e4, x* 1%, tau=1",
+                       "sample": "n=2^%d" % log2n, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": d["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+
+    import paper_1503_03520_gb300 as l1
+    import workloads as W
+
+    params = W.c2_scaled(args.log2n, seed=rank)
+    ctx = l1.Context(local)
+    inst = ctx.generate(params)
+    m, n, nnz = inst.m, inst.n, inst.nnz
+    k1b, k2b = bytes_per_iteration(m, n, nnz)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    # ---- device-timed region: W warm-up + K timed FISTA iterations ---------------------
+    inst.fista_begin(tau=1.0, tol=0.0, max_iter=10 ** 12, stream=stream)
+    for _ in range(args.warmup):
+        inst.fista_step(1, stream=stream)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kms = inst.fista_step(args.steps, timed=True, stream=stream)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    _, fres = inst.fista_end(stream=stream, allow=(4, 5))
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = (k1b + k2b) * world / (ms_per_step * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel --------------------------------------------------
+    k1_ms, k2_ms = kms[0] / args.steps, kms[1] / args.steps
+    if k2_ms >= k1_ms:
+        dom, dom_ms, dom_bytes = "k_fista_k2", k2_ms, k2b
+    else:
+        dom, dom_ms, dom_bytes = "k_fista_k1", k1_ms, k1b
+    peak, peak_src = measured_hbm_peak()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src + " (hbm_gbs, copy)",
+                "traffic": profiled_traffic(dom), "algorithmic_bytes": dom_bytes,
+                "k1_ms": k1_ms, "k2_ms": k2_ms,
+                "k1_frac": k1b / (k1_ms * 1e-3) / 1e9 / peak, "k2_frac": k2b / (k2_ms * 1e-3) / 1e9 / peak}
+
+    # ---- e2e through the public API with host buffers -----------------------------------------
+    x0 = torch.zeros(n, dtype=torch.float64).pin_memory()
+    xo = torch.zeros(n, dtype=torch.float64).pin_memory()
+    x0.numpy()[:] = 0.0
+    e2e_times = []
+    for i in range(args.warmup + args.e2e_steps):
+        barrier()
+        t = time.perf_counter()
+        _, r = inst.solve_fista(x0=x0, x_out=xo, tau=1.0, tol=0.0, max_iter=E2E_ITERS, check_every=E2E_ITERS,
+                                stream=stream, allow=(5,))
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t)
+    e2e_s = statistics.median(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    # warm start from x0 costs one extra product A x0 (counted as K1's matrix traffic)
+    e2e_bytes = E2E_ITERS * (k1b + k2b) + nnz * 8 + (m + 1) * 4 + n * 4 + m * 4
+    e2e = {"value": e2e_bytes * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n, "iters_per_step": E2E_ITERS, "steps": args.e2e_steps,
+           "api": "l1ls_solve_fista(x0=pinned host, x_out=pinned host)"}
+
+    # ---- time to the 1e-6 gap (reported beside the metric) --------------------------------
+    solves = {}
+    if not args.no_solves:
+        for method in ("fista", "pdncg"):
+            fn = inst.solve_fista if method == "fista" else inst.solve_pdncg
+            barrier()
+            t = time.perf_counter()
+            _, r = fn(tau=1.0, tol=W.C2_TOL, max_iter=200000 if method == "fista" else 200,
+                      time_limit_s=args.solve_limit, stream=stream, allow=(4, 5))
+            el = time.perf_counter() - t
+            solves[method] = {"seconds": el, "iters": r["iters"], "cg_iters": r["cg_iters"],
+                              "products": r["products"], "rel_gap": r["rel_gap"], "status": r["status_name"],
+                              "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]}
+
+    inst.free()
+    ctx.close()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            log2n = 20
+            d = cpu_oracle_iterations(log2n, 1, 0, args.cpu_budget)
+            cpu = {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "%d oracle FISTA iterations (numpy + scipy.sparse, FP64, single thread) on the "
+                             "n=2^%d, m=2^%d instance of the same recipe, %.1f s" % (d["steps"], log2n, log2n + 1,
+                                                                                     d["seconds"])}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (generator of Sec. 3-6, seeded)",
+                "config": {"workload": "c2: m=2^%d, n=2^%d, nnz=%d (~8/col), FP32 values, int32 indices, "
+                                       "kappa(A)=1e4, x* 1%%, tau=1, one FISTA iteration per step"
+                                       % (args.log2n + 1, args.log2n, nnz),
+                           "l2": "inputs larger than L2 (A is %.2f GB per product)" % (nnz * 8 / 1e9),
+                           "parallelism": "replicas (one instance per GPU)" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 2 * args.steps, "fista_rel_gap_after_steps": fres["rel_gap"],
+                "time_to_gap": {"tol": W.C2_TOL, **solves}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=24)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-solves", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--solve-limit", type=float, default=60.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -142,14 +142,17 @@ l1ls_status l1ls_matvec(const l1ls_inst* inst, const void* x, l1ls_dtype vec_dty
 l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream);
 
 /* Solver options.  Defaults (l1ls_solve_opts_default): tau 1, rel_gap_tol 1e-6,
- * max_iter 100000 (FISTA iterations; Newton steps for pdNCG: 200), no time limit, mu 1e-5,
- * mu_min 1e-14, pcg_rtol 0.1, pcg_max 1000, ls_max 50, armijo 1e-4, check_every 32. */
+ * max_iter 100000 (FISTA iterations; Newton steps for pdNCG), no time limit, mu 1e-5,
+ * mu_min 1e-14, mu_start 1, pcg_rtol 0.1, pcg_max 1000, ls_max 50, armijo 1e-4,
+ * check_every 32.  pdNCG only: mu (the paper's smoothing parameter, Sec. 8.3) is reached by
+ * continuation from mu_start (divided by 10 after each full Newton step); below mu it is
+ * divided by 10 again, down to mu_min, when a full step fails to halve the gap. */
 typedef struct {
     double tau;
     double rel_gap_tol;
     int64_t max_iter;
     double time_limit_s;      /* <= 0: none */
-    double mu, mu_min, pcg_rtol, armijo;
+    double mu, mu_min, mu_start, pcg_rtol, armijo;
     int32_t ls_max, pcg_max;
     int32_t check_every;      /* iterations per graph launch between host checks          */
     int32_t reserved;
@@ -178,11 +181,26 @@ typedef struct {
 l1ls_status l1ls_solve_fista(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
                              l1ls_result* res, void* stream);
 
+/* FISTA in steps, for callers that drive the iteration themselves (benchmarks, schedulers):
+ *   l1ls_fista_begin  sets up the state of l1ls_solve_fista at x0 (NULL: 0) and enqueues it;
+ *   l1ls_fista_step   enqueues `iters` further iterations (two kernels each) without any
+ *                     host synchronisation; iterations after the stop test fired are no-ops.
+ *                     With kernel_ms != NULL (2 floats) CUDA events on `stream` bracket the
+ *                     two kernels of every iteration and their summed durations in ms are
+ *                     returned (this synchronises `stream`).
+ *   l1ls_fista_end    waits for `stream`, then returns the last certified iterate (x_out may
+ *                     be NULL) and its certificate; status ENOCONV if the stop test has not
+ *                     fired yet.
+ * One FISTA run per instance at a time; l1ls_solve_fista is begin + graph-captured steps + end. */
+l1ls_status l1ls_fista_begin(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, void* stream);
+l1ls_status l1ls_fista_step(l1ls_inst* inst, int64_t iters, float* kernel_ms, void* stream);
+l1ls_status l1ls_fista_end(l1ls_inst* inst, double* x_out, l1ls_result* res, void* stream);
+
 /* pdNCG (Sec. 8.1, parameters of Sec. 8.3): primal-dual Newton-CG on the pseudo-Huber
  * smoothing (Eqs. pseudoHuber, prob2, bd4) with diagonal-preconditioned CG stopped at
- * relative residual pcg_rtol, a halving Armijo line search of at most ls_max trials, and
- * mu reduced tenfold when a full Newton step fails to halve the gap.  Certified with the
- * same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista. */
+ * relative residual pcg_rtol (in the preconditioner's norm), a halving Armijo line search of
+ * at most ls_max trials, and mu-continuation as described with l1ls_solve_opts.  Certified
+ * with the same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista. */
 l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
                              l1ls_result* res, void* stream);
 

@@ -31,9 +31,16 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
     its curvature mu^2 / w^3 spans ~15 decades and steps shrink to ~1e-4.)
   - Armijo constant 1e-4; psi_mu evaluated as x^2 / (sqrt(mu^2 + x^2) + mu) and the line
     search through per-coordinate differences, the same quantities without cancellation.
-  - mu-continuation: the smoothed minimiser carries an O(mu) bias in the l1 certificate
-    (about 0.2 tau mu per zero of x*), so when a full Newton step (alpha = 1) fails to halve
-    the gap, mu <- max(mu / 10, mu_min).
+  - PCG's relative residual is measured in the norm of the preconditioner,
+    sqrt(res^T M^{-1} res) <= 0.1 sqrt(grad^T M^{-1} grad).  In the 2-norm the residual is
+    dominated by the coordinates at zero (curvature ~ tau/mu) that the diagonal
+    preconditioner resolves in one step, so PCG stopped before solving the support block.
+  - mu-continuation: mu starts at mu_start (1, the scale of x*) and is divided by 10 after
+    every full Newton step (alpha = 1) until it reaches the paper's mu; the smoothed minimiser
+    then still carries an O(mu) bias in the l1 certificate (about 0.2 tau mu per zero of
+    x*), so below mu a full step that fails to halve the gap divides mu by 10 again, down
+    to mu_min.  With mu fixed at 1e-5 from x = 0 the iteration stalls on instances with
+    n >= 2^16 (measured), because coordinates leave zero only by grad / (tau / mu) per step.
 """
 
 import math
@@ -121,7 +128,7 @@ def psi_diff_terms(x, d, alpha, mu):
 
 
 def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, pcg_max=1000,
-          ls_max=50, armijo=1e-4, stall=0.5, x0=None):
+          ls_max=50, armijo=1e-4, stall=0.5, x0=None, mu_start=1.0):
     """Primal-dual Newton-CG with the certificate above.
 
     Returns dict(x, iters, products, cg_iters, ls_trials, P, D, gap, rel_gap, mu, status).
@@ -129,7 +136,7 @@ def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, 
     m, n = A.shape
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     gd = np.zeros(n)                                                # dual estimate g
-    mu = mu0
+    mu = max(mu_start, mu0)
     colnorm2 = np.asarray(A.multiply(A).sum(axis=0)).ravel()       # diag(A^T A)
     products = 0
     cg_total = 0
@@ -150,20 +157,22 @@ def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, 
             return dict(x=x, iters=it, products=products, cg_iters=cg_total, ls_trials=ls_total,
                         P=P, D=D, gap=gap, rel_gap=rel, mu=mu,
                         status=STATUS_OK if rel <= tol else STATUS_NOCONV)
-        if prev_full and gap > stall * prev_gap:
+        if prev_full and mu > mu0:
+            mu = max(mu * 0.1, mu0)
+        elif prev_full and gap > stall * prev_gap:
             mu = max(mu * 0.1, mu_min)
         prev_gap = gap
         w = np.sqrt(mu * mu + x * x)
         grad = tau * x / w - atr                                    # grad f^mu
         hdiag = tau * (1.0 - gd * x / w) / w                        # primal-dual psi curvature
         minv = 1.0 / (hdiag + colnorm2)
-        gnorm = math.sqrt(float(grad @ grad))
         # PCG on (diag(hdiag) + A^T A) d = -grad from d = 0.
         d = np.zeros(n)
         res = -grad
         z = minv * res
         p = z.copy()
         rz = float(res @ z)
+        rz0 = rz
         for _ in range(pcg_max):
             Ap = A @ p
             Hp = hdiag * p + A.T @ Ap
@@ -175,10 +184,10 @@ def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, 
             alpha = rz / pHp
             d += alpha * p
             res -= alpha * Hp
-            if math.sqrt(float(res @ res)) <= pcg_rtol * gnorm:
-                break
             z = minv * res
             rz_new = float(res @ z)
+            if math.sqrt(rz_new) <= pcg_rtol * math.sqrt(rz0):
+                break
             p = z + (rz_new / rz) * p
             rz = rz_new
         # Backtracking Armijo line search on f^mu.

@@ -13,8 +13,6 @@ import os
 
 import numpy as np
 
-from . import _build
-
 __all__ = ["Context", "Instance", "L1LSError", "lib", "library_path", "F64", "F32", "BF16"]
 
 F64, F32, BF16 = 0, 1, 2
@@ -42,7 +40,7 @@ class InstInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("rel_gap_tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("time_limit_s", ctypes.c_double), ("mu", ctypes.c_double), ("mu_min", ctypes.c_double),
-                ("pcg_rtol", ctypes.c_double), ("armijo", ctypes.c_double), ("ls_max", ctypes.c_int32),
+                ("mu_start", ctypes.c_double), ("pcg_rtol", ctypes.c_double), ("armijo", ctypes.c_double), ("ls_max", ctypes.c_int32),
                 ("pcg_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
@@ -64,11 +62,11 @@ class L1LSError(RuntimeError):
         self.status = status
 
 
-library_path = _build.LIB_PATH
+library_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libl1ls.so")
 
 if not os.path.exists(library_path):
     raise ImportError("libl1ls.so is not built (%s); run __graft_entry__.build() or "
-                      "python -m paper_1503_03520_gb300._build" % library_path)
+                      "python paper_1503_03520_gb300/_build.py" % library_path)
 
 lib = ctypes.CDLL(library_path)
 
@@ -85,6 +83,9 @@ _sig = {
     "l1ls_rmatvec": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "l1ls_solve_fista": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Result), _P]),
     "l1ls_solve_pdncg": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Result), _P]),
+    "l1ls_fista_begin": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P]),
+    "l1ls_fista_step": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
+    "l1ls_fista_end": (ctypes.c_int, [_P, _P, ctypes.POINTER(Result), _P]),
     "l1ls_gen_params_default": (None, [ctypes.POINTER(GenParams)]),
     "l1ls_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "l1ls_last_error": (ctypes.c_char_p, []),
@@ -264,6 +265,23 @@ class Instance:
     def solve_fista(self, x0=None, x_out=None, stream=None, allow=(4, 5), **opts):
         """FISTA to the duality-gap tolerance; returns (x, result dict)."""
         return self._solve(lib.l1ls_solve_fista, x0, x_out, stream, opts, allow)
+
+    def fista_begin(self, x0=None, stream=None, **opts):
+        o = solve_opts(**opts)
+        p0 = _vec_ptr(x0)[0] if x0 is not None else None
+        _check(lib.l1ls_fista_begin(self._h, ctypes.byref(o), p0, _stream_ptr(stream)))
+
+    def fista_step(self, iters=1, timed=False, stream=None):
+        """Enqueue iterations; with timed=True returns the summed K1 / K2 times in ms."""
+        ms = (ctypes.c_float * 2)()
+        _check(lib.l1ls_fista_step(self._h, int(iters), ms if timed else None, _stream_ptr(stream)))
+        return (ms[0], ms[1]) if timed else None
+
+    def fista_end(self, x_out=None, stream=None, allow=(4, 5)):
+        res = Result()
+        pout = _vec_ptr(x_out)[0] if x_out is not None else None
+        _check(lib.l1ls_fista_end(self._h, pout, ctypes.byref(res), _stream_ptr(stream)), allow=allow)
+        return x_out, res.as_dict()
 
     def solve_pdncg(self, x0=None, x_out=None, stream=None, allow=(4, 5), **opts):
         """Primal-dual Newton-CG to the duality-gap tolerance; returns (x, result dict)."""

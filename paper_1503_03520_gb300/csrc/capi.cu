@@ -132,6 +132,7 @@ void l1ls_solve_opts_default(l1ls_solve_opts* o) {
     o->time_limit_s = 0.0;
     o->mu = 1e-5;
     o->mu_min = 1e-14;
+    o->mu_start = 1.0;
     o->pcg_rtol = 0.1;
     o->armijo = 1e-4;
     o->ls_max = 50;

@@ -209,17 +209,22 @@ struct FistaWork {
     int grid1 = 0, grid2 = 0;
     cudaGraphExec_t exec = nullptr;
     int exec_chunk = 0;
-    cudaStream_t exec_stream = nullptr;
+    int64_t enqueued = 0;           // iterations enqueued since begin (parity of the next one)
+    bool active = false;
+    cudaEvent_t ev[2][3] = {};
     ~FistaWork() {
         if (exec) cudaGraphExecDestroy(exec);
         if (host_st) cudaFreeHost(host_st);
+        for (auto& row : ev)
+            for (auto& e : row)
+                if (e) cudaEventDestroy(e);
     }
 };
 
 template <class V, class Vec>
-l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
+l1ls_status enqueue_k1(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     // parity 0: iteration k odd (x_{k-1} in X[0]); parity 1: k even (x_{k-1} in X[1])
-    const int c = parity, o = 1 - parity;
+    const int c = parity;
     K1Args<V, Vec> a1;
     a1.ptr = I->csr_ptr;
     a1.col = I->csr_col;
@@ -234,6 +239,12 @@ l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st
     a1.st = w->st;
     a1.m = I->m;
     k_fista_k1<V, Vec><<<w->grid1, kBlock, 0, st>>>(a1);
+    return L1LS_OK;
+}
+
+template <class V, class Vec>
+l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
+    const int c = parity, o = 1 - parity;
     K2Args<V, Vec> a2;
     a2.ptr = I->csc_ptr;
     a2.col = I->csc_row;
@@ -250,9 +261,13 @@ l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st
 }
 
 template <class V, class Vec>
-l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
-                cudaStream_t st) {
-    auto t0 = std::chrono::steady_clock::now();
+l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
+    L1LS_TRY(enqueue_k1<V, Vec>(I, w, parity, st));
+    return enqueue_k2<V, Vec>(I, w, parity, st);
+}
+
+template <class V, class Vec>
+l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStream_t st) {
     const int64_t m = I->m, n = I->n;
     FistaWork* w = static_cast<FistaWork*>(I->fista_work);
     if (!w) {
@@ -273,8 +288,12 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 2 + 1024));
         L1LS_TRY(I->alloc_n(&w->st, 1));
         L1LS_CUDA(cudaMallocHost((void**)&w->host_st, sizeof(FistaState)));
+        for (int k = 0; k < 2; ++k) {
+            L1LS_CUDA(cudaEventCreate(&w->ev[k][0]));
+            L1LS_CUDA(cudaEventCreate(&w->ev[k][1]));
+            L1LS_CUDA(cudaEventCreate(&w->ev[k][2]));
+        }
     }
-    // initial point
     FistaState h{};
     h.tau = o->tau;
     h.L = I->lipschitz;
@@ -302,6 +321,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         const void* xsrc = sizeof(Vec) == 8 ? (const void*)w->X[0] : (const void*)w->X32[0];
         L1LS_TRY(spmv_plain(I, false, xsrc, sizeof(Vec) == 8 ? L1LS_F64 : L1LS_F32, w->ax, false, st));
         h.products = 1;
+        L1LS_CUDA(cudaStreamSynchronize(st));
+        L1LS_CUDA(cudaMemcpy(&h.l1_cur, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost));
     } else {
         L1LS_CUDA(cudaMemsetAsync(w->X[0], 0, sizeof(double) * n, st));
         L1LS_CUDA(cudaMemsetAsync(w->X[1], 0, sizeof(double) * n, st));
@@ -313,66 +334,72 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         h.products = 0;
         h.l1_cur = 0.0;
     }
-    // upload the scalar state without clobbering l1_cur when it was computed on the device
-    if (x0) {
-        L1LS_CUDA(cudaStreamSynchronize(st));
-        double l1 = 0.0;
-        L1LS_CUDA(cudaMemcpy(&l1, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost));
-        h.l1_cur = l1;
-    }
     h.cnt1 = h.cnt2 = 0;
     *w->host_st = h;
     L1LS_CUDA(cudaMemcpyAsync(w->st, w->host_st, sizeof(FistaState), cudaMemcpyHostToDevice, st));
+    w->enqueued = 0;
+    w->active = true;
+    return L1LS_OK;
+}
 
-    int chunk = o->check_every > 0 ? o->check_every : 32;
-    if (chunk & 1) ++chunk;
-    if (!w->exec || w->exec_chunk != chunk) {
-        if (w->exec) {
-            cudaGraphExecDestroy(w->exec);
-            w->exec = nullptr;
-        }
-        cudaStream_t cap;
-        L1LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        cudaGraph_t graph;
-        L1LS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < chunk; ++i) enqueue_iteration<V, Vec>(I, w, i & 1, cap);
-        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-        if (ce != cudaSuccess) {
-            cudaStreamDestroy(cap);
-            return cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
-        }
-        L1LS_CUDA(cudaGraphInstantiate(&w->exec, graph, 0));
-        cudaGraphDestroy(graph);
-        cudaStreamDestroy(cap);
-        w->exec_chunk = chunk;
-    }
-    l1ls_status final_status = L1LS_OK;
-    // the device stops by itself at max_iter; the host cap only guards against a stuck flag
-    const int64_t max_launches = o->max_iter / chunk + 3;
-    for (int64_t launch = 0;; ++launch) {
-        if (launch >= max_launches) {
-            final_status = L1LS_ECUDA;
-            set_error(L1LS_ECUDA, "internal: FISTA did not raise its stop flag");
-            break;
-        }
-        L1LS_CUDA(cudaGraphLaunch(w->exec, st));
-        L1LS_CUDA(cudaMemcpyAsync(w->host_st, w->st, sizeof(FistaState), cudaMemcpyDeviceToHost, st));
-        L1LS_CUDA(cudaStreamSynchronize(st));
-        if (w->host_st->stop) {
-            final_status = (l1ls_status)w->host_st->status;
-            break;
-        }
-        if (o->time_limit_s > 0) {
-            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            if (el > o->time_limit_s) {
-                final_status = L1LS_ETIMEOUT;
-                break;
+// Enqueue `iters` iterations one by one (parity tracked on the host).  With kernel_ms, CUDA
+// events bracket K1 and K2 of every iteration and their summed durations are returned
+// (the stream is synchronised for that).
+template <class V, class Vec>
+l1ls_status step(Inst* I, int64_t iters, float* kernel_ms, cudaStream_t st) {
+    FistaWork* w = static_cast<FistaWork*>(I->fista_work);
+    if (!w || !w->active) return set_error(L1LS_EINVAL, "l1ls_fista_step without l1ls_fista_begin");
+    float acc[2] = {0.f, 0.f};
+    for (int64_t i = 0; i < iters; ++i) {
+        const int parity = (int)(w->enqueued & 1);
+        if (kernel_ms) {
+            cudaEvent_t* e = w->ev[i & 1];
+            if (i >= 2) {   // collect the timings of the iteration that used these events
+                L1LS_CUDA(cudaEventSynchronize(e[2]));
+                float a = 0.f, b = 0.f;
+                L1LS_CUDA(cudaEventElapsedTime(&a, e[0], e[1]));
+                L1LS_CUDA(cudaEventElapsedTime(&b, e[1], e[2]));
+                acc[0] += a;
+                acc[1] += b;
             }
+            L1LS_CUDA(cudaEventRecord(e[0], st));
+            L1LS_TRY(enqueue_k1<V, Vec>(I, w, parity, st));
+            L1LS_CUDA(cudaEventRecord(e[1], st));
+            L1LS_TRY(enqueue_k2<V, Vec>(I, w, parity, st));
+            L1LS_CUDA(cudaEventRecord(e[2], st));
+        } else {
+            L1LS_TRY(enqueue_iteration<V, Vec>(I, w, parity, st));
         }
+        ++w->enqueued;
     }
-    const FistaState& f = *w->host_st;
-    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X[f.cert_iter & 1], sizeof(double) * n, cudaMemcpyDefault, st));
+    L1LS_CUDA(cudaGetLastError());
+    if (kernel_ms) {
+        for (int64_t i = std::max<int64_t>(0, iters - 2); i < iters; ++i) {
+            cudaEvent_t* e = w->ev[i & 1];
+            L1LS_CUDA(cudaEventSynchronize(e[2]));
+            float a = 0.f, b = 0.f;
+            L1LS_CUDA(cudaEventElapsedTime(&a, e[0], e[1]));
+            L1LS_CUDA(cudaEventElapsedTime(&b, e[1], e[2]));
+            acc[0] += a;
+            acc[1] += b;
+        }
+        kernel_ms[0] = acc[0];
+        kernel_ms[1] = acc[1];
+    }
+    return L1LS_OK;
+}
+
+l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_status, double seconds,
+                cudaStream_t st) {
+    FistaWork* w = static_cast<FistaWork*>(I->fista_work);
+    if (!w || !w->active) return set_error(L1LS_EINVAL, "l1ls_fista_end without l1ls_fista_begin");
+    L1LS_CUDA(cudaMemcpyAsync(w->host_st, w->st, sizeof(FistaState), cudaMemcpyDeviceToHost, st));
     L1LS_CUDA(cudaStreamSynchronize(st));
+    const FistaState& f = *w->host_st;
+    if (final_status == L1LS_OK) final_status = f.stop ? (l1ls_status)f.status : L1LS_ENOCONV;
+    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X[f.cert_iter & 1], sizeof(double) * I->n, cudaMemcpyDefault, st));
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    w->active = false;
     if (res) {
         memset(res, 0, sizeof(*res));
         res->iters = f.cert_iter;
@@ -382,15 +409,74 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         res->gap = f.gap;
         res->rel_gap = f.rel;
         res->status = final_status;
-        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        res->seconds = seconds;
     }
     if (final_status != L1LS_OK) {
         const char* why = final_status == L1LS_ENOCONV ? "iteration limit reached"
                           : final_status == L1LS_ETIMEOUT ? "time limit reached"
-                                                          : "NaN or Inf in the iteration";
+                          : final_status == L1LS_ENUMERIC ? "NaN or Inf in the iteration"
+                                                          : "internal error";
         return set_error(final_status, "FISTA: %s (rel_gap %.3e)", why, f.rel);
     }
     return L1LS_OK;
+}
+
+template <class V, class Vec>
+l1ls_status graph_for(Inst* I, FistaWork* w, int chunk) {
+    if (w->exec && w->exec_chunk == chunk) return L1LS_OK;
+    if (w->exec) {
+        cudaGraphExecDestroy(w->exec);
+        w->exec = nullptr;
+    }
+    cudaStream_t cap;
+    L1LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    L1LS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) enqueue_iteration<V, Vec>(I, w, i & 1, cap);
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+    }
+    L1LS_CUDA(cudaGraphInstantiate(&w->exec, graph, 0));
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    w->exec_chunk = chunk;
+    return L1LS_OK;
+}
+
+template <class V, class Vec>
+l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    L1LS_TRY(begin<V, Vec>(I, o, x0, st));
+    FistaWork* w = static_cast<FistaWork*>(I->fista_work);
+    int chunk = o->check_every > 0 ? o->check_every : 32;
+    if (chunk & 1) ++chunk;
+    L1LS_TRY(graph_for<V, Vec>(I, w, chunk));
+    l1ls_status final_status = L1LS_OK;
+    // the device stops by itself at max_iter; the host cap only guards against a stuck flag
+    const int64_t max_launches = o->max_iter / chunk + 3;
+    for (int64_t launch = 0;; ++launch) {
+        if (launch >= max_launches) {
+            final_status = L1LS_ECUDA;
+            break;
+        }
+        L1LS_CUDA(cudaGraphLaunch(w->exec, st));
+        w->enqueued += chunk;
+        L1LS_CUDA(cudaMemcpyAsync(w->host_st, w->st, sizeof(FistaState), cudaMemcpyDeviceToHost, st));
+        L1LS_CUDA(cudaStreamSynchronize(st));
+        if (w->host_st->stop) break;
+        if (o->time_limit_s > 0) {
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > o->time_limit_s) {
+                final_status = L1LS_ETIMEOUT;
+                break;
+            }
+        }
+    }
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return end(I, x_out, res, final_status, secs, st);
 }
 
 }  // namespace
@@ -408,12 +494,50 @@ l1ls_status fista_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, dou
 
 using namespace l1ls;
 
-extern "C" l1ls_status l1ls_solve_fista(l1ls_inst* h, const l1ls_solve_opts* o, const double* x0, double* x_out,
-                                        l1ls_result* res, void* stream) {
-    if (!h || !o) return set_error(L1LS_EINVAL, "NULL argument");
+static l1ls_status check_opts(const l1ls_solve_opts* o) {
+    if (!o) return set_error(L1LS_EINVAL, "NULL options");
     if (!(o->tau > 0.0) || !(o->rel_gap_tol >= 0.0) || o->max_iter < 0)
         return set_error(L1LS_EINVAL, "bad solver options");
+    return L1LS_OK;
+}
+
+extern "C" l1ls_status l1ls_solve_fista(l1ls_inst* h, const l1ls_solve_opts* o, const double* x0, double* x_out,
+                                        l1ls_result* res, void* stream) {
+    if (!h) return set_error(L1LS_EINVAL, "NULL argument");
+    L1LS_TRY(check_opts(o));
     Inst* I = reinterpret_cast<Inst*>(h);
     L1LS_CUDA(cudaSetDevice(I->ctx->device));
     return fista_solve(I, o, x0, x_out, res, (cudaStream_t)stream);
+}
+
+extern "C" l1ls_status l1ls_fista_begin(l1ls_inst* h, const l1ls_solve_opts* o, const double* x0, void* stream) {
+    if (!h) return set_error(L1LS_EINVAL, "NULL argument");
+    L1LS_TRY(check_opts(o));
+    Inst* I = reinterpret_cast<Inst*>(h);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (I->dtype) {
+        case L1LS_F64: return begin<double, double>(I, o, x0, st);
+        case L1LS_F32: return begin<float, float>(I, o, x0, st);
+        default: return begin<__nv_bfloat16, float>(I, o, x0, st);
+    }
+}
+
+extern "C" l1ls_status l1ls_fista_step(l1ls_inst* h, int64_t iters, float* kernel_ms, void* stream) {
+    if (!h || iters < 0) return set_error(L1LS_EINVAL, "bad argument");
+    Inst* I = reinterpret_cast<Inst*>(h);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (I->dtype) {
+        case L1LS_F64: return step<double, double>(I, iters, kernel_ms, st);
+        case L1LS_F32: return step<float, float>(I, iters, kernel_ms, st);
+        default: return step<__nv_bfloat16, float>(I, iters, kernel_ms, st);
+    }
+}
+
+extern "C" l1ls_status l1ls_fista_end(l1ls_inst* h, double* x_out, l1ls_result* res, void* stream) {
+    if (!h) return set_error(L1LS_EINVAL, "NULL argument");
+    Inst* I = reinterpret_cast<Inst*>(h);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    return end(I, x_out, res, L1LS_OK, 0.0, (cudaStream_t)stream);
 }

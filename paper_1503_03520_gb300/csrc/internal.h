@@ -18,15 +18,15 @@ namespace l1ls {
 l1ls_status set_error(l1ls_status st, const char* fmt, ...);
 l1ls_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
-#define L1LS_CUDA(call)                                                          \
+#define L1LS_CUDA(...)                                                           \
     do {                                                                         \
-        cudaError_t e_ = (call);                                                 \
-        if (e_ != cudaSuccess) return ::l1ls::cuda_error(e_, #call, __FILE__, __LINE__); \
+        cudaError_t e_ = (__VA_ARGS__);                                          \
+        if (e_ != cudaSuccess) return ::l1ls::cuda_error(e_, #__VA_ARGS__, __FILE__, __LINE__); \
     } while (0)
 
-#define L1LS_TRY(call)                                                           \
+#define L1LS_TRY(...)                                                            \
     do {                                                                         \
-        l1ls_status s_ = (call);                                                 \
+        l1ls_status s_ = (__VA_ARGS__);                                          \
         if (s_ != L1LS_OK) return s_;                                            \
     } while (0)
 

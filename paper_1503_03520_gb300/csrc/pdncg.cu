@@ -4,11 +4,12 @@
 // Newton step (one host round trip per phase; all arithmetic in the kernels):
 //   N1  r = b - A x                               (partials ||r||^2, b.r)
 //   N2  a = A^T r                                 (partials max|a|, ||x||_1); last CTA: gap
-//       certificate at x, stop test, mu-continuation (mu /= 10 when a full Newton step
-//       failed to halve the gap)
+//       certificate at x, stop test, mu-continuation (mu /= 10 after a full Newton step
+//       until the paper's mu; below it when a full step failed to halve the gap)
 //   N3  w = sqrt(mu^2 + x^2), grad = tau x / w - a, h = tau (1 - g x / w) / w (primal-dual
 //       curvature with the dual estimate g), M^{-1} = 1 / (h + diag(A^T A)), PCG start
-//   PCG iteration (stopped at ||res|| <= pcg_rtol ||grad|| or pcg_max):
+//   PCG iteration (stopped when the residual in the preconditioner's norm falls to
+//   pcg_rtol of its start, or at pcg_max):
 //   C1  Ap = A p          C2  Hp = h p + A^T Ap, alpha = rz / p.Hp
 //   C3  d += alpha p, res -= alpha Hp, beta    C4  p = M^{-1} res + beta p
 //   L1  Ad = A d (r.Ad, ||Ad||^2);  LT  Armijo trials, four halvings per pass, per-coordinate
@@ -30,12 +31,12 @@ constexpr int kBlock = 256;
 constexpr int kTrialsPerPass = 4;
 
 struct PdState {
-    double tau, tol, mu, mu_min, pcg_rtol, armijo, stall;
+    double tau, tol, mu, mu_target, mu_min, pcg_rtol, armijo, stall;
     int64_t max_newton, pcg_max, ls_max;
     double P, D, gap, rel, prev_gap;
     int32_t prev_full, pad0;
     double k1[2];
-    double gnorm2, rz, alpha, beta;
+    double gnorm2, rz, rz0, alpha, beta;
     int32_t cg_done, pad1;
     int64_t cg_it;
     double rAd, AdAd, step;
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
             st->status = L1LS_ENOCONV;
             st->stop = 1;
         } else {
-            if (st->prev_full && gap > st->stall * st->prev_gap) st->mu = fmax(st->mu * 0.1, st->mu_min);
+            if (st->prev_full && st->mu > st->mu_target) st->mu = fmax(st->mu * 0.1, st->mu_target);
+            else if (st->prev_full && gap > st->stall * st->prev_gap) st->mu = fmax(st->mu * 0.1, st->mu_min);
             st->prev_gap = gap;
         }
     }
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x
     if (grid_reduce_last<kBlock, 2>(q, 0u, partials, &st->cnt[2], tot, red) && threadIdx.x == 0) {
         st->gnorm2 = tot[0];
         st->rz = tot[1];
+        st->rz0 = tot[1];
         st->cg_done = 0;
         st->cg_it = 0;
     }
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(kBlock) k_pd_cgupd(double* __restrict__ d, dou
     double tot[2];
     if (grid_reduce_last<kBlock, 2>(q, 0u, partials, &st->cnt[5], tot, red) && threadIdx.x == 0) {
         st->cg_it += 1;
-        if (sqrt(tot[0]) <= st->pcg_rtol * sqrt(st->gnorm2) || st->cg_it >= st->pcg_max) {
+        // relative residual in the preconditioner's norm: sqrt(res.M^-1 res) vs sqrt(grad.M^-1 grad)
+        if (sqrt(tot[1]) <= st->pcg_rtol * sqrt(st->rz0) || st->cg_it >= st->pcg_max) {
             st->cg_done = 1;
         } else {
             st->beta = tot[1] / st->rz;
@@ -430,7 +434,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     memset(&h, 0, sizeof(h));
     h.tau = o->tau;
     h.tol = o->rel_gap_tol;
-    h.mu = o->mu;
+    h.mu = o->mu_start > o->mu ? o->mu_start : o->mu;
+    h.mu_target = o->mu;
     h.mu_min = o->mu_min;
     h.pcg_rtol = o->pcg_rtol;
     h.armijo = o->armijo;

@@ -12,11 +12,14 @@ def oracle_instance(params):
 
 
 def round_bf16(a):
-    """Round FP64 values to bfloat16 (round to nearest even) through FP32, as doubles."""
-    f = np.asarray(a, dtype=np.float64).astype(np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    """Round FP64 values directly to bfloat16 (8 significant bits, round half to even)."""
+    v = np.asarray(a, dtype=np.float64)
+    out = np.zeros_like(v)
+    nz = v != 0
+    e = np.floor(np.log2(np.abs(v[nz])))
+    q = np.exp2(e - 7)                  # spacing of bf16 numbers in the binade of v
+    out[nz] = np.round(v[nz] / q) * q   # exact scaling; np.round rounds half to even
+    return out
 
 
 def stored_values(A, dtype):

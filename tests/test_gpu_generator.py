@@ -62,7 +62,9 @@ def test_generator_matches_oracle(ctx, case):
         assert np.abs(ex["b"] - ref.b).max() <= 50 * params["kappa"] * 2.2e-16 * scale
         info = inst.info
         assert info["f_star"] == pytest.approx(ref.f_star, rel=1e-12)
-        assert info["lam_max"] == pytest.approx(ref.lam_max, rel=1e-10)
+        # the oracle reaches A^T b through e = tau A G Sigma^-2 G^T g, whose rounding grows like
+        # kappa^2 eps; the device evaluates R Sigma^2 R^T x* + tau g directly
+        assert info["lam_max"] == pytest.approx(ref.lam_max, rel=max(1e-10, 10 * params["kappa"] ** 2 * 2.2e-16))
         # transposed storage: the same matrix
         et = inst.export_t()
         At = ref.A.tocsc()
