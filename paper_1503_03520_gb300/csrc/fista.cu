@@ -65,36 +65,38 @@ struct K2Args {
     int64_t n;
 };
 
-template <class V> constexpr int cap_of() { return sizeof(V) == 8 ? 2048 : 4096; }
-
 template <class V, class Vec>
 __global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
     using Acc = Vec;
-    constexpr int CAP = cap_of<V>();
-    __shared__ CsrSmem<kBlock, CAP, Acc> sm;
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     const Vec beta = (Vec)a.st->beta;
     double p[3] = {0.0, 0.0, 0.0};
-    const int64_t ntiles = (a.m + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, a.m - r0);
-        const Acc u = csr_tile<kBlock, CAP, V, Vec, Acc>(a.ptr, a.col, a.val, a.x, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t r = r0 + threadIdx.x;
-            const Vec axo = a.ax[r];
-            const Vec bb = a.b[r];
-            const Vec ay = u + beta * (u - axo);
-            const Vec rr = bb - ay;
+    struct Ops {
+        Vec axo, bb;
+    };
+    warp_csr<V, Vec, Acc>(
+        a.ptr, a.col, a.val, a.x, a.m, wbuf,
+        [&](int64_t r, bool has) {
+            Ops o{Vec(0), Vec(0)};
+            if (has) {
+                o.axo = a.ax[r];
+                o.bb = a.b[r];
+            }
+            return o;
+        },
+        [&](int64_t r, Acc u, const Ops& o) {
+            const Vec ay = u + beta * (u - o.axo);
+            const Vec rr = o.bb - ay;
             a.ax[r] = u;
             a.res[r] = rr;
-            const double du = (double)u - (double)bb;
+            const double du = (double)u - (double)o.bb;
             p[0] += du * du;
-            p[1] += (double)bb * (double)rr;
+            p[1] += (double)o.bb * (double)rr;
             p[2] += (double)rr * (double)rr;
-        }
-    }
+        });
     block_reduce<kBlock, 3>(p, 0u, red);
     double tot[3];
     if (grid_reduce_last<kBlock, 3>(p, 0u, a.partials, &a.st->cnt1, tot, red) && threadIdx.x == 0) {
@@ -140,30 +142,35 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new) {
 template <class V, class Vec>
 __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
-    constexpr int CAP = cap_of<V>();
-    __shared__ CsrSmem<kBlock, CAP, Acc> sm;
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
     __shared__ double red[2 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const double invL = 1.0 / L, thr = tau / L;
     double p[2] = {0.0, 0.0};
-    const int64_t ntiles = (a.n + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, a.n - r0);
-        const Acc gacc = csr_tile<kBlock, CAP, V, Vec, Acc>(a.ptr, a.col, a.val, a.res, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t j = r0 + threadIdx.x;
+    struct Ops {
+        double x1, x0;
+    };
+    warp_csr<V, Vec, Acc>(
+        a.ptr, a.col, a.val, a.res, a.n, wbuf,
+        [&](int64_t j, bool has) {
+            Ops o{0.0, 0.0};
+            if (has) {
+                o.x1 = a.xc[j];
+                o.x0 = a.xo[j];
+            }
+            return o;
+        },
+        [&](int64_t j, Acc gacc, const Ops& o) {
             const double g = (double)gacc;
-            const double x1 = a.xc[j], x0 = a.xo[j];
-            const double y = x1 + beta * (x1 - x0);
+            const double y = o.x1 + beta * (o.x1 - o.x0);
             const double xn = soft_threshold(y + g * invL, thr);
             a.xo[j] = xn;
             if (a.xo32) a.xo32[j] = __double2float_rn(xn);
             p[0] = fmax(p[0], fabs(g));
             p[1] += fabs(xn);
-        }
-    }
+        });
     block_reduce<kBlock, 2>(p, 1u, red);
     double tot[2];
     if (grid_reduce_last<kBlock, 2>(p, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
@@ -191,7 +198,7 @@ int grid_of(const Inst* I, K kernel, int64_t rows) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
     if (per_sm < 1) per_sm = 1;
-    const int64_t ntiles = (rows + kBlock - 1) / kBlock;
+    const int64_t ntiles = (rows + 31) / 32 / (kBlock / 32) + 1;   // blocks with one warp tile per warp
     const int64_t g = (int64_t)I->ctx->num_sms * per_sm;
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, g));
 }
@@ -274,14 +281,14 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         w = new FistaWork();
         I->fista_work = w;
         I->fista_work_free = [](void* p) { delete static_cast<FistaWork*>(p); };
-        L1LS_TRY(I->alloc_n(&w->X[0], n));
-        L1LS_TRY(I->alloc_n(&w->X[1], n));
+        L1LS_TRY(I->alloc_n(&w->X[0], pad32(n)));
+        L1LS_TRY(I->alloc_n(&w->X[1], pad32(n)));
         if (sizeof(Vec) == 4) {
-            L1LS_TRY(I->alloc_n(&w->X32[0], n));
-            L1LS_TRY(I->alloc_n(&w->X32[1], n));
+            L1LS_TRY(I->alloc_n(&w->X32[0], pad32(n)));
+            L1LS_TRY(I->alloc_n(&w->X32[1], pad32(n)));
         }
-        L1LS_TRY(I->alloc(&w->ax, sizeof(Vec) * m));
-        L1LS_TRY(I->alloc(&w->res, sizeof(Vec) * m));
+        L1LS_TRY(I->alloc(&w->ax, sizeof(Vec) * pad32(m)));
+        L1LS_TRY(I->alloc(&w->res, sizeof(Vec) * pad32(m)));
         w->grid1 = grid_of(I, k_fista_k1<V, Vec>, m);
         w->grid2 = grid_of(I, k_fista_k2<V, Vec>, n);
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));

@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "spmv.cuh"
 
 namespace l1ls {
 
@@ -333,6 +334,14 @@ __global__ void k_csr_fill(Geo g, const int32_t* __restrict__ perm, const int32_
     }
 }
 
+// most nonzeros in a tile of 32 rows
+__global__ void k_tile_max(const int32_t* __restrict__ ptr, int64_t nrows, int* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t * 32 >= nrows) return;
+    const int64_t r1 = min(t * 32 + 32, nrows);
+    atomicMax(out, ptr[r1] - ptr[t * 32]);
+}
+
 template <class V>
 __global__ void k_cast(const double* __restrict__ in, int64_t count, V* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -389,8 +398,10 @@ template <class V>
 l1ls_status cast_and_norms(Inst* I, const double* csc64, const double* csr64, cudaStream_t st) {
     V* cv = nullptr;
     V* rv = nullptr;
-    L1LS_TRY(I->alloc_n(&cv, I->nnz));
-    L1LS_TRY(I->alloc_n(&rv, I->nnz));
+    L1LS_TRY(I->alloc_n(&cv, I->nnz + kPad));
+    L1LS_TRY(I->alloc_n(&rv, I->nnz + kPad));
+    L1LS_CUDA(cudaMemsetAsync(cv + I->nnz, 0, sizeof(V) * kPad, st));
+    L1LS_CUDA(cudaMemsetAsync(rv + I->nnz, 0, sizeof(V) * kPad, st));
     k_cast<V><<<nblk(I->nnz), 256, 0, st>>>(csc64, I->nnz, cv);
     k_cast<V><<<nblk(I->nnz), 256, 0, st>>>(csr64, I->nnz, rv);
     k_colnorm2<V><<<nblk(I->n), 256, 0, st>>>(I->csc_ptr, cv, I->n, I->colnorm2);
@@ -459,11 +470,17 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         // persistent vectors
         GEN_TRY(I->alloc_n(&I->sigma, n));
         GEN_TRY(I->alloc_n(&I->xstar, n));
-        GEN_TRY(I->alloc_n(&I->bhat, m));
+        GEN_TRY(I->alloc_n(&I->bhat, pad32(m)));
+        GEN_CUDA(cudaMemsetAsync(I->bhat, 0, sizeof(double) * pad32(m), st));
         GEN_TRY(I->alloc_n(&I->perm, m));
         GEN_TRY(I->alloc_n(&I->perm_inv, m));
         GEN_TRY(I->alloc_n(&I->colnorm2, n));
-        if (I->dtype != L1LS_F64) GEN_TRY(I->alloc_n(&I->bhat32, m));
+        if (I->dtype != L1LS_F64) {
+            GEN_TRY(I->alloc_n(&I->bhat32, pad32(m)));
+            GEN_CUDA(cudaMemsetAsync(I->bhat32, 0, sizeof(float) * pad32(m), st));
+        }
+        GEN_TRY(I->alloc_n(&I->dev_err, 1));
+        GEN_CUDA(cudaMemsetAsync(I->dev_err, 0, sizeof(int), st));
 
         // singular values: sigma_i = kappa^(-rank_i/(n-1))
         uint32_t* order_n = nullptr;
@@ -534,7 +551,8 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_TRY(exclusive_scan_i32(cnt, n, I->csc_ptr, &nnz, st));
         I->nnz = nnz;
         double *csc64 = nullptr, *csr64 = nullptr;
-        GEN_TRY(I->alloc_n(&I->csc_row, nnz));
+        GEN_TRY(I->alloc_n(&I->csc_row, nnz + kPad));
+        GEN_CUDA(cudaMemsetAsync(I->csc_row + nnz, 0, sizeof(int32_t) * kPad, st));
         GEN_TRY(tmp.get(&csc64, nnz));
         k_csc_fill<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, I->sigma, I->csc_ptr, I->csc_row, csc64);
         GEN_CUDA(cudaGetLastError());
@@ -550,7 +568,8 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         int* err = nullptr;
         GEN_TRY(tmp.get(&err, 1));
         GEN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-        GEN_TRY(I->alloc_n(&I->csr_col, nnz));
+        GEN_TRY(I->alloc_n(&I->csr_col, nnz + kPad));
+        GEN_CUDA(cudaMemsetAsync(I->csr_col + nnz, 0, sizeof(int32_t) * kPad, st));
         GEN_TRY(tmp.get(&csr64, nnz));
         k_csr_fill<<<nblk(m), 256, 0, st>>>(g, I->perm, I->csc_ptr, I->csc_row, csc64, I->csr_ptr, I->csr_col, csr64,
                                              err);
@@ -562,10 +581,20 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         }
         if (I->bhat32) k_to_f32<<<nblk(m), 256, 0, st>>>(I->bhat, m, I->bhat32);
         GEN_CUDA(cudaGetLastError());
+        int* tmax = nullptr;
+        GEN_TRY(tmp.get(&tmax, 2));
+        GEN_CUDA(cudaMemsetAsync(tmax, 0, 2 * sizeof(int), st));
+        k_tile_max<<<nblk((m + 31) / 32), 256, 0, st>>>(I->csr_ptr, m, tmax);
+        k_tile_max<<<nblk((n + 31) / 32), 256, 0, st>>>(I->csc_ptr, n, tmax + 1);
+        GEN_CUDA(cudaGetLastError());
+        int htmax[2] = {0, 0};
+        GEN_CUDA(cudaMemcpyAsync(htmax, tmax, sizeof(htmax), cudaMemcpyDeviceToHost, st));
         int herr = 0;
         GEN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
         GEN_CUDA(cudaStreamSynchronize(st));
         if (herr) return fail(set_error(L1LS_ECUDA, "internal: an entry of CSR(A) was not found in CSR(A^T)"));
+        I->csr_tile_max = htmax[0];
+        I->csc_tile_max = htmax[1];
         I->f_star = p->tau * hred[0] + 0.5 * hred[1];
         I->lam_max = hred[2];
         I->lipschitz = 1.0;   // sigma_max = kappa^0 = 1

@@ -75,6 +75,8 @@ struct Inst {
     int32_t* perm = nullptr;    // P: (P v)_i = v_{perm[i]}
     int32_t* perm_inv = nullptr;
     double f_star = 0, lipschitz = 1, lam_max = 0;
+    int64_t csr_tile_max = 0, csc_tile_max = 0;   // most nonzeros in a 32-row tile
+    int* dev_err = nullptr;                       // set by kernels whose bounded waits expired
     size_t bytes = 0;
     // solver work spaces (allocated on first use, owned by the instance)
     void* fista_work = nullptr;
@@ -90,6 +92,9 @@ struct Inst {
     }
     void free_all();
 };
+
+// entries to allocate for a vector read in whole 32-entry tiles
+inline int64_t pad32(int64_t count) { return (count + 31) / 32 * 32 + 32; }
 
 // value size of a stored dtype
 inline size_t dtype_size(int dt) { return dt == L1LS_F64 ? 8 : dt == L1LS_F32 ? 4 : 2; }

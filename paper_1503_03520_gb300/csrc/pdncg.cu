@@ -47,7 +47,6 @@ struct PdState {
     unsigned cnt[8];
 };
 
-template <class V> constexpr int cap_of() { return sizeof(V) == 8 ? 2048 : 4096; }
 
 __device__ __forceinline__ bool halted(const PdState* st) { return *(volatile const int32_t*)&st->stop != 0; }
 
@@ -58,24 +57,19 @@ __global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__
                                                      const Vec* __restrict__ b, Vec* __restrict__ r, int64_t m,
                                                      double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
     __shared__ double red[2 * 32];
     if (halted(st)) return;
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double p[2] = {0.0, 0.0};
-    const int64_t ntiles = (m + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, m - r0);
-        const Acc u = csr_tile<kBlock, cap_of<V>(), V, X, Acc>(ptr, col, val, x, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t i = r0 + threadIdx.x;
-            const Vec bb = b[i];
+    warp_csr<V, X, Acc>(
+        ptr, col, val, x, m, wbuf, [&](int64_t i, bool has) { return has ? b[i] : Vec(0); },
+        [&](int64_t i, Acc u, const Vec& bb) {
             const Vec rr = bb - u;
             r[i] = rr;
             p[0] += (double)rr * (double)rr;
             p[1] += (double)bb * (double)rr;
-        }
-    }
+        });
     block_reduce<kBlock, 2>(p, 0u, red);
     double tot[2];
     if (grid_reduce_last<kBlock, 2>(p, 0u, partials, &st->cnt[0], tot, red) && threadIdx.x == 0) {
@@ -91,22 +85,18 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
                                                    const double* __restrict__ x, double* __restrict__ atr, int64_t n,
                                                    double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
     __shared__ double red[2 * 32];
     if (halted(st)) return;
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double p[2] = {0.0, 0.0};
-    const int64_t ntiles = (n + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, n - r0);
-        const Acc a = csr_tile<kBlock, cap_of<V>(), V, Vec, Acc>(ptr, col, val, r, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t j = r0 + threadIdx.x;
+    warp_csr<V, Vec, Acc>(
+        ptr, col, val, r, n, wbuf, [&](int64_t j, bool has) { return has ? x[j] : 0.0; },
+        [&](int64_t j, Acc a, const double& xj) {
             atr[j] = (double)a;
             p[0] = fmax(p[0], fabs((double)a));
-            p[1] += fabs(x[j]);
-        }
-    }
+            p[1] += fabs(xj);
+        });
     block_reduce<kBlock, 2>(p, 1u, red);
     double tot[2];
     if (grid_reduce_last<kBlock, 2>(p, 1u, partials, &st->cnt[1], tot, red) && threadIdx.x == 0) {
@@ -186,25 +176,21 @@ __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ pt
                                                   Vec* __restrict__ out, const Vec* __restrict__ r, int64_t m,
                                                   double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     if (!LS && *(volatile int32_t*)&st->cg_done) return;
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double p[2] = {0.0, 0.0};
-    const int64_t ntiles = (m + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, m - r0);
-        const Acc u = csr_tile<kBlock, cap_of<V>(), V, X, Acc>(ptr, col, val, x, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t i = r0 + threadIdx.x;
+    warp_csr<V, X, Acc>(
+        ptr, col, val, x, m, wbuf, [&](int64_t i, bool has) { return (LS && has) ? r[i] : Vec(0); },
+        [&](int64_t i, Acc u, const Vec& ri) {
             out[i] = u;
             if (LS) {
-                p[0] += (double)r[i] * (double)u;
+                p[0] += (double)ri * (double)u;
                 p[1] += (double)u * (double)u;
             }
-        }
-    }
+        });
     if (!LS) return;
     block_reduce<kBlock, 2>(p, 0u, red);
     double tot[2];
@@ -225,23 +211,29 @@ __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ pt
                                                   const double* __restrict__ hd, const double* __restrict__ p,
                                                   double* __restrict__ hp, int64_t n, double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ CsrSmem<kBlock, cap_of<V>(), Acc> sm;
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
     __shared__ double red[32];
     if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double q[1] = {0.0};
-    const int64_t ntiles = (n + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, n - r0);
-        const Acc a = csr_tile<kBlock, cap_of<V>(), V, Vec, Acc>(ptr, col, val, ap, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t j = r0 + threadIdx.x;
-            const double pj = p[j];
-            const double h = hd[j] * pj + (double)a;
+    struct Ops {
+        double pj, h;
+    };
+    warp_csr<V, Vec, Acc>(
+        ptr, col, val, ap, n, wbuf,
+        [&](int64_t j, bool has) {
+            Ops o{0.0, 0.0};
+            if (has) {
+                o.pj = p[j];
+                o.h = hd[j];
+            }
+            return o;
+        },
+        [&](int64_t j, Acc a, const Ops& o) {
+            const double h = o.h * o.pj + (double)a;
             hp[j] = h;
-            q[0] += pj * h;
-        }
-    }
+            q[0] += o.pj * h;
+        });
     block_reduce<kBlock, 1>(q, 0u, red);
     double tot[1];
     if (grid_reduce_last<kBlock, 1>(q, 0u, partials, &st->cnt[4], tot, red) && threadIdx.x == 0) {
@@ -367,7 +359,7 @@ int grid_for(const Inst* I, K kernel, int64_t rows) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
     if (per_sm < 1) per_sm = 1;
-    const int64_t ntiles = (rows + kBlock - 1) / kBlock;
+    const int64_t ntiles = (rows + 31) / 32 / (kBlock / 32) + 1;   // blocks with one warp tile per warp
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)I->ctx->num_sms * per_sm));
 }
 

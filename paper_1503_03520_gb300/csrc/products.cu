@@ -11,26 +11,17 @@ namespace {
 
 constexpr int kBlock = 256;
 
-template <class V, class Acc>
-constexpr int cap_for() { return sizeof(Acc) == 8 ? 2048 : 4096; }
-
 template <class V, class X, class Acc>
 __global__ void __launch_bounds__(kBlock) k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                  const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
                                                  const int32_t* __restrict__ out_perm, X* __restrict__ y) {
-    constexpr int CAP = cap_for<V, Acc>();
-    __shared__ CsrSmem<kBlock, CAP, Acc> sm;
-    const int64_t ntiles = (nrows + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * kBlock;
-        const int nr = (int)min((int64_t)kBlock, nrows - r0);
-        const Acc acc = csr_tile<kBlock, CAP, V, X, Acc>(ptr, col, val, x, r0, nr, sm);
-        if ((int)threadIdx.x < nr) {
-            const int64_t r = r0 + threadIdx.x;
-            const int64_t dst = out_perm ? out_perm[r] : r;
-            y[dst] = (X)acc;
-        }
-    }
+    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
+    warp_csr<V, X, Acc>(ptr, col, val, x, nrows, wbuf, [&](int64_t, bool) { return NoOps{}; },
+                        [&](int64_t r, Acc acc, const NoOps&) {
+                            const int64_t dst = out_perm ? out_perm[r] : r;
+                            y[dst] = (X)acc;
+                        });
 }
 
 template <class X>

@@ -1,24 +1,25 @@
-// CSR "stream" traversal shared by every product kernel.
+// CSR traversal shared by every product kernel: one warp per tile of 32 rows.
 //
-// A CTA owns a tile of BLOCK consecutive rows.  It stages the tile's row pointers in
-// shared memory, then streams the tile's nonzeros (values and column indices, read once
-// with evict-first loads) in coalesced chunks of CAP entries, gathers the vector entry
-// of each nonzero and stores the product in shared memory; thread t then sums the
-// products of row t in nonzero order.  Rows of the generated matrices hold 0-16 entries,
-// so a thread per row keeps the sums short while the loads stay fully coalesced.
-// Persistent kernels walk tiles tile = blockIdx.x + k * gridDim.x, which fixes the order
-// of every reduction for a given grid.
+// Lane l owns row r0 + l.  The warp streams the tile's nonzeros (values and column indices,
+// read once with 16-byte evict-first vector loads, kEPL = 8 consecutive entries per lane, so
+// a chunk covers 256 entries) from the 16-byte-aligned position at or below the tile's first
+// entry; entries outside the tile are masked before their vector entry is gathered.  The
+// products go to a warp-private shared-memory buffer and lane l sums the entries of its own
+// row in nonzero order, so every row sum has a fixed order.  Rows of the generated matrices
+// hold 0-16 entries.  No block-wide barrier is involved: warps advance independently and
+// the epilogue operands of a tile are loaded before its nonzeros, so the memory system sees
+// the loads of many tiles at once.  Warps walk tiles tile = warp_id + k * total_warps.
+//
+// Nonzero arrays must be allocated with kPad entries of slack after nnz (vector tails).
 #pragma once
 
 #include "common.cuh"
 
 namespace l1ls {
 
-template <class T> __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
-template <> __device__ __forceinline__ __nv_bfloat16 ld_stream<__nv_bfloat16>(const __nv_bfloat16* p) {
-    unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(p));
-    return __ushort_as_bfloat16(u);
-}
+constexpr int kEPL = 8;       // nonzeros per lane per chunk
+constexpr int kPad = kEPL;    // slack entries after the nonzero arrays
+constexpr int kWarpChunk = 32 * kEPL;
 
 template <class Acc, class V> __device__ __forceinline__ Acc val_to_acc(V v);
 template <> __device__ __forceinline__ double val_to_acc<double, double>(double v) { return v; }
@@ -31,37 +32,73 @@ template <> __device__ __forceinline__ double vec_to_acc<double, float>(float v)
 template <> __device__ __forceinline__ float vec_to_acc<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ float vec_to_acc<float, double>(double v) { return (float)v; }
 
-template <int BLOCK, int CAP, class Acc>
-struct CsrSmem {
-    Acc prod[CAP];
-    int32_t ptr[BLOCK + 1];
-};
-
-// Row sums of one tile [r0, r0 + nr); returns the sum of row r0 + threadIdx.x (0 if outside).
-template <int BLOCK, int CAP, class V, class X, class Acc>
-__device__ __forceinline__ Acc csr_tile(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                        const V* __restrict__ val, const X* __restrict__ x, int64_t r0, int nr,
-                                        CsrSmem<BLOCK, CAP, Acc>& sm) {
-    for (int i = threadIdx.x; i <= nr; i += BLOCK) sm.ptr[i] = __ldcs(ptr + r0 + i);
-    __syncthreads();
-    const int32_t e0 = sm.ptr[0], e1 = sm.ptr[nr];
-    const int t = threadIdx.x;
-    const int32_t rb = t < nr ? sm.ptr[t] : e1;
-    const int32_t re = t < nr ? sm.ptr[t + 1] : e1;
-    Acc acc = Acc(0);
-    for (int32_t c = e0; c < e1; c += CAP) {
-        const int32_t ce = min(c + CAP, e1);
-#pragma unroll 4
-        for (int32_t e = c + t; e < ce; e += BLOCK) {
-            const int32_t j = ld_stream(col + e);
-            sm.prod[e - c] = val_to_acc<Acc>(ld_stream(val + e)) * vec_to_acc<Acc>(__ldg(x + j));
-        }
-        __syncthreads();
-        const int32_t lo = max(rb, c), hi = min(re, ce);
-        for (int32_t e = lo; e < hi; ++e) acc += sm.prod[e - c];
-        __syncthreads();
-    }
-    return acc;
+// kEPL consecutive entries starting at a 16-byte-aligned address, streaming loads
+template <class T>
+__device__ __forceinline__ void load_run(const T* __restrict__ p, T (&out)[kEPL]) {
+    constexpr int kVecs = (int)(kEPL * sizeof(T) / 16);
+    static_assert(kVecs * 16 == kEPL * sizeof(T), "run must be a whole number of 16-byte vectors");
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    uint4 w[kVecs];
+#pragma unroll
+    for (int i = 0; i < kVecs; ++i) w[i] = __ldcs(q + i);
+    memcpy(out, w, sizeof(w));
 }
+
+// Traverse all rows of a CSR matrix; `pre(row, valid)` returns the epilogue operands of a
+// row (loaded before the nonzeros), `epi(row, sum, operands)` consumes the row sum.
+// `wbuf` is this warp's shared buffer of kWarpChunk accumulators.
+template <class V, class X, class Acc, class Pre, class Epi>
+__device__ __forceinline__ void warp_csr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                         const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
+                                         Acc* __restrict__ wbuf, Pre pre, Epi epi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t ntiles = (nrows + 31) >> 5;
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
+        const int64_t r = (t << 5) + lane;
+        const bool has = r < nrows;
+        int32_t rb = 0, re = 0;
+        if (has) {
+            rb = __ldcs(ptr + r);
+            re = __ldcs(ptr + r + 1);
+        }
+        auto ops = pre(r, has);
+        const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
+        const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
+        const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
+        Acc acc = Acc(0);
+        for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
+            const int32_t base = c + lane * kEPL;
+            Acc p[kEPL];
+            if (base < e1) {
+                int32_t cj[kEPL];
+                V vv[kEPL];
+                load_run(col + base, cj);
+                load_run(val + base, vv);
+#pragma unroll
+                for (int k = 0; k < kEPL; ++k) {
+                    const int32_t e = base + k;
+                    p[k] = (e >= e0 && e < e1) ? val_to_acc<Acc>(vv[k]) * vec_to_acc<Acc>(__ldg(x + cj[k])) : Acc(0);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kEPL; ++k) p[k] = Acc(0);
+            }
+            // entry i of the chunk lives at wbuf[(i % kEPL) * 32 + i / kEPL]: conflict-free stores
+#pragma unroll
+            for (int k = 0; k < kEPL; ++k) wbuf[k * 32 + lane] = p[k];
+            __syncwarp();
+            const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
+            for (int32_t e = lo; e < hi; ++e) {
+                const int32_t i = e - c;
+                acc += wbuf[(i & (kEPL - 1)) * 32 + (i / kEPL)];
+            }
+            __syncwarp();
+        }
+        if (has) epi(r, acc, ops);
+    }
+}
+
+struct NoOps {};
 
 }  // namespace l1ls
