@@ -37,16 +37,25 @@ E2E_ITERS = 32
 KERNEL_SOURCES = ["spmv.cuh", "fista.cu", "common.cuh"]
 
 
-def bytes_per_iteration(m, n, nnz, value_bytes=4, vec_bytes=4):
-    """Algorithmic bytes of K1 and K2 for FP32 values and FP32 products (FP64 iterates).
+def bytes_per_iteration(m, n, nnz, value_bytes=4, vec_bytes=4, paired=True):
+    """Algorithmic bytes of K1 and K2 (FP32 values and products, FP64 iterates).
 
-    K1: nnz (value + int32 index) + (m+1) row pointers + x gathered once (n FP32)
-        + A x_{k-2} read, b read, A x_{k-1} written, r written (4 m-vectors).
-    K2: nnz (value + index) + (n+1) pointers + r gathered once (m FP32) + x_{k-1}, x_{k-2}
-        read and x_k written (FP64) + FP32 shadow of x_k written.
+    Stored matrix: with one left rotation the rows 2p and 2p+1 share their columns, so each
+    orientation stores one int32 index per pair of entries and the two values:
+    nnz/2 * (4 + 2 v) bytes plus the pointers (m/2 + 1 for rows, n + 1 for columns).
+    K1: matrix (row pairs) + x gathered once (n FP32) + A x_{k-2} read, b read, A x_{k-1}
+        written, r written (4 m-vectors).
+    K2: matrix (columns) + r gathered once (m FP32) + x_{k-1}, x_{k-2} read and x_k written
+        (FP64) + the FP32 copy of x_k written.
     """
-    k1 = nnz * (value_bytes + 4) + (m + 1) * 4 + n * vec_bytes + 4 * m * vec_bytes
-    k2 = nnz * (value_bytes + 4) + (n + 1) * 4 + m * vec_bytes + 3 * n * 8 + n * 4
+    if paired:
+        mat = (nnz // 2) * (4 + 2 * value_bytes)
+        p1, p2 = (m // 2 + 1) * 4, (n + 1) * 4
+    else:
+        mat = nnz * (4 + value_bytes)
+        p1, p2 = (m + 1) * 4, (n + 1) * 4
+    k1 = mat + p1 + n * vec_bytes + 4 * m * vec_bytes
+    k2 = mat + p2 + m * vec_bytes + 3 * n * 8 + n * 4
     return k1, k2
 
 
@@ -274,8 +283,8 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    # warm start from x0 costs one extra product A x0 (counted as K1's matrix traffic)
-    e2e_bytes = E2E_ITERS * (k1b + k2b) + nnz * 8 + (m + 1) * 4 + n * 4 + m * 4
+    # warm start from x0 costs one extra product A x0 (matrix, x, y)
+    e2e_bytes = E2E_ITERS * (k1b + k2b) + (nnz // 2) * 12 + (m // 2 + 1) * 4 + n * 4 + m * 4
     e2e = {"value": e2e_bytes * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n, "iters_per_step": E2E_ITERS, "steps": args.e2e_steps,
            "api": "l1ls_solve_fista(x0=pinned host, x_out=pinned host)"}
@@ -312,7 +321,9 @@ def run_ours(args):
                 "config": {"workload": "c2: m=2^%d, n=2^%d, nnz=%d (~8/col), FP32 values, int32 indices, "
                                        "kappa(A)=1e4, x* 1%%, tau=1, one FISTA iteration per step"
                                        % (args.log2n + 1, args.log2n, nnz),
-                           "l2": "inputs larger than L2 (A is %.2f GB per product)" % (nnz * 8 / 1e9),
+                           "storage": "row-pair CSR and column CSR of P1^T A: one int32 index and two FP32 "
+                                      "values per pair of entries",
+                           "l2": "inputs larger than L2 (A is %.2f GB per product)" % (nnz * 6 / 1e9),
                            "parallelism": "replicas (one instance per GPU)" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps, "fista_rel_gap_after_steps": fres["rel_gap"],

@@ -65,20 +65,19 @@ struct K2Args {
     int64_t n;
 };
 
-template <class V, class Vec>
+template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
     using Acc = Vec;
-    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
-    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     const Vec beta = (Vec)a.st->beta;
     double p[3] = {0.0, 0.0, 0.0};
     struct Ops {
         Vec axo, bb;
     };
-    warp_csr<V, Vec, Acc>(
-        a.ptr, a.col, a.val, a.x, a.m, wbuf,
+    rows_of<PAIRED, V, Vec, Acc>(
+        a.ptr, a.col, a.val, a.x, a.m, sm.warp_buf(),
         [&](int64_t r, bool has) {
             Ops o{Vec(0), Vec(0)};
             if (has) {
@@ -139,21 +138,20 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new) {
     }
 }
 
-template <class V, class Vec>
+template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
-    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[2 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
-    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const double invL = 1.0 / L, thr = tau / L;
     double p[2] = {0.0, 0.0};
     struct Ops {
         double x1, x0;
     };
-    warp_csr<V, Vec, Acc>(
-        a.ptr, a.col, a.val, a.res, a.n, wbuf,
+    cols_of<PAIRED, V, Vec, Acc>(
+        a.ptr, a.col, a.val, a.res, a.n, sm.warp_buf(),
         [&](int64_t j, bool has) {
             Ops o{0.0, 0.0};
             if (has) {
@@ -245,7 +243,14 @@ l1ls_status enqueue_k1(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a1.partials = w->part1;
     a1.st = w->st;
     a1.m = I->m;
-    k_fista_k1<V, Vec><<<w->grid1, kBlock, 0, st>>>(a1);
+    if (I->paired) {
+        a1.ptr = I->prow_ptr;
+        a1.col = I->prow_col;
+        a1.val = static_cast<const V*>(I->prow_val);
+        k_fista_k1<V, Vec, true><<<w->grid1, kBlock, 0, st>>>(a1);
+    } else {
+        k_fista_k1<V, Vec, false><<<w->grid1, kBlock, 0, st>>>(a1);
+    }
     return L1LS_OK;
 }
 
@@ -263,7 +268,14 @@ l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a2.partials = w->part2;
     a2.st = w->st;
     a2.n = I->n;
-    k_fista_k2<V, Vec><<<w->grid2, kBlock, 0, st>>>(a2);
+    if (I->paired) {
+        a2.ptr = I->pcol_ptr;
+        a2.col = I->pcol_pair;
+        a2.val = static_cast<const V*>(I->pcol_val);
+        k_fista_k2<V, Vec, true><<<w->grid2, kBlock, 0, st>>>(a2);
+    } else {
+        k_fista_k2<V, Vec, false><<<w->grid2, kBlock, 0, st>>>(a2);
+    }
     return L1LS_OK;
 }
 
@@ -289,8 +301,13 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         }
         L1LS_TRY(I->alloc(&w->ax, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->res, sizeof(Vec) * pad32(m)));
-        w->grid1 = grid_of(I, k_fista_k1<V, Vec>, m);
-        w->grid2 = grid_of(I, k_fista_k2<V, Vec>, n);
+        if (I->paired) {
+            w->grid1 = grid_of(I, k_fista_k1<V, Vec, true>, m / 2);
+            w->grid2 = grid_of(I, k_fista_k2<V, Vec, true>, n);
+        } else {
+            w->grid1 = grid_of(I, k_fista_k1<V, Vec, false>, m);
+            w->grid2 = grid_of(I, k_fista_k2<V, Vec, false>, n);
+        }
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
         L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 2 + 1024));
         L1LS_TRY(I->alloc_n(&w->st, 1));

@@ -353,6 +353,54 @@ __global__ void k_to_f32(const double* __restrict__ in, int64_t count, float* __
     if (i < count) out[i] = __double2float_rn(in[i]);
 }
 
+// paired rows: pair p takes the columns of row 2p and the values of rows 2p and 2p+1
+template <class V>
+__global__ void k_pair_rows(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                            const V* __restrict__ val, int64_t npairs, int32_t* __restrict__ pptr,
+                            int32_t* __restrict__ pcol, V* __restrict__ pval, int* __restrict__ err) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > npairs) return;
+    const int32_t a = ptr[2 * p];
+    pptr[p] = a / 2;
+    if (p == npairs) return;
+    const int32_t b = ptr[2 * p + 1], c = ptr[2 * p + 2];
+    if ((a & 1) || b - a != c - b) {
+        atomicExch(err, 2);
+        return;
+    }
+    for (int32_t k = 0; k < b - a; ++k) {
+        if (col[a + k] != col[b + k]) atomicExch(err, 2);
+        const int32_t o = a / 2 + k;
+        pcol[o] = col[a + k];
+        pval[2 * (int64_t)o] = val[a + k];
+        pval[2 * (int64_t)o + 1] = val[b + k];
+    }
+}
+
+// paired columns: consecutive rows (2p, 2p+1) of a column become one entry
+template <class V>
+__global__ void k_pair_cols(const int32_t* __restrict__ ptr, const int32_t* __restrict__ row,
+                            const V* __restrict__ val, int64_t n, int32_t* __restrict__ qptr,
+                            int32_t* __restrict__ qpair, V* __restrict__ qval, int* __restrict__ err) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n) return;
+    const int32_t a = ptr[j];
+    qptr[j] = a / 2;
+    if (j == n) return;
+    const int32_t b = ptr[j + 1];
+    if ((a & 1) || ((b - a) & 1)) {
+        atomicExch(err, 3);
+        return;
+    }
+    for (int32_t e = a; e < b; e += 2) {
+        if ((row[e] & 1) || row[e + 1] != row[e] + 1) atomicExch(err, 3);
+        const int32_t o = e / 2;
+        qpair[o] = row[e] >> 1;
+        qval[2 * (int64_t)o] = val[e];
+        qval[2 * (int64_t)o + 1] = val[e + 1];
+    }
+}
+
 template <class V>
 __global__ void k_colnorm2(const int32_t* __restrict__ ptr, const V* __restrict__ vals, int64_t n,
                            double* __restrict__ out) {
@@ -408,6 +456,29 @@ l1ls_status cast_and_norms(Inst* I, const double* csc64, const double* csr64, cu
     L1LS_CUDA(cudaGetLastError());
     I->csc_val = cv;
     I->csr_val = rv;
+    if (I->p.left_stages == 1) {
+        const int64_t np = I->nnz / 2, npairs = I->m / 2;
+        V* pv = nullptr;
+        V* qv = nullptr;
+        L1LS_TRY(I->alloc_n(&I->prow_ptr, npairs + 1));
+        L1LS_TRY(I->alloc_n(&I->prow_col, np + kPad));
+        L1LS_TRY(I->alloc_n(&pv, 2 * (np + kPad)));
+        L1LS_TRY(I->alloc_n(&I->pcol_ptr, I->n + 1));
+        L1LS_TRY(I->alloc_n(&I->pcol_pair, np + kPad));
+        L1LS_TRY(I->alloc_n(&qv, 2 * (np + kPad)));
+        L1LS_CUDA(cudaMemsetAsync(I->prow_col + np, 0, sizeof(int32_t) * kPad, st));
+        L1LS_CUDA(cudaMemsetAsync(I->pcol_pair + np, 0, sizeof(int32_t) * kPad, st));
+        L1LS_CUDA(cudaMemsetAsync(pv + 2 * np, 0, sizeof(V) * 2 * kPad, st));
+        L1LS_CUDA(cudaMemsetAsync(qv + 2 * np, 0, sizeof(V) * 2 * kPad, st));
+        k_pair_rows<V><<<nblk(npairs + 1), 256, 0, st>>>(I->csr_ptr, I->csr_col, rv, npairs, I->prow_ptr,
+                                                          I->prow_col, pv, I->dev_err);
+        k_pair_cols<V><<<nblk(I->n + 1), 256, 0, st>>>(I->csc_ptr, I->csc_row, cv, I->n, I->pcol_ptr, I->pcol_pair,
+                                                        qv, I->dev_err);
+        L1LS_CUDA(cudaGetLastError());
+        I->prow_val = pv;
+        I->pcol_val = qv;
+        I->paired = true;
+    }
     return L1LS_OK;
 }
 
@@ -589,10 +660,12 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_CUDA(cudaGetLastError());
         int htmax[2] = {0, 0};
         GEN_CUDA(cudaMemcpyAsync(htmax, tmax, sizeof(htmax), cudaMemcpyDeviceToHost, st));
-        int herr = 0;
+        int herr = 0, herr2 = 0;
         GEN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GEN_CUDA(cudaMemcpyAsync(&herr2, I->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         GEN_CUDA(cudaStreamSynchronize(st));
         if (herr) return fail(set_error(L1LS_ECUDA, "internal: an entry of CSR(A) was not found in CSR(A^T)"));
+        if (herr2) return fail(set_error(L1LS_ECUDA, "internal: the paired storage found unpaired rows (%d)", herr2));
         I->csr_tile_max = htmax[0];
         I->csc_tile_max = htmax[1];
         I->f_star = p->tau * hred[0] + 0.5 * hred[1];

@@ -67,6 +67,14 @@ struct Inst {
     int32_t* csc_ptr = nullptr;
     int32_t* csc_row = nullptr;
     void* csc_val = nullptr;
+    // paired storage (left_stages == 1): one index per row pair, two values per entry
+    bool paired = false;
+    int32_t* prow_ptr = nullptr;   // m/2 + 1
+    int32_t* prow_col = nullptr;   // nnz/2 (+pad)
+    void* prow_val = nullptr;      // nnz values: (row 2p, row 2p+1) per entry
+    int32_t* pcol_ptr = nullptr;   // n + 1
+    int32_t* pcol_pair = nullptr;  // nnz/2 (+pad)
+    void* pcol_val = nullptr;      // nnz values: (row 2p, row 2p+1) per entry
     double* bhat = nullptr;     // P1^T b in FP64
     float* bhat32 = nullptr;    // FP32 copy (products in FP32)
     double* xstar = nullptr;

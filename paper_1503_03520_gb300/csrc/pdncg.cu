@@ -51,19 +51,18 @@ struct PdState {
 __device__ __forceinline__ bool halted(const PdState* st) { return *(volatile const int32_t*)&st->stop != 0; }
 
 // ---- N1: r = b - A x --------------------------------------------------------------------
-template <class V, class Vec, class X>
+template <class V, class Vec, class X, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                      const V* __restrict__ val, const X* __restrict__ x,
                                                      const Vec* __restrict__ b, Vec* __restrict__ r, int64_t m,
                                                      double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[2 * 32];
     if (halted(st)) return;
-    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double p[2] = {0.0, 0.0};
-    warp_csr<V, X, Acc>(
-        ptr, col, val, x, m, wbuf, [&](int64_t i, bool has) { return has ? b[i] : Vec(0); },
+    rows_of<PAIRED, V, X, Acc>(
+        ptr, col, val, x, m, sm.warp_buf(), [&](int64_t i, bool has) { return has ? b[i] : Vec(0); },
         [&](int64_t i, Acc u, const Vec& bb) {
             const Vec rr = bb - u;
             r[i] = rr;
@@ -79,19 +78,18 @@ __global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__
 }
 
 // ---- N2: a = A^T r, certificate ---------------------------------------------------------
-template <class V, class Vec>
+template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                    const V* __restrict__ val, const Vec* __restrict__ r,
                                                    const double* __restrict__ x, double* __restrict__ atr, int64_t n,
                                                    double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[2 * 32];
     if (halted(st)) return;
-    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double p[2] = {0.0, 0.0};
-    warp_csr<V, Vec, Acc>(
-        ptr, col, val, r, n, wbuf, [&](int64_t j, bool has) { return has ? x[j] : 0.0; },
+    cols_of<PAIRED, V, Vec, Acc>(
+        ptr, col, val, r, n, sm.warp_buf(), [&](int64_t j, bool has) { return has ? x[j] : 0.0; },
         [&](int64_t j, Acc a, const double& xj) {
             atr[j] = (double)a;
             p[0] = fmax(p[0], fabs((double)a));
@@ -170,20 +168,19 @@ __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x
 }
 
 // ---- C1: Ap = A p (also L1: Ad = A d with partials) -------------------------------------
-template <class V, class Vec, class X, bool LS>
+template <class V, class Vec, class X, bool LS, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                   const V* __restrict__ val, const X* __restrict__ x,
                                                   Vec* __restrict__ out, const Vec* __restrict__ r, int64_t m,
                                                   double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     if (!LS && *(volatile int32_t*)&st->cg_done) return;
-    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double p[2] = {0.0, 0.0};
-    warp_csr<V, X, Acc>(
-        ptr, col, val, x, m, wbuf, [&](int64_t i, bool has) { return (LS && has) ? r[i] : Vec(0); },
+    rows_of<PAIRED, V, X, Acc>(
+        ptr, col, val, x, m, sm.warp_buf(), [&](int64_t i, bool has) { return (LS && has) ? r[i] : Vec(0); },
         [&](int64_t i, Acc u, const Vec& ri) {
             out[i] = u;
             if (LS) {
@@ -205,22 +202,21 @@ __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ pt
 }
 
 // ---- C2: Hp = h p + A^T Ap, alpha ------------------------------------------------------
-template <class V, class Vec>
+template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                   const V* __restrict__ val, const Vec* __restrict__ ap,
                                                   const double* __restrict__ hd, const double* __restrict__ p,
                                                   double* __restrict__ hp, int64_t n, double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ Acc wbuf_all[(kBlock / 32) * kWarpChunk];
+    __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[32];
     if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
-    Acc* wbuf = wbuf_all + (threadIdx.x >> 5) * kWarpChunk;
     double q[1] = {0.0};
     struct Ops {
         double pj, h;
     };
-    warp_csr<V, Vec, Acc>(
-        ptr, col, val, ap, n, wbuf,
+    cols_of<PAIRED, V, Vec, Acc>(
+        ptr, col, val, ap, n, sm.warp_buf(),
         [&](int64_t j, bool has) {
             Ops o{0.0, 0.0};
             if (has) {
@@ -380,24 +376,38 @@ struct PdWork {
     }
 };
 
-template <class V, class Vec>
+// row and column orientation of the stored matrix (plain or paired)
+template <class V, bool PAIRED>
+void views(const Inst* I, Csr<V>& rows, Csr<V>& cols) {
+    if (PAIRED) {
+        rows = {I->prow_ptr, I->prow_col, static_cast<const V*>(I->prow_val)};
+        cols = {I->pcol_ptr, I->pcol_pair, static_cast<const V*>(I->pcol_val)};
+    } else {
+        rows = {I->csr_ptr, I->csr_col, static_cast<const V*>(I->csr_val)};
+        cols = {I->csc_ptr, I->csc_row, static_cast<const V*>(I->csc_val)};
+    }
+}
+
+template <class V, class Vec, bool PAIRED>
 void enqueue_cg(Inst* I, PdWork* w, cudaStream_t s) {
-    const V* rv = static_cast<const V*>(I->csr_val);
-    const V* cv = static_cast<const V*>(I->csc_val);
+    Csr<V> R, C;
+    views<V, PAIRED>(I, R, C);
     if constexpr (sizeof(Vec) == 8)
-        k_pd_ax<V, Vec, double, false><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->p, (Vec*)w->ap,
-                                                                nullptr, I->m, w->part, w->st);
+        k_pd_ax<V, Vec, double, false, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->p, (Vec*)w->ap,
+                                                                        nullptr, I->m, w->part, w->st);
     else
-        k_pd_ax<V, Vec, float, false><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->p32, (Vec*)w->ap,
-                                                               nullptr, I->m, w->part, w->st);
-    k_pd_hp<V, Vec><<<w->gn, kBlock, 0, s>>>(I->csc_ptr, I->csc_row, cv, (const Vec*)w->ap, w->hd, w->p, w->hp, I->n,
-                                             w->part, w->st);
+        k_pd_ax<V, Vec, float, false, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->p32, (Vec*)w->ap,
+                                                                       nullptr, I->m, w->part, w->st);
+    k_pd_hp<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->ap, w->hd, w->p, w->hp,
+                                                     I->n, w->part, w->st);
     k_pd_cgupd<<<w->gv, kBlock, 0, s>>>(w->d, w->rcg, w->p, w->hp, w->minv, I->n, w->part, w->st);
     k_pd_pupd<float><<<w->gv, kBlock, 0, s>>>(w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->rcg, w->minv, I->n, w->st);
 }
 
-template <class V, class Vec>
+template <class V, class Vec, bool PAIRED>
 l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res, cudaStream_t s) {
+    Csr<V> R, C;
+    views<V, PAIRED>(I, R, C);
     auto t0 = std::chrono::steady_clock::now();
     const int64_t m = I->m, n = I->n;
     PdWork* w = static_cast<PdWork*>(I->pd_work);
@@ -408,11 +418,11 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         for (double** v : {&w->X, &w->gd, &w->atr, &w->grad, &w->hd, &w->minv, &w->rcg, &w->p, &w->hp, &w->d})
             L1LS_TRY(I->alloc_n(v, n));
         if (sizeof(Vec) == 4) L1LS_TRY(I->alloc_n(&w->p32, n));
-        L1LS_TRY(I->alloc(&w->r, sizeof(Vec) * m));
-        L1LS_TRY(I->alloc(&w->ap, sizeof(Vec) * m));
-        L1LS_TRY(I->alloc(&w->ad, sizeof(Vec) * m));
-        w->gm = grid_for(I, k_pd_resid<V, Vec, double>, m);
-        w->gn = grid_for(I, k_pd_atr<V, Vec>, n);
+        L1LS_TRY(I->alloc(&w->r, sizeof(Vec) * pad32(m)));
+        L1LS_TRY(I->alloc(&w->ap, sizeof(Vec) * pad32(m)));
+        L1LS_TRY(I->alloc(&w->ad, sizeof(Vec) * pad32(m)));
+        w->gm = grid_for(I, k_pd_resid<V, Vec, double, PAIRED>, PAIRED ? m / 2 : m);
+        w->gn = grid_for(I, k_pd_atr<V, Vec, PAIRED>, n);
         w->gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)I->ctx->num_sms * 8));
         const int gmax = std::max(w->gm, std::max(w->gn, w->gv));
         L1LS_TRY(I->alloc_n(&w->part, (int64_t)gmax * (kTrialsPerPass + 1)));
@@ -438,8 +448,6 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     h.prev_gap = INFINITY;
     *w->host = h;
     L1LS_CUDA(cudaMemcpyAsync(w->st, w->host, sizeof(PdState), cudaMemcpyHostToDevice, s));
-    const V* rv = static_cast<const V*>(I->csr_val);
-    const V* cv = static_cast<const V*>(I->csc_val);
     const Vec* bvec = sizeof(Vec) == 8 ? (const Vec*)I->bhat : (const Vec*)I->bhat32;
     l1ls_status final_status = L1LS_OK;
     int chunk = o->check_every > 0 ? std::min(o->check_every, 16) : 8;
@@ -452,7 +460,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         L1LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph;
         L1LS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < chunk; ++i) enqueue_cg<V, Vec>(I, w, cap);
+        for (int i = 0; i < chunk; ++i) enqueue_cg<V, Vec, PAIRED>(I, w, cap);
         cudaError_t ce = cudaStreamEndCapture(cap, &graph);
         if (ce != cudaSuccess) {
             cudaStreamDestroy(cap);
@@ -466,10 +474,10 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     const int ls_passes = (o->ls_max + kTrialsPerPass - 1) / kTrialsPerPass;
     for (;;) {
         // N1 gathers the FP64 iterate (once per Newton step)
-        k_pd_resid<V, Vec, double><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->X, bvec, (Vec*)w->r, m,
-                                                            w->part, w->st);
-        k_pd_atr<V, Vec><<<w->gn, kBlock, 0, s>>>(I->csc_ptr, I->csc_row, cv, (const Vec*)w->r, w->X, w->atr, n,
-                                                  w->part, w->st);
+        k_pd_resid<V, Vec, double, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->X, bvec, (Vec*)w->r, m,
+                                                                    w->part, w->st);
+        k_pd_atr<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->r, w->X, w->atr, n,
+                                                          w->part, w->st);
         L1LS_CUDA(cudaGetLastError());
         L1LS_CUDA(cudaMemcpyAsync(w->host, w->st, sizeof(PdState), cudaMemcpyDeviceToHost, s));
         L1LS_CUDA(cudaStreamSynchronize(s));
@@ -497,8 +505,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
             if (w->host->cg_done) break;
         }
         if (final_status != L1LS_OK) break;
-        k_pd_ax<V, Vec, double, true><<<w->gm, kBlock, 0, s>>>(I->csr_ptr, I->csr_col, rv, w->d, (Vec*)w->ad,
-                                                               (const Vec*)w->r, m, w->part, w->st);
+        k_pd_ax<V, Vec, double, true, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->d, (Vec*)w->ad,
+                                                                       (const Vec*)w->r, m, w->part, w->st);
         for (int t = 0; t < ls_passes; ++t)
             k_pd_trial<<<w->gv, kBlock, 0, s>>>(w->X, w->d, w->grad, n, w->part, w->st);
         k_pd_apply<<<w->gv, kBlock, 0, s>>>(w->X, w->gd, w->d, n, w->st);
@@ -534,10 +542,17 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
 
 l1ls_status pdncg_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
                         cudaStream_t st) {
+    if (I->paired) {
+        switch (I->dtype) {
+            case L1LS_F64: return run<double, double, true>(I, o, x0, x_out, res, st);
+            case L1LS_F32: return run<float, float, true>(I, o, x0, x_out, res, st);
+            default: return run<__nv_bfloat16, float, true>(I, o, x0, x_out, res, st);
+        }
+    }
     switch (I->dtype) {
-        case L1LS_F64: return run<double, double>(I, o, x0, x_out, res, st);
-        case L1LS_F32: return run<float, float>(I, o, x0, x_out, res, st);
-        default: return run<__nv_bfloat16, float>(I, o, x0, x_out, res, st);
+        case L1LS_F64: return run<double, double, false>(I, o, x0, x_out, res, st);
+        case L1LS_F32: return run<float, float, false>(I, o, x0, x_out, res, st);
+        default: return run<__nv_bfloat16, float, false>(I, o, x0, x_out, res, st);
     }
 }
 

@@ -102,3 +102,148 @@ __device__ __forceinline__ void warp_csr(const int32_t* __restrict__ ptr, const 
 struct NoOps {};
 
 }  // namespace l1ls
+
+namespace l1ls {
+
+// ---- paired storage ----------------------------------------------------------------------
+// With one left rotation, rows 2p and 2p+1 of P1^T A share their column set and every column
+// holds complete row pairs.  Both orientations are stored with one index per pair of
+// entries and the two values side by side:
+//   rows:    pair p -> entries (column j, value in row 2p, value in row 2p+1)
+//   columns: column j -> entries (pair p, value in row 2p, value in row 2p+1)
+// A row-pair traversal gathers x[j] once for two rows; a column traversal gathers the two
+// entries (2p, 2p+1) of the input as one 8- or 16-byte load.
+
+template <class T> struct Two;
+template <> struct Two<float> { using type = float2; };
+template <> struct Two<double> { using type = double2; };
+
+template <class T, int N>
+__device__ __forceinline__ void load_span(const T* __restrict__ p, T (&out)[N]) {
+    constexpr int kVecs = (int)(N * sizeof(T) / 16);
+    static_assert(kVecs * 16 == N * sizeof(T), "span must be a whole number of 16-byte vectors");
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    uint4 w[kVecs];
+#pragma unroll
+    for (int i = 0; i < kVecs; ++i) w[i] = __ldcs(q + i);
+    memcpy(out, w, sizeof(w));
+}
+
+// ROWS = true : npairs row pairs; x gathered at the column index; pre / epi are called per
+//               row (2p and 2p+1) exactly as for warp_csr.
+// ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
+// wbuf: this warp's 2 * kWarpChunk accumulators.
+template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
+__device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                          const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
+                                          Acc* __restrict__ wbuf, Pre pre, Epi epi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t ntiles = (nrows + 31) >> 5;
+    Acc* w0 = wbuf;
+    Acc* w1 = wbuf + kWarpChunk;
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
+        const int64_t r = (t << 5) + lane;
+        const bool has = r < nrows;
+        int32_t rb = 0, re = 0;
+        if (has) {
+            rb = __ldcs(ptr + r);
+            re = __ldcs(ptr + r + 1);
+        }
+        auto ops0 = pre(ROWS ? 2 * r : r, has);
+        auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
+        const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
+        const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
+        const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
+        Acc a0 = Acc(0), a1 = Acc(0);
+        for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
+            const int32_t base = c + lane * kEPL;
+            Acc p0[kEPL], p1[kEPL];
+            if (base < e1) {
+                int32_t ij[kEPL];
+                V vv[2 * kEPL];
+                load_span<int32_t, kEPL>(idx + base, ij);
+                load_span<V, 2 * kEPL>(val2 + 2 * (int64_t)base, vv);
+#pragma unroll
+                for (int k = 0; k < kEPL; ++k) {
+                    const int32_t e = base + k;
+                    const bool in = e >= e0 && e < e1;
+                    const Acc v0 = val_to_acc<Acc>(vv[2 * k]), v1 = val_to_acc<Acc>(vv[2 * k + 1]);
+                    if (ROWS) {
+                        const Acc xv = in ? vec_to_acc<Acc>(__ldg(x + ij[k])) : Acc(0);
+                        p0[k] = v0 * xv;
+                        p1[k] = v1 * xv;
+                    } else {
+                        Acc g0 = Acc(0), g1 = Acc(0);
+                        if (in) {
+                            const typename Two<X>::type g =
+                                __ldg(reinterpret_cast<const typename Two<X>::type*>(x) + ij[k]);
+                            g0 = vec_to_acc<Acc>(g.x);
+                            g1 = vec_to_acc<Acc>(g.y);
+                        }
+                        p0[k] = v0 * g0 + v1 * g1;
+                        p1[k] = Acc(0);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kEPL; ++k) p0[k] = p1[k] = Acc(0);
+            }
+#pragma unroll
+            for (int k = 0; k < kEPL; ++k) {
+                w0[k * 32 + lane] = p0[k];
+                if (ROWS) w1[k * 32 + lane] = p1[k];
+            }
+            __syncwarp();
+            const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
+            for (int32_t e = lo; e < hi; ++e) {
+                const int32_t i = e - c;
+                const int32_t q = (i & (kEPL - 1)) * 32 + (i / kEPL);
+                a0 += w0[q];
+                if (ROWS) a1 += w1[q];
+            }
+            __syncwarp();
+        }
+        if (has) {
+            if (ROWS) {
+                epi(2 * r, a0, ops0);
+                epi(2 * r + 1, a1, ops1);
+            } else {
+                epi(r, a0, ops0);
+            }
+        }
+    }
+}
+
+// Row traversal of A (nrows rows) in plain or paired storage.
+template <bool PAIRED, class V, class X, class Acc, class Pre, class Epi>
+__device__ __forceinline__ void rows_of(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                        const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
+                                        Acc* __restrict__ wbuf, Pre pre, Epi epi) {
+    if constexpr (PAIRED) warp_pcsr<true, V, X, Acc>(ptr, idx, val, x, nrows / 2, wbuf, pre, epi);
+    else warp_csr<V, X, Acc>(ptr, idx, val, x, nrows, wbuf, pre, epi);
+}
+
+// Column traversal of A (rows of A^T, ncols of them) in plain or paired storage.
+template <bool PAIRED, class V, class X, class Acc, class Pre, class Epi>
+__device__ __forceinline__ void cols_of(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                        const V* __restrict__ val, const X* __restrict__ x, int64_t ncols,
+                                        Acc* __restrict__ wbuf, Pre pre, Epi epi) {
+    if constexpr (PAIRED) warp_pcsr<false, V, X, Acc>(ptr, idx, val, x, ncols, wbuf, pre, epi);
+    else warp_csr<V, X, Acc>(ptr, idx, val, x, ncols, wbuf, pre, epi);
+}
+
+// shared accumulators per block for either storage
+template <class Acc, int BLOCK> struct TraversalSmem {
+    Acc buf[(BLOCK / 32) * 2 * kWarpChunk];
+    __device__ Acc* warp_buf() { return buf + (threadIdx.x >> 5) * 2 * kWarpChunk; }
+};
+
+// Matrix operands of one orientation
+template <class V> struct Csr {
+    const int32_t* ptr;
+    const int32_t* idx;
+    const V* val;
+};
+
+}  // namespace l1ls
