@@ -46,7 +46,7 @@ def bytes_per_iteration(m, n, nnz, value_bytes=4, vec_bytes=4, paired=True):
     K1: matrix (row pairs) + x gathered once (n FP32) + A x_{k-2} read, b read, A x_{k-1}
         written, r written (4 m-vectors).
     K2: matrix (columns) + r gathered once (m FP32) + x_{k-1}, x_{k-2} read and x_k written
-        (FP64) + the FP32 copy of x_k written.
+        (8 bytes each: float-float pairs, the hi half being what K1 gathers).
     """
     if paired:
         mat = (nnz // 2) * (4 + 2 * value_bytes)
@@ -55,7 +55,7 @@ def bytes_per_iteration(m, n, nnz, value_bytes=4, vec_bytes=4, paired=True):
         mat = nnz * (4 + value_bytes)
         p1, p2 = (m + 1) * 4, (n + 1) * 4
     k1 = mat + p1 + n * vec_bytes + 4 * m * vec_bytes
-    k2 = mat + p2 + m * vec_bytes + 3 * n * 8 + n * 4
+    k2 = mat + p2 + m * vec_bytes + 3 * n * 8
     return k1, k2
 
 

@@ -133,3 +133,60 @@ __device__ __forceinline__ double soft_threshold(double v, double t) {
 }
 
 }  // namespace l1ls
+
+namespace l1ls {
+
+// ---- float-float arithmetic ---------------------------------------------------------------
+// A value is hi + lo with |lo| <= ulp(hi)/2: about 48 significand bits, carried entirely on
+// the FP32 pipes (the FP64 pipe of this part runs at a small fraction of the FP32 rate).
+// Error-free transformations: TwoSum (Knuth, TAOCP vol. 2), FastTwoSum (Dekker 1971) and
+// TwoProduct by a fused multiply-add; additions and products follow the double-word
+// algorithms of Dekker (1971) and Bailey's double-double library.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    const ff t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    ff p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_from_float(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ ff ff_from_double(double d) {   // FP64 pipe: use outside hot loops
+    const float hi = __double2float_rn(d);
+    return {hi, __double2float_rn(d - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_abs(ff a) { return a.hi < 0.0f ? ff_neg(a) : a; }
+// shrinkage S_t(v) of Sec. 2 in float-float: sign(v) max(|v| - t, 0)
+__device__ __forceinline__ ff ff_soft_threshold(ff v, ff t) {
+    const ff a = ff_sub(ff_abs(v), t);
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    return v.hi < 0.0f ? ff_neg(a) : a;
+}
+
+}  // namespace l1ls

@@ -12,7 +12,10 @@
 // captured in one CUDA graph and launched without host round trips.  x_{k-1} and x_{k-2}
 // alternate between two buffers; a chunk holds an even number of iterations.
 // FP64 values: all vectors FP64.  FP32 / BF16 values: products, residuals and A x in FP32
-// (FP32 accumulation), iterates and every reduction in FP64, FP32 shadow of x for gathers.
+// (FP32 accumulation); the iterates are float-float pairs (hi, lo) updated in float-float
+// arithmetic, K1 gathers the hi part, and the gap partials are accumulated in float-float
+// and reduced across the grid in FP64.  (The FP64 pipe of this part is a small fraction of
+// the FP32 rate; FP64 per row in these epilogues bounded both kernels before.)
 #include <chrono>
 #include <cmath>
 
@@ -57,9 +60,12 @@ struct K2Args {
     const int32_t* col;
     const V* val;
     const Vec* res;
-    const double* xc;    // x_{k-1}
-    double* xo;          // in: x_{k-2}; out: x_k
-    float* xo32;         // FP32 shadow of x_k (nullptr for FP64 values)
+    const double* xc;    // x_{k-1} (FP64 values)
+    double* xo;          // in: x_{k-2}; out: x_k (FP64 values)
+    const float* xch;    // x_{k-1} as float-float (FP32 / BF16 values)
+    const float* xcl;
+    float* xoh;          // in: x_{k-2}; out: x_k as float-float
+    float* xol;
     double* partials;
     FistaState* st;
     int64_t n;
@@ -73,6 +79,7 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
     if (*(volatile int32_t*)&a.st->stop) return;
     const Vec beta = (Vec)a.st->beta;
     double p[3] = {0.0, 0.0, 0.0};
+    ff q[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     struct Ops {
         Vec axo, bb;
     };
@@ -91,11 +98,25 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
             const Vec rr = o.bb - ay;
             a.ax[r] = u;
             a.res[r] = rr;
-            const double du = (double)u - (double)o.bb;
-            p[0] += du * du;
-            p[1] += (double)o.bb * (double)rr;
-            p[2] += (double)rr * (double)rr;
+            if constexpr (sizeof(Vec) == 4) {
+                const ff d = two_sum(u, -o.bb);                  // u - b exactly
+                ff sq = two_prod(d.hi, d.hi);
+                sq.lo = __fmaf_rn(2.0f * d.hi, d.lo, sq.lo);
+                q[0] = ff_add(q[0], sq);
+                q[1] = ff_add(q[1], two_prod(o.bb, rr));
+                q[2] = ff_add(q[2], two_prod(rr, rr));
+            } else {
+                const double du = (double)u - (double)o.bb;
+                p[0] += du * du;
+                p[1] += (double)o.bb * (double)rr;
+                p[2] += (double)rr * (double)rr;
+            }
         });
+    if constexpr (sizeof(Vec) == 4) {
+        p[0] = ff_to_double(q[0]);
+        p[1] = ff_to_double(q[1]);
+        p[2] = ff_to_double(q[2]);
+    }
     block_reduce<kBlock, 3>(p, 0u, red);
     double tot[3];
     if (grid_reduce_last<kBlock, 3>(p, 0u, a.partials, &a.st->cnt1, tot, red) && threadIdx.x == 0) {
@@ -147,28 +168,57 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const double invL = 1.0 / L, thr = tau / L;
     double p[2] = {0.0, 0.0};
-    struct Ops {
-        double x1, x0;
-    };
-    cols_of<PAIRED, V, Vec, Acc>(
-        a.ptr, a.col, a.val, a.res, a.n, sm.warp_buf(),
-        [&](int64_t j, bool has) {
-            Ops o{0.0, 0.0};
-            if (has) {
-                o.x1 = a.xc[j];
-                o.x0 = a.xo[j];
-            }
-            return o;
-        },
-        [&](int64_t j, Acc gacc, const Ops& o) {
-            const double g = (double)gacc;
-            const double y = o.x1 + beta * (o.x1 - o.x0);
-            const double xn = soft_threshold(y + g * invL, thr);
-            a.xo[j] = xn;
-            if (a.xo32) a.xo32[j] = __double2float_rn(xn);
-            p[0] = fmax(p[0], fabs(g));
-            p[1] += fabs(xn);
-        });
+    if constexpr (sizeof(Vec) == 4) {
+        const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(invL), thr_f = ff_from_double(thr);
+        float gmax = 0.0f;
+        ff l1 = {0.0f, 0.0f};
+        struct Ops {
+            ff x1, x0;
+        };
+        cols_of<PAIRED, V, Vec, Acc>(
+            a.ptr, a.col, a.val, a.res, a.n, sm.warp_buf(),
+            [&](int64_t j, bool has) {
+                Ops o{{0.f, 0.f}, {0.f, 0.f}};
+                if (has) {
+                    o.x1 = {a.xch[j], a.xcl[j]};
+                    o.x0 = {a.xoh[j], a.xol[j]};
+                }
+                return o;
+            },
+            [&](int64_t j, Acc g, const Ops& o) {
+                const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
+                const ff v = ff_add(y, ff_mul(ff_from_float(g), invL_f));
+                const ff xn = ff_soft_threshold(v, thr_f);
+                a.xoh[j] = xn.hi;
+                a.xol[j] = xn.lo;
+                gmax = fmaxf(gmax, fabsf(g));
+                l1 = ff_add(l1, ff_abs(xn));
+            });
+        p[0] = (double)gmax;
+        p[1] = ff_to_double(l1);
+    } else {
+        struct Ops {
+            double x1, x0;
+        };
+        cols_of<PAIRED, V, Vec, Acc>(
+            a.ptr, a.col, a.val, a.res, a.n, sm.warp_buf(),
+            [&](int64_t j, bool has) {
+                Ops o{0.0, 0.0};
+                if (has) {
+                    o.x1 = a.xc[j];
+                    o.x0 = a.xo[j];
+                }
+                return o;
+            },
+            [&](int64_t j, Acc gacc, const Ops& o) {
+                const double g = (double)gacc;
+                const double y = o.x1 + beta * (o.x1 - o.x0);
+                const double xn = soft_threshold(y + g * invL, thr);
+                a.xo[j] = xn;
+                p[0] = fmax(p[0], fabs(g));
+                p[1] += fabs(xn);
+            });
+    }
     block_reduce<kBlock, 2>(p, 1u, red);
     double tot[2];
     if (grid_reduce_last<kBlock, 2>(p, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
@@ -186,9 +236,17 @@ __global__ void k_abs_sum(const double* __restrict__ x, int64_t n, double* __res
     if (grid_reduce_last<kBlock, 1>(v, 0u, partials, counter, tot, red) && threadIdx.x == 0) *out = tot[0];
 }
 
-__global__ void k_d2f(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
+__global__ void k_d2ff(const double* __restrict__ in, int64_t n, float* __restrict__ hi, float* __restrict__ lo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = __double2float_rn(in[i]);
+    if (i >= n) return;
+    const ff v = ff_from_double(in[i]);
+    hi[i] = v.hi;
+    lo[i] = v.lo;
+}
+
+__global__ void k_ff2d(const float* __restrict__ hi, const float* __restrict__ lo, int64_t n, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ff_to_double({hi[i], lo[i]});
 }
 
 template <class K>
@@ -203,8 +261,10 @@ int grid_of(const Inst* I, K kernel, int64_t rows) {
 
 // Per-instance FISTA work space and cached graph.
 struct FistaWork {
-    double* X[2] = {nullptr, nullptr};
-    float* X32[2] = {nullptr, nullptr};
+    double* X[2] = {nullptr, nullptr};   // FP64 values: iterates
+    float* Xh[2] = {nullptr, nullptr};   // FP32 / BF16 values: iterates as float-float
+    float* Xl[2] = {nullptr, nullptr};
+    double* tmp64 = nullptr;             // FP64 staging of x0 / x_out
     void* ax = nullptr;
     void* res = nullptr;
     double* part1 = nullptr;
@@ -235,7 +295,7 @@ l1ls_status enqueue_k1(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a1.col = I->csr_col;
     a1.val = static_cast<const V*>(I->csr_val);
     if constexpr (sizeof(Vec) == 8) a1.x = reinterpret_cast<const Vec*>(w->X[c]);
-    else a1.x = reinterpret_cast<const Vec*>(w->X32[c]);
+    else a1.x = reinterpret_cast<const Vec*>(w->Xh[c]);   // hi part of the float-float iterate
     a1.ax = static_cast<Vec*>(w->ax);
     a1.res = static_cast<Vec*>(w->res);
     if constexpr (sizeof(Vec) == 8) a1.b = reinterpret_cast<const Vec*>(I->bhat);
@@ -264,7 +324,10 @@ l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a2.res = static_cast<const Vec*>(w->res);
     a2.xc = w->X[c];
     a2.xo = w->X[o];
-    a2.xo32 = sizeof(Vec) == 8 ? nullptr : w->X32[o];
+    a2.xch = w->Xh[c];
+    a2.xcl = w->Xl[c];
+    a2.xoh = w->Xh[o];
+    a2.xol = w->Xl[o];
     a2.partials = w->part2;
     a2.st = w->st;
     a2.n = I->n;
@@ -293,12 +356,16 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         w = new FistaWork();
         I->fista_work = w;
         I->fista_work_free = [](void* p) { delete static_cast<FistaWork*>(p); };
-        L1LS_TRY(I->alloc_n(&w->X[0], pad32(n)));
-        L1LS_TRY(I->alloc_n(&w->X[1], pad32(n)));
-        if (sizeof(Vec) == 4) {
-            L1LS_TRY(I->alloc_n(&w->X32[0], pad32(n)));
-            L1LS_TRY(I->alloc_n(&w->X32[1], pad32(n)));
+        if (sizeof(Vec) == 8) {
+            L1LS_TRY(I->alloc_n(&w->X[0], pad32(n)));
+            L1LS_TRY(I->alloc_n(&w->X[1], pad32(n)));
+        } else {
+            for (int k = 0; k < 2; ++k) {
+                L1LS_TRY(I->alloc_n(&w->Xh[k], pad32(n)));
+                L1LS_TRY(I->alloc_n(&w->Xl[k], pad32(n)));
+            }
         }
+        L1LS_TRY(I->alloc_n(&w->tmp64, pad32(n)));
         L1LS_TRY(I->alloc(&w->ax, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->res, sizeof(Vec) * pad32(m)));
         if (I->paired) {
@@ -330,29 +397,35 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     h.cert_iter = 0;
     h.stop = 0;
     h.status = L1LS_OK;
+    const unsigned nb = (unsigned)((n + 255) / 256);
     if (x0) {
-        L1LS_CUDA(cudaMemcpyAsync(w->X[0], x0, sizeof(double) * n, cudaMemcpyDefault, st));
-        L1LS_CUDA(cudaMemcpyAsync(w->X[1], w->X[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        unsigned nb = (unsigned)((n + 255) / 256);
-        if (sizeof(Vec) == 4) {
-            k_d2f<<<nb, 256, 0, st>>>(w->X[0], n, w->X32[0]);
-            k_d2f<<<nb, 256, 0, st>>>(w->X[0], n, w->X32[1]);
+        // x0 (device or host FP64) -> FP64 staging -> iterate buffers
+        L1LS_CUDA(cudaMemcpyAsync(w->tmp64, x0, sizeof(double) * n, cudaMemcpyDefault, st));
+        if (sizeof(Vec) == 8) {
+            L1LS_CUDA(cudaMemcpyAsync(w->X[0], w->tmp64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            L1LS_CUDA(cudaMemcpyAsync(w->X[1], w->tmp64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            k_d2ff<<<nb, 256, 0, st>>>(w->tmp64, n, w->Xh[0], w->Xl[0]);
+            k_d2ff<<<nb, 256, 0, st>>>(w->tmp64, n, w->Xh[1], w->Xl[1]);
         }
         // ||x0||_1 into the state, A x0 into ax (relabelled rows)
         L1LS_CUDA(cudaMemsetAsync(&w->st->cnt1, 0, sizeof(unsigned), st));
-        k_abs_sum<<<256, kBlock, 0, st>>>(w->X[0], n, w->part2, &w->st->cnt1, &w->st->l1_cur);
+        k_abs_sum<<<256, kBlock, 0, st>>>(w->tmp64, n, w->part2, &w->st->cnt1, &w->st->l1_cur);
         L1LS_CUDA(cudaGetLastError());
-        const void* xsrc = sizeof(Vec) == 8 ? (const void*)w->X[0] : (const void*)w->X32[0];
+        const void* xsrc = sizeof(Vec) == 8 ? (const void*)w->X[0] : (const void*)w->Xh[0];
         L1LS_TRY(spmv_plain(I, false, xsrc, sizeof(Vec) == 8 ? L1LS_F64 : L1LS_F32, w->ax, false, st));
         h.products = 1;
         L1LS_CUDA(cudaStreamSynchronize(st));
         L1LS_CUDA(cudaMemcpy(&h.l1_cur, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost));
     } else {
-        L1LS_CUDA(cudaMemsetAsync(w->X[0], 0, sizeof(double) * n, st));
-        L1LS_CUDA(cudaMemsetAsync(w->X[1], 0, sizeof(double) * n, st));
-        if (sizeof(Vec) == 4) {
-            L1LS_CUDA(cudaMemsetAsync(w->X32[0], 0, sizeof(float) * n, st));
-            L1LS_CUDA(cudaMemsetAsync(w->X32[1], 0, sizeof(float) * n, st));
+        if (sizeof(Vec) == 8) {
+            L1LS_CUDA(cudaMemsetAsync(w->X[0], 0, sizeof(double) * n, st));
+            L1LS_CUDA(cudaMemsetAsync(w->X[1], 0, sizeof(double) * n, st));
+        } else {
+            for (int k = 0; k < 2; ++k) {
+                L1LS_CUDA(cudaMemsetAsync(w->Xh[k], 0, sizeof(float) * n, st));
+                L1LS_CUDA(cudaMemsetAsync(w->Xl[k], 0, sizeof(float) * n, st));
+            }
         }
         L1LS_CUDA(cudaMemsetAsync(w->ax, 0, sizeof(Vec) * m, st));
         h.products = 0;
@@ -421,7 +494,16 @@ l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_stat
     L1LS_CUDA(cudaStreamSynchronize(st));
     const FistaState& f = *w->host_st;
     if (final_status == L1LS_OK) final_status = f.stop ? (l1ls_status)f.status : L1LS_ENOCONV;
-    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X[f.cert_iter & 1], sizeof(double) * I->n, cudaMemcpyDefault, st));
+    if (x_out) {
+        const int c = (int)(f.cert_iter & 1);
+        if (w->X[c]) {
+            L1LS_CUDA(cudaMemcpyAsync(x_out, w->X[c], sizeof(double) * I->n, cudaMemcpyDefault, st));
+        } else {
+            k_ff2d<<<(unsigned)((I->n + 255) / 256), 256, 0, st>>>(w->Xh[c], w->Xl[c], I->n, w->tmp64);
+            L1LS_CUDA(cudaGetLastError());
+            L1LS_CUDA(cudaMemcpyAsync(x_out, w->tmp64, sizeof(double) * I->n, cudaMemcpyDefault, st));
+        }
+    }
     L1LS_CUDA(cudaStreamSynchronize(st));
     w->active = false;
     if (res) {
