@@ -141,6 +141,23 @@ l1ls_status l1ls_matvec(const l1ls_inst* inst, const void* x, l1ls_dtype vec_dty
 /* x = A^T y (Algorithm MvPAt).  y: m entries, x: n entries, as for l1ls_matvec. */
 l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream);
 
+/* x = A^T y like l1ls_rmatvec, for callers that cannot allocate device memory: code that runs
+ * while a CUDA graph is being captured, real-time loops that must not block on the
+ * device-wide synchronisation cudaMalloc / cudaFree may imply, hosts that give the library a
+ * fixed memory budget.  (The paper has no counterpart; this is an interface of this library.)
+ *   y, x: DEVICE pointers only (m and n entries of vec_dtype, L1LS_F64 or L1LS_F32).
+ *   The one m-vector of scratch the product needs lives in a fixed array compiled into the
+ *   library: 2^20 doubles (8 MiB) held by every GPU that loads the library until the process
+ *   exits.  Instances with m > 2^20 are rejected with L1LS_EINVAL.
+ *   No cudaMalloc, cudaFree or other allocating call is made.  The first call on a device
+ *   looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents (every entry used is
+ *   written before it is read, so nothing needs clearing).  Calls whose work overlaps on the
+ *   GPU (different streams, or different threads) race on the array: order them.
+ *   Enqueued on `stream`; errors as for l1ls_rmatvec. */
+l1ls_status l1ls_rmatvec_noalloc(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream);
+
 /* Solver options.  Defaults (l1ls_solve_opts_default): tau 1, rel_gap_tol 1e-6,
  * max_iter 100000 (FISTA iterations; Newton steps for pdNCG), no time limit, mu 1e-5,
  * mu_min 1e-14, mu_start 1, pcg_rtol 0.1, pcg_max 1000, ls_max 50, armijo 1e-4,

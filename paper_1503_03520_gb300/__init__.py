@@ -81,6 +81,7 @@ _sig = {
     "l1ls_inst_export_t": (ctypes.c_int, [_P, _P, _P, _P]),
     "l1ls_matvec": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "l1ls_rmatvec": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    "l1ls_rmatvec_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "l1ls_solve_fista": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Result), _P]),
     "l1ls_solve_pdncg": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Result), _P]),
     "l1ls_fista_begin": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P]),
@@ -248,6 +249,10 @@ class Instance:
     def rmatvec(self, y, x=None, stream=None):
         """x = A^T y."""
         return self._product(lib.l1ls_rmatvec, y, x, self.n, stream)
+
+    def rmatvec_noalloc(self, y, x, stream=None):
+        """x = A^T y with device buffers and no allocation (fixed scratch, m <= 2^20)."""
+        return self._product(lib.l1ls_rmatvec_noalloc, y, x, self.n, stream)
 
     def _solve(self, fn, x0, x_out, stream, opts, allow):
         o = opts if isinstance(opts, SolveOpts) else solve_opts(**opts)

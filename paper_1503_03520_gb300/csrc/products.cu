@@ -2,6 +2,8 @@
 // matrix-free; here A is stored).  A is held as P1^T A, so
 //   A x   = P1 (P1^T A) x          : row rho of P1^T A lands in y[perm_inv[rho]],
 //   A^T y = (P1^T A)^T (P1^T y)    : (P1^T y)[rho] = y[perm_inv[rho]], gathered first.
+#include <mutex>
+
 #include "internal.h"
 #include "spmv.cuh"
 
@@ -130,4 +132,61 @@ extern "C" l1ls_status l1ls_matvec(const l1ls_inst* inst, const void* x, l1ls_dt
 
 extern "C" l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream) {
     return product_entry(inst, y, vec_dtype, x, stream, true);
+}
+
+// ---- x = A^T y without any allocation -------------------------------------------------------
+// For callers that cannot allocate device memory: code running while a CUDA graph is being
+// captured, real-time loops that must not synchronise the device (cudaMalloc / cudaFree can),
+// and hosts that hand the library a fixed memory budget.  l1ls_rmatvec needs one m-vector of
+// scratch (y gathered into the stored row order); here that scratch is a fixed-size array
+// in the device image of the library instead of a context staging buffer.
+namespace l1ls {
+namespace {
+
+constexpr int64_t kNoAllocMaxRows = int64_t(1) << 20;   // rows; 8 MiB per device
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxRows];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (the current device), looked up once.
+l1ls_status noalloc_scratch(int device, void** out) {
+    if (device < 0 || device >= kMaxDevices) return set_error(L1LS_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return L1LS_OK;
+}
+
+}  // namespace
+}  // namespace l1ls
+
+extern "C" l1ls_status l1ls_rmatvec_noalloc(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x,
+                                            void* stream) {
+    if (!inst || !y || !x) return set_error(L1LS_EINVAL, "NULL argument");
+    if (vec_dtype != L1LS_F64 && vec_dtype != L1LS_F32)
+        return set_error(L1LS_EINVAL, "vec_dtype must be L1LS_F64 or L1LS_F32");
+    const Inst* I = reinterpret_cast<const Inst*>(inst);
+    if (I->m > kNoAllocMaxRows)
+        return set_error(L1LS_EINVAL, "l1ls_rmatvec_noalloc supports m <= %lld rows (instance has m = %lld)",
+                         (long long)kNoAllocMaxRows, (long long)I->m);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    void* scratch = nullptr;
+    L1LS_TRY(noalloc_scratch(I->ctx->device, &scratch));
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned nb = (unsigned)((I->m + 255) / 256);
+    if (vec_dtype == L1LS_F64) {
+        k_gather<double><<<nb, 256, 0, st>>>((const double*)y, I->perm_inv, I->m, (double*)scratch);
+        L1LS_CUDA(cudaGetLastError());
+        return dispatch<double>(I, true, (const double*)scratch, (double*)x, nullptr, st);
+    }
+    k_gather<float><<<nb, 256, 0, st>>>((const float*)y, I->perm_inv, I->m, (float*)scratch);
+    L1LS_CUDA(cudaGetLastError());
+    return dispatch<float>(I, true, (const float*)scratch, (float*)x, nullptr, st);
 }
