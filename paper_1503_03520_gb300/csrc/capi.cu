@@ -265,8 +265,9 @@ l1ls_status l1ls_inst_export(const l1ls_inst* h, int64_t* row_ptr, int32_t* col_
     L1LS_CUDA(cudaSetDevice(I->ctx->device));
     L1LS_CUDA(cudaDeviceSynchronize());
     const int64_t m = I->m, n = I->n, nnz = I->nnz;
-    std::vector<int32_t> pm((size_t)m), ptr((size_t)m + 1), col((size_t)nnz);
+    std::vector<int32_t> pm((size_t)m), st((size_t)m), ptr((size_t)m + 1), col((size_t)nnz);
     L1LS_CUDA(cudaMemcpy(pm.data(), I->perm, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+    L1LS_CUDA(cudaMemcpy(st.data(), I->store_of_row, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
     if (row_ptr || col_idx || vals) {
         L1LS_CUDA(cudaMemcpy(ptr.data(), I->csr_ptr, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost));
         L1LS_CUDA(cudaMemcpy(col.data(), I->csr_col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
@@ -274,8 +275,8 @@ l1ls_status l1ls_inst_export(const l1ls_inst* h, int64_t* row_ptr, int32_t* col_
         L1LS_TRY(values_to_host(I, I->csr_val, nnz, v));
         int64_t o = 0;
         if (row_ptr) row_ptr[0] = 0;
-        for (int64_t i = 0; i < m; ++i) {           // row i of A = row perm[i] of P1^T A
-            const int64_t r = pm[i];
+        for (int64_t i = 0; i < m; ++i) {           // row i of A = stored row store_of_row[i]
+            const int64_t r = st[i];
             for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e, ++o) {
                 if (col_idx) col_idx[o] = col[e];
                 if (vals) vals[o] = v[e];
@@ -286,7 +287,7 @@ l1ls_status l1ls_inst_export(const l1ls_inst* h, int64_t* row_ptr, int32_t* col_
     if (b) {
         std::vector<double> bh((size_t)m);
         L1LS_CUDA(cudaMemcpy(bh.data(), I->bhat, sizeof(double) * m, cudaMemcpyDeviceToHost));
-        for (int64_t i = 0; i < m; ++i) b[i] = bh[pm[i]];
+        for (int64_t i = 0; i < m; ++i) b[i] = bh[st[i]];
     }
     if (xstar) L1LS_CUDA(cudaMemcpy(xstar, I->xstar, sizeof(double) * n, cudaMemcpyDeviceToHost));
     if (sigma) L1LS_CUDA(cudaMemcpy(sigma, I->sigma, sizeof(double) * I->nsq, cudaMemcpyDeviceToHost));
@@ -302,7 +303,7 @@ l1ls_status l1ls_inst_export_t(const l1ls_inst* h, int64_t* col_ptr, int32_t* ro
     L1LS_CUDA(cudaDeviceSynchronize());
     const int64_t m = I->m, n = I->n, nnz = I->nnz;
     std::vector<int32_t> pinv((size_t)m), ptr((size_t)n + 1), row((size_t)nnz);
-    L1LS_CUDA(cudaMemcpy(pinv.data(), I->perm_inv, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+    L1LS_CUDA(cudaMemcpy(pinv.data(), I->row_of_store, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
     L1LS_CUDA(cudaMemcpy(ptr.data(), I->csc_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
     L1LS_CUDA(cudaMemcpy(row.data(), I->csc_row, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
     std::vector<double> v;

@@ -401,6 +401,136 @@ __global__ void k_pair_cols(const int32_t* __restrict__ ptr, const int32_t* __re
     }
 }
 
+// ---- storage order of the row pairs ------------------------------------------------------
+// Pair p holds the rows perm[2p], perm[2p+1] of Sigma R^T.  Pairs are stored in the order of
+// the smaller of the two (pairs of two empty rows last), so consecutive stored pairs and the
+// columns that touch them meet nearby entries of the gathered vectors for one of their two
+// halves.  Any order of whole pairs describes the same problem (rows of A permuted).
+__global__ void k_pair_keys(const int32_t* __restrict__ perm, int64_t npairs, int64_t n, uint64_t* __restrict__ keys) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const int64_t a = perm[2 * p], b = perm[2 * p + 1];
+    const int64_t k = a < b ? a : b;
+    keys[p] = (uint64_t)(k < n ? k : n + p);
+}
+
+__global__ void k_qpos(const uint32_t* __restrict__ order, int64_t npairs, int32_t* __restrict__ qpos) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < npairs) qpos[order[r]] = (int32_t)r;
+}
+
+// entries per stored pair, in the new order
+__global__ void k_pair_counts(const int32_t* __restrict__ pptr, const uint32_t* __restrict__ order, int64_t npairs,
+                              int32_t* __restrict__ cnt) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < npairs) cnt[r] = pptr[order[r] + 1] - pptr[order[r]];
+}
+
+template <class V>
+__global__ void k_move_pair_rows(const int32_t* __restrict__ optr, const int32_t* __restrict__ ocol,
+                                 const V* __restrict__ oval, const uint32_t* __restrict__ order, int64_t npairs,
+                                 const int32_t* __restrict__ nptr, int32_t* __restrict__ ncol, V* __restrict__ nval) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= npairs) return;
+    const int64_t o = order[r];
+    const int32_t a = optr[o], c = optr[o + 1] - a, d = nptr[r];
+    for (int32_t k = 0; k < c; ++k) {
+        ncol[d + k] = ocol[a + k];
+        nval[2 * (int64_t)(d + k)] = oval[2 * (int64_t)(a + k)];
+        nval[2 * (int64_t)(d + k) + 1] = oval[2 * (int64_t)(a + k) + 1];
+    }
+}
+
+// plain rows 2r, 2r+1 <- 2 order[r], 2 order[r] + 1 (row pointers from the pair pointers)
+template <class V>
+__global__ void k_move_plain_rows(const int32_t* __restrict__ optr, const int32_t* __restrict__ ocol,
+                                  const V* __restrict__ oval, const uint32_t* __restrict__ order, int64_t npairs,
+                                  const int32_t* __restrict__ npptr, int32_t* __restrict__ nptr,
+                                  int32_t* __restrict__ ncol, V* __restrict__ nval) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > npairs) return;
+    nptr[2 * r] = 2 * npptr[r];
+    if (r == npairs) return;
+    const int64_t o = order[r];
+    const int32_t c = optr[2 * o + 1] - optr[2 * o];
+    nptr[2 * r + 1] = 2 * npptr[r] + c;
+    for (int t = 0; t < 2; ++t) {
+        const int32_t a = optr[2 * o + t], d = 2 * npptr[r] + t * c;
+        for (int32_t k = 0; k < c; ++k) {
+            ncol[d + k] = ocol[a + k];
+            nval[d + k] = oval[a + k];
+        }
+    }
+}
+
+// paired columns: pair index -> stored position, entries re-sorted by it
+template <class V>
+__global__ void k_remap_pair_cols(const int32_t* __restrict__ ptr, int32_t* __restrict__ pair, V* __restrict__ val2,
+                                  const int32_t* __restrict__ qpos, int64_t n) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int32_t a = ptr[j], c = ptr[j + 1] - a;
+    for (int32_t k = 0; k < c; ++k) pair[a + k] = qpos[pair[a + k]];
+    for (int32_t k = 1; k < c; ++k) {               // insertion sort (a column holds <= 16 pairs)
+        const int32_t key = pair[a + k];
+        const V v0 = val2[2 * (int64_t)(a + k)], v1 = val2[2 * (int64_t)(a + k) + 1];
+        int32_t q = k;
+        while (q > 0 && pair[a + q - 1] > key) {
+            pair[a + q] = pair[a + q - 1];
+            val2[2 * (int64_t)(a + q)] = val2[2 * (int64_t)(a + q - 1)];
+            val2[2 * (int64_t)(a + q) + 1] = val2[2 * (int64_t)(a + q - 1) + 1];
+            --q;
+        }
+        pair[a + q] = key;
+        val2[2 * (int64_t)(a + q)] = v0;
+        val2[2 * (int64_t)(a + q) + 1] = v1;
+    }
+}
+
+// plain columns: row q -> 2 qpos[q >> 1] + (q & 1), re-sorted (pairs stay adjacent)
+template <class V>
+__global__ void k_remap_plain_cols(const int32_t* __restrict__ ptr, int32_t* __restrict__ row, V* __restrict__ val,
+                                   const int32_t* __restrict__ qpos, int64_t n) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int32_t a = ptr[j], c = ptr[j + 1] - a;
+    for (int32_t k = 0; k < c; ++k) {
+        const int32_t q = row[a + k];
+        row[a + k] = 2 * qpos[q >> 1] + (q & 1);
+    }
+    for (int32_t k = 1; k < c; ++k) {
+        const int32_t key = row[a + k];
+        const V v = val[a + k];
+        int32_t q = k;
+        while (q > 0 && row[a + q - 1] > key) {
+            row[a + q] = row[a + q - 1];
+            val[a + q] = val[a + q - 1];
+            --q;
+        }
+        row[a + q] = key;
+        val[a + q] = v;
+    }
+}
+
+template <class T>
+__global__ void k_move_pair_entries(const T* __restrict__ in, const uint32_t* __restrict__ order, int64_t npairs,
+                                    T* __restrict__ out) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= npairs) return;
+    out[2 * r] = in[2 * (int64_t)order[r]];
+    out[2 * r + 1] = in[2 * (int64_t)order[r] + 1];
+}
+
+__global__ void k_store_maps(const int32_t* __restrict__ perm_inv, const uint32_t* __restrict__ order, int64_t m,
+                             int32_t* __restrict__ row_of_store, int32_t* __restrict__ store_of_row) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m) return;
+    const int64_t q = 2 * (int64_t)order[s >> 1] + (s & 1);
+    const int32_t i = perm_inv[q];
+    row_of_store[s] = i;
+    store_of_row[i] = (int32_t)s;
+}
+
 template <class V>
 __global__ void k_colnorm2(const int32_t* __restrict__ ptr, const V* __restrict__ vals, int64_t n,
                            double* __restrict__ out) {
@@ -482,6 +612,67 @@ l1ls_status cast_and_norms(Inst* I, const double* csc64, const double* csr64, cu
     return L1LS_OK;
 }
 
+l1ls_status argsort_stream(uint64_t seed, uint64_t tag, int64_t count, uint32_t* order, TempList& tmp,
+                           cudaStream_t st);
+
+template <class V>
+l1ls_status reorder_pairs(Inst* I, cudaStream_t st) {
+    const int64_t m = I->m, n = I->n, npairs = m / 2, nnz = I->nnz, np = nnz / 2;
+    TempList tmp(st);
+    uint64_t* keys = nullptr;
+    uint32_t* order = nullptr;
+    int32_t *qpos = nullptr, *cnt = nullptr, *nptr = nullptr, *ncol = nullptr, *nrptr = nullptr, *nrcol = nullptr;
+    V *nval = nullptr, *nrval = nullptr;
+    L1LS_TRY(tmp.get(&keys, npairs));
+    L1LS_TRY(tmp.get(&order, npairs));
+    L1LS_TRY(tmp.get(&qpos, npairs));
+    L1LS_TRY(tmp.get(&cnt, npairs));
+    L1LS_TRY(tmp.get(&nptr, npairs + 1));
+    L1LS_TRY(tmp.get(&ncol, np + kPad));
+    L1LS_TRY(tmp.get(&nval, 2 * (np + kPad)));
+    L1LS_TRY(tmp.get(&nrptr, m + 1));
+    L1LS_TRY(tmp.get(&nrcol, nnz + kPad));
+    L1LS_TRY(tmp.get(&nrval, nnz + kPad));
+    k_pair_keys<<<nblk(npairs), 256, 0, st>>>(I->perm, npairs, n, keys);
+    L1LS_CUDA(cudaGetLastError());
+    L1LS_TRY(radix_argsort_u64(keys, npairs, order, st));
+    k_qpos<<<nblk(npairs), 256, 0, st>>>(order, npairs, qpos);
+    k_pair_counts<<<nblk(npairs), 256, 0, st>>>(I->prow_ptr, order, npairs, cnt);
+    L1LS_CUDA(cudaGetLastError());
+    int64_t tot = 0;
+    L1LS_TRY(exclusive_scan_i32(cnt, npairs, nptr, &tot, st));
+    if (tot != np) return set_error(L1LS_ECUDA, "internal: pair reorder lost entries");
+    const V* pv = static_cast<const V*>(I->prow_val);
+    const V* rv = static_cast<const V*>(I->csr_val);
+    k_move_pair_rows<V><<<nblk(npairs), 256, 0, st>>>(I->prow_ptr, I->prow_col, pv, order, npairs, nptr, ncol, nval);
+    k_move_plain_rows<V><<<nblk(npairs + 1), 256, 0, st>>>(I->csr_ptr, I->csr_col, rv, order, npairs, nptr, nrptr,
+                                                            nrcol, nrval);
+    k_remap_pair_cols<V><<<nblk(n), 256, 0, st>>>(I->pcol_ptr, I->pcol_pair, static_cast<V*>(I->pcol_val), qpos, n);
+    k_remap_plain_cols<V><<<nblk(n), 256, 0, st>>>(I->csc_ptr, I->csc_row, static_cast<V*>(I->csc_val), qpos, n);
+    L1LS_CUDA(cudaGetLastError());
+    L1LS_CUDA(cudaMemcpyAsync(I->prow_ptr, nptr, sizeof(int32_t) * (npairs + 1), cudaMemcpyDeviceToDevice, st));
+    L1LS_CUDA(cudaMemcpyAsync(I->prow_col, ncol, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
+    L1LS_CUDA(cudaMemcpyAsync(I->prow_val, nval, sizeof(V) * 2 * np, cudaMemcpyDeviceToDevice, st));
+    L1LS_CUDA(cudaMemcpyAsync(I->csr_ptr, nrptr, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToDevice, st));
+    L1LS_CUDA(cudaMemcpyAsync(I->csr_col, nrcol, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
+    L1LS_CUDA(cudaMemcpyAsync(I->csr_val, nrval, sizeof(V) * nnz, cudaMemcpyDeviceToDevice, st));
+    // right-hand side in the stored order
+    double* nb = nullptr;
+    L1LS_TRY(tmp.get(&nb, m));
+    k_move_pair_entries<double><<<nblk(npairs), 256, 0, st>>>(I->bhat, order, npairs, nb);
+    L1LS_CUDA(cudaMemcpyAsync(I->bhat, nb, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    if (I->bhat32) {
+        float* nb32 = nullptr;
+        L1LS_TRY(tmp.get(&nb32, m));
+        k_move_pair_entries<float><<<nblk(npairs), 256, 0, st>>>(I->bhat32, order, npairs, nb32);
+        L1LS_CUDA(cudaMemcpyAsync(I->bhat32, nb32, sizeof(float) * m, cudaMemcpyDeviceToDevice, st));
+    }
+    k_store_maps<<<nblk(m), 256, 0, st>>>(I->perm_inv, order, m, I->row_of_store, I->store_of_row);
+    L1LS_CUDA(cudaGetLastError());
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    return L1LS_OK;
+}
+
 l1ls_status validate(const l1ls_gen_params* p) {
     if (!p) return set_error(L1LS_EINVAL, "params is NULL");
     if (p->m < 2 || p->n < 2) return set_error(L1LS_EINVAL, "m and n must be >= 2");
@@ -545,6 +736,8 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_CUDA(cudaMemsetAsync(I->bhat, 0, sizeof(double) * pad32(m), st));
         GEN_TRY(I->alloc_n(&I->perm, m));
         GEN_TRY(I->alloc_n(&I->perm_inv, m));
+        GEN_TRY(I->alloc_n(&I->store_of_row, m));
+        GEN_TRY(I->alloc_n(&I->row_of_store, m));
         GEN_TRY(I->alloc_n(&I->colnorm2, n));
         if (I->dtype != L1LS_F64) {
             GEN_TRY(I->alloc_n(&I->bhat32, pad32(m)));
@@ -651,6 +844,17 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
             default: GEN_TRY(cast_and_norms<__nv_bfloat16>(I, csc64, csr64, st)); break;
         }
         if (I->bhat32) k_to_f32<<<nblk(m), 256, 0, st>>>(I->bhat, m, I->bhat32);
+        GEN_CUDA(cudaGetLastError());
+        if (I->paired) {
+            switch (I->dtype) {
+                case L1LS_F64: GEN_TRY(reorder_pairs<double>(I, st)); break;
+                case L1LS_F32: GEN_TRY(reorder_pairs<float>(I, st)); break;
+                default: GEN_TRY(reorder_pairs<__nv_bfloat16>(I, st)); break;
+            }
+        } else {
+            GEN_CUDA(cudaMemcpyAsync(I->store_of_row, I->perm, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
+            GEN_CUDA(cudaMemcpyAsync(I->row_of_store, I->perm_inv, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
+        }
         GEN_CUDA(cudaGetLastError());
         int* tmax = nullptr;
         GEN_TRY(tmp.get(&tmax, 2));

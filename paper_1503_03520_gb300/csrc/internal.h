@@ -82,6 +82,9 @@ struct Inst {
     double* colnorm2 = nullptr; // diag(A^T A) from the stored values
     int32_t* perm = nullptr;    // P: (P v)_i = v_{perm[i]}
     int32_t* perm_inv = nullptr;
+    // storage order of the rows: row i of A is stored as row store_of_row[i]
+    int32_t* store_of_row = nullptr;
+    int32_t* row_of_store = nullptr;
     double f_star = 0, lipschitz = 1, lam_max = 0;
     int64_t csr_tile_max = 0, csc_tile_max = 0;   // most nonzeros in a 32-row tile
     int* dev_err = nullptr;                       // set by kernels whose bounded waits expired

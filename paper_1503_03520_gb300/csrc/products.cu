@@ -1,7 +1,8 @@
 // Plain products y = A x and x = A^T y (Algorithms MvPA / MvPAt compute the same products
-// matrix-free; here A is stored).  A is held as P1^T A, so
-//   A x   = P1 (P1^T A) x          : row rho of P1^T A lands in y[perm_inv[rho]],
-//   A^T y = (P1^T A)^T (P1^T y)    : (P1^T y)[rho] = y[perm_inv[rho]], gathered first.
+// matrix-free; here A is stored).  A is held with its rows in a storage order (row s of the
+// stored matrix is row row_of_store[s] of A), so
+//   A x   : stored row s lands in y[row_of_store[s]],
+//   A^T y : y is first gathered into the storage order, ys[s] = y[row_of_store[s]].
 #include <mutex>
 
 #include "internal.h"
@@ -81,7 +82,7 @@ l1ls_status spmv_plain(const Inst* I, bool transpose, const void* in, int vec_dt
                        cudaStream_t st) {
     const size_t es = vec_dtype == L1LS_F64 ? 8 : 4;
     if (!transpose) {
-        const int32_t* op = unpermute_rows ? I->perm_inv : nullptr;
+        const int32_t* op = unpermute_rows ? I->row_of_store : nullptr;
         if (vec_dtype == L1LS_F64) return dispatch<double>(I, false, (const double*)in, (double*)out, op, st);
         return dispatch<float>(I, false, (const float*)in, (float*)out, op, st);
     }
@@ -90,8 +91,8 @@ l1ls_status spmv_plain(const Inst* I, bool transpose, const void* in, int vec_dt
         void* scratch = nullptr;
         L1LS_TRY(I->ctx->staging(2, es * (size_t)I->m, &scratch));
         unsigned nb = (unsigned)((I->m + 255) / 256);
-        if (vec_dtype == L1LS_F64) k_gather<double><<<nb, 256, 0, st>>>((const double*)in, I->perm_inv, I->m, (double*)scratch);
-        else k_gather<float><<<nb, 256, 0, st>>>((const float*)in, I->perm_inv, I->m, (float*)scratch);
+        if (vec_dtype == L1LS_F64) k_gather<double><<<nb, 256, 0, st>>>((const double*)in, I->row_of_store, I->m, (double*)scratch);
+        else k_gather<float><<<nb, 256, 0, st>>>((const float*)in, I->row_of_store, I->m, (float*)scratch);
         L1LS_CUDA(cudaGetLastError());
         src = scratch;
     }
@@ -182,11 +183,11 @@ extern "C" l1ls_status l1ls_rmatvec_noalloc(const l1ls_inst* inst, const void* y
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned nb = (unsigned)((I->m + 255) / 256);
     if (vec_dtype == L1LS_F64) {
-        k_gather<double><<<nb, 256, 0, st>>>((const double*)y, I->perm_inv, I->m, (double*)scratch);
+        k_gather<double><<<nb, 256, 0, st>>>((const double*)y, I->row_of_store, I->m, (double*)scratch);
         L1LS_CUDA(cudaGetLastError());
         return dispatch<double>(I, true, (const double*)scratch, (double*)x, nullptr, st);
     }
-    k_gather<float><<<nb, 256, 0, st>>>((const float*)y, I->perm_inv, I->m, (float*)scratch);
+    k_gather<float><<<nb, 256, 0, st>>>((const float*)y, I->row_of_store, I->m, (float*)scratch);
     L1LS_CUDA(cudaGetLastError());
     return dispatch<float>(I, true, (const float*)scratch, (float*)x, nullptr, st);
 }
