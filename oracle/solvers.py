@@ -82,8 +82,13 @@ def soft_threshold(v, t):
     return np.sign(v) * np.maximum(np.abs(v) - t, 0.0)
 
 
-def fista(A, b, tau, L, tol, max_iter, x0=None):
-    """FISTA with the certificate above.  Returns dict(x, iters, products, P, D, gap, rel_gap, status)."""
+def fista(A, b, tau, L, tol, max_iter, x0=None, restart=False):
+    """FISTA with the certificate above.  Returns dict(x, x_next, iters, products, P, D, gap,
+    rel_gap, status, restarts).
+
+    restart=True adds the gradient restart of O'Donoghue & Candes (2015, "Adaptive restart for
+    accelerated gradient schemes"), not used by the paper: when (y_k - x_k)^T (x_k - x_{k-1}) > 0
+    the momentum is dropped (t <- 1, so y_{k+1} = x_k)."""
     n = A.shape[1]
     x_cur = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)   # x_{k-1}
     x_old = x_cur.copy()                                                              # x_{k-2}
@@ -93,6 +98,7 @@ def fista(A, b, tau, L, tol, max_iter, x0=None):
     beta = 0.0
     best_D = -math.inf
     k = 1
+    restarts = 0
     while True:
         u = A @ x_cur                                   # A x_{k-1}
         P = tau * np.abs(x_cur).sum() + 0.5 * float((u - b) @ (u - b))
@@ -104,13 +110,19 @@ def fista(A, b, tau, L, tol, max_iter, x0=None):
         best_D = max(best_D, dual_value(b, r, g, tau))
         gap = P - best_D
         rel = gap / max(abs(P), TINY)
-        if rel <= tol or k - 1 >= max_iter:
-            return dict(x=x_cur, iters=k - 1, products=products, P=P, D=best_D, gap=gap,
-                        rel_gap=rel, status=STATUS_OK if rel <= tol else STATUS_NOCONV)
         x_new = soft_threshold(y + g / L, tau / L)
-        t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
-        beta = (t - 1.0) / t_new
-        t = t_new
+        if rel <= tol or k - 1 >= max_iter:
+            # x_next: the prox-gradient step from y_k, one past the certified iterate
+            return dict(x=x_cur, x_next=x_new, iters=k - 1, products=products, P=P, D=best_D, gap=gap,
+                        rel_gap=rel, status=STATUS_OK if rel <= tol else STATUS_NOCONV, restarts=restarts)
+        if restart and float((y - x_new) @ (x_new - x_cur)) > 0.0:
+            t = 1.0
+            beta = 0.0
+            restarts += 1
+        else:
+            t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
+            beta = (t - 1.0) / t_new
+            t = t_new
         x_old, x_cur = x_cur, x_new
         Ax_old = u
         k += 1

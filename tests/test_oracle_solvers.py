@@ -126,3 +126,42 @@ def test_planted_dual_scaling_error_is_caught(monkeypatch):
     y = np.zeros(32)
     r = b - A @ y
     assert solvers.dual_value(b, r, A.T @ r, 1.0) > inst.f_star
+
+
+def test_fista_restart_recursion_written_out():
+    """The gradient restart (O'Donoghue & Candes 2015) written out from its rule: after the
+    prox step from y, if (y - x_new)^T (x_new - x) > 0 the momentum is dropped (t = 1)."""
+    inst = _small(seed=6, kappa=100.0, m=24, n=12, right=2)
+    A, b, L, tau = inst.A.toarray(), inst.b, inst.lipschitz, 0.3
+    x, x_prev, t, beta, nres = np.zeros(12), np.zeros(12), 1.0, 0.0, 0
+    for _ in range(1000):
+        y = x + beta * (x - x_prev)
+        xn = solvers.soft_threshold(y - A.T @ (A @ y - b) / L, tau / L)
+        if (y - xn) @ (xn - x) > 0:
+            t, beta, nres = 1.0, 0.0, nres + 1
+        else:
+            t_new = (1 + math.sqrt(1 + 4 * t * t)) / 2
+            beta, t = (t - 1) / t_new, t_new
+        x_prev, x = x, xn
+    r = solvers.fista(inst.A, b, tau, L, 0.0, 1000, restart=True)
+    assert nres >= 2 and r["restarts"] == nres
+    assert np.allclose(r["x"], x, atol=1e-12)
+
+
+@pytest.mark.parametrize("tau_factor", [1.0, 0.4])
+def test_fista_restart_reaches_brute_force_optimum(tau_factor):
+    inst = _small(seed=7, right=2, kappa=300.0)
+    xb, fb = brute_force(inst.A, inst.b, tau_factor)
+    r = solvers.fista(inst.A, inst.b, tau_factor, inst.lipschitz, 1e-12, 200000, restart=True)
+    assert r["status"] == 0
+    assert np.allclose(r["x"], xb, atol=1e-4)
+    assert math.isclose(r["P"], fb, rel_tol=1e-11)
+
+
+def test_fista_next_iterate_is_one_prox_step_past_the_certified_one():
+    """x_next (the warm start of the next tau of a path) is the prox-gradient step from y_k:
+    stopping one iteration later returns it as the certified iterate."""
+    inst = generate(GenParams(m=256, n=128, seed=8, kappa=100.0, right_stages=2, xstar_frac=0.05))
+    a = solvers.fista(inst.A, inst.b, 0.5, inst.lipschitz, 0.0, 17)
+    c = solvers.fista(inst.A, inst.b, 0.5, inst.lipschitz, 0.0, 18)
+    assert np.array_equal(a["x_next"], c["x"])
