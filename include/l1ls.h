@@ -39,6 +39,7 @@ extern "C" {
 
 typedef struct l1ls_ctx l1ls_ctx;     /* one GPU: streams, work buffers, memory budget      */
 typedef struct l1ls_inst l1ls_inst;   /* a generated instance resident in device memory     */
+typedef struct l1ls_batch l1ls_batch; /* a ragged batch of instances solved together         */
 
 typedef enum {
     L1LS_OK = 0,
@@ -172,7 +173,13 @@ typedef struct {
     double mu, mu_min, mu_start, pcg_rtol, armijo;
     int32_t ls_max, pcg_max;
     int32_t check_every;      /* iterations per graph launch between host checks          */
-    int32_t reserved;
+    int32_t restart;          /* FISTA: 1 = gradient restart of O'Donoghue & Candes (t <- 1 when
+                                 (y_k - x_k)^T (x_k - x_{k-1}) > 0); 0 = none, as in the paper  */
+    int32_t accum;            /* FISTA, FP32 / BF16 values in paired storage: 0 = products summed
+                                 in FP32 (the default); 1 = products of the float-float iterate and
+                                 residual summed in float-float (about 44 bits), for gaps below
+                                 the FP32 floor at small tau or large kappa.  EINVAL otherwise.
+                                 Batches always use 1.                                         */
 } l1ls_solve_opts;
 
 void l1ls_solve_opts_default(l1ls_solve_opts* o);
@@ -220,6 +227,30 @@ l1ls_status l1ls_fista_end(l1ls_inst* inst, double* x_out, l1ls_result* res, voi
  * with the same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista. */
 l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
                              l1ls_result* res, void* stream);
+
+/* Ragged batches and tau paths (the regularisation study of Sec. 8.8 as a workload).
+ *   l1ls_batch_create   groups `count` instances of one context that have one left stage and
+ *                       FP32 or BF16 values (all the same); it allocates their iterates and
+ *                       the batch tables (counted in the context budget).  The instances must
+ *                       outlive the batch.
+ *   l1ls_batch_solve_path  solves every instance i along its path taus[i*ntau .. i*ntau+ntau-1]
+ *                       with FISTA (as l1ls_solve_fista: o->rel_gap_tol, o->max_iter per tau,
+ *                       o->time_limit_s for the whole call; o->tau is ignored), all instances in
+ *                       one persistent cooperative kernel per o->check_every FISTA steps.  The
+ *                       first tau starts from 0; each later tau starts from the last iterate of
+ *                       the previous one (one prox-gradient step past the certified iterate).
+ *                       results: count*ntau entries (instance-major), filled per tau; x_out: NULL
+ *                       or count pointers (each NULL, device or host; n doubles) receiving the
+ *                       certified solution at the last tau.  An instance's results do not depend
+ *                       on the other instances of the batch or on the kernel schedule.  Blocking.
+ *   l1ls_batch_get_schedule  block size chosen by the built-in autotuner (0 before the first
+ *                       solve) and the time of its two probe steps per candidate (ms).
+ * Errors: EINVAL, ENOMEM, ECUDA (including an expired bounded grid barrier), ETIMEOUT. */
+l1ls_status l1ls_batch_create(l1ls_ctx* ctx, int count, l1ls_inst* const* insts, l1ls_batch** out);
+l1ls_status l1ls_batch_solve_path(l1ls_batch* batch, const double* taus, int ntau, const l1ls_solve_opts* o,
+                                  l1ls_result* results, double* const* x_out, void* stream);
+l1ls_status l1ls_batch_get_schedule(const l1ls_batch* batch, int* block, double* tune_ms_256, double* tune_ms_128);
+l1ls_status l1ls_batch_free(l1ls_batch* batch);
 
 /* Thread-local message describing the last non-OK status returned on this thread. */
 const char* l1ls_last_error(void);

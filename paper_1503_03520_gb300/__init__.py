@@ -41,7 +41,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("rel_gap_tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("time_limit_s", ctypes.c_double), ("mu", ctypes.c_double), ("mu_min", ctypes.c_double),
                 ("mu_start", ctypes.c_double), ("pcg_rtol", ctypes.c_double), ("armijo", ctypes.c_double), ("ls_max", ctypes.c_int32),
-                ("pcg_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("pcg_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("accum", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -87,6 +88,12 @@ _sig = {
     "l1ls_fista_begin": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P]),
     "l1ls_fista_step": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
     "l1ls_fista_end": (ctypes.c_int, [_P, _P, ctypes.POINTER(Result), _P]),
+    "l1ls_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "l1ls_batch_solve_path": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                             ctypes.POINTER(SolveOpts), _P, _P, _P]),
+    "l1ls_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]),
+    "l1ls_batch_free": (ctypes.c_int, [_P]),
     "l1ls_gen_params_default": (None, [ctypes.POINTER(GenParams)]),
     "l1ls_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "l1ls_last_error": (ctypes.c_char_p, []),
@@ -291,6 +298,53 @@ class Instance:
     def solve_pdncg(self, x0=None, x_out=None, stream=None, allow=(4, 5), **opts):
         """Primal-dual Newton-CG to the duality-gap tolerance; returns (x, result dict)."""
         return self._solve(lib.l1ls_solve_pdncg, x0, x_out, stream, opts, allow)
+
+
+class Batch:
+    """A ragged batch of instances (paired storage, FP32 or BF16 values) solved together."""
+
+    def __init__(self, ctx, instances):
+        self.ctx = ctx
+        self.instances = list(instances)
+        arr = (_P * len(self.instances))(*[i._h for i in self.instances])
+        h = _P()
+        _check(lib.l1ls_batch_create(ctx._h, len(self.instances), arr, ctypes.byref(h)))
+        self._h = h
+
+    def solve_path(self, taus, x_out=None, stream=None, allow=(4, 5), **opts):
+        """taus: (count, ntau) array.  Returns a list (per instance) of lists (per tau) of result dicts."""
+        t = np.ascontiguousarray(np.asarray(taus, dtype=np.float64))
+        count, ntau = t.shape
+        o = solve_opts(**opts)
+        res = (Result * (count * ntau))()
+        xs = None
+        keep = []
+        if x_out is not None:
+            ptrs = []
+            for v in x_out:
+                if v is None:
+                    ptrs.append(None)
+                else:
+                    p, _, k = _vec_ptr(v)
+                    keep.append(k)
+                    ptrs.append(p.value)
+            xs = (_P * count)(*ptrs)
+        st = lib.l1ls_batch_solve_path(self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ntau,
+                                       ctypes.byref(o), res, xs, _stream_ptr(stream))
+        _check(st, allow=allow)
+        return [[res[i * ntau + j].as_dict() for j in range(ntau)] for i in range(count)]
+
+    def schedule(self):
+        b = ctypes.c_int()
+        a = ctypes.c_double()
+        c = ctypes.c_double()
+        _check(lib.l1ls_batch_get_schedule(self._h, ctypes.byref(b), ctypes.byref(a), ctypes.byref(c)))
+        return {"block": b.value, "probe_ms_256": a.value, "probe_ms_128": c.value}
+
+    def free(self):
+        if self._h:
+            _check(lib.l1ls_batch_free(self._h))
+            self._h = None
 
 
 def version():

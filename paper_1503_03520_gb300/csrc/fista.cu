@@ -38,6 +38,8 @@ struct FistaState {
     double P, D, gap, rel;
     int32_t stop, status;
     unsigned cnt1, cnt2;
+    int32_t restart, pad;
+    int64_t restarts;
 };
 
 template <class V, class Vec>
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
     }
 }
 
-__device__ void fista_finalize(FistaState* st, double amax, double l1_new) {
+__device__ void fista_finalize(FistaState* st, double amax, double l1_new, double restart_test) {
     const double tau = st->tau;
     const double P = __dadd_rn(__dmul_rn(tau, st->l1_cur), __dmul_rn(0.5, st->k1[0]));
     const double s = amax <= tau ? 1.0 : tau / amax;
@@ -150,10 +152,16 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new) {
         st->status = L1LS_ENOCONV;
         st->stop = 1;
     } else {
-        const double t = st->t;
-        const double tn = __dmul_rn(0.5, __dadd_rn(1.0, sqrt(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
-        st->beta = (t - 1.0) / tn;
-        st->t = tn;
+        if (st->restart && restart_test > 0.0) {     // momentum against the step: drop it
+            st->t = 1.0;
+            st->beta = 0.0;
+            st->restarts += 1;
+        } else {
+            const double t = st->t;
+            const double tn = __dmul_rn(0.5, __dadd_rn(1.0, sqrt(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, t), t)))));
+            st->beta = (t - 1.0) / tn;
+            st->t = tn;
+        }
         st->l1_cur = l1_new;
         st->iter += 1;
     }
@@ -163,15 +171,16 @@ template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<Acc, kBlock> sm;
-    __shared__ double red[2 * 32];
+    __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const double invL = 1.0 / L, thr = tau / L;
-    double p[2] = {0.0, 0.0};
+    const bool rs = a.st->restart != 0;
+    double p[3] = {0.0, 0.0, 0.0};
     if constexpr (sizeof(Vec) == 4) {
         const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(invL), thr_f = ff_from_double(thr);
         float gmax = 0.0f;
-        ff l1 = {0.0f, 0.0f};
+        ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
         struct Ops {
             ff x1, x0;
         };
@@ -193,9 +202,11 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
                 a.xol[j] = xn.lo;
                 gmax = fmaxf(gmax, fabsf(g));
                 l1 = ff_add(l1, ff_abs(xn));
+                if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
             });
         p[0] = (double)gmax;
         p[1] = ff_to_double(l1);
+        p[2] = ff_to_double(rt);
     } else {
         struct Ops {
             double x1, x0;
@@ -217,12 +228,139 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
                 a.xo[j] = xn;
                 p[0] = fmax(p[0], fabs(g));
                 p[1] += fabs(xn);
+                if (rs) p[2] += (y - xn) * (xn - o.x1);
             });
     }
-    block_reduce<kBlock, 2>(p, 1u, red);
-    double tot[2];
-    if (grid_reduce_last<kBlock, 2>(p, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
-        fista_finalize(a.st, tot[0], tot[1]);
+    block_reduce<kBlock, 3>(p, 1u, red);
+    double tot[3];
+    if (grid_reduce_last<kBlock, 3>(p, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
+        fista_finalize(a.st, tot[0], tot[1], tot[2]);
+}
+
+// ---- compensated kernels (opts.accum = 1; FP32 / BF16 values in paired storage) ----------
+// The same two kernels with both products accumulated in float-float (pcsr_tile_ff): K1
+// gathers the high and low words of x_{k-1}, keeps A x in float-float and writes the residual
+// of each row pair as one float4 {hi, hi, lo, lo}; K2 gathers it and forms A^T r in
+// float-float.  FP32 sums of the products put a floor of about 1e-5 .. 1e-2 under the relative
+// gap at small tau (the residual is a small difference of large terms, and its rounding error
+// does not shrink with the objective); these kernels remove that floor at about twice the
+// arithmetic and 16 more bytes per row and 4 more per gathered column of traffic.
+
+template <class V>
+struct K1CArgs {
+    const int32_t* ptr;
+    const int32_t* col;
+    const V* val;
+    const float* xh;     // x_{k-1}, float-float
+    const float* xl;
+    float2* ax;          // in: A x_{k-2}; out: A x_{k-1} (float-float)
+    float4* res;         // out: r_k per row pair
+    const float* b;
+    double* partials;
+    FistaState* st;
+    int64_t m;
+};
+
+template <class V>
+struct K2CArgs {
+    const int32_t* ptr;
+    const int32_t* pair;
+    const V* val;
+    const float4* res;
+    const float* xch;
+    const float* xcl;
+    float* xoh;
+    float* xol;
+    double* partials;
+    FistaState* st;
+    int64_t n;
+};
+
+template <class V>
+__global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
+    __shared__ CompSmem<kBlock> sm;
+    __shared__ double red[3 * 32];
+    if (*(volatile int32_t*)&a.st->stop) return;
+    const ff beta = ff_from_double(a.st->beta);
+    float* resf = reinterpret_cast<float*>(a.res);
+    ff q[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    struct Ops {
+        ff axo;
+        float bb;
+    };
+    auto pre = [&](int64_t r, bool has) {
+        Ops o{{0.f, 0.f}, 0.f};
+        if (has) {
+            const float2 v = a.ax[r];
+            o.axo = {v.x, v.y};
+            o.bb = a.b[r];
+        }
+        return o;
+    };
+    auto epi = [&](int64_t r, ff u, const Ops& o) {
+        const ff ay = ff_add(u, ff_mul(beta, ff_sub(u, o.axo)));
+        const ff rr = ff_sub(ff_from_float(o.bb), ay);
+        a.ax[r] = make_float2(u.hi, u.lo);
+        resf[4 * (r >> 1) + (r & 1)] = rr.hi;
+        resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
+        const ff d = ff_sub(u, ff_from_float(o.bb));
+        q[0] = ff_add(q[0], ff_mul(d, d));
+        q[1] = ff_add(q[1], ff_mul(ff_from_float(o.bb), rr));
+        q[2] = ff_add(q[2], ff_mul(rr, rr));
+    };
+    const int64_t npairs = a.m / 2;
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (npairs + 31) >> 5;
+    for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
+        pcsr_tile_ff<true, V>(t, a.ptr, a.col, a.val, a.xh, a.xl, nullptr, npairs, sm.warp_buf(), pre, epi);
+    double p[3] = {ff_to_double(q[0]), ff_to_double(q[1]), ff_to_double(q[2])};
+    block_reduce<kBlock, 3>(p, 0u, red);
+    double tot[3];
+    if (grid_reduce_last<kBlock, 3>(p, 0u, a.partials, &a.st->cnt1, tot, red) && threadIdx.x == 0) {
+        a.st->k1[0] = tot[0];
+        a.st->k1[1] = tot[1];
+        a.st->k1[2] = tot[2];
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
+    __shared__ CompSmem<kBlock> sm;
+    __shared__ double red[3 * 32];
+    if (*(volatile int32_t*)&a.st->stop) return;
+    const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
+    const bool rs = a.st->restart != 0;
+    const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
+    float gmax = 0.0f;
+    ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
+    struct Ops {
+        ff x1, x0;
+    };
+    auto pre = [&](int64_t j, bool has) {
+        Ops o{{0.f, 0.f}, {0.f, 0.f}};
+        if (has) {
+            o.x1 = {a.xch[j], a.xcl[j]};
+            o.x0 = {a.xoh[j], a.xol[j]};
+        }
+        return o;
+    };
+    auto epi = [&](int64_t j, ff g, const Ops& o) {
+        const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
+        const ff v = ff_add(y, ff_mul(g, invL_f));
+        const ff xn = ff_soft_threshold(v, thr_f);
+        a.xoh[j] = xn.hi;
+        a.xol[j] = xn.lo;
+        gmax = fmaxf(gmax, fabsf(g.hi));
+        l1 = ff_add(l1, ff_abs(xn));
+        if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+    };
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (a.n + 31) >> 5;
+    for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
+        pcsr_tile_ff<false, V>(t, a.ptr, a.pair, a.val, nullptr, nullptr, a.res, a.n, sm.warp_buf(), pre, epi);
+    double p[3] = {(double)gmax, ff_to_double(l1), ff_to_double(rt)};
+    block_reduce<kBlock, 3>(p, 1u, red);
+    double tot[3];
+    if (grid_reduce_last<kBlock, 3>(p, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
+        fista_finalize(a.st, tot[0], tot[1], tot[2]);
 }
 
 __global__ void k_abs_sum(const double* __restrict__ x, int64_t n, double* __restrict__ partials,
@@ -267,6 +405,11 @@ struct FistaWork {
     double* tmp64 = nullptr;             // FP64 staging of x0 / x_out
     void* ax = nullptr;
     void* res = nullptr;
+    float2* ax_ff = nullptr;             // compensated kernels: A x and the pair residual
+    float4* res_ff = nullptr;
+    int grid1c = 0, grid2c = 0;
+    bool comp = false;                   // this run uses the compensated kernels
+    int exec_comp = -1;
     double* part1 = nullptr;
     double* part2 = nullptr;
     FistaState* st = nullptr;
@@ -342,15 +485,65 @@ l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     return L1LS_OK;
 }
 
+template <class V>
+void enqueue_k1c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
+    K1CArgs<V> a;
+    a.ptr = I->prow_ptr;
+    a.col = I->prow_col;
+    a.val = static_cast<const V*>(I->prow_val);
+    a.xh = w->Xh[parity];
+    a.xl = w->Xl[parity];
+    a.ax = w->ax_ff;
+    a.res = w->res_ff;
+    a.b = I->bhat32;
+    a.partials = w->part1;
+    a.st = w->st;
+    a.m = I->m;
+    k_fista_k1c<V><<<w->grid1c, kBlock, 0, st>>>(a);
+}
+
+template <class V>
+void enqueue_k2c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
+    const int c = parity, o = 1 - parity;
+    K2CArgs<V> a;
+    a.ptr = I->pcol_ptr;
+    a.pair = I->pcol_pair;
+    a.val = static_cast<const V*>(I->pcol_val);
+    a.res = w->res_ff;
+    a.xch = w->Xh[c];
+    a.xcl = w->Xl[c];
+    a.xoh = w->Xh[o];
+    a.xol = w->Xl[o];
+    a.partials = w->part2;
+    a.st = w->st;
+    a.n = I->n;
+    k_fista_k2c<V><<<w->grid2c, kBlock, 0, st>>>(a);
+}
+
+template <class V, class Vec>
+l1ls_status enqueue_one(Inst* I, FistaWork* w, int parity, int which, cudaStream_t st) {
+    if constexpr (sizeof(Vec) == 4) {
+        if (w->comp) {
+            if (which == 0) enqueue_k1c<V>(I, w, parity, st);
+            else enqueue_k2c<V>(I, w, parity, st);
+            return L1LS_OK;
+        }
+    }
+    return which == 0 ? enqueue_k1<V, Vec>(I, w, parity, st) : enqueue_k2<V, Vec>(I, w, parity, st);
+}
+
 template <class V, class Vec>
 l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
-    L1LS_TRY(enqueue_k1<V, Vec>(I, w, parity, st));
-    return enqueue_k2<V, Vec>(I, w, parity, st);
+    L1LS_TRY((enqueue_one<V, Vec>(I, w, parity, 0, st)));
+    return enqueue_one<V, Vec>(I, w, parity, 1, st);
 }
 
 template <class V, class Vec>
 l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStream_t st) {
     const int64_t m = I->m, n = I->n;
+    if (o->accum != 0 && (sizeof(Vec) == 8 || !I->paired))
+        return set_error(L1LS_EINVAL, "accum = 1 (float-float products) needs FP32 or BF16 values in paired storage");
+    if (o->accum != 0 && o->accum != 1) return set_error(L1LS_EINVAL, "accum must be 0 or 1");
     FistaWork* w = static_cast<FistaWork*>(I->fista_work);
     if (!w) {
         w = new FistaWork();
@@ -376,7 +569,7 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
             w->grid2 = grid_of(I, k_fista_k2<V, Vec, false>, n);
         }
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
-        L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 2 + 1024));
+        L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 3 + 1024));
         L1LS_TRY(I->alloc_n(&w->st, 1));
         L1LS_CUDA(cudaMallocHost((void**)&w->host_st, sizeof(FistaState)));
         for (int k = 0; k < 2; ++k) {
@@ -385,6 +578,15 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
             L1LS_CUDA(cudaEventCreate(&w->ev[k][2]));
         }
     }
+    if constexpr (sizeof(Vec) == 4) {
+        if (o->accum == 1 && !w->ax_ff) {
+            L1LS_TRY(I->alloc_n(&w->ax_ff, pad32(m)));
+            L1LS_TRY(I->alloc_n(&w->res_ff, pad32(m) / 2 + 1));
+            w->grid1c = grid_of(I, k_fista_k1c<V>, m / 2);
+            w->grid2c = grid_of(I, k_fista_k2c<V>, n);
+        }
+    }
+    w->comp = o->accum == 1;
     FistaState h{};
     h.tau = o->tau;
     h.L = I->lipschitz;
@@ -397,6 +599,8 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     h.cert_iter = 0;
     h.stop = 0;
     h.status = L1LS_OK;
+    h.restart = o->restart;
+    h.restarts = 0;
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (x0) {
         // x0 (device or host FP64) -> FP64 staging -> iterate buffers
@@ -412,9 +616,15 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         L1LS_CUDA(cudaMemsetAsync(&w->st->cnt1, 0, sizeof(unsigned), st));
         k_abs_sum<<<256, kBlock, 0, st>>>(w->tmp64, n, w->part2, &w->st->cnt1, &w->st->l1_cur);
         L1LS_CUDA(cudaGetLastError());
-        const void* xsrc = sizeof(Vec) == 8 ? (const void*)w->X[0] : (const void*)w->Xh[0];
-        L1LS_TRY(spmv_plain(I, false, xsrc, sizeof(Vec) == 8 ? L1LS_F64 : L1LS_F32, w->ax, false, st));
-        h.products = 1;
+        if (w->comp) {
+            // beta_1 = 0: A x_{k-2} is not used at k = 1 (any finite value will do)
+            L1LS_CUDA(cudaMemsetAsync(w->ax_ff, 0, sizeof(float2) * m, st));
+            h.products = 0;
+        } else {
+            const void* xsrc = sizeof(Vec) == 8 ? (const void*)w->X[0] : (const void*)w->Xh[0];
+            L1LS_TRY(spmv_plain(I, false, xsrc, sizeof(Vec) == 8 ? L1LS_F64 : L1LS_F32, w->ax, false, st));
+            h.products = 1;
+        }
         L1LS_CUDA(cudaStreamSynchronize(st));
         L1LS_CUDA(cudaMemcpy(&h.l1_cur, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost));
     } else {
@@ -428,6 +638,7 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
             }
         }
         L1LS_CUDA(cudaMemsetAsync(w->ax, 0, sizeof(Vec) * m, st));
+        if (w->comp) L1LS_CUDA(cudaMemsetAsync(w->ax_ff, 0, sizeof(float2) * m, st));
         h.products = 0;
         h.l1_cur = 0.0;
     }
@@ -460,9 +671,9 @@ l1ls_status step(Inst* I, int64_t iters, float* kernel_ms, cudaStream_t st) {
                 acc[1] += b;
             }
             L1LS_CUDA(cudaEventRecord(e[0], st));
-            L1LS_TRY(enqueue_k1<V, Vec>(I, w, parity, st));
+            L1LS_TRY((enqueue_one<V, Vec>(I, w, parity, 0, st)));
             L1LS_CUDA(cudaEventRecord(e[1], st));
-            L1LS_TRY(enqueue_k2<V, Vec>(I, w, parity, st));
+            L1LS_TRY((enqueue_one<V, Vec>(I, w, parity, 1, st)));
             L1LS_CUDA(cudaEventRecord(e[2], st));
         } else {
             L1LS_TRY(enqueue_iteration<V, Vec>(I, w, parity, st));
@@ -529,7 +740,7 @@ l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_stat
 
 template <class V, class Vec>
 l1ls_status graph_for(Inst* I, FistaWork* w, int chunk) {
-    if (w->exec && w->exec_chunk == chunk) return L1LS_OK;
+    if (w->exec && w->exec_chunk == chunk && w->exec_comp == (int)w->comp) return L1LS_OK;
     if (w->exec) {
         cudaGraphExecDestroy(w->exec);
         w->exec = nullptr;
@@ -548,6 +759,7 @@ l1ls_status graph_for(Inst* I, FistaWork* w, int chunk) {
     cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
     w->exec_chunk = chunk;
+    w->exec_comp = (int)w->comp;
     return L1LS_OK;
 }
 

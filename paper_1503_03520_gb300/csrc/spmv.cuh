@@ -133,86 +133,96 @@ __device__ __forceinline__ void load_span(const T* __restrict__ p, T (&out)[N]) 
 //               row (2p and 2p+1) exactly as for warp_csr.
 // ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
 // wbuf: this warp's 2 * kWarpChunk accumulators.
+// One tile t (32 row pairs, or 32 columns) of the paired traversal; see warp_pcsr.
+template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
+__device__ __forceinline__ void pcsr_tile(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                          const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
+                                          Acc* __restrict__ wbuf, Pre& pre, Epi& epi) {
+    const int lane = threadIdx.x & 31;
+    Acc* w0 = wbuf;
+    Acc* w1 = wbuf + kWarpChunk;
+    const int64_t r = (t << 5) + lane;
+    const bool has = r < nrows;
+    int32_t rb = 0, re = 0;
+    if (has) {
+        rb = __ldcs(ptr + r);
+        re = __ldcs(ptr + r + 1);
+    }
+    auto ops0 = pre(ROWS ? 2 * r : r, has);
+    auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
+    const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
+    const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
+    const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
+    Acc a0 = Acc(0), a1 = Acc(0);
+    for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
+        const int32_t base = c + lane * kEPL;
+        Acc p0[kEPL], p1[kEPL];
+        if (base < e1) {
+            int32_t ij[kEPL];
+            V vv[2 * kEPL];
+            load_span<int32_t, kEPL>(idx + base, ij);
+            load_span<V, 2 * kEPL>(val2 + 2 * (int64_t)base, vv);
+#pragma unroll
+            for (int k = 0; k < kEPL; ++k) {
+                const int32_t e = base + k;
+                const bool in = e >= e0 && e < e1;
+                const Acc v0 = val_to_acc<Acc>(vv[2 * k]), v1 = val_to_acc<Acc>(vv[2 * k + 1]);
+                if (ROWS) {
+                    const Acc xv = in ? vec_to_acc<Acc>(__ldg(x + ij[k])) : Acc(0);
+                    p0[k] = v0 * xv;
+                    p1[k] = v1 * xv;
+                } else {
+                    Acc g0 = Acc(0), g1 = Acc(0);
+                    if (in) {
+                        const typename Two<X>::type g = __ldg(reinterpret_cast<const typename Two<X>::type*>(x) + ij[k]);
+                        g0 = vec_to_acc<Acc>(g.x);
+                        g1 = vec_to_acc<Acc>(g.y);
+                    }
+                    p0[k] = v0 * g0 + v1 * g1;
+                    p1[k] = Acc(0);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kEPL; ++k) p0[k] = p1[k] = Acc(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kEPL; ++k) {
+            w0[k * 32 + lane] = p0[k];
+            if (ROWS) w1[k * 32 + lane] = p1[k];
+        }
+        __syncwarp();
+        const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
+        for (int32_t e = lo; e < hi; ++e) {
+            const int32_t i = e - c;
+            const int32_t q = (i & (kEPL - 1)) * 32 + (i / kEPL);
+            a0 += w0[q];
+            if (ROWS) a1 += w1[q];
+        }
+        __syncwarp();
+    }
+    if (has) {
+        if (ROWS) {
+            epi(2 * r, a0, ops0);
+            epi(2 * r + 1, a1, ops1);
+        } else {
+            epi(r, a0, ops0);
+        }
+    }
+}
+
+// ROWS = true : npairs row pairs; x gathered at the column index; pre / epi are called per
+//               row (2p and 2p+1) exactly as for warp_csr.
+// ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
+// wbuf: this warp's 2 * kWarpChunk accumulators.
 template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
 __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                           const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
                                           Acc* __restrict__ wbuf, Pre pre, Epi epi) {
-    const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ntiles = (nrows + 31) >> 5;
-    Acc* w0 = wbuf;
-    Acc* w1 = wbuf + kWarpChunk;
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
-        const int64_t r = (t << 5) + lane;
-        const bool has = r < nrows;
-        int32_t rb = 0, re = 0;
-        if (has) {
-            rb = __ldcs(ptr + r);
-            re = __ldcs(ptr + r + 1);
-        }
-        auto ops0 = pre(ROWS ? 2 * r : r, has);
-        auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
-        const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
-        const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
-        const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
-        Acc a0 = Acc(0), a1 = Acc(0);
-        for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
-            const int32_t base = c + lane * kEPL;
-            Acc p0[kEPL], p1[kEPL];
-            if (base < e1) {
-                int32_t ij[kEPL];
-                V vv[2 * kEPL];
-                load_span<int32_t, kEPL>(idx + base, ij);
-                load_span<V, 2 * kEPL>(val2 + 2 * (int64_t)base, vv);
-#pragma unroll
-                for (int k = 0; k < kEPL; ++k) {
-                    const int32_t e = base + k;
-                    const bool in = e >= e0 && e < e1;
-                    const Acc v0 = val_to_acc<Acc>(vv[2 * k]), v1 = val_to_acc<Acc>(vv[2 * k + 1]);
-                    if (ROWS) {
-                        const Acc xv = in ? vec_to_acc<Acc>(__ldg(x + ij[k])) : Acc(0);
-                        p0[k] = v0 * xv;
-                        p1[k] = v1 * xv;
-                    } else {
-                        Acc g0 = Acc(0), g1 = Acc(0);
-                        if (in) {
-                            const typename Two<X>::type g =
-                                __ldg(reinterpret_cast<const typename Two<X>::type*>(x) + ij[k]);
-                            g0 = vec_to_acc<Acc>(g.x);
-                            g1 = vec_to_acc<Acc>(g.y);
-                        }
-                        p0[k] = v0 * g0 + v1 * g1;
-                        p1[k] = Acc(0);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kEPL; ++k) p0[k] = p1[k] = Acc(0);
-            }
-#pragma unroll
-            for (int k = 0; k < kEPL; ++k) {
-                w0[k * 32 + lane] = p0[k];
-                if (ROWS) w1[k * 32 + lane] = p1[k];
-            }
-            __syncwarp();
-            const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
-            for (int32_t e = lo; e < hi; ++e) {
-                const int32_t i = e - c;
-                const int32_t q = (i & (kEPL - 1)) * 32 + (i / kEPL);
-                a0 += w0[q];
-                if (ROWS) a1 += w1[q];
-            }
-            __syncwarp();
-        }
-        if (has) {
-            if (ROWS) {
-                epi(2 * r, a0, ops0);
-                epi(2 * r + 1, a1, ops1);
-            } else {
-                epi(r, a0, ops0);
-            }
-        }
-    }
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += nwarps)
+        pcsr_tile<ROWS, V, X, Acc>(t, ptr, idx, val2, x, nrows, wbuf, pre, epi);
 }
 
 // Row traversal of A (nrows rows) in plain or paired storage.
@@ -244,6 +254,116 @@ template <class V> struct Csr {
     const int32_t* ptr;
     const int32_t* idx;
     const V* val;
+};
+
+}  // namespace l1ls
+
+namespace l1ls {
+
+// ---- compensated paired traversals ---------------------------------------------------------
+// Products of the FP32 (or BF16) matrix with float-float vectors, accumulated in float-float:
+// each term a * (h + l) is TwoProduct(a, h) with a * l added to its low word, and the sums are
+// float-float additions (Dekker 1971; Bailey's double-single arithmetic).  The result carries
+// about 44 bits, enough for the residual b - A y of a nearly fitted row (a small difference of
+// large terms) and for A^T r at a small tau, where plain FP32 holds the duality-gap
+// certificate above 1e-6 (the floor grows as tau, and with it the objective, shrinks along a
+// path).  The tile structure is that of pcsr_tile; the warp buffer holds high and low words.
+//
+// Inputs: the row traversal gathers a float-float vector kept as two FP32 arrays (high and low
+// words); the column traversal gathers the residual of row pair p as one float4
+// {hi(2p), hi(2p+1), lo(2p), lo(2p+1)}, both rows with one 16-byte load.
+
+template <bool ROWS, class V, class Pre, class Epi>
+__device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                             const V* __restrict__ val2, const float* __restrict__ xh,
+                                             const float* __restrict__ xl, const float4* __restrict__ r4, int64_t nrows,
+                                             float* __restrict__ wbuf, Pre& pre, Epi& epi) {
+    // ROWS: nrows row pairs, (xh, xl) gathered at the column index (pre / epi per row, 2p and
+    // 2p+1); otherwise nrows columns, the pair residual r4 gathered at p.
+    const int lane = threadIdx.x & 31;
+    float* w0h = wbuf;
+    float* w0l = wbuf + kWarpChunk;
+    float* w1h = wbuf + 2 * kWarpChunk;
+    float* w1l = wbuf + 3 * kWarpChunk;
+    const int64_t r = (t << 5) + lane;
+    const bool has = r < nrows;
+    int32_t rb = 0, re = 0;
+    if (has) {
+        rb = __ldcs(ptr + r);
+        re = __ldcs(ptr + r + 1);
+    }
+    auto ops0 = pre(ROWS ? 2 * r : r, has);
+    auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
+    const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
+    const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
+    const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
+    ff a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+    for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
+        const int32_t base = c + lane * kEPL;
+        ff p0[kEPL], p1[kEPL];
+        if (base < e1) {
+            int32_t ij[kEPL];
+            V vv[2 * kEPL];
+            load_span<int32_t, kEPL>(idx + base, ij);
+            load_span<V, 2 * kEPL>(val2 + 2 * (int64_t)base, vv);
+#pragma unroll
+            for (int k = 0; k < kEPL; ++k) {
+                const int32_t e = base + k;
+                const bool in = e >= e0 && e < e1;
+                const float v0 = val_to_acc<float>(vv[2 * k]), v1 = val_to_acc<float>(vv[2 * k + 1]);
+                if (ROWS) {
+                    const float hx = in ? __ldg(xh + ij[k]) : 0.f;
+                    const float lx = in ? __ldg(xl + ij[k]) : 0.f;
+                    p0[k] = two_prod(v0, hx);
+                    p0[k].lo = __fmaf_rn(v0, lx, p0[k].lo);
+                    p1[k] = two_prod(v1, hx);
+                    p1[k].lo = __fmaf_rn(v1, lx, p1[k].lo);
+                } else {
+                    const float4 g = in ? __ldg(r4 + ij[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    ff q0 = two_prod(v0, g.x);
+                    q0.lo = __fmaf_rn(v0, g.z, q0.lo);
+                    ff q1 = two_prod(v1, g.y);
+                    q1.lo = __fmaf_rn(v1, g.w, q1.lo);
+                    p0[k] = ff_add(q0, q1);
+                    p1[k] = {0.f, 0.f};
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kEPL; ++k) p0[k] = p1[k] = {0.f, 0.f};
+        }
+#pragma unroll
+        for (int k = 0; k < kEPL; ++k) {
+            w0h[k * 32 + lane] = p0[k].hi;
+            w0l[k * 32 + lane] = p0[k].lo;
+            if (ROWS) {
+                w1h[k * 32 + lane] = p1[k].hi;
+                w1l[k * 32 + lane] = p1[k].lo;
+            }
+        }
+        __syncwarp();
+        const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
+        for (int32_t e = lo; e < hi; ++e) {
+            const int32_t i = e - c;
+            const int32_t q = (i & (kEPL - 1)) * 32 + (i / kEPL);
+            a0 = ff_add(a0, {w0h[q], w0l[q]});
+            if (ROWS) a1 = ff_add(a1, {w1h[q], w1l[q]});
+        }
+        __syncwarp();
+    }
+    if (has) {
+        if (ROWS) {
+            epi(2 * r, a0, ops0);
+            epi(2 * r + 1, a1, ops1);
+        } else {
+            epi(r, a0, ops0);
+        }
+    }
+}
+
+template <int BLOCK> struct CompSmem {
+    float buf[(BLOCK / 32) * 4 * kWarpChunk];
+    __device__ float* warp_buf() { return buf + (threadIdx.x >> 5) * 4 * kWarpChunk; }
 };
 
 }  // namespace l1ls

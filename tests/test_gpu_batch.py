@@ -1,0 +1,99 @@
+"""Batched FISTA along tau paths (the tau study of Sec. 8.8 as a workload) against the oracle.
+
+Each instance's path is also solved by the oracle's FISTA on the stored problem (values
+rounded once to FP32), warm-started the same way (the next tau starts from the iterate one
+prox-gradient step past the certified one).  An instance solved alone and inside a batch must
+give identical results (every reduction order depends only on the instance)."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import oracle_instance, stored_values
+from oracle import solvers
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(1024, 512), (2000, 1000), (4096, 2048), (6002, 3001), (10000, 5000), (16384, 8192)]
+NTAU = 4
+
+
+def _params(k, m, n):
+    return W.params(m=m, n=n, seed=40 + k, kappa=10.0 ** (2 + 0.2 * k), right_stages=2, left_stages=1,
+                    xstar_frac=0.02, value_dtype="f32")
+
+
+def _taus(lam_max):
+    return [0.9 * lam_max * 10.0 ** (-j / 1.5) for j in range(NTAU)]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_1503_03520_gb300 as l1
+    ctx = l1.Context(0)
+    params = [_params(k, m, n) for k, (m, n) in enumerate(SIZES)]
+    refs = [oracle_instance(p) for p in params]
+    insts = [ctx.generate(p) for p in params]
+    taus = np.array([_taus(r.lam_max) for r in refs])
+    yield ctx, params, refs, insts, taus
+    for i in insts:
+        i.free()
+    ctx.close()
+
+
+def test_batch_path_matches_oracle(setup):
+    import paper_1503_03520_gb300 as l1
+    ctx, params, refs, insts, taus = setup
+    batch = l1.Batch(ctx, insts)
+    xs = [np.zeros(i.n) for i in insts]
+    res = batch.solve_path(taus, x_out=xs, tol=1e-6, max_iter=100000, restart=1)
+    assert batch.schedule()["block"] in (128, 256)
+    for k, ref in enumerate(refs):
+        A = stored_values(ref.A, "f32")
+        b = ref.b.astype(np.float32).astype(np.float64)
+        x0 = None
+        for j in range(NTAU):
+            r = res[k][j]
+            assert r["status"] == 0 and r["rel_gap"] <= 1e-6, (k, j, r)
+            o = solvers.fista(A, b, taus[k, j], 1.0, 1e-6, 100000, x0=x0, restart=True)
+            # restarts are decided on rounded sums, so the paths may part after a restart
+            assert abs(r["iters"] - o["iters"]) <= max(5, 0.15 * o["iters"]), (k, j, r["iters"], o["iters"])
+            assert abs(r["f"] - o["P"]) <= 2e-6 * o["P"], (k, j)
+            x0 = o["x_next"]
+        # the certificate of the returned solution, recomputed by the oracle on the stored problem
+        P, D, gap, rel = solvers.certificate(A, b, taus[k, -1], xs[k])
+        assert rel <= 1e-5
+    batch.free()
+
+
+def test_alone_equals_in_the_mix(setup):
+    import paper_1503_03520_gb300 as l1
+    ctx, params, refs, insts, taus = setup
+    full = l1.Batch(ctx, insts)
+    xs_full = [np.zeros(i.n) for i in insts]
+    res_full = full.solve_path(taus, x_out=xs_full, tol=1e-6, max_iter=100000, restart=1)
+    full.free()
+    for k in (0, 3, 5):
+        alone = l1.Batch(ctx, [insts[k]])
+        x_alone = [np.zeros(insts[k].n)]
+        res_alone = alone.solve_path(taus[k:k + 1], x_out=x_alone, tol=1e-6, max_iter=100000, restart=1)
+        alone.free()
+        for j in range(NTAU):
+            a, f = res_alone[0][j], res_full[k][j]
+            assert (a["iters"], a["f"], a["gap"], a["rel_gap"]) == (f["iters"], f["f"], f["gap"], f["rel_gap"])
+        assert np.array_equal(x_alone[0], xs_full[k])
+
+
+def test_batch_rejects_mixed_or_unpaired(setup):
+    import paper_1503_03520_gb300 as l1
+    ctx, params, refs, insts, taus = setup
+    plain = ctx.generate(W.params(m=512, n=256, left_stages=0, value_dtype="f32"))
+    f64 = ctx.generate(W.params(m=512, n=256, value_dtype="f64"))
+    try:
+        for bad in ([insts[0], plain], [insts[0], f64]):
+            with pytest.raises(l1.L1LSError) as e:
+                l1.Batch(ctx, bad)
+            assert e.value.status == 1
+    finally:
+        plain.free()
+        f64.free()

@@ -123,3 +123,59 @@ def test_device_buffers_in_place(c1):
     xh, rh = inst.solve_fista(tau=1.0, tol=1e-8, max_iter=100000)
     assert np.array_equal(xo.cpu().numpy(), xh)      # deterministic reductions
     assert rh["iters"] == r["iters"]
+
+
+@pytest.mark.parametrize("tau", [0.3, 0.05])
+def test_fista_restart_matches_oracle(ctx, tau):
+    """FISTA with the gradient restart (an option; not in the paper) against the oracle's."""
+    params = W.params(m=2000, n=1000, right_stages=2, kappa=300.0, seed=41, xstar_frac=0.02)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        x, r = inst.solve_fista(tau=tau, tol=1e-8, max_iter=200000, restart=1)
+        assert r["status"] == 0 and r["rel_gap"] <= 1e-8
+        o = solvers.fista(ref.A, ref.b, tau, 1.0, 1e-8, 200000, restart=True)
+        assert o["status"] == 0
+        assert abs(r["iters"] - o["iters"]) <= max(5, 0.15 * o["iters"])
+        fo = solvers.objective(ref.A, ref.b, tau, o["x"])
+        fg = solvers.objective(ref.A, ref.b, tau, x)
+        assert abs(fg - fo) <= 2e-8 * fo
+    finally:
+        inst.free()
+
+
+@pytest.mark.parametrize("restart,tau_exp", [(0, 0.5), (1, 2.0)])
+def test_fista_compensated_products_reach_small_gaps_at_small_tau(ctx, restart, tau_exp):
+    """accum = 1 (float-float products) against the oracle's FP64 FISTA on the stored FP32
+    problem, down to a tau (1e-2 of lambda_max) where FP32 sums of the products stall above
+    the 1e-6 gap.  (Without the restart FISTA needs more than 1e5 iterations there.)"""
+    params = W.params(m=2000, n=1000, right_stages=2, left_stages=1, kappa=10.0 ** 2.2, seed=41, xstar_frac=0.02,
+                      value_dtype="f32")
+    ref = oracle_instance(params)
+    A = stored_values(ref.A, "f32")
+    b = ref.b.astype(np.float32).astype(np.float64)
+    tau = 0.9 * ref.lam_max * 10.0 ** -tau_exp
+    inst = ctx.generate(params)
+    try:
+        x, r = inst.solve_fista(tau=tau, tol=1e-6, max_iter=100000, restart=restart, accum=1)
+        o = solvers.fista(A, b, tau, 1.0, 1e-6, 100000, restart=bool(restart))
+        assert o["status"] == 0
+        assert r["status"] == 0 and r["rel_gap"] <= 1e-6
+        slack = max(3, 0.01 * o["iters"]) if not restart else max(5, 0.15 * o["iters"])
+        assert abs(r["iters"] - o["iters"]) <= slack, (r["iters"], o["iters"])
+        assert abs(r["f"] - o["P"]) <= 2e-6 * o["P"]
+        assert solvers.certificate(A, b, tau, x)[3] <= 1e-5
+    finally:
+        inst.free()
+
+
+def test_compensated_products_need_paired_fp32_values(ctx):
+    import paper_1503_03520_gb300 as l1
+    for p in (W.params(m=512, n=256, left_stages=0, value_dtype="f32"), W.params(m=512, n=256, value_dtype="f64")):
+        inst = ctx.generate(p)
+        try:
+            with pytest.raises(l1.L1LSError) as e:
+                inst.solve_fista(tau=1.0, accum=1)
+            assert e.value.status == 1
+        finally:
+            inst.free()
