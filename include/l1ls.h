@@ -195,6 +195,8 @@ typedef struct {
     double mu;                /* final smoothing parameter (pdNCG)                            */
     int32_t status;           /* l1ls_status of the solve                                     */
     int32_t reserved;
+    double queue_s;           /* serving (l1ls_poll): submission to admission, seconds         */
+    double latency_s;         /* serving (l1ls_poll): submission to completion, seconds        */
 } l1ls_result;
 
 /* FISTA (Sec. 8.1; Beck & Teboulle) with fixed L = info.lipschitz from x0 (NULL: 0).  Stops
@@ -239,20 +241,68 @@ l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const do
  *                       one persistent cooperative kernel per o->check_every FISTA steps.  The
  *                       first tau starts from 0; each later tau starts from the last iterate of
  *                       the previous one (one prox-gradient step past the certified iterate).
- *                       results: count*ntau entries (instance-major), filled per tau; x_out: NULL
+ *                       results: count*ntau entries (instance-major), filled per tau (a tau not
+ *                       finished when the call ends early gets the call's status); x_out: NULL
  *                       or count pointers (each NULL, device or host; n doubles) receiving the
  *                       certified solution at the last tau.  An instance's results do not depend
  *                       on the other instances of the batch or on the kernel schedule.  Blocking.
- *   l1ls_batch_get_schedule  block size chosen by the built-in autotuner (0 before the first
- *                       solve) and the time of its two probe steps per candidate (ms).
+ *   l1ls_batch_get_schedule  schedule chosen by the built-in autotuner (0 before the first
+ *                       solve): threads per block and entries per lane of the traversal, and
+ *                       tune_ms (4 doubles, may be NULL): the time of the four probe steps of
+ *                       each candidate (256, 8), (128, 8), (256, 4), (128, 4), in ms.
+ *   l1ls_batch_get_stats  of the last solve: batch steps run (each one FISTA step of every
+ *                       active instance) and the device time of its launches in ms (CUDA
+ *                       events on the solve's stream around the launch loop).
  * Errors: EINVAL, ENOMEM, ECUDA (including an expired bounded grid barrier), ETIMEOUT. */
 l1ls_status l1ls_batch_create(l1ls_ctx* ctx, int count, l1ls_inst* const* insts, l1ls_batch** out);
 l1ls_status l1ls_batch_solve_path(l1ls_batch* batch, const double* taus, int ntau, const l1ls_solve_opts* o,
                                   l1ls_result* results, double* const* x_out, void* stream);
-l1ls_status l1ls_batch_get_schedule(const l1ls_batch* batch, int* block, double* tune_ms_256, double* tune_ms_128);
+l1ls_status l1ls_batch_get_schedule(const l1ls_batch* batch, int* block, int* entries_per_lane, double* tune_ms);
+l1ls_status l1ls_batch_get_stats(const l1ls_batch* batch, int64_t* steps, double* device_ms);
 l1ls_status l1ls_batch_free(l1ls_batch* batch);
 
 /* Thread-local message describing the last non-OK status returned on this thread. */
+/* Serving: solve requests admitted by device-memory footprint and run concurrently.
+ * A request is (generator parameters, solver options, method): the instance is generated on
+ * the device, solved to o->rel_gap_tol at o->tau, and freed; the caller receives x (n
+ * doubles) and the certificate.  Each context runs `slots` worker threads, each with its own
+ * CUDA stream.  Requests are admitted in submission order: the oldest waiting request starts
+ * as soon as a slot is free and its footprint (l1ls_footprint) fits next to the footprints of
+ * the running requests within the capacity; later requests never overtake it.  Requests
+ * that arrive while others run are admitted as slots and memory free up, and their kernels
+ * overlap on the device.  A request's result does not depend on the other requests.
+ *   l1ls_serve_config  optional, before the first l1ls_submit: slots (1..256; default 8) and
+ *                      the capacity in bytes (0: the context budget not yet used).  EBUSY if
+ *                      the loop is already running.
+ *   l1ls_submit        queues a request; returns at once with its ticket.  o->tau < 0 means
+ *                      |o->tau| * lambda_max of the generated instance.  EBUSY if its
+ *                      footprint exceeds the whole capacity, EINVAL for bad options (bad
+ *                      generator parameters are reported by l1ls_poll).
+ *   l1ls_poll          waits up to wait_ms (0: no wait) for the request.  Not finished: EBUSY
+ *                      (nothing written, the ticket stays valid).  Finished: fills res
+ *                      (including queue_s and latency_s) and x_out (n doubles, host, may be
+ *                      NULL), releases the ticket, and returns the request's status (OK,
+ *                      ENOCONV, ETIMEOUT, ENUMERIC, EINVAL, ENOMEM, ECUDA or ECANCELLED).
+ *                      Unknown or released ticket: ENOTFOUND.
+ *   l1ls_cancel        a queued request never runs (l1ls_poll then returns ECANCELLED); a
+ *                      running one stops at its next host check and returns ECANCELLED.
+ *   l1ls_serve_stats   counters of the loop (all zero before the first request).
+ * l1ls_destroy cancels every request and joins the workers.  These functions may be called
+ * from any thread. */
+typedef enum { L1LS_FISTA = 0, L1LS_PDNCG = 1 } l1ls_method;
+typedef struct {
+    int32_t slots, running, peak_running, reserved0;
+    uint64_t completed, queued;
+    uint64_t capacity_bytes, reserved_bytes, peak_reserved_bytes;
+} l1ls_serve_info;
+size_t l1ls_footprint(const l1ls_gen_params* p, int method);
+l1ls_status l1ls_serve_config(l1ls_ctx* ctx, int slots, size_t capacity_bytes);
+l1ls_status l1ls_submit(l1ls_ctx* ctx, const l1ls_gen_params* p, const l1ls_solve_opts* o, int method,
+                        uint64_t* ticket);
+l1ls_status l1ls_poll(l1ls_ctx* ctx, uint64_t ticket, int wait_ms, l1ls_result* res, double* x_out);
+l1ls_status l1ls_cancel(l1ls_ctx* ctx, uint64_t ticket);
+l1ls_status l1ls_serve_stats(l1ls_ctx* ctx, l1ls_serve_info* info);
+
 const char* l1ls_last_error(void);
 
 /* Library version string. */

@@ -49,12 +49,24 @@ class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("products", ctypes.c_int64), ("cg_iters", ctypes.c_int64),
                 ("ls_trials", ctypes.c_int64), ("f", ctypes.c_double), ("dual", ctypes.c_double),
                 ("gap", ctypes.c_double), ("rel_gap", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("mu", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mu", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
         d["status_name"] = STATUS.get(self.status, str(self.status))
         return d
+
+
+class ServeInfo(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("running", ctypes.c_int32), ("peak_running", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("capacity_bytes", ctypes.c_uint64), ("reserved_bytes", ctypes.c_uint64),
+                ("peak_reserved_bytes", ctypes.c_uint64)]
+
+
+FISTA, PDNCG = 0, 1
+METHODS = {"fista": FISTA, "pdncg": PDNCG}
 
 
 class L1LSError(RuntimeError):
@@ -91,9 +103,17 @@ _sig = {
     "l1ls_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "l1ls_batch_solve_path": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                              ctypes.POINTER(SolveOpts), _P, _P, _P]),
-    "l1ls_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+    "l1ls_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_double)]),
+    "l1ls_batch_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "l1ls_batch_free": (ctypes.c_int, [_P]),
+    "l1ls_footprint": (ctypes.c_size_t, [ctypes.POINTER(GenParams), ctypes.c_int]),
+    "l1ls_serve_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_size_t]),
+    "l1ls_submit": (ctypes.c_int, [_P, ctypes.POINTER(GenParams), ctypes.POINTER(SolveOpts), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    "l1ls_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result), _P]),
+    "l1ls_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "l1ls_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServeInfo)]),
     "l1ls_gen_params_default": (None, [ctypes.POINTER(GenParams)]),
     "l1ls_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "l1ls_last_error": (ctypes.c_char_p, []),
@@ -184,6 +204,38 @@ class Context:
         _check(lib.l1ls_generate(self._h, ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)))
         return Instance(self, h)
 
+    # ---- serving ----------------------------------------------------------------------
+    def serve_config(self, slots=8, capacity_bytes=0):
+        _check(lib.l1ls_serve_config(self._h, int(slots), int(capacity_bytes)))
+
+    def submit(self, params, method="fista", **opts):
+        """Queue a solve request (generate + solve); returns its ticket."""
+        p = gen_params(params) if isinstance(params, dict) else params
+        o = solve_opts(**opts)
+        t = ctypes.c_uint64()
+        _check(lib.l1ls_submit(self._h, ctypes.byref(p), ctypes.byref(o), METHODS.get(method, method), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket, wait_ms=0, n=None):
+        """None while the request runs; else (status, result dict, x or None)."""
+        res = Result()
+        x = np.zeros(n) if n else None
+        st = lib.l1ls_poll(self._h, ctypes.c_uint64(ticket), int(wait_ms), ctypes.byref(res),
+                           x.ctypes.data_as(_P) if x is not None else None)
+        if st == 7:          # EBUSY: not finished
+            return None
+        if st == 8:
+            _check(st)
+        return st, res.as_dict(), x
+
+    def cancel(self, ticket):
+        _check(lib.l1ls_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def serve_stats(self):
+        i = ServeInfo()
+        _check(lib.l1ls_serve_stats(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in ServeInfo._fields_ if k != "reserved0"}
+
     def close(self):
         if self._h:
             _check(lib.l1ls_destroy(self._h))
@@ -206,6 +258,13 @@ class Instance:
         _check(lib.l1ls_inst_get_info(h, ctypes.byref(info)))
         self.info = {k: getattr(info, k) for k, _ in InstInfo._fields_}
         self.m, self.n, self.nnz = info.m, info.n, info.nnz
+
+    def refresh_info(self):
+        """Re-read the instance info (device_bytes grows when solver work spaces are allocated)."""
+        info = InstInfo()
+        _check(lib.l1ls_inst_get_info(self._h, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in InstInfo._fields_}
+        return self.info
 
     def free(self):
         if self._h:
@@ -335,16 +394,31 @@ class Batch:
         return [[res[i * ntau + j].as_dict() for j in range(ntau)] for i in range(count)]
 
     def schedule(self):
+        """The autotuned schedule: block size, entries per lane, probe times of the 4 candidates."""
         b = ctypes.c_int()
-        a = ctypes.c_double()
-        c = ctypes.c_double()
-        _check(lib.l1ls_batch_get_schedule(self._h, ctypes.byref(b), ctypes.byref(a), ctypes.byref(c)))
-        return {"block": b.value, "probe_ms_256": a.value, "probe_ms_128": c.value}
+        e = ctypes.c_int()
+        ms = (ctypes.c_double * 4)()
+        _check(lib.l1ls_batch_get_schedule(self._h, ctypes.byref(b), ctypes.byref(e), ms))
+        return {"block": b.value, "entries_per_lane": e.value, "probe_ms": list(ms),
+                "candidates": [(256, 8), (128, 8), (256, 4), (128, 4)]}
+
+    def stats(self):
+        """Of the last solve: batch steps run and the device time of their launches (ms)."""
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(lib.l1ls_batch_get_stats(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return {"steps": n.value, "device_ms": ms.value}
 
     def free(self):
         if self._h:
             _check(lib.l1ls_batch_free(self._h))
             self._h = None
+
+
+def footprint(params, method="fista"):
+    """Device bytes the serving loop reserves for a request (an upper bound)."""
+    p = gen_params(params) if isinstance(params, dict) else params
+    return lib.l1ls_footprint(ctypes.byref(p), METHODS.get(method, method))
 
 
 def version():

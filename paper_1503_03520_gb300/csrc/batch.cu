@@ -3,15 +3,20 @@
 //
 // The instances keep their own paired matrices, right-hand sides and iterates; the batch adds
 // a device table of descriptors and two global tile lists (row-pair tiles and column tiles
-// of every instance).  One launch runs `steps` FISTA steps; each step has three phases
+// of every instance).  The unit of work is a segment of 8 tiles (a tile: 32 row pairs or 32
+// columns) of one instance.  One launch runs `steps` FISTA steps; each step has two phases
 // separated by bounded grid barriers:
-//   1. every warp takes row-pair tiles of active instances: K1's product, its epilogue and the
-//      tile's gap partials, reduced in the warp and written per tile;
-//   2. column tiles: K2's product, the momentum and shrinkage, per-tile partials;
-//   3. one warp per instance reduces its tiles' partials in tile order (FP64) and takes the
-//      scalar step of FISTA (Sec. 8.1) with the certificate; when the tolerance is met it
-//      records the result and moves to the next tau of its path, warm-started from the last
-//      iterate computed (one prox-gradient step past the certified one), or retires.
+//   1. every warp takes row-pair segments of active instances: K1's product, its epilogue and
+//      the segment's gap partials (each lane sums its rows in tile order, then the warp), one
+//      write per segment;
+//   2. column segments: K2's product, the momentum and shrinkage, per-segment partials.
+// Per-instance sums need no phase of their own: the warp that completes the last segment of an
+// instance (an atomic count per instance, after a memory fence) sums the segment partials in
+// segment order.  That warp then holds the instance's totals: after phase 1 it
+// stores the sums of K1; after phase 2 it takes the scalar step of FISTA (Sec. 8.1) with the
+// certificate, and when the tolerance is met records the result and moves to the next tau of
+// the path, warm-started from the last iterate computed (one prox-gradient step past the
+// certified one), or retires the instance.
 // Every sum has a fixed order that depends only on the instance, so an instance's results
 // are identical whatever else is in the batch and whatever schedule the autotuner picks.
 // Both products and all vectors are float-float (compensated traversals): along a path tau
@@ -46,13 +51,16 @@ struct BDesc {
     float* xh[2];              // iterates x_{k-1}, x_{k-2} (alternating), float-float:
     float* xl[2];              //   high and low words
     int64_t m, n;
-    int64_t t1_begin, t2_begin;
+    int64_t s1_begin, s2_begin;    // first segment of the instance in each segment list
+    int64_t n1, n2;                // tiles of the instance: row-pair tiles, column tiles
+    int64_t ns1, ns2;              // segments of the instance
 };
 
 struct BState {
     double tau, L, tol;
     int64_t max_iter;
     double t, beta, best_d, l1_cur;
+    double k1[3];              // phase-1 sums: ||A x - b||^2, b.r, r.r
     int64_t iter;
     int32_t stop, status, tau_idx, ntau, final_buf, restart;
 };
@@ -72,7 +80,7 @@ __device__ __forceinline__ BState load_state(const BState* p) {
 struct BResult {
     double P, D, gap, rel;
     int64_t iters;
-    int32_t status, pad;
+    int32_t status, done;      // done: written by the kernel (the tau was finished)
 };
 
 struct BArgs {
@@ -80,11 +88,13 @@ struct BArgs {
     BState* state;
     BResult* results;
     const double* taus;        // [inst][ntau]
-    const int32_t* tinst1;     // row-pair tile -> instance
-    const int32_t* tinst2;     // column tile -> instance
-    int64_t ntiles1, ntiles2;
-    double* part1;             // [tile][3]
-    double* part2;             // [tile][3]
+    const int32_t* sinst1;     // row-pair segment -> instance
+    const int32_t* sinst2;     // column segment -> instance
+    int64_t nseg1, nseg2;
+    double* part1;             // [segment][3]
+    double* part2;             // [segment][3]
+    unsigned* instcnt1;        // segments done per instance (reset by the instance's last warp)
+    unsigned* instcnt2;
     int ninst, ntau_max;
     unsigned* bar_count;
     unsigned* bar_gen;
@@ -134,7 +144,195 @@ __device__ __forceinline__ ff warp_sum_ff(ff v) {
     return v;
 }
 
-template <int BLOCK, class V>
+constexpr int kSegTiles = 8;
+
+// Count this warp's segment (lane 0 already wrote its partials at part[K sg]) in its instance;
+// see the file comment.  Returns true on the one warp that completed the instance, with the
+// instance totals in tot (every lane).  Partial 0 is combined by max when MAX0, else summed.
+template <int K, bool MAX0>
+__device__ bool segment_done(int64_t s_begin, int64_t nseg, const double* part, unsigned* instcnt, double (&tot)[K]) {
+    const int lane = threadIdx.x & 31;
+    __threadfence();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(instcnt, 1u) == (unsigned)(nseg - 1);
+    if (!__shfl_sync(0xffffffffu, last, 0)) return false;
+    if (lane == 0) *instcnt = 0u;
+    __threadfence();
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0.0;
+    for (int64_t q = lane; q < nseg; q += 32)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double w = __ldcg(part + K * (s_begin + q) + k);
+            v[k] = (MAX0 && k == 0) ? fmax(v[k], w) : v[k] + w;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double w = __shfl_down_sync(0xffffffffu, v[k], o);
+            v[k] = (MAX0 && k == 0) ? fmax(v[k], w) : v[k] + w;
+        }
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = __shfl_sync(0xffffffffu, v[k], 0);
+    return true;
+}
+
+// The scalar step of instance i after its phase 2 (lane 0 of the completing warp).
+__device__ void finish_step(const BArgs& a, int64_t i, int cur, double gm, double l1n, double rtn) {
+    BState st = load_state(&a.state[i]);
+    const double tau = st.tau;
+    const double P = __dadd_rn(__dmul_rn(tau, st.l1_cur), __dmul_rn(0.5, st.k1[0]));
+    const double sc = gm <= tau ? 1.0 : tau / gm;
+    const double D = __dadd_rn(__dmul_rn(sc, st.k1[1]), -__dmul_rn(__dmul_rn(__dmul_rn(0.5, sc), sc), st.k1[2]));
+    st.best_d = fmax(st.best_d, D);
+    const double gap = P - st.best_d;
+    const double rel = gap / fmax(fabs(P), 1e-300);
+    const bool bad = !isfinite(P) || !isfinite(D);
+    if (bad || rel <= st.tol || st.iter - 1 >= st.max_iter) {
+        BResult& R = a.results[i * a.ntau_max + st.tau_idx];
+        R.P = P;
+        R.D = st.best_d;
+        R.gap = gap;
+        R.rel = rel;
+        R.iters = st.iter - 1;
+        R.status = bad ? L1LS_ENUMERIC : (rel <= st.tol ? L1LS_OK : L1LS_ENOCONV);
+        R.done = 1;
+        if (!bad && st.tau_idx + 1 < st.ntau) {
+            st.tau_idx += 1;
+            st.tau = a.taus[i * a.ntau_max + st.tau_idx];
+            st.t = 1.0;
+            st.beta = 0.0;
+            st.best_d = -INFINITY;
+            st.iter = 1;
+            st.l1_cur = l1n;          // warm start: the iterate just computed
+        } else {
+            st.stop = 1;
+            st.final_buf = cur;      // the certified iterate x_{k-1}
+            atomicSub(a.active, 1);
+        }
+    } else {
+        if (st.restart && rtn > 0.0) {
+            st.t = 1.0;
+            st.beta = 0.0;
+        } else {
+            const double tk = st.t;
+            const double tn = __dmul_rn(0.5, __dadd_rn(1.0, sqrt(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, tk), tk)))));
+            st.beta = (tk - 1.0) / tn;
+            st.t = tn;
+        }
+        st.l1_cur = l1n;
+        st.iter += 1;
+    }
+    a.state[i] = st;
+}
+
+// One row-pair segment (tiles t0 .. t1-1) of instance d: K1's product and epilogue; returns
+// the segment's partials ||A x - b||^2, b.r, r.r in out (lane 0).  Not inlined: the two phases
+// then get their registers allocated separately.
+template <class V, int EPL>
+__device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, double beta_d, int64_t t0, int64_t t1,
+                                         float* wbuf, double* out) {
+    const int32_t* rptr = dp->rptr;
+    const int32_t* rcol = dp->rcol;
+    const V* rval = static_cast<const V*>(dp->rval);
+    const float* xh = dp->xh[cur];
+    const float* xl = dp->xl[cur];
+    float2* ax = dp->ax;
+    const float* bv = dp->b;
+    float* resf = reinterpret_cast<float*>(dp->res);
+    const int64_t npairs = dp->m / 2;
+    const ff beta = ff_from_double(beta_d);
+    ff q0 = {0.f, 0.f}, q1 = {0.f, 0.f}, q2 = {0.f, 0.f};
+    struct Ops {
+        ff axo;
+        float bb;
+    };
+    auto pre = [ax, bv](int64_t r, bool has) {
+        Ops o{{0.f, 0.f}, 0.f};
+        if (has) {
+            const float2 v = ax[r];
+            o.axo = {v.x, v.y};
+            o.bb = bv[r];
+        }
+        return o;
+    };
+    auto epi = [&](int64_t r, ff u, const Ops& o) {
+        // A y = A x_k + beta (A x_k - A x_{k-1}), r = b - A y (Sec. 8.1)
+        const ff ay = ff_add(u, ff_mul(beta, ff_sub(u, o.axo)));
+        const ff rr = ff_sub(ff_from_float(o.bb), ay);
+        ax[r] = make_float2(u.hi, u.lo);
+        resf[4 * (r >> 1) + (r & 1)] = rr.hi;
+        resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
+        const ff dd = ff_sub(u, ff_from_float(o.bb));
+        q0 = ff_add(q0, ff_mul(dd, dd));
+        q1 = ff_add(q1, ff_mul(ff_from_float(o.bb), rr));
+        q2 = ff_add(q2, ff_mul(rr, rr));
+    };
+#pragma unroll 1
+    for (int64_t t = t0; t < t1; ++t)
+        pcsr_tile_ff<true, V, EPL>(t, rptr, rcol, rval, xh, xl, nullptr, npairs, wbuf, pre, epi);
+    q0 = warp_sum_ff(q0);
+    q1 = warp_sum_ff(q1);
+    q2 = warp_sum_ff(q2);
+    out[0] = ff_to_double(q0);
+    out[1] = ff_to_double(q1);
+    out[2] = ff_to_double(q2);
+}
+
+// One column segment of instance d: K2's product, momentum and shrinkage into x[nxt];
+// returns max |A^T r|, sum |x_{k+1}| and the restart test's partial in out (lane 0).
+template <class V, int EPL>
+__device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, double beta, double L, double tau,
+                                         bool rs, int64_t t0, int64_t t1, float* wbuf, double* out) {
+    const int32_t* cptr = dp->cptr;
+    const int32_t* cpair = dp->cpair;
+    const V* cval = static_cast<const V*>(dp->cval);
+    const float4* res = dp->res;
+    const float* x1h = dp->xh[cur];
+    const float* x1l = dp->xl[cur];
+    float* x0h = dp->xh[cur ^ 1];
+    float* x0l = dp->xl[cur ^ 1];
+    const int64_t n = dp->n;
+    const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
+    float gmax = 0.0f;
+    ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
+    struct Ops {
+        ff x1, x0;
+    };
+    auto pre = [x1h, x1l, x0h, x0l](int64_t j, bool has) {
+        Ops o{{0.f, 0.f}, {0.f, 0.f}};
+        if (has) {
+            o.x1 = {x1h[j], x1l[j]};
+            o.x0 = {x0h[j], x0l[j]};
+        }
+        return o;
+    };
+    auto epi = [&](int64_t j, ff g, const Ops& o) {
+        // y = x_k + beta (x_k - x_{k-1}); x_{k+1} = S_{tau/L}(y + A^T r / L) (Sec. 8.1)
+        const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
+        const ff v = ff_add(y, ff_mul(g, invL_f));
+        const ff xn = ff_soft_threshold(v, thr_f);
+        x0h[j] = xn.hi;
+        x0l[j] = xn.lo;
+        gmax = fmaxf(gmax, fabsf(g.hi));
+        l1 = ff_add(l1, ff_abs(xn));
+        if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+    };
+#pragma unroll 1
+    for (int64_t t = t0; t < t1; ++t)
+        pcsr_tile_ff<false, V, EPL>(t, cptr, cpair, cval, nullptr, nullptr, res, n, wbuf, pre, epi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_down_sync(0xffffffffu, gmax, o));
+    l1 = warp_sum_ff(l1);
+    rt = warp_sum_ff(rt);
+    out[0] = (double)gmax;
+    out[1] = ff_to_double(l1);
+    out[2] = ff_to_double(rt);
+}
+
+template <int BLOCK, int EPL, class V>
 __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
     __shared__ CompSmem<BLOCK> sm;   // 4 * kWarpChunk floats per warp; phase 2 uses half
     const int lane = threadIdx.x & 31;
@@ -143,177 +341,38 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
     for (int s = 0; s < a.steps; ++s) {
         if (*(volatile int*)a.active == 0) return;
         const int64_t step = a.step0 + s;
-        const int cur = (int)(step & 1), nxt = cur ^ 1;
-        // ---- phase 1: row-pair tiles (A x, residual, gap partials)
-        for (int64_t t = gw; t < a.ntiles1; t += nw) {
-            const int i = a.tinst1[t];
-            double* pp = a.part1 + 3 * t;
-            if (__ldcg(&a.state[i].stop)) {
-                if (lane == 0) pp[0] = pp[1] = pp[2] = 0.0;
-                continue;
-            }
-            const BDesc d = a.desc[i];
-            const ff beta = ff_from_double(__ldcg(&a.state[i].beta));
-            float* resf = reinterpret_cast<float*>(d.res);
-            ff q[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            struct Ops {
-                ff axo;
-                float bb;
-            };
-            auto pre = [&](int64_t r, bool has) {
-                Ops o{{0.f, 0.f}, 0.f};
-                if (has) {
-                    const float2 v = d.ax[r];
-                    o.axo = {v.x, v.y};
-                    o.bb = d.b[r];
-                }
-                return o;
-            };
-            auto epi = [&](int64_t r, ff u, const Ops& o) {
-                // A y = A x_k + beta (A x_k - A x_{k-1}), r = b - A y (Sec. 8.1)
-                const ff ay = ff_add(u, ff_mul(beta, ff_sub(u, o.axo)));
-                const ff rr = ff_sub(ff_from_float(o.bb), ay);
-                d.ax[r] = make_float2(u.hi, u.lo);
-                resf[4 * (r >> 1) + (r & 1)] = rr.hi;
-                resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
-                const ff dd = ff_sub(u, ff_from_float(o.bb));
-                q[0] = ff_add(q[0], ff_mul(dd, dd));
-                q[1] = ff_add(q[1], ff_mul(ff_from_float(o.bb), rr));
-                q[2] = ff_add(q[2], ff_mul(rr, rr));
-            };
-            pcsr_tile_ff<true, V>(t - d.t1_begin, d.rptr, d.rcol, static_cast<const V*>(d.rval), d.xh[cur], d.xl[cur],
-                                  nullptr, d.m / 2, sm.warp_buf(), pre, epi);
-            for (int k = 0; k < 3; ++k) q[k] = warp_sum_ff(q[k]);
-            if (lane == 0) {
-                pp[0] = ff_to_double(q[0]);
-                pp[1] = ff_to_double(q[1]);
-                pp[2] = ff_to_double(q[2]);
-            }
-        }
-        if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
-        // ---- phase 2: column tiles (A^T r, momentum, shrinkage)
-        for (int64_t t = gw; t < a.ntiles2; t += nw) {
-            const int i = a.tinst2[t];
-            double* pp = a.part2 + 3 * t;
-            if (__ldcg(&a.state[i].stop)) {
-                if (lane == 0) pp[0] = pp[1] = pp[2] = 0.0;
-                continue;
-            }
-            const bool rs = __ldcg(&a.state[i].restart) != 0;
-            const BDesc d = a.desc[i];
-            const double beta = __ldcg(&a.state[i].beta), L = __ldcg(&a.state[i].L), tau = __ldcg(&a.state[i].tau);
-            const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
-            float gmax = 0.0f;
-            ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
-            struct Ops {
-                ff x1, x0;
-            };
-            auto pre = [&](int64_t j, bool has) {
-                Ops o{{0.f, 0.f}, {0.f, 0.f}};
-                if (has) {
-                    o.x1 = {d.xh[cur][j], d.xl[cur][j]};
-                    o.x0 = {d.xh[nxt][j], d.xl[nxt][j]};
-                }
-                return o;
-            };
-            auto epi = [&](int64_t j, ff g, const Ops& o) {
-                // y = x_k + beta (x_k - x_{k-1}); x_{k+1} = S_{tau/L}(y + A^T r / L) (Sec. 8.1)
-                const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
-                const ff v = ff_add(y, ff_mul(g, invL_f));
-                const ff xn = ff_soft_threshold(v, thr_f);
-                d.xh[nxt][j] = xn.hi;
-                d.xl[nxt][j] = xn.lo;
-                gmax = fmaxf(gmax, fabsf(g.hi));
-                l1 = ff_add(l1, ff_abs(xn));
-                if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
-            };
-            pcsr_tile_ff<false, V>(t - d.t2_begin, d.cptr, d.cpair, static_cast<const V*>(d.cval), nullptr, nullptr,
-                                   d.res, d.n, sm.warp_buf(), pre, epi);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_down_sync(0xffffffffu, gmax, o));
-            l1 = warp_sum_ff(l1);
-            rt = warp_sum_ff(rt);
-            if (lane == 0) {
-                pp[0] = (double)gmax;
-                pp[1] = ff_to_double(l1);
-                pp[2] = ff_to_double(rt);
-            }
-        }
-        if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
-        // ---- phase 3: one warp per instance, scalar step and tau path
-        for (int64_t i = gw; i < a.ninst; i += nw) {
+        const int cur = (int)(step & 1);
+        // ---- phase 1: row-pair segments (A x, residual, gap partials)
+        for (int64_t sg = gw; sg < a.nseg1; sg += nw) {
+            const int i = a.sinst1[sg];
             if (__ldcg(&a.state[i].stop)) continue;
-            const BDesc d = a.desc[i];
-            const int64_t n1 = (d.m / 2 + 31) / 32, n2 = (d.n + 31) / 32;
-            double s0 = 0, s1 = 0, s2 = 0, gm = 0, l1n = 0, rtn = 0;
-            for (int64_t t = lane; t < n1; t += 32) {
-                const double* pp = a.part1 + 3 * (d.t1_begin + t);
-                s0 += __ldcg(pp);
-                s1 += __ldcg(pp + 1);
-                s2 += __ldcg(pp + 2);
-            }
-            for (int64_t t = lane; t < n2; t += 32) {
-                const double* pp = a.part2 + 3 * (d.t2_begin + t);
-                gm = fmax(gm, __ldcg(pp));
-                l1n += __ldcg(pp + 1);
-                rtn += __ldcg(pp + 2);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s0 += __shfl_down_sync(0xffffffffu, s0, o);
-                s1 += __shfl_down_sync(0xffffffffu, s1, o);
-                s2 += __shfl_down_sync(0xffffffffu, s2, o);
-                gm = fmax(gm, __shfl_down_sync(0xffffffffu, gm, o));
-                l1n += __shfl_down_sync(0xffffffffu, l1n, o);
-                rtn += __shfl_down_sync(0xffffffffu, rtn, o);
-            }
-            if (lane == 0) {
-                BState st = load_state(&a.state[i]);
-                const double tau = st.tau;
-                const double P = __dadd_rn(__dmul_rn(tau, st.l1_cur), __dmul_rn(0.5, s0));
-                const double sc = gm <= tau ? 1.0 : tau / gm;
-                const double D = __dadd_rn(__dmul_rn(sc, s1), -__dmul_rn(__dmul_rn(__dmul_rn(0.5, sc), sc), s2));
-                st.best_d = fmax(st.best_d, D);
-                const double gap = P - st.best_d;
-                const double rel = gap / fmax(fabs(P), 1e-300);
-                const bool bad = !isfinite(P) || !isfinite(D);
-                if (bad || rel <= st.tol || st.iter - 1 >= st.max_iter) {
-                    BResult& R = a.results[(int64_t)i * a.ntau_max + st.tau_idx];
-                    R.P = P;
-                    R.D = st.best_d;
-                    R.gap = gap;
-                    R.rel = rel;
-                    R.iters = st.iter - 1;
-                    R.status = bad ? L1LS_ENUMERIC : (rel <= st.tol ? L1LS_OK : L1LS_ENOCONV);
-                    if (!bad && st.tau_idx + 1 < st.ntau) {
-                        st.tau_idx += 1;
-                        st.tau = a.taus[(int64_t)i * a.ntau_max + st.tau_idx];
-                        st.t = 1.0;
-                        st.beta = 0.0;
-                        st.best_d = -INFINITY;
-                        st.iter = 1;
-                        st.l1_cur = l1n;          // warm start: the iterate just computed
-                    } else {
-                        st.stop = 1;
-                        st.final_buf = cur;      // the certified iterate x_{k-1}
-                        atomicSub(a.active, 1);
-                    }
-                } else {
-                    if (st.restart && rtn > 0.0) {
-                        st.t = 1.0;
-                        st.beta = 0.0;
-                    } else {
-                        const double tk = st.t;
-                        const double tn =
-                            __dmul_rn(0.5, __dadd_rn(1.0, sqrt(__dadd_rn(1.0, __dmul_rn(__dmul_rn(4.0, tk), tk)))));
-                        st.beta = (tk - 1.0) / tn;
-                        st.t = tn;
-                    }
-                    st.l1_cur = l1n;
-                    st.iter += 1;
-                }
-                a.state[i] = st;
-            }
+            const BDesc* dp = a.desc + i;
+            const int64_t sb = dp->s1_begin, ns = dp->ns1;
+            const int64_t t0 = (sg - sb) * kSegTiles, t1 = min(dp->n1, t0 + kSegTiles);
+            double part[3];
+            row_segment<V, EPL>(dp, cur, __ldcg(&a.state[i].beta), t0, t1, sm.warp_buf(), part);
+            if (lane == 0)
+                for (int k = 0; k < 3; ++k) a.part1[3 * sg + k] = part[k];
+            double tot[3];
+            if (segment_done<3, false>(sb, ns, a.part1, a.instcnt1 + i, tot) && lane == 0)
+                for (int k = 0; k < 3; ++k) a.state[i].k1[k] = tot[k];
+        }
+        if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
+        // ---- phase 2: column segments (A^T r, momentum, shrinkage), then the scalar step
+        for (int64_t sg = gw; sg < a.nseg2; sg += nw) {
+            const int i = a.sinst2[sg];
+            if (__ldcg(&a.state[i].stop)) continue;
+            const BDesc* dp = a.desc + i;
+            const int64_t sb = dp->s2_begin, ns = dp->ns2;
+            const int64_t t0 = (sg - sb) * kSegTiles, t1 = min(dp->n2, t0 + kSegTiles);
+            double part[3];
+            col_segment<V, EPL>(dp, cur, __ldcg(&a.state[i].beta), __ldcg(&a.state[i].L), __ldcg(&a.state[i].tau),
+                           __ldcg(&a.state[i].restart) != 0, t0, t1, sm.warp_buf(), part);
+            if (lane == 0)
+                for (int k = 0; k < 3; ++k) a.part2[3 * sg + k] = part[k];
+            double tot[3];
+            if (segment_done<3, true>(sb, ns, a.part2, a.instcnt2 + i, tot) && lane == 0)
+                finish_step(a, i, cur, tot[0], tot[1], tot[2]);
         }
         if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
     }
@@ -330,22 +389,24 @@ struct Batch {
     Ctx* ctx = nullptr;
     std::vector<Inst*> insts;
     int dtype = L1LS_F32;
-    int64_t ntiles1 = 0, ntiles2 = 0;
+    int64_t nseg1 = 0, nseg2 = 0;
     BDesc* d_desc = nullptr;
     BState* d_state = nullptr;
-    int32_t* d_tinst1 = nullptr;
-    int32_t* d_tinst2 = nullptr;
+    int32_t* d_sinst1 = nullptr;
+    int32_t* d_sinst2 = nullptr;
     double* d_part1 = nullptr;
     double* d_part2 = nullptr;
+    unsigned* d_cnt = nullptr;    // instance counters of phase 1, then of phase 2
     unsigned* d_bar = nullptr;    // [count, gen]
     int* d_err = nullptr;
     int* d_active = nullptr;
     float* slab = nullptr;        // per-instance vectors
     size_t slab_bytes = 0;
     std::vector<BDesc> desc;
-    int block = 0;                // chosen by the autotuner (0: not yet)
-    int grid = 0;
-    double tune_ms[2] = {0, 0};
+    int sched = -1;               // schedule chosen by the autotuner (-1: not yet)
+    double tune_ms[4] = {0, 0, 0, 0};
+    int64_t last_steps = 0;       // of the last solve
+    double last_ms = 0.0;
     struct Alloc {
         void* p;
         size_t bytes;
@@ -364,9 +425,13 @@ struct Batch {
 
 namespace {
 
-template <int BLOCK, class V>
+// Schedules: (threads per block, entries per lane and chunk) of the persistent kernel.
+constexpr int kSchedBlock[4] = {256, 128, 256, 128};
+constexpr int kSchedEPL[4] = {8, 8, 4, 4};
+
+template <int BLOCK, int EPL, class V>
 l1ls_status launch_batch(Batch* B, BArgs& args, cudaStream_t st, int* grid_out) {
-    auto kern = k_batch<BLOCK, V>;
+    auto kern = k_batch<BLOCK, EPL, V>;
     int per_sm = 0;
     L1LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, 0));
     if (per_sm < 1) return set_error(L1LS_ECUDA, "batched kernel does not fit on an SM");
@@ -377,14 +442,20 @@ l1ls_status launch_batch(Batch* B, BArgs& args, cudaStream_t st, int* grid_out) 
     return L1LS_OK;
 }
 
-l1ls_status launch_any(Batch* B, int block, BArgs& args, cudaStream_t st) {
+template <class V>
+l1ls_status launch_sched(Batch* B, int sched, BArgs& args, cudaStream_t st) {
     int grid = 0;
-    if (B->dtype == L1LS_F32) {
-        if (block == 128) return launch_batch<128, float>(B, args, st, &grid);
-        return launch_batch<256, float>(B, args, st, &grid);
+    switch (sched) {
+        case 0: return launch_batch<256, 8, V>(B, args, st, &grid);
+        case 1: return launch_batch<128, 8, V>(B, args, st, &grid);
+        case 2: return launch_batch<256, 4, V>(B, args, st, &grid);
+        default: return launch_batch<128, 4, V>(B, args, st, &grid);
     }
-    if (block == 128) return launch_batch<128, __nv_bfloat16>(B, args, st, &grid);
-    return launch_batch<256, __nv_bfloat16>(B, args, st, &grid);
+}
+
+l1ls_status launch_any(Batch* B, int sched, BArgs& args, cudaStream_t st) {
+    if (B->dtype == L1LS_F32) return launch_sched<float>(B, sched, args, st);
+    return launch_sched<__nv_bfloat16>(B, sched, args, st);
 }
 
 }  // namespace
@@ -446,27 +517,32 @@ extern "C" l1ls_status l1ls_batch_create(l1ls_ctx* hctx, int count, l1ls_inst* c
         }
         d.m = I->m;
         d.n = I->n;
-        d.t1_begin = (int64_t)t1.size();
-        d.t2_begin = (int64_t)t2.size();
         const int64_t n1 = (I->m / 2 + 31) / 32, n2 = (I->n + 31) / 32;
-        t1.insert(t1.end(), (size_t)n1, i);
-        t2.insert(t2.end(), (size_t)n2, i);
+        d.n1 = n1;
+        d.n2 = n2;
+        d.ns1 = (n1 + kSegTiles - 1) / kSegTiles;
+        d.ns2 = (n2 + kSegTiles - 1) / kSegTiles;
+        d.s1_begin = (int64_t)t1.size();
+        d.s2_begin = (int64_t)t2.size();
+        t1.insert(t1.end(), (size_t)d.ns1, i);
+        t2.insert(t2.end(), (size_t)d.ns2, i);
         B->desc.push_back(d);
     }
-    B->ntiles1 = (int64_t)t1.size();
-    B->ntiles2 = (int64_t)t2.size();
+    B->nseg1 = (int64_t)t1.size();
+    B->nseg2 = (int64_t)t2.size();
     if ((s = B->get(&B->d_desc, count)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_state, count)) != L1LS_OK) return fail(s);
-    if ((s = B->get(&B->d_tinst1, B->ntiles1)) != L1LS_OK) return fail(s);
-    if ((s = B->get(&B->d_tinst2, B->ntiles2)) != L1LS_OK) return fail(s);
-    if ((s = B->get(&B->d_part1, 3 * B->ntiles1)) != L1LS_OK) return fail(s);
-    if ((s = B->get(&B->d_part2, 3 * B->ntiles2)) != L1LS_OK) return fail(s);
+    if ((s = B->get(&B->d_sinst1, B->nseg1)) != L1LS_OK) return fail(s);
+    if ((s = B->get(&B->d_sinst2, B->nseg2)) != L1LS_OK) return fail(s);
+    if ((s = B->get(&B->d_part1, 3 * B->nseg1)) != L1LS_OK) return fail(s);
+    if ((s = B->get(&B->d_part2, 3 * B->nseg2)) != L1LS_OK) return fail(s);
+    if ((s = B->get(&B->d_cnt, 2 * (int64_t)count)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_bar, 2)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_err, 1)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_active, 1)) != L1LS_OK) return fail(s);
     cudaError_t e = cudaMemcpy(B->d_desc, B->desc.data(), sizeof(BDesc) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_tinst1, t1.data(), sizeof(int32_t) * t1.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_tinst2, t2.data(), sizeof(int32_t) * t2.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_sinst1, t1.data(), sizeof(int32_t) * t1.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_sinst2, t2.data(), sizeof(int32_t) * t2.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(batch tables)", __FILE__, __LINE__));
     *out = reinterpret_cast<l1ls_batch*>(B);
     return L1LS_OK;
@@ -518,6 +594,7 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     L1LS_CUDA(cudaMemcpyAsync(B->d_state, hs.data(), sizeof(BState) * count, cudaMemcpyHostToDevice, st));
     L1LS_CUDA(cudaMemsetAsync(B->slab, 0, B->slab_bytes, st));
     L1LS_CUDA(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), st));
+    L1LS_CUDA(cudaMemsetAsync(B->d_cnt, 0, sizeof(unsigned) * 2 * (size_t)count, st));
     L1LS_CUDA(cudaMemsetAsync(B->d_err, 0, sizeof(int), st));
     L1LS_CUDA(cudaMemcpyAsync(B->d_active, &count, sizeof(int), cudaMemcpyHostToDevice, st));
     BArgs args{};
@@ -525,12 +602,14 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     args.state = B->d_state;
     args.results = d_res;
     args.taus = d_taus;
-    args.tinst1 = B->d_tinst1;
-    args.tinst2 = B->d_tinst2;
-    args.ntiles1 = B->ntiles1;
-    args.ntiles2 = B->ntiles2;
+    args.sinst1 = B->d_sinst1;
+    args.sinst2 = B->d_sinst2;
+    args.nseg1 = B->nseg1;
+    args.nseg2 = B->nseg2;
     args.part1 = B->d_part1;
     args.part2 = B->d_part2;
+    args.instcnt1 = B->d_cnt;
+    args.instcnt2 = B->d_cnt + count;
     args.ninst = count;
     args.ntau_max = ntau;
     args.bar_count = B->d_bar;
@@ -539,28 +618,33 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     args.active = B->d_active;
     int64_t step = 0;
     const int chunk = o->check_every > 0 ? o->check_every : 32;
-    // autotuner: time two steps with each block size on the live solve (results do not depend
-    // on the schedule), keep the faster
-    if (B->block == 0) {
+    cudaEvent_t ev[2];
+    L1LS_CUDA(cudaEventCreate(&ev[0]));
+    L1LS_CUDA(cudaEventCreate(&ev[1]));
+    L1LS_CUDA(cudaEventRecord(ev[0], st));
+    // autotuner: time four steps of each schedule on the live solve (results do not depend on
+    // the schedule: every sum keeps its order), keep the fastest
+    if (B->sched < 0) {
         cudaEvent_t e0, e1;
         L1LS_CUDA(cudaEventCreate(&e0));
         L1LS_CUDA(cudaEventCreate(&e1));
-        const int cands[2] = {256, 128};
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < 4; ++c) {
             args.step0 = step;
-            args.steps = 2;
+            args.steps = 4;
             L1LS_CUDA(cudaEventRecord(e0, st));
-            L1LS_TRY(launch_any(B, cands[c], args, st));
+            L1LS_TRY(launch_any(B, c, args, st));
             L1LS_CUDA(cudaEventRecord(e1, st));
             L1LS_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             L1LS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             B->tune_ms[c] = ms;
-            step += 2;
+            step += 4;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        B->block = B->tune_ms[1] < B->tune_ms[0] ? 128 : 256;
+        B->sched = 0;
+        for (int c = 1; c < 4; ++c)
+            if (B->tune_ms[c] < B->tune_ms[B->sched]) B->sched = c;
     }
     l1ls_status final_status = L1LS_OK;
     const int64_t max_steps = (o->max_iter + 2) * (int64_t)ntau + 16;
@@ -585,9 +669,17 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
         }
         args.step0 = step;
         args.steps = chunk;
-        L1LS_TRY(launch_any(B, B->block, args, st));
+        L1LS_TRY(launch_any(B, B->sched, args, st));
         step += chunk;
     }
+    L1LS_CUDA(cudaEventRecord(ev[1], st));
+    L1LS_CUDA(cudaEventSynchronize(ev[1]));
+    float loop_ms = 0.f;
+    L1LS_CUDA(cudaEventElapsedTime(&loop_ms, ev[0], ev[1]));
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    B->last_steps = step;
+    B->last_ms = loop_ms;
     std::vector<BResult> hr((size_t)count * ntau);
     L1LS_CUDA(cudaMemcpyAsync(hr.data(), d_res, sizeof(BResult) * count * ntau, cudaMemcpyDeviceToHost, st));
     L1LS_CUDA(cudaMemcpyAsync(hs.data(), B->d_state, sizeof(BState) * count, cudaMemcpyDeviceToHost, st));
@@ -603,7 +695,8 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
             r.dual = hr[k].D;
             r.gap = hr[k].gap;
             r.rel_gap = hr[k].rel;
-            r.status = final_status == L1LS_OK ? hr[k].status : final_status;
+            // taus finished before a time limit or an error keep their own status
+            r.status = hr[k].done ? hr[k].status : (final_status == L1LS_OK ? L1LS_ECUDA : final_status);
             r.seconds = secs;
         }
     }
@@ -626,12 +719,21 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     return final_status;
 }
 
-extern "C" l1ls_status l1ls_batch_get_schedule(const l1ls_batch* h, int* block, double* tune_ms_256,
-                                               double* tune_ms_128) {
+extern "C" l1ls_status l1ls_batch_get_schedule(const l1ls_batch* h, int* block, int* entries_per_lane,
+                                               double* tune_ms) {
     if (!h) return set_error(L1LS_EINVAL, "batch is NULL");
     const Batch* B = reinterpret_cast<const Batch*>(h);
-    if (block) *block = B->block;
-    if (tune_ms_256) *tune_ms_256 = B->tune_ms[0];
-    if (tune_ms_128) *tune_ms_128 = B->tune_ms[1];
+    if (block) *block = B->sched < 0 ? 0 : kSchedBlock[B->sched];
+    if (entries_per_lane) *entries_per_lane = B->sched < 0 ? 0 : kSchedEPL[B->sched];
+    if (tune_ms)
+        for (int c = 0; c < 4; ++c) tune_ms[c] = B->tune_ms[c];
+    return L1LS_OK;
+}
+
+extern "C" l1ls_status l1ls_batch_get_stats(const l1ls_batch* h, int64_t* steps, double* device_ms) {
+    if (!h) return set_error(L1LS_EINVAL, "batch is NULL");
+    const Batch* B = reinterpret_cast<const Batch*>(h);
+    if (steps) *steps = B->last_steps;
+    if (device_ms) *device_ms = B->last_ms;
     return L1LS_OK;
 }

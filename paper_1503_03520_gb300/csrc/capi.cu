@@ -37,14 +37,14 @@ bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-l1ls_status Ctx::alloc(void** p, size_t bytes) {
+l1ls_status Ctx::alloc(void** p, size_t bytes, cudaStream_t st, bool stream_ordered) {
     {
         std::lock_guard<std::mutex> g(mem_mu);
         if (used + bytes > budget)
             return set_error(L1LS_ENOMEM, "device memory budget exceeded (%zu + %zu > %zu bytes)", used, bytes, budget);
         used += bytes;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = stream_ordered ? cudaMallocAsync(p, bytes, st) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         std::lock_guard<std::mutex> g(mem_mu);
         used -= bytes;
@@ -54,9 +54,10 @@ l1ls_status Ctx::alloc(void** p, size_t bytes) {
     return L1LS_OK;
 }
 
-void Ctx::release(void* p, size_t bytes) {
+void Ctx::release(void* p, size_t bytes, cudaStream_t st, bool stream_ordered) {
     if (!p) return;
-    cudaFree(p);
+    if (stream_ordered) cudaFreeAsync(p, st);
+    else cudaFree(p);
     std::lock_guard<std::mutex> g(mem_mu);
     used -= bytes;
 }
@@ -78,7 +79,7 @@ l1ls_status Ctx::staging(int which, size_t bytes, void** out) {
 }
 
 l1ls_status Inst::alloc(void** p, size_t bytes) {
-    L1LS_TRY(ctx->alloc(p, bytes));
+    L1LS_TRY(ctx->alloc(p, bytes, alloc_st, stream_ordered));
     allocs.push_back({*p, bytes});
     this->bytes += bytes;
     return L1LS_OK;
@@ -88,7 +89,7 @@ void Inst::free_all() {
     if (fista_work && fista_work_free) fista_work_free(fista_work);
     if (pd_work && pd_work_free) pd_work_free(pd_work);
     fista_work = pd_work = nullptr;
-    for (auto& a : allocs) ctx->release(a.p, a.bytes);
+    for (auto& a : allocs) ctx->release(a.p, a.bytes, alloc_st, stream_ordered);
     allocs.clear();
     bytes = 0;
 }
@@ -170,6 +171,8 @@ l1ls_status l1ls_destroy(l1ls_ctx* h) {
     if (!h) return set_error(L1LS_EINVAL, "ctx is NULL");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     cudaSetDevice(c->device);
+    if (c->server && c->server_stop) c->server_stop(c->server);   // cancels and joins the workers
+    c->server = nullptr;
     cudaDeviceSynchronize();
     {
         std::lock_guard<std::mutex> g(c->inst_mu);

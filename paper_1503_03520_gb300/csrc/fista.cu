@@ -413,7 +413,7 @@ struct FistaWork {
     double* part1 = nullptr;
     double* part2 = nullptr;
     FistaState* st = nullptr;
-    FistaState* host_st = nullptr;   // pinned
+    FistaState* host_st = nullptr;   // host copy of the state
     int grid1 = 0, grid2 = 0;
     cudaGraphExec_t exec = nullptr;
     int exec_chunk = 0;
@@ -422,7 +422,7 @@ struct FistaWork {
     cudaEvent_t ev[2][3] = {};
     ~FistaWork() {
         if (exec) cudaGraphExecDestroy(exec);
-        if (host_st) cudaFreeHost(host_st);
+        delete host_st;
         for (auto& row : ev)
             for (auto& e : row)
                 if (e) cudaEventDestroy(e);
@@ -571,7 +571,7 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
         L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 3 + 1024));
         L1LS_TRY(I->alloc_n(&w->st, 1));
-        L1LS_CUDA(cudaMallocHost((void**)&w->host_st, sizeof(FistaState)));
+        w->host_st = new FistaState();   // pageable: no allocation that synchronises the device
         for (int k = 0; k < 2; ++k) {
             L1LS_CUDA(cudaEventCreate(&w->ev[k][0]));
             L1LS_CUDA(cudaEventCreate(&w->ev[k][1]));
@@ -732,6 +732,7 @@ l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_stat
         const char* why = final_status == L1LS_ENOCONV ? "iteration limit reached"
                           : final_status == L1LS_ETIMEOUT ? "time limit reached"
                           : final_status == L1LS_ENUMERIC ? "NaN or Inf in the iteration"
+                          : final_status == L1LS_ECANCELLED ? "cancelled"
                                                           : "internal error";
         return set_error(final_status, "FISTA: %s (rel_gap %.3e)", why, f.rel);
     }
@@ -785,6 +786,10 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         L1LS_CUDA(cudaMemcpyAsync(w->host_st, w->st, sizeof(FistaState), cudaMemcpyDeviceToHost, st));
         L1LS_CUDA(cudaStreamSynchronize(st));
         if (w->host_st->stop) break;
+        if (cancel_requested()) {
+            final_status = L1LS_ECANCELLED;
+            break;
+        }
         if (o->time_limit_s > 0) {
             double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             if (el > o->time_limit_s) {

@@ -546,6 +546,119 @@ __global__ void k_colnorm2(const int32_t* __restrict__ ptr, const V* __restrict_
     out[j] = s;
 }
 
+// ---- IGen2 (Sec. 3.2, m < n): A = [B, N~] with B = L Sigma R^T square (m x m) ------------
+constexpr int kNMax = 64;           // nonzeros per column of N
+constexpr int kNTries = 4096;       // candidate rows drawn per column before giving up
+
+// Column i of N~ (step 4): the first d distinct rows among draw(NROW, i*4096 + t) mod m
+// (t = 0, 1, ...), the k-th accepted row with value 2 U(draw(NVAL, i*d + k)) - 1; then, in
+// ascending row order, dot = N_i^T e and N~_i = xi_i tau / |dot| N_i (unscaled when dot = 0,
+// where |N~_i^T e| <= tau holds anyway).  e and b are read in the stored row order
+// (original row r is stored row perm[r]).  Writes rows (stored index) and values, the
+// column's sum |N~_i| and |N~_i^T b| (for lambda_max).
+__global__ void k_igen2_cols(uint64_t seed, int64_t m, int64_t ncols, int d, double tau,
+                             const double* __restrict__ ehat, const double* __restrict__ bhat,
+                             const int32_t* __restrict__ perm, int32_t* __restrict__ rows_out,
+                             double* __restrict__ vals_out, double* __restrict__ col_abs, double* __restrict__ col_atb,
+                             int* __restrict__ err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncols) return;
+    int64_t rows[kNMax];
+    double v[kNMax];
+    const uint64_t krow = sm_stream(seed, kTagNRow), kval = sm_stream(seed, kTagNVal);
+    int cnt = 0;
+    for (int64_t t = 0; cnt < d; ++t) {
+        if (t >= kNTries) {
+            atomicExch(err, 1);
+            return;
+        }
+        const int64_t r = (int64_t)(sm_output(krow, (uint64_t)(i * kNTries + t)) % (uint64_t)m);
+        bool seen = false;
+        for (int k = 0; k < cnt; ++k) seen |= rows[k] == r;
+        if (seen) continue;
+        rows[cnt] = r;
+        v[cnt] = __dadd_rn(2.0 * u01(sm_output(kval, (uint64_t)(i * d + cnt))), -1.0);
+        ++cnt;
+    }
+    for (int a = 1; a < d; ++a) {                 // ascending rows (insertion sort)
+        const int64_t r = rows[a];
+        const double x = v[a];
+        int k = a - 1;
+        for (; k >= 0 && rows[k] > r; --k) {
+            rows[k + 1] = rows[k];
+            v[k + 1] = v[k];
+        }
+        rows[k + 1] = r;
+        v[k + 1] = x;
+    }
+    double dot = 0.0;
+    for (int k = 0; k < d; ++k) dot = __dadd_rn(dot, __dmul_rn(v[k], ehat[perm[rows[k]]]));
+    if (dot != 0.0) {
+        const double xi = __dadd_rn(2.0 * u01(sm_output(sm_stream(seed, kTagXi), (uint64_t)i)), -1.0);
+        const double scale = __ddiv_rn(__dmul_rn(xi, tau), fabs(dot));
+        for (int k = 0; k < d; ++k) v[k] = __dmul_rn(scale, v[k]);
+    }
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < d; ++k) {
+        rows_out[i * d + k] = perm[rows[k]];
+        vals_out[i * d + k] = v[k];
+        sa += fabs(v[k]);
+        sb = __dadd_rn(sb, __dmul_rn(v[k], bhat[perm[rows[k]]]));
+    }
+    col_abs[i] = sa;
+    col_atb[i] = fabs(sb);
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ out, int64_t count, int32_t v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = v;
+}
+
+// CSC -> CSR for IGen2 (any structure): per-row counts, scatter, then each row sorted by
+// column so the result does not depend on the order of the atomic scatter.
+__global__ void k_row_counts(const int32_t* __restrict__ row, int64_t nnz, int32_t* __restrict__ cnt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) atomicAdd(cnt + row[e], 1);
+}
+__global__ void k_scatter_rows(const int32_t* __restrict__ cptr, const int32_t* __restrict__ row,
+                               const double* __restrict__ cval, int64_t n, int32_t* __restrict__ fill,
+                               int32_t* __restrict__ rcol, double* __restrict__ rval) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int32_t e = cptr[j]; e < cptr[j + 1]; ++e) {
+        const int32_t pos = atomicAdd(fill + row[e], 1);
+        rcol[pos] = (int32_t)j;
+        rval[pos] = cval[e];
+    }
+}
+__global__ void k_sort_rows(const int32_t* __restrict__ rptr, int64_t m, int32_t* __restrict__ rcol,
+                            double* __restrict__ rval) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    const int32_t b = rptr[r], e = rptr[r + 1];
+    for (int32_t a = b + 1; a < e; ++a) {
+        const int32_t c = rcol[a];
+        const double x = rval[a];
+        int32_t k = a - 1;
+        for (; k >= b && rcol[k] > c; --k) {
+            rcol[k + 1] = rcol[k];
+            rval[k + 1] = rval[k];
+        }
+        rcol[k + 1] = c;
+        rval[k + 1] = x;
+    }
+}
+// per row: sum |a_rj| over the columns j >= m0 (the N~ part; sorted rows keep it last)
+__global__ void k_row_abs_tail(const int32_t* __restrict__ rptr, const int32_t* __restrict__ rcol,
+                               const double* __restrict__ rval, int64_t m, int64_t m0, double* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    double s = 0.0;
+    for (int32_t e = rptr[r]; e < rptr[r + 1]; ++e)
+        if (rcol[e] >= m0) s += fabs(rval[e]);
+    out[r] = s;
+}
+
 inline unsigned nblk(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b); }
 
 struct TempList {
@@ -586,7 +699,7 @@ l1ls_status cast_and_norms(Inst* I, const double* csc64, const double* csr64, cu
     L1LS_CUDA(cudaGetLastError());
     I->csc_val = cv;
     I->csr_val = rv;
-    if (I->p.left_stages == 1) {
+    if (I->p.left_stages == 1 && I->m >= I->n) {   // paired storage (IGen only)
         const int64_t np = I->nnz / 2, npairs = I->m / 2;
         V* pv = nullptr;
         V* qv = nullptr;
@@ -678,7 +791,8 @@ l1ls_status validate(const l1ls_gen_params* p) {
     if (p->m < 2 || p->n < 2) return set_error(L1LS_EINVAL, "m and n must be >= 2");
     if (p->m > (uint64_t)INT32_MAX - 2 || p->n > (uint64_t)INT32_MAX - 2)
         return set_error(L1LS_EINVAL, "m and n must be below 2^31 - 2");
-    if (p->m < p->n) return set_error(L1LS_EINVAL, "m < n (IGen2) is not supported by l1ls_generate yet");
+    if (p->m < p->n && (p->n_nnz_per_col < 1 || p->n_nnz_per_col > kNMax || (uint64_t)p->n_nnz_per_col > p->m))
+        return set_error(L1LS_EINVAL, "IGen2 (m < n): n_nnz_per_col must be in [1, min(%d, m)]", kNMax);
     if (!(p->kappa >= 1.0) || !std::isfinite(p->kappa)) return set_error(L1LS_EINVAL, "kappa must be >= 1");
     if (!(p->tau > 0.0)) return set_error(L1LS_EINVAL, "tau must be > 0");
     if (p->right_stages < 1 || p->right_stages > kWMax)
@@ -693,23 +807,28 @@ l1ls_status validate(const l1ls_gen_params* p) {
 
 }  // namespace
 
-l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out) {
+l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out,
+                              bool stream_ordered) {
     L1LS_TRY(validate(p));
     Inst* I = new Inst();
     I->ctx = ctx;
+    I->stream_ordered = stream_ordered;
+    I->alloc_st = st;
     I->p = *p;
     I->m = (int64_t)p->m;
     I->n = (int64_t)p->n;
-    I->nsq = I->n;
+    const bool igen2 = p->m < p->n;             // Procedure IGen2 (Sec. 3.2): A = [B, N~]
+    I->nsq = igen2 ? (int64_t)p->m : (int64_t)p->n;
+    I->igen2 = igen2;
     I->dtype = p->value_dtype;
     int64_t s = (int64_t)std::floor(p->xstar_frac * (double)p->n + 0.5);
     if (s < 1) s = 1;
     if (s > I->m) s = I->m;
     if (s > I->n) s = I->n;
     I->s = s;
-    const int64_t m = I->m, n = I->n;
+    const int64_t m = I->m, n = I->n, nsq = I->nsq;
     const double vt = std::isnan(p->vartheta) ? p->theta : p->vartheta;
-    Geo g{m, n, p->right_stages, p->left_stages, std::cos(p->theta), std::sin(p->theta), std::cos(vt), std::sin(vt)};
+    Geo g{m, nsq, p->right_stages, p->left_stages, std::cos(p->theta), std::sin(p->theta), std::cos(vt), std::sin(vt)};
 
     auto fail = [&](l1ls_status e) {
         I->free_all();
@@ -730,7 +849,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
     {
         TempList tmp(st);
         // persistent vectors
-        GEN_TRY(I->alloc_n(&I->sigma, n));
+        GEN_TRY(I->alloc_n(&I->sigma, nsq));
         GEN_TRY(I->alloc_n(&I->xstar, n));
         GEN_TRY(I->alloc_n(&I->bhat, pad32(m)));
         GEN_CUDA(cudaMemsetAsync(I->bhat, 0, sizeof(double) * pad32(m), st));
@@ -749,8 +868,8 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         // singular values: sigma_i = kappa^(-rank_i/(n-1))
         uint32_t* order_n = nullptr;
         GEN_TRY(tmp.get(&order_n, n));
-        GEN_TRY(argsort_stream(p->seed, kTagSigma, n, order_n, tmp, st));
-        k_sigma<<<nblk(n), 256, 0, st>>>(order_n, n, std::log(p->kappa), I->sigma);
+        GEN_TRY(argsort_stream(p->seed, kTagSigma, nsq, order_n, tmp, st));
+        k_sigma<<<nblk(nsq), 256, 0, st>>>(order_n, nsq, std::log(p->kappa), I->sigma);
         GEN_CUDA(cudaGetLastError());
         // row permutation P (P1 = P2 = P)
         if (p->left_stages == 1) {
@@ -762,8 +881,8 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
             k_identity_perm<<<nblk(m), 256, 0, st>>>(m, I->perm, I->perm_inv);
         }
         GEN_CUDA(cudaGetLastError());
-        // support of x*: the s smallest keys
-        GEN_TRY(argsort_stream(p->seed, kTagSupport, n, order_n, tmp, st));
+        // support of x*: the s smallest keys (among the first m columns for IGen2)
+        GEN_TRY(argsort_stream(p->seed, kTagSupport, nsq, order_n, tmp, st));
         uint8_t* flag = nullptr;
         GEN_TRY(tmp.get(&flag, n));
         GEN_CUDA(cudaMemsetAsync(flag, 0, n, st));
@@ -777,21 +896,23 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_TRY(tmp.get(&zb, n));
         GEN_TRY(tmp.get(&ul, n));
         GEN_TRY(tmp.get(&ehat, m));
-        k_xstar_g<<<nblk(n), 256, 0, st>>>(p->seed, n, n, flag, p->xstar_lo, p->xstar_hi, p->g_offsupport, I->xstar,
+        k_xstar_g<<<nblk(n), 256, 0, st>>>(p->seed, n, nsq, flag, p->xstar_lo, p->xstar_hi, p->g_offsupport, I->xstar,
                                             gvec);
         GEN_CUDA(cudaGetLastError());
-        // IGen step 3 by the route of Sec. 4: R^T g and R^T x* (T_w^T first)
-        GEN_CUDA(cudaMemcpyAsync(vg, gvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        GEN_CUDA(cudaMemcpyAsync(vx, I->xstar, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        // IGen step 3 by the route of Sec. 4: R^T g and R^T x* (T_w^T first).  IGen2 step 3,
+        // e = tau B^{-T} g = tau L Sigma^{-1} R^T g, and b = B x* + e are the same expressions
+        // on the square part (x* is zero on the columns of N).
+        GEN_CUDA(cudaMemcpyAsync(vg, gvec, sizeof(double) * nsq, cudaMemcpyDeviceToDevice, st));
+        GEN_CUDA(cudaMemcpyAsync(vx, I->xstar, sizeof(double) * nsq, cudaMemcpyDeviceToDevice, st));
         for (int k = p->right_stages; k >= 1; --k) {
-            k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(vg, n, (k - 1) & 1, g.c, g.s, 1);
-            k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(vx, n, (k - 1) & 1, g.c, g.s, 1);
+            k_stage<<<nblk(nsq / 2 + 1), 256, 0, st>>>(vg, nsq, (k - 1) & 1, g.c, g.s, 1);
+            k_stage<<<nblk(nsq / 2 + 1), 256, 0, st>>>(vx, nsq, (k - 1) & 1, g.c, g.s, 1);
         }
-        k_scale<<<nblk(n), 256, 0, st>>>(vg, vx, I->sigma, n, p->tau, ze, zb, ul);
+        k_scale<<<nblk(nsq), 256, 0, st>>>(vg, vx, I->sigma, nsq, p->tau, ze, zb, ul);
         k_left<<<nblk(m), 256, 0, st>>>(ze, zb, I->perm, g, ehat, I->bhat);
-        // A^T b = R u (T_1 first) for lambda_max
+        // B^T b = R u (T_1 first) for lambda_max
         for (int k = 1; k <= p->right_stages; ++k)
-            k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(ul, n, (k - 1) & 1, g.c, g.s, 0);
+            k_stage<<<nblk(nsq / 2 + 1), 256, 0, st>>>(ul, nsq, (k - 1) & 1, g.c, g.s, 0);
         GEN_CUDA(cudaGetLastError());
         double* red = nullptr;
         double* partials = nullptr;
@@ -800,7 +921,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_TRY(tmp.get(&partials, 3 * 512));
         GEN_TRY(tmp.get(&counter, 1));
         GEN_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-        k_reduce3<<<512, 256, 0, st>>>(I->xstar, n, ehat, m, ul, n, partials, counter, red);
+        k_reduce3<<<512, 256, 0, st>>>(I->xstar, n, ehat, m, ul, nsq, partials, counter, red);
         GEN_CUDA(cudaGetLastError());
         double hred[3];
         GEN_CUDA(cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st));
@@ -809,20 +930,43 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         int32_t* cnt = nullptr;
         GEN_TRY(tmp.get(&cnt, (m > n ? m : n)));
         GEN_TRY(I->alloc_n(&I->csc_ptr, n + 1));
-        k_csc_count<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, cnt);
+        k_csc_count<<<nblk(nsq), 256, 0, st>>>(g, I->perm_inv, cnt);
+        const int d = p->n_nnz_per_col;
+        if (igen2) k_fill_i32<<<nblk(n - nsq), 256, 0, st>>>(cnt + nsq, n - nsq, d);
         GEN_CUDA(cudaGetLastError());
         int64_t nnz = 0;
         GEN_TRY(exclusive_scan_i32(cnt, n, I->csc_ptr, &nnz, st));
+        if (nnz > (int64_t)INT32_MAX - 2 * kPad)
+            return fail(set_error(L1LS_EINVAL, "nnz = %lld does not fit 32-bit offsets", (long long)nnz));
         I->nnz = nnz;
+        const int64_t nnz_sq = nnz - (n - nsq) * (int64_t)d * (igen2 ? 1 : 0);
         double *csc64 = nullptr, *csr64 = nullptr;
         GEN_TRY(I->alloc_n(&I->csc_row, nnz + kPad));
         GEN_CUDA(cudaMemsetAsync(I->csc_row + nnz, 0, sizeof(int32_t) * kPad, st));
         GEN_TRY(tmp.get(&csc64, nnz));
-        k_csc_fill<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, I->sigma, I->csc_ptr, I->csc_row, csc64);
+        k_csc_fill<<<nblk(nsq), 256, 0, st>>>(g, I->perm_inv, I->sigma, I->csc_ptr, I->csc_row, csc64);
         GEN_CUDA(cudaGetLastError());
+        double *col_abs = nullptr, *col_atb = nullptr, *row_abs = nullptr, *red2 = nullptr;
+        int* err_n = nullptr;
+        if (igen2) {
+            // IGen2 step 4: the columns of N~ after those of B
+            GEN_TRY(tmp.get(&col_abs, n - nsq));
+            GEN_TRY(tmp.get(&col_atb, n - nsq));
+            GEN_TRY(tmp.get(&err_n, 1));
+            GEN_CUDA(cudaMemsetAsync(err_n, 0, sizeof(int), st));
+            k_igen2_cols<<<nblk(n - nsq, 128), 128, 0, st>>>(p->seed, m, n - nsq, d, p->tau, ehat, I->bhat, I->perm,
+                                                             I->csc_row + nnz_sq, csc64 + nnz_sq, col_abs, col_atb,
+                                                             err_n);
+            GEN_CUDA(cudaGetLastError());
+        }
         // CSR(Ahat): counts, scan, fill by lookup in CSR(Ahat^T)
         GEN_TRY(I->alloc_n(&I->csr_ptr, m + 1));
-        k_csr_count<<<nblk(m), 256, 0, st>>>(g, I->perm, cnt);
+        if (igen2) {
+            GEN_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * m, st));
+            k_row_counts<<<nblk(nnz), 256, 0, st>>>(I->csc_row, nnz, cnt);
+        } else {
+            k_csr_count<<<nblk(m), 256, 0, st>>>(g, I->perm, cnt);
+        }
         GEN_CUDA(cudaGetLastError());
         int64_t nnz_r = 0;
         GEN_TRY(exclusive_scan_i32(cnt, m, I->csr_ptr, &nnz_r, st));
@@ -835,8 +979,26 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_TRY(I->alloc_n(&I->csr_col, nnz + kPad));
         GEN_CUDA(cudaMemsetAsync(I->csr_col + nnz, 0, sizeof(int32_t) * kPad, st));
         GEN_TRY(tmp.get(&csr64, nnz));
-        k_csr_fill<<<nblk(m), 256, 0, st>>>(g, I->perm, I->csc_ptr, I->csc_row, csc64, I->csr_ptr, I->csr_col, csr64,
-                                             err);
+        if (igen2) {
+            int32_t* fill = nullptr;
+            GEN_TRY(tmp.get(&fill, m));
+            GEN_CUDA(cudaMemcpyAsync(fill, I->csr_ptr, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
+            k_scatter_rows<<<nblk(n), 256, 0, st>>>(I->csc_ptr, I->csc_row, csc64, n, fill, I->csr_col, csr64);
+            k_sort_rows<<<nblk(m), 256, 0, st>>>(I->csr_ptr, m, I->csr_col, csr64);
+            // step size: sigma_max^2 + ||N~||_1 ||N~||_inf, and lambda_max over the columns of N~
+            GEN_TRY(tmp.get(&row_abs, m));
+            GEN_TRY(tmp.get(&red2, 9));
+            k_row_abs_tail<<<nblk(m), 256, 0, st>>>(I->csr_ptr, I->csr_col, csr64, m, nsq, row_abs);
+            GEN_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+            k_reduce3<<<512, 256, 0, st>>>(nullptr, 0, nullptr, 0, col_abs, n - nsq, partials, counter, red2);
+            GEN_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+            k_reduce3<<<512, 256, 0, st>>>(nullptr, 0, nullptr, 0, row_abs, m, partials, counter, red2 + 3);
+            GEN_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+            k_reduce3<<<512, 256, 0, st>>>(nullptr, 0, nullptr, 0, col_atb, n - nsq, partials, counter, red2 + 6);
+        } else {
+            k_csr_fill<<<nblk(m), 256, 0, st>>>(g, I->perm, I->csc_ptr, I->csc_row, csc64, I->csr_ptr, I->csr_col,
+                                                 csr64, err);
+        }
         GEN_CUDA(cudaGetLastError());
         switch (I->dtype) {
             case L1LS_F64: GEN_TRY(cast_and_norms<double>(I, csc64, csr64, st)); break;
@@ -845,7 +1007,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         }
         if (I->bhat32) k_to_f32<<<nblk(m), 256, 0, st>>>(I->bhat, m, I->bhat32);
         GEN_CUDA(cudaGetLastError());
-        if (I->paired) {
+        if (I->paired) {   // (never for IGen2: the columns of N~ do not keep row pairs together)
             switch (I->dtype) {
                 case L1LS_F64: GEN_TRY(reorder_pairs<double>(I, st)); break;
                 case L1LS_F32: GEN_TRY(reorder_pairs<float>(I, st)); break;
@@ -864,10 +1026,17 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_CUDA(cudaGetLastError());
         int htmax[2] = {0, 0};
         GEN_CUDA(cudaMemcpyAsync(htmax, tmax, sizeof(htmax), cudaMemcpyDeviceToHost, st));
-        int herr = 0, herr2 = 0;
+        int herr = 0, herr2 = 0, herr3 = 0;
+        double hred2[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         GEN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
         GEN_CUDA(cudaMemcpyAsync(&herr2, I->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (igen2) {
+            GEN_CUDA(cudaMemcpyAsync(&herr3, err_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GEN_CUDA(cudaMemcpyAsync(hred2, red2, sizeof(hred2), cudaMemcpyDeviceToHost, st));
+        }
         GEN_CUDA(cudaStreamSynchronize(st));
+        if (herr3) return fail(set_error(L1LS_EINVAL, "IGen2: %d distinct rows of %lld not found in %d draws", d,
+                                         (long long)m, kNTries));
         if (herr) return fail(set_error(L1LS_ECUDA, "internal: an entry of CSR(A) was not found in CSR(A^T)"));
         if (herr2) return fail(set_error(L1LS_ECUDA, "internal: the paired storage found unpaired rows (%d)", herr2));
         I->csr_tile_max = htmax[0];
@@ -875,6 +1044,11 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         I->f_star = p->tau * hred[0] + 0.5 * hred[1];
         I->lam_max = hred[2];
         I->lipschitz = 1.0;   // sigma_max = kappa^0 = 1
+        if (igen2) {
+            // hred2: [2] max column sum |N~|, [5] max row sum |N~|, [8] max |N~^T b|
+            I->lipschitz = 1.0 + hred2[2] * hred2[5];
+            I->lam_max = std::max(I->lam_max, hred2[8]);
+        }
     }
     GEN_CUDA(cudaStreamSynchronize(st));
 #undef GEN_TRY

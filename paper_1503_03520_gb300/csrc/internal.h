@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdint>
 #include <mutex>
@@ -46,9 +47,15 @@ struct Ctx {
     std::vector<Inst*> insts;   // instances owned by the context
     std::mutex inst_mu;
 
-    l1ls_status alloc(void** p, size_t bytes);
-    void release(void* p, size_t bytes);
+    // stream_ordered: cudaMallocAsync / cudaFreeAsync on `st` (no device-wide synchronisation;
+    // the serving workers allocate this way so that their work overlaps)
+    l1ls_status alloc(void** p, size_t bytes, cudaStream_t st = nullptr, bool stream_ordered = false);
+    void release(void* p, size_t bytes, cudaStream_t st = nullptr, bool stream_ordered = false);
     l1ls_status staging(int which, size_t bytes, void** out);
+    // serving loop (created by the first l1ls_submit or l1ls_serve_config)
+    void* server = nullptr;
+    void (*server_stop)(void*) = nullptr;
+    std::mutex server_mu;
 };
 
 // ---- instance -----------------------------------------------------------------------------
@@ -89,6 +96,8 @@ struct Inst {
     int64_t csr_tile_max = 0, csc_tile_max = 0;   // most nonzeros in a 32-row tile
     int* dev_err = nullptr;                       // set by kernels whose bounded waits expired
     size_t bytes = 0;
+    bool stream_ordered = false;    // allocations ordered on alloc_st (serving workers)
+    cudaStream_t alloc_st = nullptr;
     // solver work spaces (allocated on first use, owned by the instance)
     void* fista_work = nullptr;
     void (*fista_work_free)(void*) = nullptr;
@@ -114,7 +123,12 @@ inline size_t dtype_size(int dt) { return dt == L1LS_F64 ? 8 : dt == L1LS_F32 ? 
 bool is_device_pointer(const void* p);
 
 // ---- entry points implemented per file ------------------------------------------------
-l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out);
+l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out,
+                              bool stream_ordered = false);
+
+// the serving worker's cancel flag (null elsewhere); solver loops poll it between launches
+extern thread_local const std::atomic<int>* tl_cancel;
+inline bool cancel_requested() { return tl_cancel && tl_cancel->load(std::memory_order_relaxed) != 0; }
 
 // products on device buffers (relabelled row order), vec_dtype F64 or F32
 l1ls_status spmv_plain(const Inst* I, bool transpose, const void* x, int vec_dtype, void* y,

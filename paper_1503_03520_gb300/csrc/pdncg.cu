@@ -372,7 +372,7 @@ struct PdWork {
     int cg_chunk = 0;
     ~PdWork() {
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
-        if (host) cudaFreeHost(host);
+        delete host;
     }
 };
 
@@ -427,7 +427,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         const int gmax = std::max(w->gm, std::max(w->gn, w->gv));
         L1LS_TRY(I->alloc_n(&w->part, (int64_t)gmax * (kTrialsPerPass + 1)));
         L1LS_TRY(I->alloc_n(&w->st, 1));
-        L1LS_CUDA(cudaMallocHost((void**)&w->host, sizeof(PdState)));
+        w->host = new PdState();   // pageable: no allocation that synchronises the device
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
@@ -490,6 +490,10 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
             final_status = L1LS_ETIMEOUT;
             break;
         }
+        if (cancel_requested()) {
+            final_status = L1LS_ECANCELLED;
+            break;
+        }
         k_pd_init<float><<<w->gv, kBlock, 0, s>>>(w->X, w->gd, w->atr, I->colnorm2, w->grad, w->hd, w->minv, w->rcg,
                                                   w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->d, n, w->part, w->st);
         L1LS_CUDA(cudaGetLastError());
@@ -532,6 +536,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     if (final_status != L1LS_OK) {
         const char* why = final_status == L1LS_ENOCONV ? "Newton iteration limit reached"
                           : final_status == L1LS_ETIMEOUT ? "time limit reached"
+                          : final_status == L1LS_ECANCELLED ? "cancelled"
                                                           : "NaN or Inf in the iteration";
         return set_error(final_status, "pdNCG: %s (rel_gap %.3e)", why, f.rel);
     }

@@ -273,18 +273,21 @@ namespace l1ls {
 // words); the column traversal gathers the residual of row pair p as one float4
 // {hi(2p), hi(2p+1), lo(2p), lo(2p+1)}, both rows with one 16-byte load.
 
-template <bool ROWS, class V, class Pre, class Epi>
+template <bool ROWS, class V, int EPL = kEPL, class Pre, class Epi>
 __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                              const V* __restrict__ val2, const float* __restrict__ xh,
                                              const float* __restrict__ xl, const float4* __restrict__ r4, int64_t nrows,
                                              float* __restrict__ wbuf, Pre& pre, Epi& epi) {
     // ROWS: nrows row pairs, (xh, xl) gathered at the column index (pre / epi per row, 2p and
-    // 2p+1); otherwise nrows columns, the pair residual r4 gathered at p.
+    // 2p+1); otherwise nrows columns, the pair residual r4 gathered at p.  EPL entries per lane
+    // and chunk (4 or 8): fewer registers with 4, more loads in flight with 8.
+    static_assert(EPL == 4 || EPL == 8, "EPL must be 4 or 8");
+    constexpr int kChunk = 32 * EPL;
     const int lane = threadIdx.x & 31;
     float* w0h = wbuf;
-    float* w0l = wbuf + kWarpChunk;
-    float* w1h = wbuf + 2 * kWarpChunk;
-    float* w1l = wbuf + 3 * kWarpChunk;
+    float* w0l = wbuf + kChunk;
+    float* w1h = wbuf + 2 * kChunk;
+    float* w1l = wbuf + 3 * kChunk;
     const int64_t r = (t << 5) + lane;
     const bool has = r < nrows;
     int32_t rb = 0, re = 0;
@@ -298,16 +301,16 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
     const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
     const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
     ff a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
-    for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
-        const int32_t base = c + lane * kEPL;
-        ff p0[kEPL], p1[kEPL];
+    for (int32_t c = e0 & ~(EPL - 1); c < e1; c += kChunk) {
+        const int32_t base = c + lane * EPL;
+        ff p0[EPL], p1[EPL];
         if (base < e1) {
-            int32_t ij[kEPL];
-            V vv[2 * kEPL];
-            load_span<int32_t, kEPL>(idx + base, ij);
-            load_span<V, 2 * kEPL>(val2 + 2 * (int64_t)base, vv);
+            int32_t ij[EPL];
+            V vv[2 * EPL];
+            load_span<int32_t, EPL>(idx + base, ij);
+            load_span<V, 2 * EPL>(val2 + 2 * (int64_t)base, vv);
 #pragma unroll
-            for (int k = 0; k < kEPL; ++k) {
+            for (int k = 0; k < EPL; ++k) {
                 const int32_t e = base + k;
                 const bool in = e >= e0 && e < e1;
                 const float v0 = val_to_acc<float>(vv[2 * k]), v1 = val_to_acc<float>(vv[2 * k + 1]);
@@ -330,10 +333,10 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < kEPL; ++k) p0[k] = p1[k] = {0.f, 0.f};
+            for (int k = 0; k < EPL; ++k) p0[k] = p1[k] = {0.f, 0.f};
         }
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k) {
+        for (int k = 0; k < EPL; ++k) {
             w0h[k * 32 + lane] = p0[k].hi;
             w0l[k * 32 + lane] = p0[k].lo;
             if (ROWS) {
@@ -342,10 +345,10 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
             }
         }
         __syncwarp();
-        const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
+        const int32_t lo = max(rb, c), hi = min(re, c + kChunk);
         for (int32_t e = lo; e < hi; ++e) {
             const int32_t i = e - c;
-            const int32_t q = (i & (kEPL - 1)) * 32 + (i / kEPL);
+            const int32_t q = (i & (EPL - 1)) * 32 + (i / EPL);
             a0 = ff_add(a0, {w0h[q], w0l[q]});
             if (ROWS) a1 = ff_add(a1, {w1h[q], w1l[q]});
         }

@@ -47,7 +47,8 @@ def test_batch_path_matches_oracle(setup):
     batch = l1.Batch(ctx, insts)
     xs = [np.zeros(i.n) for i in insts]
     res = batch.solve_path(taus, x_out=xs, tol=1e-6, max_iter=100000, restart=1)
-    assert batch.schedule()["block"] in (128, 256)
+    sch = batch.schedule()
+    assert (sch["block"], sch["entries_per_lane"]) in sch["candidates"]
     for k, ref in enumerate(refs):
         A = stored_values(ref.A, "f32")
         b = ref.b.astype(np.float32).astype(np.float64)

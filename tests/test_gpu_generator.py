@@ -98,3 +98,66 @@ def test_invalid_parameters_are_rejected(ctx):
         with pytest.raises(l1.L1LSError) as e:
             ctx.generate(W.params(**bad))
         assert e.value.status == 1
+
+
+IGEN2_CASES = [
+    dict(m=1024, n=2048, right_stages=2, left_stages=1, kappa=1e2, value_dtype="f64", seed=11),
+    dict(m=3001, n=6007, right_stages=1, left_stages=0, kappa=1e3, value_dtype="f32", seed=12, n_nnz_per_col=5),
+    dict(m=4096, n=5000, right_stages=3, left_stages=1, kappa=1e4, value_dtype="bf16", seed=13, n_nnz_per_col=16),
+]
+
+
+@pytest.mark.parametrize("case", IGEN2_CASES, ids=lambda c: "m%d_n%d_%s" % (c["m"], c["n"], c["value_dtype"]))
+def test_igen2_generator_matches_oracle(ctx, case):
+    """Procedure IGen2 (Sec. 3.2): A = [B, N~] with the square part of Eq. (bd8)."""
+    params = W.params(**case)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        m, n = params["m"], params["n"]
+        info = inst.info
+        assert info["igen2"] == 1 and inst.nnz == ref.A.nnz
+        ex = inst.export()
+        A = csr_from_export(ex, m, n)
+        assert np.array_equal(ex["indptr"], ref.A.indptr.astype(np.int64))
+        assert np.array_equal(ex["indices"], ref.A.indices.astype(np.int32))
+        assert np.array_equal(np.flatnonzero(ex["xstar"]), ref.support)
+        assert ref.support.max() < m
+        assert np.array_equal(ex["xstar"], ref.xstar)
+        assert len(ex["sigma"]) == m
+        # values: the scale of a column of N~ divides by N_i^T e, summed in another order on the
+        # device than by the oracle's dot product: agreement to a few FP64 ulps before storage
+        dt = params["value_dtype"]
+        diff = np.abs(A.data - ref.A.data)
+        if dt == "f64":
+            assert np.all(diff <= 1e-13 * np.abs(ref.A.data) + 1e-14 * np.abs(ref.A.data).max())
+        else:
+            assert np.all(diff <= ulp(ref.A.data, dt) + 1e-15)
+        scale = np.abs(ref.b).max()
+        assert np.abs(ex["b"] - ref.b).max() <= 50 * params["kappa"] * 2.2e-16 * scale
+        assert info["f_star"] == pytest.approx(ref.f_star, rel=1e-12)
+        # a bound built from the values of N~, whose scale divides by a cancelling dot product
+        assert info["lipschitz"] == pytest.approx(ref.lipschitz, rel=1e-11)
+        assert info["lam_max"] == pytest.approx(ref.lam_max, rel=max(1e-10, 10 * params["kappa"] ** 2 * 2.2e-16))
+        et = inst.export_t()
+        At = ref.A.tocsc()
+        At.sort_indices()
+        assert np.array_equal(et["indptr"], At.indptr.astype(np.int64))
+        assert np.array_equal(et["indices"], At.indices.astype(np.int32))
+        if dt == "f64":
+            # Eq. (bd10): A^T (b - A x*) = tau g with |g_i| <= 1, g_i = sign(x*_i) on the support
+            tau = params["tau"]
+            gt = A.T @ (ex["b"] - A @ ex["xstar"]) / tau
+            S = ref.support
+            assert np.abs(gt[S] - np.sign(ex["xstar"][S])).max() <= 1e-9 * params["kappa"]
+            assert np.abs(gt).max() <= 1.0 + 1e-9 * params["kappa"]
+    finally:
+        inst.free()
+
+
+def test_igen2_rejects_bad_column_counts(ctx):
+    import paper_1503_03520_gb300 as l1
+    for d in (0, 65):
+        with pytest.raises(l1.L1LSError) as e:
+            ctx.generate(W.params(m=256, n=512, n_nnz_per_col=d))
+        assert e.value.status == 1

@@ -213,3 +213,14 @@ def test_planted_sign_error_is_caught(monkeypatch):
     inst = generate(GenParams(m=64, n=32, seed=1, kappa=10.0, right_stages=2))
     x = np.random.default_rng(0).standard_normal(32)
     assert not np.allclose(mvpa(inst, x), inst.A @ x, atol=1e-8)
+
+
+def test_igen2_step_size_bounds_the_spectrum():
+    """IGen2's FISTA step size: sigma_max^2 + ||N~||_1 ||N~||_inf >= ||A||_2^2, since
+    ||[B N~]||^2 <= ||B||^2 + ||N~||^2 and ||N~||_2^2 <= ||N~||_1 ||N~||_inf."""
+    for seed in (1, 2):
+        inst = generate(GenParams(m=48, n=80, seed=seed, kappa=30.0, right_stages=2, xstar_frac=0.1,
+                                  n_nnz_per_col=5))
+        top = np.linalg.svd(inst.A.toarray(), compute_uv=False)[0]
+        assert inst.lipschitz >= top ** 2 * (1 - 1e-12)
+        assert inst.lipschitz <= 1.0 + 5.0 * 48
