@@ -199,6 +199,127 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_form(l1, W, ctx, iters_per_tau):
+    """C4: 256 instances along 16-tau paths in the batched kernel, against the same paths
+    solved one instance at a time with FP64 values (a 1-in-16 subsample), equal tolerance and
+    iteration caps."""
+    import numpy as np
+    import torch
+    params = W.c4_batch(256)
+    insts = [ctx.generate(p) for p in params]
+    taus = np.array([W.c4_tau_path(i.info["lam_max"]) for i in insts])
+    b = l1.Batch(ctx, insts)
+    opts = dict(tol=1e-6, max_iter=iters_per_tau, restart=1)
+    t = time.perf_counter()
+    res = b.solve_path(taus, **opts)
+    el = time.perf_counter() - t
+    st = b.stats()
+    sched = b.schedule()
+    b.free()
+    it = sum(r["iters"] for rr in res for r in rr)
+    ok = sum(r["status"] == 0 for rr in res for r in rr)
+    for i in insts:
+        i.free()
+    sub = list(range(0, 256, 16))
+    t_one, it_one, ok_one = 0.0, 0, 0
+    for i in sub:
+        inst = ctx.generate(dict(params[i], value_dtype="f64"))
+        x0 = None
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for tau in taus[i]:
+            x0, r = inst.solve_fista(tau=float(tau), x0=x0, allow=(4, 5), **opts)
+            it_one += r["iters"]
+            ok_one += r["status"] == 0
+        t_one += time.perf_counter() - t
+        inst.free()
+    rate, rate_one = it / el, it_one / t_one
+    return {"workload": "c4: 256 instances, n = 2^U[12,18], m = 2n, ~8/col, kappa 10^U[2,5], x* 1%%, 16 taus "
+                        "0.9 lambda_max .. 1e-3, warm-started, tol 1e-6, at most %d FISTA iterations per tau"
+                        % iters_per_tau,
+            "batched": {"seconds": el, "instance_iterations": it, "instance_iterations_per_s": rate,
+                        "certified": ok, "of": 256 * 16, "steps": st["steps"],
+                        "ms_per_step": st["device_ms"] / max(1, st["steps"]), "schedule": sched,
+                        "values": "FP32, float-float products and iterates"},
+            "one_at_a_time_fp64": {"seconds": t_one, "instances": len(sub), "instance_iterations": it_one,
+                                   "instance_iterations_per_s": rate_one, "certified": ok_one,
+                                   "of": len(sub) * 16, "api": "l1ls_solve_fista per instance and tau"},
+            "speedup_instance_iterations": rate / rate_one}
+
+
+def serve_form(l1, W, count, rate, log2n_hi, limit_s):
+    """C5: Poisson arrivals into the serving loop (8 slots, FP32 values) against the same
+    requests served FIFO one at a time with FP64 values (one slot)."""
+    import numpy as np
+    reqs = W.c5_requests(count, rate, log2n_hi=log2n_hi)
+
+    def run(dtype, slots, accum):
+        ctx = l1.Context(0)
+        ctx.serve_config(slots=slots)
+        of = dict(tol=1e-6, max_iter=20000, restart=1, time_limit_s=limit_s, accum=accum)
+        op = dict(tol=1e-6, max_iter=100, time_limit_s=limit_s)
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            now = time.perf_counter() - t0
+            if r["t"] > now:
+                time.sleep(r["t"] - now)
+            o = of if r["method"] == "fista" else op
+            tickets.append(ctx.submit(dict(r["params"], value_dtype=dtype), method=r["method"], tau=-r["tau_factor"],
+                                      **o))
+        out = []
+        for t in tickets:
+            while True:
+                o = ctx.poll(t, wait_ms=100)
+                if o is not None:
+                    out.append(o)
+                    break
+        el = time.perf_counter() - t0
+        st = ctx.serve_stats()
+        ctx.close()
+        lat = np.array([o[1]["latency_s"] for o in out])
+        ok = int(sum(o[0] == 0 for o in out))
+        return {"seconds": el, "certified": ok, "of": len(out), "certified_per_s": ok / el,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "peak_running": st["peak_running"],
+                "statuses": {l1.STATUS.get(k, str(k)): int(v) for k, v in
+                             enumerate(np.bincount([o[0] for o in out], minlength=10)) if v}}
+
+    served = run("f32", 8, 1)
+    fifo = run("f64", 1, 0)
+    return {"workload": "c5: %d Poisson requests at %g/s, n = 2^U[10,%d], m in {n/2, 2n}, kappa 10^U[2,6], "
+                        "x* 0.5-5%%, tau = 10^U[-2,0] lambda_max, FISTA (kappa <= 1e3, restart) or pdNCG, tol 1e-6, "
+                        "%g s limit per request" % (count, rate, log2n_hi, limit_s),
+            "served": served, "fifo_fp64": fifo,
+            "speedup_certified_per_s": served["certified_per_s"] / max(fifo["certified_per_s"], 1e-12)}
+
+
+def precision_form(l1, W, limit_s):
+    """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
+    column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
+    BF16) to a 1e-6 gap (1e-4 for BF16), against the FP64 optimum x*, f* of the generator."""
+    import numpy as np
+    ctx = l1.Context(0)
+    rows = []
+    for kappa in (1e2, 1e4, 1e6):
+        for dt in ("f64", "f32", "bf16"):
+            inst = ctx.generate(W.c3(kappa, dt))
+            xs = inst.xstar()
+            tol = 1e-4 if dt == "bf16" else 1e-6
+            t = time.perf_counter()
+            x, r = inst.solve_fista(tau=1.0, tol=tol, max_iter=10 ** 6, restart=1, accum=0 if dt == "f64" else 1,
+                                    time_limit_s=limit_s, allow=(4, 5))
+            el = time.perf_counter() - t
+            f_star = inst.info["f_star"]
+            rows.append({"kappa": kappa, "values": dt, "tol": tol, "status": r["status_name"], "iters": r["iters"],
+                         "seconds": el, "rel_gap": r["rel_gap"], "rel_err_f": abs(r["f"] - f_star) / f_star,
+                         "rel_err_x": float(np.linalg.norm(x - xs) / np.linalg.norm(xs))})
+            inst.free()
+    ctx.close()
+    return {"workload": "c3: m=2^22, n=2^21, ~16/col, x* 2%%, tau=1, FISTA with restart, %g s limit" % limit_s,
+            "runs": rows}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -304,7 +425,15 @@ def run_ours(args):
                               "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]}
 
     inst.free()
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {"batch": batch_form(l1, W, ctx, args.batch_iters)}
     ctx.close()
+    if rank == 0 and not args.no_forms:
+        forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_limit)
+    if rank == 0 and args.precision:
+        forms = forms or {}
+        forms["precision"] = precision_form(l1, W, args.precision_limit)
 
     if rank == 0:
         cpu = None
@@ -327,7 +456,7 @@ def run_ours(args):
                            "parallelism": "replicas (one instance per GPU)" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps, "fista_rel_gap_after_steps": fres["rel_gap"],
-                "time_to_gap": {"tol": W.C2_TOL, **solves}}
+                "time_to_gap": {"tol": W.C2_TOL, **solves}, "forms": forms}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -344,7 +473,15 @@ def main():
     ap.add_argument("--no-solves", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--solve-limit", type=float, default=60.0)
+    ap.add_argument("--solve-limit", type=float, default=30.0)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched (c4) and serving (c5) legs")
+    ap.add_argument("--batch-iters", type=int, default=300, help="c4: FISTA iterations per tau at most")
+    ap.add_argument("--serve-count", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=300.0)
+    ap.add_argument("--serve-log2n", type=int, default=20, help="c5: largest log2 n of a request")
+    ap.add_argument("--serve-limit", type=float, default=2.0, help="c5: time limit per request (s)")
+    ap.add_argument("--precision", action="store_true", help="add the c3 precision sweep (about 1-2 min)")
+    ap.add_argument("--precision-limit", type=float, default=8.0, help="c3: time limit per solve (s)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

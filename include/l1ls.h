@@ -175,10 +175,10 @@ typedef struct {
     int32_t check_every;      /* iterations per graph launch between host checks          */
     int32_t restart;          /* FISTA: 1 = gradient restart of O'Donoghue & Candes (t <- 1 when
                                  (y_k - x_k)^T (x_k - x_{k-1}) > 0); 0 = none, as in the paper  */
-    int32_t accum;            /* FISTA, FP32 / BF16 values in paired storage: 0 = products summed
-                                 in FP32 (the default); 1 = products of the float-float iterate and
-                                 residual summed in float-float (about 44 bits), for gaps below
-                                 the FP32 floor at small tau or large kappa.  EINVAL otherwise.
+    int32_t accum;            /* FISTA, FP32 / BF16 values: 0 = products summed in FP32 (the
+                                 default); 1 = products of the float-float iterate and residual
+                                 summed in float-float (about 44 bits), for gaps below the FP32
+                                 floor at small tau or large kappa.  EINVAL with FP64 values.
                                  Batches always use 1.                                         */
 } l1ls_solve_opts;
 

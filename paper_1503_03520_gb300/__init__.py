@@ -284,6 +284,12 @@ class Instance:
                                     xs.ctypes.data, sg.ctypes.data, pm.ctypes.data))
         return dict(indptr=rp, indices=ci, data=va, b=b, xstar=xs, sigma=sg, perm=pm)
 
+    def xstar(self):
+        """The generator's optimal x* (n doubles) without exporting the matrix."""
+        xs = np.zeros(self.n, np.float64)
+        _check(lib.l1ls_inst_export(self._h, None, None, None, None, xs.ctypes.data, None, None))
+        return xs
+
     def export_t(self):
         cp = np.zeros(self.n + 1, np.int64)
         ri = np.zeros(self.nnz, np.int32)

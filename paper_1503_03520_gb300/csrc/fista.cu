@@ -28,6 +28,11 @@ namespace l1ls {
 namespace {
 
 constexpr int kBlock = 256;
+// resident blocks per SM the K1 / K2 register allocation is sized for (a build parameter:
+// 4 gives 64 registers per thread, 5 gives 48 with some spills)
+#ifndef L1LS_FISTA_MIN_BLOCKS
+#define L1LS_FISTA_MIN_BLOCKS 1
+#endif
 
 struct FistaState {
     double tau, L, tol;
@@ -74,7 +79,7 @@ struct K2Args {
 };
 
 template <class V, class Vec, bool PAIRED>
-__global__ void __launch_bounds__(kBlock) k_fista_k1(K1Args<V, Vec> a) {
+__global__ void __launch_bounds__(kBlock, L1LS_FISTA_MIN_BLOCKS) k_fista_k1(K1Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[3 * 32];
@@ -168,7 +173,7 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new, doubl
 }
 
 template <class V, class Vec, bool PAIRED>
-__global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
+__global__ void __launch_bounds__(kBlock, L1LS_FISTA_MIN_BLOCKS) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[3 * 32];
@@ -237,11 +242,11 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2(K2Args<V, Vec> a) {
         fista_finalize(a.st, tot[0], tot[1], tot[2]);
 }
 
-// ---- compensated kernels (opts.accum = 1; FP32 / BF16 values in paired storage) ----------
-// The same two kernels with both products accumulated in float-float (pcsr_tile_ff): K1
-// gathers the high and low words of x_{k-1}, keeps A x in float-float and writes the residual
-// of each row pair as one float4 {hi, hi, lo, lo}; K2 gathers it and forms A^T r in
-// float-float.  FP32 sums of the products put a floor of about 1e-5 .. 1e-2 under the relative
+// ---- compensated kernels (opts.accum = 1; FP32 / BF16 values) ----------------------------
+// The same two kernels with both products accumulated in float-float (tile_ff): K1 gathers
+// the high and low words of x_{k-1}, keeps A x in float-float and writes the residual in
+// float-float (paired storage: one float4 {hi, hi, lo, lo} per row pair; plain: one float2
+// per row); K2 gathers it and forms A^T r in float-float.  FP32 sums of the products put a floor of about 1e-5 .. 1e-2 under the relative
 // gap at small tau (the residual is a small difference of large terms, and its rounding error
 // does not shrink with the objective); these kernels remove that floor at about twice the
 // arithmetic and 16 more bytes per row and 4 more per gathered column of traffic.
@@ -254,7 +259,7 @@ struct K1CArgs {
     const float* xh;     // x_{k-1}, float-float
     const float* xl;
     float2* ax;          // in: A x_{k-2}; out: A x_{k-1} (float-float)
-    float4* res;         // out: r_k per row pair
+    float* res;          // out: r_k (layout above)
     const float* b;
     double* partials;
     FistaState* st;
@@ -264,9 +269,9 @@ struct K1CArgs {
 template <class V>
 struct K2CArgs {
     const int32_t* ptr;
-    const int32_t* pair;
+    const int32_t* pair;     // pair index (paired) or row index (plain) per entry
     const V* val;
-    const float4* res;
+    const float* res;
     const float* xch;
     const float* xcl;
     float* xoh;
@@ -276,13 +281,13 @@ struct K2CArgs {
     int64_t n;
 };
 
-template <class V>
+template <class V, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
     __shared__ CompSmem<kBlock> sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const ff beta = ff_from_double(a.st->beta);
-    float* resf = reinterpret_cast<float*>(a.res);
+    float* resf = a.res;
     ff q[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     struct Ops {
         ff axo;
@@ -301,17 +306,22 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
         const ff ay = ff_add(u, ff_mul(beta, ff_sub(u, o.axo)));
         const ff rr = ff_sub(ff_from_float(o.bb), ay);
         a.ax[r] = make_float2(u.hi, u.lo);
-        resf[4 * (r >> 1) + (r & 1)] = rr.hi;
-        resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
+        if (PAIRED) {
+            resf[4 * (r >> 1) + (r & 1)] = rr.hi;
+            resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
+        } else {
+            resf[2 * r] = rr.hi;
+            resf[2 * r + 1] = rr.lo;
+        }
         const ff d = ff_sub(u, ff_from_float(o.bb));
         q[0] = ff_add(q[0], ff_mul(d, d));
         q[1] = ff_add(q[1], ff_mul(ff_from_float(o.bb), rr));
         q[2] = ff_add(q[2], ff_mul(rr, rr));
     };
-    const int64_t npairs = a.m / 2;
-    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (npairs + 31) >> 5;
+    const int64_t nrows = PAIRED ? a.m / 2 : a.m;
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (nrows + 31) >> 5;
     for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
-        pcsr_tile_ff<true, V>(t, a.ptr, a.col, a.val, a.xh, a.xl, nullptr, npairs, sm.warp_buf(), pre, epi);
+        tile_ff<true, PAIRED, V>(t, a.ptr, a.col, a.val, a.xh, a.xl, nullptr, nrows, sm.warp_buf(), pre, epi);
     double p[3] = {ff_to_double(q[0]), ff_to_double(q[1]), ff_to_double(q[2])};
     block_reduce<kBlock, 3>(p, 0u, red);
     double tot[3];
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
     }
 }
 
-template <class V>
+template <class V, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
     __shared__ CompSmem<kBlock> sm;
     __shared__ double red[3 * 32];
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
     };
     const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (a.n + 31) >> 5;
     for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
-        pcsr_tile_ff<false, V>(t, a.ptr, a.pair, a.val, nullptr, nullptr, a.res, a.n, sm.warp_buf(), pre, epi);
+        tile_ff<false, PAIRED, V>(t, a.ptr, a.pair, a.val, nullptr, nullptr, a.res, a.n, sm.warp_buf(), pre, epi);
     double p[3] = {(double)gmax, ff_to_double(l1), ff_to_double(rt)};
     block_reduce<kBlock, 3>(p, 1u, red);
     double tot[3];
@@ -405,8 +415,8 @@ struct FistaWork {
     double* tmp64 = nullptr;             // FP64 staging of x0 / x_out
     void* ax = nullptr;
     void* res = nullptr;
-    float2* ax_ff = nullptr;             // compensated kernels: A x and the pair residual
-    float4* res_ff = nullptr;
+    float2* ax_ff = nullptr;             // compensated kernels: A x and the residual (2m floats)
+    float* res_ff = nullptr;
     int grid1c = 0, grid2c = 0;
     bool comp = false;                   // this run uses the compensated kernels
     int exec_comp = -1;
@@ -488,9 +498,9 @@ l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
 template <class V>
 void enqueue_k1c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     K1CArgs<V> a;
-    a.ptr = I->prow_ptr;
-    a.col = I->prow_col;
-    a.val = static_cast<const V*>(I->prow_val);
+    a.ptr = I->paired ? I->prow_ptr : I->csr_ptr;
+    a.col = I->paired ? I->prow_col : I->csr_col;
+    a.val = static_cast<const V*>(I->paired ? I->prow_val : I->csr_val);
     a.xh = w->Xh[parity];
     a.xl = w->Xl[parity];
     a.ax = w->ax_ff;
@@ -499,16 +509,17 @@ void enqueue_k1c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a.partials = w->part1;
     a.st = w->st;
     a.m = I->m;
-    k_fista_k1c<V><<<w->grid1c, kBlock, 0, st>>>(a);
+    if (I->paired) k_fista_k1c<V, true><<<w->grid1c, kBlock, 0, st>>>(a);
+    else k_fista_k1c<V, false><<<w->grid1c, kBlock, 0, st>>>(a);
 }
 
 template <class V>
 void enqueue_k2c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     const int c = parity, o = 1 - parity;
     K2CArgs<V> a;
-    a.ptr = I->pcol_ptr;
-    a.pair = I->pcol_pair;
-    a.val = static_cast<const V*>(I->pcol_val);
+    a.ptr = I->paired ? I->pcol_ptr : I->csc_ptr;
+    a.pair = I->paired ? I->pcol_pair : I->csc_row;
+    a.val = static_cast<const V*>(I->paired ? I->pcol_val : I->csc_val);
     a.res = w->res_ff;
     a.xch = w->Xh[c];
     a.xcl = w->Xl[c];
@@ -517,7 +528,8 @@ void enqueue_k2c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a.partials = w->part2;
     a.st = w->st;
     a.n = I->n;
-    k_fista_k2c<V><<<w->grid2c, kBlock, 0, st>>>(a);
+    if (I->paired) k_fista_k2c<V, true><<<w->grid2c, kBlock, 0, st>>>(a);
+    else k_fista_k2c<V, false><<<w->grid2c, kBlock, 0, st>>>(a);
 }
 
 template <class V, class Vec>
@@ -541,8 +553,8 @@ l1ls_status enqueue_iteration(Inst* I, FistaWork* w, int parity, cudaStream_t st
 template <class V, class Vec>
 l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStream_t st) {
     const int64_t m = I->m, n = I->n;
-    if (o->accum != 0 && (sizeof(Vec) == 8 || !I->paired))
-        return set_error(L1LS_EINVAL, "accum = 1 (float-float products) needs FP32 or BF16 values in paired storage");
+    if (o->accum != 0 && sizeof(Vec) == 8)
+        return set_error(L1LS_EINVAL, "accum = 1 (float-float products) needs FP32 or BF16 values");
     if (o->accum != 0 && o->accum != 1) return set_error(L1LS_EINVAL, "accum must be 0 or 1");
     FistaWork* w = static_cast<FistaWork*>(I->fista_work);
     if (!w) {
@@ -581,9 +593,14 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     if constexpr (sizeof(Vec) == 4) {
         if (o->accum == 1 && !w->ax_ff) {
             L1LS_TRY(I->alloc_n(&w->ax_ff, pad32(m)));
-            L1LS_TRY(I->alloc_n(&w->res_ff, pad32(m) / 2 + 1));
-            w->grid1c = grid_of(I, k_fista_k1c<V>, m / 2);
-            w->grid2c = grid_of(I, k_fista_k2c<V>, n);
+            L1LS_TRY(I->alloc_n(&w->res_ff, 2 * pad32(m)));
+            if (I->paired) {
+                w->grid1c = grid_of(I, k_fista_k1c<V, true>, m / 2);
+                w->grid2c = grid_of(I, k_fista_k2c<V, true>, n);
+            } else {
+                w->grid1c = grid_of(I, k_fista_k1c<V, false>, m);
+                w->grid2c = grid_of(I, k_fista_k2c<V, false>, n);
+            }
         }
     }
     w->comp = o->accum == 1;

@@ -133,21 +133,17 @@ __device__ __forceinline__ void load_span(const T* __restrict__ p, T (&out)[N]) 
 //               row (2p and 2p+1) exactly as for warp_csr.
 // ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
 // wbuf: this warp's 2 * kWarpChunk accumulators.
-// One tile t (32 row pairs, or 32 columns) of the paired traversal; see warp_pcsr.
+// One tile t (32 row pairs, or 32 columns) of the paired traversal whose row extents rb, re
+// (this lane's row) are already loaded; see warp_pcsr.
 template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
-__device__ __forceinline__ void pcsr_tile(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                          const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
-                                          Acc* __restrict__ wbuf, Pre& pre, Epi& epi) {
+__device__ __forceinline__ void pcsr_tile_body(int64_t t, int32_t rb, int32_t re, const int32_t* __restrict__ idx,
+                                               const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
+                                               Acc* __restrict__ wbuf, Pre& pre, Epi& epi) {
     const int lane = threadIdx.x & 31;
     Acc* w0 = wbuf;
     Acc* w1 = wbuf + kWarpChunk;
     const int64_t r = (t << 5) + lane;
     const bool has = r < nrows;
-    int32_t rb = 0, re = 0;
-    if (has) {
-        rb = __ldcs(ptr + r);
-        re = __ldcs(ptr + r + 1);
-    }
     auto ops0 = pre(ROWS ? 2 * r : r, has);
     auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
     const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
@@ -211,6 +207,19 @@ __device__ __forceinline__ void pcsr_tile(int64_t t, const int32_t* __restrict__
     }
 }
 
+template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
+__device__ __forceinline__ void pcsr_tile(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                          const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
+                                          Acc* __restrict__ wbuf, Pre& pre, Epi& epi) {
+    const int64_t r = (t << 5) + (threadIdx.x & 31);
+    int32_t rb = 0, re = 0;
+    if (r < nrows) {
+        rb = __ldcs(ptr + r);
+        re = __ldcs(ptr + r + 1);
+    }
+    pcsr_tile_body<ROWS, V, X, Acc>(t, rb, re, idx, val2, x, nrows, wbuf, pre, epi);
+}
+
 // ROWS = true : npairs row pairs; x gathered at the column index; pre / epi are called per
 //               row (2p and 2p+1) exactly as for warp_csr.
 // ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
@@ -219,10 +228,27 @@ template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
 __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                           const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
                                           Acc* __restrict__ wbuf, Pre pre, Epi epi) {
+    // the row extents of the warp's next tile are loaded before the current tile is processed,
+    // so the pointer round trip overlaps the previous tile's work
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ntiles = (nrows + 31) >> 5;
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += nwarps)
-        pcsr_tile<ROWS, V, X, Acc>(t, ptr, idx, val2, x, nrows, wbuf, pre, epi);
+    const int lane = threadIdx.x & 31;
+    int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int32_t nb = 0, ne = 0;
+    if (t < ntiles && (t << 5) + lane < nrows) {
+        nb = __ldcs(ptr + (t << 5) + lane);
+        ne = __ldcs(ptr + (t << 5) + lane + 1);
+    }
+    for (; t < ntiles; t += nwarps) {
+        const int32_t rb = nb, re = ne;
+        const int64_t tn = t + nwarps;
+        nb = ne = 0;
+        if (tn < ntiles && (tn << 5) + lane < nrows) {
+            nb = __ldcs(ptr + (tn << 5) + lane);
+            ne = __ldcs(ptr + (tn << 5) + lane + 1);
+        }
+        pcsr_tile_body<ROWS, V, X, Acc>(t, rb, re, idx, val2, x, nrows, wbuf, pre, epi);
+    }
 }
 
 // Row traversal of A (nrows rows) in plain or paired storage.
@@ -260,7 +286,7 @@ template <class V> struct Csr {
 
 namespace l1ls {
 
-// ---- compensated paired traversals ---------------------------------------------------------
+// ---- compensated traversals ---------------------------------------------------------------
 // Products of the FP32 (or BF16) matrix with float-float vectors, accumulated in float-float:
 // each term a * (h + l) is TwoProduct(a, h) with a * l added to its low word, and the sums are
 // float-float additions (Dekker 1971; Bailey's double-single arithmetic).  The result carries
@@ -270,24 +296,29 @@ namespace l1ls {
 // path).  The tile structure is that of pcsr_tile; the warp buffer holds high and low words.
 //
 // Inputs: the row traversal gathers a float-float vector kept as two FP32 arrays (high and low
-// words); the column traversal gathers the residual of row pair p as one float4
-// {hi(2p), hi(2p+1), lo(2p), lo(2p+1)}, both rows with one 16-byte load.
+// words).  The column traversal gathers the residual: in paired storage the residual of row
+// pair p is one float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} (both rows with one 16-byte load),
+// in plain storage one float2 {hi, lo} per row.
 
-template <bool ROWS, class V, int EPL = kEPL, class Pre, class Epi>
-__device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                             const V* __restrict__ val2, const float* __restrict__ xh,
-                                             const float* __restrict__ xl, const float4* __restrict__ r4, int64_t nrows,
-                                             float* __restrict__ wbuf, Pre& pre, Epi& epi) {
-    // ROWS: nrows row pairs, (xh, xl) gathered at the column index (pre / epi per row, 2p and
-    // 2p+1); otherwise nrows columns, the pair residual r4 gathered at p.  EPL entries per lane
-    // and chunk (4 or 8): fewer registers with 4, more loads in flight with 8.
+template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
+__device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                        const V* __restrict__ val, const float* __restrict__ xh,
+                                        const float* __restrict__ xl, const void* __restrict__ rin, int64_t nrows,
+                                        float* __restrict__ wbuf, Pre& pre, Epi& epi) {
+    // ROWS: nrows rows (PAIRED: row pairs; pre / epi per row, 2p and 2p+1), (xh, xl) gathered
+    // at the column index; otherwise nrows columns, the residual rin gathered at the pair (or
+    // row) index.  EPL entries per lane and chunk (4 or 8): fewer registers with 4, more loads
+    // in flight with 8 (plain BF16 storage needs 8 for whole 16-byte value loads).
     static_assert(EPL == 4 || EPL == 8, "EPL must be 4 or 8");
+    constexpr int kVals = PAIRED ? 2 : 1;
+    static_assert((kVals * EPL * sizeof(V)) % 16 == 0, "value spans must be whole 16-byte vectors");
     constexpr int kChunk = 32 * EPL;
     const int lane = threadIdx.x & 31;
     float* w0h = wbuf;
     float* w0l = wbuf + kChunk;
     float* w1h = wbuf + 2 * kChunk;
     float* w1l = wbuf + 3 * kChunk;
+    constexpr bool kTwoRows = ROWS && PAIRED;
     const int64_t r = (t << 5) + lane;
     const bool has = r < nrows;
     int32_t rb = 0, re = 0;
@@ -295,8 +326,8 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
         rb = __ldcs(ptr + r);
         re = __ldcs(ptr + r + 1);
     }
-    auto ops0 = pre(ROWS ? 2 * r : r, has);
-    auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
+    auto ops0 = pre(kTwoRows ? 2 * r : r, has);
+    auto ops1 = pre(kTwoRows ? 2 * r + 1 : r, kTwoRows && has);
     const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
     const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
     const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
@@ -306,28 +337,38 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
         ff p0[EPL], p1[EPL];
         if (base < e1) {
             int32_t ij[EPL];
-            V vv[2 * EPL];
+            V vv[kVals * EPL];
             load_span<int32_t, EPL>(idx + base, ij);
-            load_span<V, 2 * EPL>(val2 + 2 * (int64_t)base, vv);
+            load_span<V, kVals * EPL>(val + kVals * (int64_t)base, vv);
 #pragma unroll
             for (int k = 0; k < EPL; ++k) {
                 const int32_t e = base + k;
                 const bool in = e >= e0 && e < e1;
-                const float v0 = val_to_acc<float>(vv[2 * k]), v1 = val_to_acc<float>(vv[2 * k + 1]);
+                const float v0 = val_to_acc<float>(vv[kVals * k]);
+                const float v1 = PAIRED ? val_to_acc<float>(vv[kVals * k + kVals - 1]) : 0.f;
                 if (ROWS) {
                     const float hx = in ? __ldg(xh + ij[k]) : 0.f;
                     const float lx = in ? __ldg(xl + ij[k]) : 0.f;
                     p0[k] = two_prod(v0, hx);
                     p0[k].lo = __fmaf_rn(v0, lx, p0[k].lo);
-                    p1[k] = two_prod(v1, hx);
-                    p1[k].lo = __fmaf_rn(v1, lx, p1[k].lo);
-                } else {
-                    const float4 g = in ? __ldg(r4 + ij[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (PAIRED) {
+                        p1[k] = two_prod(v1, hx);
+                        p1[k].lo = __fmaf_rn(v1, lx, p1[k].lo);
+                    } else {
+                        p1[k] = {0.f, 0.f};
+                    }
+                } else if (PAIRED) {
+                    const float4 g = in ? __ldg(static_cast<const float4*>(rin) + ij[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
                     ff q0 = two_prod(v0, g.x);
                     q0.lo = __fmaf_rn(v0, g.z, q0.lo);
                     ff q1 = two_prod(v1, g.y);
                     q1.lo = __fmaf_rn(v1, g.w, q1.lo);
                     p0[k] = ff_add(q0, q1);
+                    p1[k] = {0.f, 0.f};
+                } else {
+                    const float2 g = in ? __ldg(static_cast<const float2*>(rin) + ij[k]) : make_float2(0.f, 0.f);
+                    p0[k] = two_prod(v0, g.x);
+                    p0[k].lo = __fmaf_rn(v0, g.y, p0[k].lo);
                     p1[k] = {0.f, 0.f};
                 }
             }
@@ -339,7 +380,7 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
         for (int k = 0; k < EPL; ++k) {
             w0h[k * 32 + lane] = p0[k].hi;
             w0l[k * 32 + lane] = p0[k].lo;
-            if (ROWS) {
+            if (kTwoRows) {
                 w1h[k * 32 + lane] = p1[k].hi;
                 w1l[k * 32 + lane] = p1[k].lo;
             }
@@ -350,18 +391,27 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
             const int32_t i = e - c;
             const int32_t q = (i & (EPL - 1)) * 32 + (i / EPL);
             a0 = ff_add(a0, {w0h[q], w0l[q]});
-            if (ROWS) a1 = ff_add(a1, {w1h[q], w1l[q]});
+            if (kTwoRows) a1 = ff_add(a1, {w1h[q], w1l[q]});
         }
         __syncwarp();
     }
     if (has) {
-        if (ROWS) {
+        if (kTwoRows) {
             epi(2 * r, a0, ops0);
             epi(2 * r + 1, a1, ops1);
         } else {
             epi(r, a0, ops0);
         }
     }
+}
+
+// paired storage (the form the batched kernel uses)
+template <bool ROWS, class V, int EPL = kEPL, class Pre, class Epi>
+__device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                             const V* __restrict__ val2, const float* __restrict__ xh,
+                                             const float* __restrict__ xl, const float4* __restrict__ r4, int64_t nrows,
+                                             float* __restrict__ wbuf, Pre& pre, Epi& epi) {
+    tile_ff<ROWS, true, V, EPL>(t, ptr, idx, val2, xh, xl, r4, nrows, wbuf, pre, epi);
 }
 
 template <int BLOCK> struct CompSmem {

@@ -169,13 +169,38 @@ def test_fista_compensated_products_reach_small_gaps_at_small_tau(ctx, restart, 
         inst.free()
 
 
-def test_compensated_products_need_paired_fp32_values(ctx):
+def test_compensated_products_need_fp32_or_bf16_values(ctx):
     import paper_1503_03520_gb300 as l1
-    for p in (W.params(m=512, n=256, left_stages=0, value_dtype="f32"), W.params(m=512, n=256, value_dtype="f64")):
-        inst = ctx.generate(p)
-        try:
-            with pytest.raises(l1.L1LSError) as e:
-                inst.solve_fista(tau=1.0, accum=1)
-            assert e.value.status == 1
-        finally:
-            inst.free()
+    inst = ctx.generate(W.params(m=512, n=256, value_dtype="f64"))
+    try:
+        with pytest.raises(l1.L1LSError) as e:
+            inst.solve_fista(tau=1.0, accum=1)
+        assert e.value.status == 1
+    finally:
+        inst.free()
+
+
+@pytest.mark.parametrize("case,frac", [(dict(m=2000, n=1000, left_stages=0, value_dtype="f32", seed=43), 0.09),
+                                       (dict(m=1000, n=2000, left_stages=1, value_dtype="f32", seed=46), 0.5),
+                                       (dict(m=1500, n=3000, left_stages=0, value_dtype="bf16", seed=43), 0.09)],
+                         ids=["plain", "igen2", "igen2_bf16"])
+def test_fista_compensated_products_in_plain_storage(ctx, case, frac):
+    """accum = 1 on instances without row pairs (no left stage, or IGen2) against the oracle.
+    (IGen2's columns of N~ scaled by xi tau / |N_i^T e| make ||A||^2 large: FISTA is slow on
+    them at small tau, so the IGen2 case takes tau = lambda_max / 2.)"""
+    params = W.params(right_stages=2, kappa=10.0 ** 2.2, xstar_frac=0.02, **case)
+    ref = oracle_instance(params)
+    A = stored_values(ref.A, case["value_dtype"])
+    b = ref.b.astype(np.float32).astype(np.float64)
+    tau = frac * ref.lam_max
+    inst = ctx.generate(params)
+    try:
+        assert inst.info["lipschitz"] == pytest.approx(ref.lipschitz, rel=1e-11)
+        x, r = inst.solve_fista(tau=tau, tol=1e-6, max_iter=100000, restart=1, accum=1)
+        o = solvers.fista(A, b, tau, inst.info["lipschitz"], 1e-6, 100000, restart=True)
+        assert o["status"] == 0
+        assert r["status"] == 0 and r["rel_gap"] <= 1e-6
+        assert abs(r["iters"] - o["iters"]) <= max(5, 0.15 * o["iters"]), (r["iters"], o["iters"])
+        assert abs(r["f"] - o["P"]) <= 2e-6 * o["P"]
+    finally:
+        inst.free()
