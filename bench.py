@@ -294,6 +294,58 @@ def serve_form(l1, W, count, rate, log2n_hi, limit_s):
             "speedup_certified_per_s": served["certified_per_s"] / max(fifo["certified_per_s"], 1e-12)}
 
 
+def mf_bytes_per_iteration(m, n, left=True):
+    """Algorithmic bytes of one matrix-free FISTA iteration (FP32 vectors, float-float iterate):
+    K1 = stage sweep (x hi, sigma, z: 12n) + rows of the left factor (perm 4m, z gathered 4n,
+    A x read and written 8m, b 4m, the rotated residual scattered to P2^T order 4n);
+    K2 = stage sweep of that n-vector with the FISTA epilogue (it and sigma 8n, both iterates
+    read 16n, the new one written 8n)."""
+    k1 = 12 * n + 8 * n + 16 * m
+    k2 = 32 * n
+    return k1, k2
+
+
+def mf_form(l1, W, log2n, steps, warmup, solve_limit):
+    """C2 with A in factored form (Algorithms MvPA / MvPAt on the device): FISTA iteration time,
+    its HBM fraction, and the time to the 1e-6 gap, beside the stored-matrix path."""
+    import torch
+    ctx = l1.Context(0)
+    params = dict(W.c2_scaled(log2n), matrix_free=1)
+    inst = ctx.generate(params)
+    m, n = inst.m, inst.n
+    k1b, k2b = mf_bytes_per_iteration(m, n)
+    stream = torch.cuda.current_stream()
+    inst.fista_begin(tau=1.0, tol=0.0, max_iter=10 ** 12, stream=stream)
+    inst.fista_step(warmup, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kms = inst.fista_step(steps, timed=True, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    it_ms = e0.elapsed_time(e1) / steps
+    inst.fista_end(stream=stream, allow=(4, 5))
+    peak, _ = measured_hbm_peak()
+    t = time.perf_counter()
+    _, r = inst.solve_fista(tau=1.0, tol=W.C2_TOL, max_iter=200000, time_limit_s=solve_limit, stream=stream,
+                            allow=(4, 5))
+    el = time.perf_counter() - t
+    out = {"workload": "c2 (m=2^%d, n=2^%d) with A not assembled: products by the stages of R, Sigma, "
+                       "the permutation and the left rotations (FP32)" % (log2n + 1, log2n),
+           "device_bytes": inst.info["device_bytes"], "iteration_ms": it_ms,
+           "k1_ms": kms[0] / steps, "k2_ms": kms[1] / steps,
+           "k1_bytes": k1b, "k2_bytes": k2b,
+           "k1_frac": k1b / (kms[0] / steps * 1e-3) / 1e9 / peak, "k2_frac": k2b / (kms[1] / steps * 1e-3) / 1e9 / peak,
+           "gbs": (k1b + k2b) / (it_ms * 1e-3) / 1e9,
+           "fista_to_gap": {"tol": W.C2_TOL, "seconds": el, "iters": r["iters"], "rel_gap": r["rel_gap"],
+                            "status": r["status_name"],
+                            "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]}}
+    inst.free()
+    ctx.close()
+    return out
+
+
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
@@ -337,10 +389,13 @@ def run_ours(args):
     import workloads as W
 
     params = W.c2_scaled(args.log2n, seed=rank)
+    if args.matrix_free:
+        params = dict(params, matrix_free=1)
     ctx = l1.Context(local)
     inst = ctx.generate(params)
     m, n, nnz = inst.m, inst.n, inst.nnz
-    k1b, k2b = bytes_per_iteration(m, n, nnz)
+    k1b, k2b = mf_bytes_per_iteration(m, n) if args.matrix_free else bytes_per_iteration(m, n, nnz)
+    k1_name, k2_name = ("k_mf_rt+k_fista_mf1", "k_fista_mf2") if args.matrix_free else ("k_fista_k1", "k_fista_k2")
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -375,9 +430,9 @@ def run_ours(args):
     # ---- roofline of the dominant kernel --------------------------------------------------
     k1_ms, k2_ms = kms[0] / args.steps, kms[1] / args.steps
     if k2_ms >= k1_ms:
-        dom, dom_ms, dom_bytes = "k_fista_k2", k2_ms, k2b
+        dom, dom_ms, dom_bytes = k2_name, k2_ms, k2b
     else:
-        dom, dom_ms, dom_bytes = "k_fista_k1", k1_ms, k1b
+        dom, dom_ms, dom_bytes = k1_name, k1_ms, k1b
     peak, peak_src = measured_hbm_peak()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -405,7 +460,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     # warm start from x0 costs one extra product A x0 (matrix, x, y)
-    e2e_bytes = E2E_ITERS * (k1b + k2b) + (nnz // 2) * 12 + (m // 2 + 1) * 4 + n * 4 + m * 4
+    e2e_bytes = E2E_ITERS * (k1b + k2b) + (k1b if args.matrix_free else (nnz // 2) * 12 + (m // 2 + 1) * 4 + n * 4 + m * 4)
     e2e = {"value": e2e_bytes * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n, "iters_per_step": E2E_ITERS, "steps": args.e2e_steps,
            "api": "l1ls_solve_fista(x0=pinned host, x_out=pinned host)"}
@@ -430,6 +485,8 @@ def run_ours(args):
         forms = {"batch": batch_form(l1, W, ctx, args.batch_iters)}
     ctx.close()
     if rank == 0 and not args.no_forms:
+        forms["matrix_free"] = mf_form(l1, W, args.log2n, args.steps, args.warmup, args.solve_limit)
+    if rank == 0 and not args.no_forms:
         forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_limit)
     if rank == 0 and args.precision:
         forms = forms or {}
@@ -450,8 +507,10 @@ def run_ours(args):
                 "config": {"workload": "c2: m=2^%d, n=2^%d, nnz=%d (~8/col), FP32 values, int32 indices, "
                                        "kappa(A)=1e4, x* 1%%, tau=1, one FISTA iteration per step"
                                        % (args.log2n + 1, args.log2n, nnz),
-                           "storage": "row-pair CSR and column CSR of P1^T A: one int32 index and two FP32 "
-                                      "values per pair of entries",
+                           "storage": ("A not assembled: products by its factors (stages of R, Sigma, "
+                                       "permutation, left rotations), FP32" if args.matrix_free else
+                                       "row-pair CSR and column CSR of P1^T A: one int32 index and two FP32 "
+                                       "values per pair of entries"),
                            "l2": "inputs larger than L2 (A is %.2f GB per product)" % (nnz * 6 / 1e9),
                            "parallelism": "replicas (one instance per GPU)" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -481,6 +540,8 @@ def main():
     ap.add_argument("--serve-log2n", type=int, default=20, help="c5: largest log2 n of a request")
     ap.add_argument("--serve-limit", type=float, default=2.0, help="c5: time limit per request (s)")
     ap.add_argument("--precision", action="store_true", help="add the c3 precision sweep (about 1-2 min)")
+    ap.add_argument("--matrix-free", action="store_true",
+                    help="time the iteration on the instance with A not assembled (Algorithms MvPA / MvPAt)")
     ap.add_argument("--precision-limit", type=float, default=8.0, help="c3: time limit per solve (s)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -73,6 +73,11 @@ typedef enum { L1LS_F64 = 0, L1LS_F32 = 1, L1LS_BF16 = 2 } l1ls_dtype;
  *   value_dtype   l1ls_dtype in which the nonzeros of A are stored (rounded from FP64).
  *   g_offsupport  0: g_i ~ U(-1,1) off the support of x*; 1: g_i = 0 there.
  *   n_nnz_per_col IGen2 only: nonzeros per column of N.
+ *   matrix_free   1: A is not assembled; products apply its factors (Algorithms MvPA /
+ *                 MvPAt of Sec. 4: the stages of R, Sigma, the permutation and the left
+ *                 rotations), so the instance holds O(m + n) memory.  IGen (m >= n) with
+ *                 FP32 value_dtype only; l1ls_matvec / l1ls_rmatvec and FISTA work on it
+ *                 (pdNCG, batches and exports of A do not: EINVAL).
  *   seed          all random draws are SplitMix64 streams of this seed.
  */
 typedef struct {
@@ -86,7 +91,7 @@ typedef struct {
     int32_t value_dtype;
     int32_t g_offsupport;
     int32_t n_nnz_per_col;
-    int32_t reserved;
+    int32_t matrix_free;
 } l1ls_gen_params;
 
 /* Fill p with the defaults: m = 2048, n = 1024, seed 0, kappa 100, tau 1, frac 0.05,
@@ -100,6 +105,7 @@ typedef struct {
     double lam_max;       /* ||A^T b||_inf: every tau >= lam_max has minimiser 0               */
     double tau_gen;
     int32_t value_dtype, right_stages, left_stages, igen2;
+    int32_t matrix_free, reserved;
     uint64_t device_bytes;/* device memory held by the instance                                */
 } l1ls_inst_info;
 

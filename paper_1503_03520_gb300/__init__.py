@@ -27,14 +27,15 @@ class GenParams(ctypes.Structure):
                 ("xstar_lo", ctypes.c_double), ("xstar_hi", ctypes.c_double), ("theta", ctypes.c_double),
                 ("vartheta", ctypes.c_double), ("right_stages", ctypes.c_int32), ("left_stages", ctypes.c_int32),
                 ("value_dtype", ctypes.c_int32), ("g_offsupport", ctypes.c_int32),
-                ("n_nnz_per_col", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_nnz_per_col", ctypes.c_int32), ("matrix_free", ctypes.c_int32)]
 
 
 class InstInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64), ("n", ctypes.c_uint64), ("nnz", ctypes.c_uint64), ("s", ctypes.c_uint64),
                 ("f_star", ctypes.c_double), ("lipschitz", ctypes.c_double), ("lam_max", ctypes.c_double),
                 ("tau_gen", ctypes.c_double), ("value_dtype", ctypes.c_int32), ("right_stages", ctypes.c_int32),
-                ("left_stages", ctypes.c_int32), ("igen2", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
+                ("left_stages", ctypes.c_int32), ("igen2", ctypes.c_int32), ("matrix_free", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -283,6 +284,17 @@ class Instance:
         _check(lib.l1ls_inst_export(self._h, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, b.ctypes.data,
                                     xs.ctypes.data, sg.ctypes.data, pm.ctypes.data))
         return dict(indptr=rp, indices=ci, data=va, b=b, xstar=xs, sigma=sg, perm=pm)
+
+    def export_vectors(self):
+        """b (original row order), x*, sigma and the row permutation, without the matrix."""
+        m, n = self.m, self.n
+        b = np.zeros(m, np.float64)
+        xs = np.zeros(n, np.float64)
+        sg = np.zeros(min(m, n), np.float64)
+        pm = np.zeros(m, np.int64)
+        _check(lib.l1ls_inst_export(self._h, None, None, None, b.ctypes.data, xs.ctypes.data, sg.ctypes.data,
+                                    pm.ctypes.data))
+        return dict(b=b, xstar=xs, sigma=sg, perm=pm)
 
     def xstar(self):
         """The generator's optimal x* (n doubles) without exporting the matrix."""

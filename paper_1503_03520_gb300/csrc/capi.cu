@@ -235,6 +235,7 @@ l1ls_status l1ls_inst_get_info(const l1ls_inst* h, l1ls_inst_info* info) {
     info->right_stages = I->p.right_stages;
     info->left_stages = I->p.left_stages;
     info->igen2 = I->igen2 ? 1 : 0;
+    info->matrix_free = I->matrix_free ? 1 : 0;
     info->device_bytes = I->bytes;
     return L1LS_OK;
 }
@@ -265,9 +266,11 @@ l1ls_status l1ls_inst_export(const l1ls_inst* h, int64_t* row_ptr, int32_t* col_
                              double* xstar, double* sigma, int64_t* perm) {
     if (!h) return set_error(L1LS_EINVAL, "inst is NULL");
     const Inst* I = reinterpret_cast<const Inst*>(h);
+    if (I->matrix_free && (row_ptr || col_idx || vals))
+        return set_error(L1LS_EINVAL, "a matrix-free instance has no assembled A to export");
     L1LS_CUDA(cudaSetDevice(I->ctx->device));
     L1LS_CUDA(cudaDeviceSynchronize());
-    const int64_t m = I->m, n = I->n, nnz = I->nnz;
+    const int64_t m = I->m, n = I->n, nnz = I->matrix_free ? 0 : I->nnz;
     std::vector<int32_t> pm((size_t)m), st((size_t)m), ptr((size_t)m + 1), col((size_t)nnz);
     L1LS_CUDA(cudaMemcpy(pm.data(), I->perm, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
     L1LS_CUDA(cudaMemcpy(st.data(), I->store_of_row, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
@@ -302,6 +305,7 @@ l1ls_status l1ls_inst_export(const l1ls_inst* h, int64_t* row_ptr, int32_t* col_
 l1ls_status l1ls_inst_export_t(const l1ls_inst* h, int64_t* col_ptr, int32_t* row_idx, double* vals) {
     if (!h) return set_error(L1LS_EINVAL, "inst is NULL");
     const Inst* I = reinterpret_cast<const Inst*>(h);
+    if (I->matrix_free) return set_error(L1LS_EINVAL, "a matrix-free instance has no assembled A to export");
     L1LS_CUDA(cudaSetDevice(I->ctx->device));
     L1LS_CUDA(cudaDeviceSynchronize());
     const int64_t m = I->m, n = I->n, nnz = I->nnz;

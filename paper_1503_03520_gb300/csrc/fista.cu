@@ -22,16 +22,20 @@
 #include "internal.h"
 #include <cstring>
 #include "spmv.cuh"
+#include "mfree.cuh"
 
 namespace l1ls {
 
 namespace {
 
 constexpr int kBlock = 256;
-// resident blocks per SM the K1 / K2 register allocation is sized for (a build parameter:
-// 4 gives 64 registers per thread, 5 gives 48 with some spills)
-#ifndef L1LS_FISTA_MIN_BLOCKS
-#define L1LS_FISTA_MIN_BLOCKS 1
+// resident blocks per SM the K1 / K2 register allocations are sized for (build parameters;
+// 4 caps a thread at 64 registers, the most that keeps 32 warps per SM)
+#ifndef L1LS_K1_MIN_BLOCKS
+#define L1LS_K1_MIN_BLOCKS 4
+#endif
+#ifndef L1LS_K2_MIN_BLOCKS
+#define L1LS_K2_MIN_BLOCKS 4
 #endif
 
 struct FistaState {
@@ -79,7 +83,7 @@ struct K2Args {
 };
 
 template <class V, class Vec, bool PAIRED>
-__global__ void __launch_bounds__(kBlock, L1LS_FISTA_MIN_BLOCKS) k_fista_k1(K1Args<V, Vec> a) {
+__global__ void __launch_bounds__(kBlock, L1LS_K1_MIN_BLOCKS) k_fista_k1(K1Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[3 * 32];
@@ -172,15 +176,15 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new, doubl
     }
 }
 
-template <class V, class Vec, bool PAIRED>
-__global__ void __launch_bounds__(kBlock, L1LS_FISTA_MIN_BLOCKS) k_fista_k2(K2Args<V, Vec> a) {
+template <class V, class Vec, bool PAIRED, bool RESTART>
+__global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<Acc, kBlock> sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const double invL = 1.0 / L, thr = tau / L;
-    const bool rs = a.st->restart != 0;
+    constexpr bool rs = RESTART;   // the gradient-restart partial (an instantiation per setting)
     double p[3] = {0.0, 0.0, 0.0};
     if constexpr (sizeof(Vec) == 4) {
         const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(invL), thr_f = ff_from_double(thr);
@@ -373,6 +377,145 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
         fista_finalize(a.st, tot[0], tot[1], tot[2]);
 }
 
+// ---- matrix-free kernels (instances generated with matrix_free = 1) ------------------------
+// K1 = z = Sigma R^T x_{k-1} (a stage sweep, mfree.cu) + k_fista_mf1: the rows of the left
+// factor, K1's epilogue, and at once the first half of A^T r: the row pair's residual rotated
+// by G~^T and scattered to P2^T order (zt), so the residual itself is never stored.  K2 =
+// k_fista_mf2: R Sigma zt by a stage sweep with K2's epilogue and the certificate.  FP32
+// products, float-float iterate.
+
+constexpr int kMfUnroll = 4;   // row pairs per thread in flight in k_fista_mf1
+
+struct MfK1Args {
+    MfLeft L;
+    const float* z;      // Sigma R^T x_{k-1}
+    float* zt;           // out: the first n entries of P2^T G~^T r_k
+    float* ax;           // in: A x_{k-2}; out: A x_{k-1}
+    const float* b;
+    double* partials;
+    FistaState* st;
+};
+
+__global__ void __launch_bounds__(kBlock, 3) k_fista_mf1(MfK1Args a) {
+    __shared__ double red[3 * 32];
+    if (*(volatile int32_t*)&a.st->stop) return;
+    const float beta = (float)a.st->beta;
+    const MfLeft& L = a.L;
+    ff q[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    // r = b - A y with A y = u + beta (u - A x_{k-2}); gap partials (u - b)^2, b.r, r.r
+    auto epi = [&](float u, float axo, float bb) {
+        const float ay = u + beta * (u - axo);
+        const float rr = bb - ay;
+        const ff d = two_sum(u, -bb);
+        ff sq = two_prod(d.hi, d.hi);
+        sq.lo = __fmaf_rn(2.0f * d.hi, d.lo, sq.lo);
+        q[0] = ff_add(q[0], sq);
+        q[1] = ff_add(q[1], two_prod(bb, rr));
+        q[2] = ff_add(q[2], two_prod(rr, rr));
+        return rr;
+    };
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L.left) {
+        const int64_t units = L.m / 2;
+        const int2* perm2 = reinterpret_cast<const int2*>(L.perm);
+        float2* ax2 = reinterpret_cast<float2*>(a.ax);
+        const float2* b2 = reinterpret_cast<const float2*>(a.b);
+        for (int64_t t0 = gid; t0 < units; t0 += stride * kMfUnroll) {
+            int2 pk[kMfUnroll];
+            float2 axo[kMfUnroll], bb[kMfUnroll];
+            float z0[kMfUnroll], z1[kMfUnroll];
+#pragma unroll
+            for (int k = 0; k < kMfUnroll; ++k) {
+                const int64_t t = t0 + k * stride;
+                pk[k] = make_int2(INT32_MAX, INT32_MAX);
+                if (t < units) {
+                    pk[k] = __ldcs(perm2 + t);
+                    axo[k] = ax2[t];
+                    bb[k] = __ldcs(b2 + t);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kMfUnroll; ++k) {
+                z0[k] = pk[k].x < L.n ? __ldg(a.z + pk[k].x) : 0.0f;
+                z1[k] = pk[k].y < L.n ? __ldg(a.z + pk[k].y) : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < kMfUnroll; ++k) {
+                const int64_t t = t0 + k * stride;
+                if (t >= units) break;
+                const float u0 = __fmaf_rn(L.ct, z0[k], -L.st * z1[k]);
+                const float u1 = __fmaf_rn(L.ct, z1[k], L.st * z0[k]);
+                const float r0 = epi(u0, axo[k].x, bb[k].x);
+                const float r1 = epi(u1, axo[k].y, bb[k].y);
+                ax2[t] = make_float2(u0, u1);
+                if (pk[k].x < L.n) a.zt[pk[k].x] = __fmaf_rn(L.ct, r0, L.st * r1);
+                if (pk[k].y < L.n) a.zt[pk[k].y] = __fmaf_rn(L.ct, r1, -L.st * r0);
+            }
+        }
+    } else {
+        for (int64_t t = gid; t < L.m; t += stride) {
+            const float u = t < L.n ? __ldg(a.z + t) : 0.0f;
+            const float rr = epi(u, a.ax[t], __ldcs(a.b + t));
+            a.ax[t] = u;
+            if (t < L.n) a.zt[t] = rr;
+        }
+    }
+    double p[3] = {ff_to_double(q[0]), ff_to_double(q[1]), ff_to_double(q[2])};
+    block_reduce<kBlock, 3>(p, 0u, red);
+    double tot[3];
+    if (grid_reduce_last<kBlock, 3>(p, 0u, a.partials, &a.st->cnt1, tot, red) && threadIdx.x == 0) {
+        a.st->k1[0] = tot[0];
+        a.st->k1[1] = tot[1];
+        a.st->k1[2] = tot[2];
+    }
+}
+
+struct MfK2Args {
+    MfRight R;
+    const float* sigma;
+    const float* z;      // P2^T G~^T r_k (first n entries)
+    const float* xch;
+    const float* xcl;
+    float* xoh;
+    float* xol;
+    double* partials;
+    FistaState* st;
+};
+
+template <bool RESTART>
+__global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
+    __shared__ float buf[kMfLen];
+    __shared__ double red[3 * 32];
+    if (*(volatile int32_t*)&a.st->stop) return;
+    const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
+    const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
+    const int64_t a0 = (int64_t)blockIdx.x * kMfTile;
+    mf_load<true>(buf, a.z, a.sigma, a0 - kMfHalo, a.R.n);
+    mf_stages<false>(buf, a0 - kMfHalo, a.R);
+    float gmax = 0.0f;
+    ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
+    for (int p = threadIdx.x; p < kMfTile; p += blockDim.x) {
+        const int64_t j = a0 + p;
+        if (j >= a.R.n) break;
+        const float g = buf[kMfHalo + p];
+        const ff x1 = {a.xch[j], a.xcl[j]}, x0 = {a.xoh[j], a.xol[j]};
+        const ff y = ff_add(x1, ff_mul(beta_f, ff_sub(x1, x0)));
+        const ff v = ff_add(y, ff_mul(ff_from_float(g), invL_f));
+        const ff xn = ff_soft_threshold(v, thr_f);
+        a.xoh[j] = xn.hi;
+        a.xol[j] = xn.lo;
+        gmax = fmaxf(gmax, fabsf(g));
+        l1 = ff_add(l1, ff_abs(xn));
+        if (RESTART) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, x1)));
+    }
+    double pp[3] = {(double)gmax, ff_to_double(l1), ff_to_double(rt)};
+    block_reduce<kMfThreads, 3>(pp, 1u, red);
+    double tot[3];
+    if (grid_reduce_last<kMfThreads, 3>(pp, 1u, a.partials, &a.st->cnt2, tot, red) && threadIdx.x == 0)
+        fista_finalize(a.st, tot[0], tot[1], tot[2]);
+}
+
 __global__ void k_abs_sum(const double* __restrict__ x, int64_t n, double* __restrict__ partials,
                           unsigned* __restrict__ counter, double* __restrict__ out) {
     __shared__ double red[32];
@@ -415,11 +558,14 @@ struct FistaWork {
     double* tmp64 = nullptr;             // FP64 staging of x0 / x_out
     void* ax = nullptr;
     void* res = nullptr;
+    float* zmf = nullptr;                // matrix-free products: Sigma R^T x, and P2^T G~^T r
+    float* zt = nullptr;
     float2* ax_ff = nullptr;             // compensated kernels: A x and the residual (2m floats)
     float* res_ff = nullptr;
     int grid1c = 0, grid2c = 0;
     bool comp = false;                   // this run uses the compensated kernels
-    int exec_comp = -1;
+    bool restart = false;                // this run uses the gradient restart
+    int exec_comp = -1, exec_restart = -1;
     double* part1 = nullptr;
     double* part2 = nullptr;
     FistaState* st = nullptr;
@@ -488,9 +634,11 @@ l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
         a2.ptr = I->pcol_ptr;
         a2.col = I->pcol_pair;
         a2.val = static_cast<const V*>(I->pcol_val);
-        k_fista_k2<V, Vec, true><<<w->grid2, kBlock, 0, st>>>(a2);
+        if (w->restart) k_fista_k2<V, Vec, true, true><<<w->grid2, kBlock, 0, st>>>(a2);
+        else k_fista_k2<V, Vec, true, false><<<w->grid2, kBlock, 0, st>>>(a2);
     } else {
-        k_fista_k2<V, Vec, false><<<w->grid2, kBlock, 0, st>>>(a2);
+        if (w->restart) k_fista_k2<V, Vec, false, true><<<w->grid2, kBlock, 0, st>>>(a2);
+        else k_fista_k2<V, Vec, false, false><<<w->grid2, kBlock, 0, st>>>(a2);
     }
     return L1LS_OK;
 }
@@ -532,9 +680,41 @@ void enqueue_k2c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     else k_fista_k2c<V, false><<<w->grid2c, kBlock, 0, st>>>(a);
 }
 
+void enqueue_mf(Inst* I, FistaWork* w, int parity, int which, cudaStream_t st) {
+    if (which == 0) {
+        mf_apply_rt(I, w->Xh[parity], w->zmf, st);
+        MfK1Args a;
+        a.L = MfLeft{I->m, I->n, I->p.left_stages, I->mf_ct, I->mf_st, I->mf_pperm};
+        a.z = w->zmf;
+        a.zt = w->zt;
+        a.ax = static_cast<float*>(w->ax);
+        a.b = I->bhat32;
+        a.partials = w->part1;
+        a.st = w->st;
+        k_fista_mf1<<<w->grid1, kBlock, 0, st>>>(a);
+    } else {
+        MfK2Args a;
+        a.R = MfRight{I->n, I->p.right_stages, I->mf_c, I->mf_s};
+        a.sigma = I->sigma32;
+        a.z = w->zt;
+        a.xch = w->Xh[parity];
+        a.xcl = w->Xl[parity];
+        a.xoh = w->Xh[1 - parity];
+        a.xol = w->Xl[1 - parity];
+        a.partials = w->part2;
+        a.st = w->st;
+        if (w->restart) k_fista_mf2<true><<<w->grid2, kMfThreads, 0, st>>>(a);
+        else k_fista_mf2<false><<<w->grid2, kMfThreads, 0, st>>>(a);
+    }
+}
+
 template <class V, class Vec>
 l1ls_status enqueue_one(Inst* I, FistaWork* w, int parity, int which, cudaStream_t st) {
     if constexpr (sizeof(Vec) == 4) {
+        if (I->matrix_free) {
+            enqueue_mf(I, w, parity, which, st);
+            return L1LS_OK;
+        }
         if (w->comp) {
             if (which == 0) enqueue_k1c<V>(I, w, parity, st);
             else enqueue_k2c<V>(I, w, parity, st);
@@ -555,6 +735,8 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     const int64_t m = I->m, n = I->n;
     if (o->accum != 0 && sizeof(Vec) == 8)
         return set_error(L1LS_EINVAL, "accum = 1 (float-float products) needs FP32 or BF16 values");
+    if (o->accum != 0 && I->matrix_free)
+        return set_error(L1LS_EINVAL, "accum = 1 is not available for matrix-free instances");
     if (o->accum != 0 && o->accum != 1) return set_error(L1LS_EINVAL, "accum must be 0 or 1");
     FistaWork* w = static_cast<FistaWork*>(I->fista_work);
     if (!w) {
@@ -573,12 +755,22 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         L1LS_TRY(I->alloc_n(&w->tmp64, pad32(n)));
         L1LS_TRY(I->alloc(&w->ax, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->res, sizeof(Vec) * pad32(m)));
-        if (I->paired) {
+        if (I->matrix_free) {
+            L1LS_TRY(I->alloc_n(&w->zmf, pad32(n)));
+            L1LS_TRY(I->alloc_n(&w->zt, pad32(n)));
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fista_mf1, kBlock, 0);
+            const int64_t units = I->p.left_stages ? m / 2 : m;
+            w->grid1 = (int)std::max<int64_t>(
+                1, std::min<int64_t>((units + (int64_t)kBlock * kMfUnroll - 1) / ((int64_t)kBlock * kMfUnroll),
+                                     (int64_t)I->ctx->num_sms * std::max(per_sm, 1)));
+            w->grid2 = (int)((n + kMfTile - 1) / kMfTile);
+        } else if (I->paired) {
             w->grid1 = grid_of(I, k_fista_k1<V, Vec, true>, m / 2);
-            w->grid2 = grid_of(I, k_fista_k2<V, Vec, true>, n);
+            w->grid2 = grid_of(I, k_fista_k2<V, Vec, true, false>, n);
         } else {
             w->grid1 = grid_of(I, k_fista_k1<V, Vec, false>, m);
-            w->grid2 = grid_of(I, k_fista_k2<V, Vec, false>, n);
+            w->grid2 = grid_of(I, k_fista_k2<V, Vec, false, false>, n);
         }
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
         L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 3 + 1024));
@@ -604,6 +796,7 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         }
     }
     w->comp = o->accum == 1;
+    w->restart = o->restart != 0;
     FistaState h{};
     h.tau = o->tau;
     h.L = I->lipschitz;
@@ -758,7 +951,8 @@ l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_stat
 
 template <class V, class Vec>
 l1ls_status graph_for(Inst* I, FistaWork* w, int chunk) {
-    if (w->exec && w->exec_chunk == chunk && w->exec_comp == (int)w->comp) return L1LS_OK;
+    if (w->exec && w->exec_chunk == chunk && w->exec_comp == (int)w->comp && w->exec_restart == (int)w->restart)
+        return L1LS_OK;
     if (w->exec) {
         cudaGraphExecDestroy(w->exec);
         w->exec = nullptr;
@@ -778,6 +972,7 @@ l1ls_status graph_for(Inst* I, FistaWork* w, int chunk) {
     cudaStreamDestroy(cap);
     w->exec_chunk = chunk;
     w->exec_comp = (int)w->comp;
+    w->exec_restart = (int)w->restart;
     return L1LS_OK;
 }
 

@@ -800,6 +800,9 @@ l1ls_status validate(const l1ls_gen_params* p) {
     if (p->left_stages != 0 && p->left_stages != 1) return set_error(L1LS_EINVAL, "left_stages must be 0 or 1");
     if (p->left_stages == 1 && (p->m & 1)) return set_error(L1LS_EINVAL, "m must be even with a left stage");
     if (p->value_dtype < L1LS_F64 || p->value_dtype > L1LS_BF16) return set_error(L1LS_EINVAL, "bad value_dtype");
+    if (p->matrix_free != 0 && p->matrix_free != 1) return set_error(L1LS_EINVAL, "matrix_free must be 0 or 1");
+    if (p->matrix_free && (p->m < p->n || p->value_dtype != L1LS_F32))
+        return set_error(L1LS_EINVAL, "matrix_free instances need m >= n and FP32 value_dtype");
     if (!(p->xstar_lo >= 0.0) || !(p->xstar_hi >= p->xstar_lo)) return set_error(L1LS_EINVAL, "bad x* magnitudes");
     if (!(p->xstar_frac >= 0.0) || !(p->xstar_frac <= 1.0)) return set_error(L1LS_EINVAL, "xstar_frac must be in [0, 1]");
     return L1LS_OK;
@@ -820,6 +823,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
     const bool igen2 = p->m < p->n;             // Procedure IGen2 (Sec. 3.2): A = [B, N~]
     I->nsq = igen2 ? (int64_t)p->m : (int64_t)p->n;
     I->igen2 = igen2;
+    I->matrix_free = p->matrix_free != 0;
     I->dtype = p->value_dtype;
     int64_t s = (int64_t)std::floor(p->xstar_frac * (double)p->n + 0.5);
     if (s < 1) s = 1;
@@ -925,6 +929,58 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_CUDA(cudaGetLastError());
         double hred[3];
         GEN_CUDA(cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st));
+
+        if (I->matrix_free) {
+            // A stays in factored form: FP32 copies of the factors for the products; the rows are
+            // kept in the order of the left rotations (row i of A is row perm[i] of it)
+            int32_t* cnt = nullptr;
+            int32_t* ptr = nullptr;
+            GEN_TRY(tmp.get(&cnt, n));
+            GEN_TRY(tmp.get(&ptr, n + 1));
+            k_csc_count<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, cnt);
+            GEN_CUDA(cudaGetLastError());
+            int64_t nnz = 0;
+            GEN_TRY(exclusive_scan_i32(cnt, n, ptr, &nnz, st));
+            I->nnz = nnz;                         // of the matrix the factors represent
+            GEN_TRY(I->alloc_n(&I->sigma32, pad32(n)));
+            GEN_CUDA(cudaMemsetAsync(I->sigma32, 0, sizeof(float) * pad32(n), st));
+            k_to_f32<<<nblk(n), 256, 0, st>>>(I->sigma, n, I->sigma32);
+            if (p->left_stages == 1) {
+                // row pairs in the order of the smaller of their two entries of P (as for the
+                // stored matrix): one of the two gathers of each pair then runs in order
+                const int64_t npairs = m / 2;
+                uint64_t* keys = nullptr;
+                uint32_t* order = nullptr;
+                double* nb = nullptr;
+                GEN_TRY(tmp.get(&keys, npairs));
+                GEN_TRY(tmp.get(&order, npairs));
+                GEN_TRY(tmp.get(&nb, m));
+                k_pair_keys<<<nblk(npairs), 256, 0, st>>>(I->perm, npairs, n, keys);
+                GEN_CUDA(cudaGetLastError());
+                GEN_TRY(radix_argsort_u64(keys, npairs, order, st));
+                GEN_TRY(I->alloc_n(&I->mf_pperm, m));
+                k_move_pair_entries<int32_t><<<nblk(npairs), 256, 0, st>>>(I->perm, order, npairs, I->mf_pperm);
+                k_move_pair_entries<double><<<nblk(npairs), 256, 0, st>>>(I->bhat, order, npairs, nb);
+                GEN_CUDA(cudaMemcpyAsync(I->bhat, nb, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+                k_store_maps<<<nblk(m), 256, 0, st>>>(I->perm_inv, order, m, I->row_of_store, I->store_of_row);
+            } else {
+                GEN_CUDA(cudaMemcpyAsync(I->store_of_row, I->perm, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
+                GEN_CUDA(cudaMemcpyAsync(I->row_of_store, I->perm_inv, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice,
+                                         st));
+            }
+            k_to_f32<<<nblk(m), 256, 0, st>>>(I->bhat, m, I->bhat32);
+            GEN_CUDA(cudaGetLastError());
+            GEN_CUDA(cudaStreamSynchronize(st));
+            I->mf_c = (float)g.c;
+            I->mf_s = (float)g.s;
+            I->mf_ct = (float)g.ct;
+            I->mf_st = (float)g.st;
+            I->f_star = p->tau * hred[0] + 0.5 * hred[1];
+            I->lam_max = hred[2];
+            I->lipschitz = 1.0;
+            *out = I;
+            return L1LS_OK;
+        }
 
         // CSR(Ahat^T): counts, scan, fill (FP64 values)
         int32_t* cnt = nullptr;

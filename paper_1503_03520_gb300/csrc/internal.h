@@ -65,6 +65,11 @@ struct Inst {
     int64_t m = 0, n = 0, nnz = 0, s = 0;
     int64_t nsq = 0;            // size of the square Givens part (n for IGen, m for IGen2)
     bool igen2 = false;
+    // matrix-free instances: no CSR; the products apply the factors (Algorithms MvPA / MvPAt)
+    bool matrix_free = false;
+    float* sigma32 = nullptr;   // Sigma in FP32 (padded to whole tiles)
+    int32_t* mf_pperm = nullptr;   // per stored row pair, the two entries of P it rotates
+    float mf_c = 0, mf_s = 0, mf_ct = 0, mf_st = 0;   // cos / sin of the right and left angles
     int dtype = L1LS_F64;
     // CSR of P1^T A (rows relabelled), m rows
     int32_t* csr_ptr = nullptr;
@@ -133,6 +138,15 @@ inline bool cancel_requested() { return tl_cancel && tl_cancel->load(std::memory
 // products on device buffers (relabelled row order), vec_dtype F64 or F32
 l1ls_status spmv_plain(const Inst* I, bool transpose, const void* x, int vec_dtype, void* y,
                        bool unpermute_rows, cudaStream_t st);
+
+// matrix-free products (csrc/mfree.cu), FP32 vectors: transpose = false: out (m) = A in (n);
+// true: out (n) = A^T in (m); the m-vector's stored row h is entry map[h] (map NULL: h);
+// z: n floats of scratch
+l1ls_status mf_product(const Inst* I, bool transpose, const float* in, float* out, const int32_t* map, float* z,
+                       cudaStream_t st);
+// the first launch of each product alone (FISTA fuses the second with its epilogues)
+l1ls_status mf_apply_rt(const Inst* I, const float* x, float* z, cudaStream_t st);
+l1ls_status mf_apply_left_t(const Inst* I, const float* y, float* z, cudaStream_t st);
 
 l1ls_status fista_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
                         cudaStream_t st);

@@ -547,6 +547,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
 
 l1ls_status pdncg_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
                         cudaStream_t st) {
+    if (I->matrix_free) return set_error(L1LS_EINVAL, "pdNCG needs the assembled matrix (matrix_free = 0)");
     if (I->paired) {
         switch (I->dtype) {
             case L1LS_F64: return run<double, double, true>(I, o, x0, x_out, res, st);

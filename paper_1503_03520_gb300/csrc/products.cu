@@ -81,6 +81,13 @@ l1ls_status dispatch(const Inst* I, bool transpose, const X* x, X* y, const int3
 l1ls_status spmv_plain(const Inst* I, bool transpose, const void* in, int vec_dtype, void* out, bool unpermute_rows,
                        cudaStream_t st) {
     const size_t es = vec_dtype == L1LS_F64 ? 8 : 4;
+    if (I->matrix_free) {
+        if (vec_dtype != L1LS_F32) return set_error(L1LS_EINVAL, "matrix-free instances take FP32 vectors");
+        void* z = nullptr;
+        L1LS_TRY(I->ctx->staging(3, sizeof(float) * (size_t)I->n, &z));
+        return mf_product(I, transpose, static_cast<const float*>(in), static_cast<float*>(out),
+                          unpermute_rows ? I->row_of_store : nullptr, static_cast<float*>(z), st);
+    }
     if (!transpose) {
         const int32_t* op = unpermute_rows ? I->row_of_store : nullptr;
         if (vec_dtype == L1LS_F64) return dispatch<double>(I, false, (const double*)in, (double*)out, op, st);
@@ -174,6 +181,7 @@ extern "C" l1ls_status l1ls_rmatvec_noalloc(const l1ls_inst* inst, const void* y
     if (vec_dtype != L1LS_F64 && vec_dtype != L1LS_F32)
         return set_error(L1LS_EINVAL, "vec_dtype must be L1LS_F64 or L1LS_F32");
     const Inst* I = reinterpret_cast<const Inst*>(inst);
+    if (I->matrix_free) return set_error(L1LS_EINVAL, "l1ls_rmatvec_noalloc needs the assembled matrix");
     if (I->m > kNoAllocMaxRows)
         return set_error(L1LS_EINVAL, "l1ls_rmatvec_noalloc supports m <= %lld rows (instance has m = %lld)",
                          (long long)kNoAllocMaxRows, (long long)I->m);
