@@ -199,6 +199,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist, device="cuda"):
+    """The largest value over all ranks (the job's time is its slowest rank's); value itself
+    without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(log2n, rank):
+    """The instance each rank times: the same recipe, its own seed (replicas, no collective)."""
+    import workloads as W
+    return W.c2_scaled(log2n, seed=rank)
+
+
 def batch_form(l1, W, ctx, iters_per_tau):
     """C4: 256 instances along 16-tau paths in the batched kernel, against the same paths
     solved one instance at a time with FP64 values (a 1-in-16 subsample), equal tolerance and
@@ -388,7 +405,7 @@ def run_ours(args):
     import paper_1503_03520_gb300 as l1
     import workloads as W
 
-    params = W.c2_scaled(args.log2n, seed=rank)
+    params = rank_workload(args.log2n, rank)
     if args.matrix_free:
         params = dict(params, matrix_free=1)
     ctx = l1.Context(local)
@@ -420,10 +437,7 @@ def run_ours(args):
     clk = clocks.stop()
     elapsed_ms = e0.elapsed_time(e1)
     _, fres = inst.fista_end(stream=stream, allow=(4, 5))
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist)
     ms_per_step = elapsed_ms / args.steps
     value = (k1b + k2b) * world / (ms_per_step * 1e-3) / 1e9
 
@@ -455,10 +469,7 @@ def run_ours(args):
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t)
     e2e_s = statistics.median(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     # warm start from x0 costs one extra product A x0 (matrix, x, y)
     e2e_bytes = E2E_ITERS * (k1b + k2b) + (k1b if args.matrix_free else (nnz // 2) * 12 + (m // 2 + 1) * 4 + n * 4 + m * 4)
     e2e = {"value": e2e_bytes * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
