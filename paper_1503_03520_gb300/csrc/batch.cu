@@ -270,9 +270,7 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
         q1 = ff_add(q1, ff_mul(ff_from_float(o.bb), rr));
         q2 = ff_add(q2, ff_mul(rr, rr));
     };
-#pragma unroll 1
-    for (int64_t t = t0; t < t1; ++t)
-        pcsr_tile_ff<true, V, EPL>(t, rptr, rcol, rval, xh, xl, nullptr, npairs, wbuf, pre, epi);
+    tiles_ff<true, true, V, EPL>(t0, t1, rptr, rcol, rval, xh, xl, nullptr, npairs, wbuf, pre, epi);
     q0 = warp_sum_ff(q0);
     q1 = warp_sum_ff(q1);
     q2 = warp_sum_ff(q2);
@@ -320,9 +318,7 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
         l1 = ff_add(l1, ff_abs(xn));
         if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
     };
-#pragma unroll 1
-    for (int64_t t = t0; t < t1; ++t)
-        pcsr_tile_ff<false, V, EPL>(t, cptr, cpair, cval, nullptr, nullptr, res, n, wbuf, pre, epi);
+    tiles_ff<false, true, V, EPL>(t0, t1, cptr, cpair, cval, nullptr, nullptr, res, n, wbuf, pre, epi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_down_sync(0xffffffffu, gmax, o));
     l1 = warp_sum_ff(l1);

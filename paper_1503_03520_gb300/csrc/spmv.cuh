@@ -20,6 +20,12 @@ namespace l1ls {
 constexpr int kEPL = 8;       // nonzeros per lane per chunk
 constexpr int kPad = kEPL;    // slack entries after the nonzero arrays
 constexpr int kWarpChunk = 32 * kEPL;
+// nonzeros per lane and chunk of the paired traversal (a build parameter, 4 or 8)
+#ifndef L1LS_PAIRED_EPL
+#define L1LS_PAIRED_EPL 8
+#endif
+constexpr int kPEPL = L1LS_PAIRED_EPL;
+static_assert(kPEPL == 4 || kPEPL == 8, "paired traversal: 4 or 8 nonzeros per lane");
 
 template <class Acc, class V> __device__ __forceinline__ Acc val_to_acc(V v);
 template <> __device__ __forceinline__ double val_to_acc<double, double>(double v) { return v; }
@@ -150,16 +156,16 @@ __device__ __forceinline__ void pcsr_tile_body(int64_t t, int32_t rb, int32_t re
     const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
     const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
     Acc a0 = Acc(0), a1 = Acc(0);
-    for (int32_t c = e0 & ~(kEPL - 1); c < e1; c += kWarpChunk) {
-        const int32_t base = c + lane * kEPL;
-        Acc p0[kEPL], p1[kEPL];
+    for (int32_t c = e0 & ~(kPEPL - 1); c < e1; c += 32 * kPEPL) {
+        const int32_t base = c + lane * kPEPL;
+        Acc p0[kPEPL], p1[kPEPL];
         if (base < e1) {
-            int32_t ij[kEPL];
-            V vv[2 * kEPL];
-            load_span<int32_t, kEPL>(idx + base, ij);
-            load_span<V, 2 * kEPL>(val2 + 2 * (int64_t)base, vv);
+            int32_t ij[kPEPL];
+            V vv[2 * kPEPL];
+            load_span<int32_t, kPEPL>(idx + base, ij);
+            load_span<V, 2 * kPEPL>(val2 + 2 * (int64_t)base, vv);
 #pragma unroll
-            for (int k = 0; k < kEPL; ++k) {
+            for (int k = 0; k < kPEPL; ++k) {
                 const int32_t e = base + k;
                 const bool in = e >= e0 && e < e1;
                 const Acc v0 = val_to_acc<Acc>(vv[2 * k]), v1 = val_to_acc<Acc>(vv[2 * k + 1]);
@@ -180,18 +186,18 @@ __device__ __forceinline__ void pcsr_tile_body(int64_t t, int32_t rb, int32_t re
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < kEPL; ++k) p0[k] = p1[k] = Acc(0);
+            for (int k = 0; k < kPEPL; ++k) p0[k] = p1[k] = Acc(0);
         }
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k) {
+        for (int k = 0; k < kPEPL; ++k) {
             w0[k * 32 + lane] = p0[k];
             if (ROWS) w1[k * 32 + lane] = p1[k];
         }
         __syncwarp();
-        const int32_t lo = max(rb, c), hi = min(re, c + kWarpChunk);
+        const int32_t lo = max(rb, c), hi = min(re, c + 32 * kPEPL);
         for (int32_t e = lo; e < hi; ++e) {
             const int32_t i = e - c;
-            const int32_t q = (i & (kEPL - 1)) * 32 + (i / kEPL);
+            const int32_t q = (i & (kPEPL - 1)) * 32 + (i / kPEPL);
             a0 += w0[q];
             if (ROWS) a1 += w1[q];
         }
@@ -301,10 +307,10 @@ namespace l1ls {
 // in plain storage one float2 {hi, lo} per row.
 
 template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
-__device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                        const V* __restrict__ val, const float* __restrict__ xh,
-                                        const float* __restrict__ xl, const void* __restrict__ rin, int64_t nrows,
-                                        float* __restrict__ wbuf, Pre& pre, Epi& epi) {
+__device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, const int32_t* __restrict__ idx,
+                                             const V* __restrict__ val, const float* __restrict__ xh,
+                                             const float* __restrict__ xl, const void* __restrict__ rin, int64_t nrows,
+                                             float* __restrict__ wbuf, Pre& pre, Epi& epi) {
     // ROWS: nrows rows (PAIRED: row pairs; pre / epi per row, 2p and 2p+1), (xh, xl) gathered
     // at the column index; otherwise nrows columns, the residual rin gathered at the pair (or
     // row) index.  EPL entries per lane and chunk (4 or 8): fewer registers with 4, more loads
@@ -321,11 +327,6 @@ __device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ p
     constexpr bool kTwoRows = ROWS && PAIRED;
     const int64_t r = (t << 5) + lane;
     const bool has = r < nrows;
-    int32_t rb = 0, re = 0;
-    if (has) {
-        rb = __ldcs(ptr + r);
-        re = __ldcs(ptr + r + 1);
-    }
     auto ops0 = pre(kTwoRows ? 2 * r : r, has);
     auto ops1 = pre(kTwoRows ? 2 * r + 1 : r, kTwoRows && has);
     const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
@@ -402,6 +403,44 @@ __device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ p
         } else {
             epi(r, a0, ops0);
         }
+    }
+}
+
+// row extents of this lane's row of tile t (0, 0 past the end)
+__device__ __forceinline__ void tile_extents(const int32_t* __restrict__ ptr, int64_t t, int64_t nrows, int32_t& rb,
+                                             int32_t& re) {
+    const int64_t r = (t << 5) + (threadIdx.x & 31);
+    rb = re = 0;
+    if (r < nrows) {
+        rb = __ldcs(ptr + r);
+        re = __ldcs(ptr + r + 1);
+    }
+}
+
+template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
+__device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                        const V* __restrict__ val, const float* __restrict__ xh,
+                                        const float* __restrict__ xl, const void* __restrict__ rin, int64_t nrows,
+                                        float* __restrict__ wbuf, Pre& pre, Epi& epi) {
+    int32_t rb, re;
+    tile_extents(ptr, t, nrows, rb, re);
+    tile_ff_body<ROWS, PAIRED, V, EPL>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
+}
+
+// tiles t0 .. t1-1 in order, each tile's row extents loaded before the previous tile's work
+template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
+__device__ __forceinline__ void tiles_ff(int64_t t0, int64_t t1, const int32_t* __restrict__ ptr,
+                                         const int32_t* __restrict__ idx, const V* __restrict__ val,
+                                         const float* __restrict__ xh, const float* __restrict__ xl,
+                                         const void* __restrict__ rin, int64_t nrows, float* __restrict__ wbuf,
+                                         Pre& pre, Epi& epi) {
+    int32_t nb, ne;
+    tile_extents(ptr, t0, nrows, nb, ne);
+#pragma unroll 1
+    for (int64_t t = t0; t < t1; ++t) {
+        const int32_t rb = nb, re = ne;
+        if (t + 1 < t1) tile_extents(ptr, t + 1, nrows, nb, ne);
+        tile_ff_body<ROWS, PAIRED, V, EPL>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
     }
 }
 
