@@ -4,8 +4,9 @@
 // The instances keep their own paired matrices, right-hand sides and iterates; the batch adds
 // a device table of descriptors and two global tile lists (row-pair tiles and column tiles
 // of every instance).  The unit of work is a segment of 8 tiles (a tile: 32 row pairs or 32
-// columns) of one instance.  One launch runs `steps` FISTA steps; each step has two phases
-// separated by bounded grid barriers:
+// columns) of one instance; warps take segments in turn from an atomic counter per phase (so
+// a warp that drew short or retired segments takes more).  One launch runs `steps` FISTA
+// steps; each step has two phases separated by bounded grid barriers:
 //   1. every warp takes row-pair segments of active instances: K1's product, its epilogue and
 //      the segment's gap partials (each lane sums its rows in tile order, then the warp), one
 //      write per segment;
@@ -93,6 +94,7 @@ struct BArgs {
     int64_t nseg1, nseg2;
     double* part1;             // [segment][3]
     double* part2;             // [segment][3]
+    unsigned* fetch;           // [2] next segment of phase 1 / phase 2 (warps take segments in turn)
     unsigned* instcnt1;        // segments done per instance (reset by the instance's last warp)
     unsigned* instcnt2;
     int ninst, ntau_max;
@@ -332,14 +334,18 @@ template <int BLOCK, int EPL, class V>
 __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
     __shared__ CompSmem<BLOCK> sm;   // 4 * kWarpChunk floats per warp; phase 2 uses half
     const int lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5);
-    const int64_t nw = (int64_t)gridDim.x * (BLOCK / 32);
     for (int s = 0; s < a.steps; ++s) {
         if (*(volatile int*)a.active == 0) return;
         const int64_t step = a.step0 + s;
         const int cur = (int)(step & 1);
-        // ---- phase 1: row-pair segments (A x, residual, gap partials)
-        for (int64_t sg = gw; sg < a.nseg1; sg += nw) {
+        // phase 2's segment counter is idle until after the next barrier
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.fetch[1] = 0u;
+        // ---- phase 1: row-pair segments (A x, residual, gap partials), taken in turn
+        for (;;) {
+            unsigned got = 0;
+            if (lane == 0) got = atomicAdd(a.fetch, 1u);
+            const int64_t sg = __shfl_sync(0xffffffffu, got, 0);
+            if (sg >= a.nseg1) break;
             const int i = a.sinst1[sg];
             if (__ldcg(&a.state[i].stop)) continue;
             const BDesc* dp = a.desc + i;
@@ -354,8 +360,13 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
                 for (int k = 0; k < 3; ++k) a.state[i].k1[k] = tot[k];
         }
         if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.fetch[0] = 0u;
         // ---- phase 2: column segments (A^T r, momentum, shrinkage), then the scalar step
-        for (int64_t sg = gw; sg < a.nseg2; sg += nw) {
+        for (;;) {
+            unsigned got = 0;
+            if (lane == 0) got = atomicAdd(a.fetch + 1, 1u);
+            const int64_t sg = __shfl_sync(0xffffffffu, got, 0);
+            if (sg >= a.nseg2) break;
             const int i = a.sinst2[sg];
             if (__ldcg(&a.state[i].stop)) continue;
             const BDesc* dp = a.desc + i;
@@ -532,7 +543,7 @@ extern "C" l1ls_status l1ls_batch_create(l1ls_ctx* hctx, int count, l1ls_inst* c
     if ((s = B->get(&B->d_sinst2, B->nseg2)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_part1, 3 * B->nseg1)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_part2, 3 * B->nseg2)) != L1LS_OK) return fail(s);
-    if ((s = B->get(&B->d_cnt, 2 * (int64_t)count)) != L1LS_OK) return fail(s);
+    if ((s = B->get(&B->d_cnt, 2 * (int64_t)count + 2)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_bar, 2)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_err, 1)) != L1LS_OK) return fail(s);
     if ((s = B->get(&B->d_active, 1)) != L1LS_OK) return fail(s);
@@ -590,7 +601,7 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     L1LS_CUDA(cudaMemcpyAsync(B->d_state, hs.data(), sizeof(BState) * count, cudaMemcpyHostToDevice, st));
     L1LS_CUDA(cudaMemsetAsync(B->slab, 0, B->slab_bytes, st));
     L1LS_CUDA(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), st));
-    L1LS_CUDA(cudaMemsetAsync(B->d_cnt, 0, sizeof(unsigned) * 2 * (size_t)count, st));
+    L1LS_CUDA(cudaMemsetAsync(B->d_cnt, 0, sizeof(unsigned) * (2 * (size_t)count + 2), st));
     L1LS_CUDA(cudaMemsetAsync(B->d_err, 0, sizeof(int), st));
     L1LS_CUDA(cudaMemcpyAsync(B->d_active, &count, sizeof(int), cudaMemcpyHostToDevice, st));
     BArgs args{};
@@ -606,6 +617,7 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     args.part2 = B->d_part2;
     args.instcnt1 = B->d_cnt;
     args.instcnt2 = B->d_cnt + count;
+    args.fetch = B->d_cnt + 2 * count;
     args.ninst = count;
     args.ntau_max = ntau;
     args.bar_count = B->d_bar;
