@@ -490,24 +490,29 @@ __global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
     if (*(volatile int32_t*)&a.st->stop) return;
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
-    const int64_t a0 = (int64_t)blockIdx.x * kMfTile;
-    mf_load<true>(buf, a.z, a.sigma, a0 - kMfHalo, a.R.n);
-    mf_stages<false>(buf, a0 - kMfHalo, a.R);
     float gmax = 0.0f;
     ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
-    for (int p = threadIdx.x; p < kMfTile; p += blockDim.x) {
-        const int64_t j = a0 + p;
-        if (j >= a.R.n) break;
-        const float g = buf[kMfHalo + p];
-        const ff x1 = {a.xch[j], a.xcl[j]}, x0 = {a.xoh[j], a.xol[j]};
-        const ff y = ff_add(x1, ff_mul(beta_f, ff_sub(x1, x0)));
-        const ff v = ff_add(y, ff_mul(ff_from_float(g), invL_f));
-        const ff xn = ff_soft_threshold(v, thr_f);
-        a.xoh[j] = xn.hi;
-        a.xol[j] = xn.lo;
-        gmax = fmaxf(gmax, fabsf(g));
-        l1 = ff_add(l1, ff_abs(xn));
-        if (RESTART) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, x1)));
+    // persistent blocks take tiles in turn (fewer per-block partials for the last block to sum)
+    const int64_t ntiles = (a.R.n + kMfTile - 1) / kMfTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t a0 = tile * kMfTile;
+        mf_load<true>(buf, a.z, a.sigma, a0 - kMfHalo, a.R.n);
+        mf_stages<false>(buf, a0 - kMfHalo, a.R);
+        for (int p = threadIdx.x; p < kMfTile; p += blockDim.x) {
+            const int64_t j = a0 + p;
+            if (j >= a.R.n) break;
+            const float g = buf[kMfHalo + p];
+            const ff x1 = {a.xch[j], a.xcl[j]}, x0 = {a.xoh[j], a.xol[j]};
+            const ff y = ff_add(x1, ff_mul(beta_f, ff_sub(x1, x0)));
+            const ff v = ff_add(y, ff_mul(ff_from_float(g), invL_f));
+            const ff xn = ff_soft_threshold(v, thr_f);
+            a.xoh[j] = xn.hi;
+            a.xol[j] = xn.lo;
+            gmax = fmaxf(gmax, fabsf(g));
+            l1 = ff_add(l1, ff_abs(xn));
+            if (RESTART) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, x1)));
+        }
+        __syncthreads();   // the tile buffer is reloaded next
     }
     double pp[3] = {(double)gmax, ff_to_double(l1), ff_to_double(rt)};
     block_reduce<kMfThreads, 3>(pp, 1u, red);
@@ -764,7 +769,10 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
             w->grid1 = (int)std::max<int64_t>(
                 1, std::min<int64_t>((units + (int64_t)kBlock * kMfUnroll - 1) / ((int64_t)kBlock * kMfUnroll),
                                      (int64_t)I->ctx->num_sms * std::max(per_sm, 1)));
-            w->grid2 = (int)((n + kMfTile - 1) / kMfTile);
+            int per_sm2 = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_fista_mf2<false>, kMfThreads, 0);
+            w->grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((n + kMfTile - 1) / kMfTile,
+                                                                     (int64_t)I->ctx->num_sms * std::max(per_sm2, 1)));
         } else if (I->paired) {
             w->grid1 = grid_of(I, k_fista_k1<V, Vec, true>, m / 2);
             w->grid2 = grid_of(I, k_fista_k2<V, Vec, true, false>, n);
