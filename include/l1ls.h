@@ -265,6 +265,12 @@ l1ls_status l1ls_batch_solve_path(l1ls_batch* batch, const double* taus, int nta
                                   l1ls_result* results, double* const* x_out, void* stream);
 l1ls_status l1ls_batch_get_schedule(const l1ls_batch* batch, int* block, int* entries_per_lane, double* tune_ms);
 l1ls_status l1ls_batch_get_stats(const l1ls_batch* batch, int64_t* steps, double* device_ms);
+/* Failure-detection self-test of the batched kernel's bounded grid barrier: runs one step in
+ * which the barrier expects one block more than the grid holds, so every block's wait runs out
+ * after max_polls polls (each with a short sleep), records the expiry and leaves the kernel.
+ * Returns L1LS_ECUDA with the message a real expiry gives, the elapsed wall time in *seconds
+ * (may be NULL), and leaves the batch and its context usable (the next solve runs normally). */
+l1ls_status l1ls_batch_barrier_selftest(l1ls_batch* batch, uint32_t max_polls, double* seconds);
 l1ls_status l1ls_batch_free(l1ls_batch* batch);
 
 /* Thread-local message describing the last non-OK status returned on this thread. */

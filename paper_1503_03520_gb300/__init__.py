@@ -108,6 +108,7 @@ _sig = {
                                                ctypes.POINTER(ctypes.c_double)]),
     "l1ls_batch_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "l1ls_batch_free": (ctypes.c_int, [_P]),
+    "l1ls_batch_barrier_selftest": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
     "l1ls_footprint": (ctypes.c_size_t, [ctypes.POINTER(GenParams), ctypes.c_int]),
     "l1ls_serve_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_size_t]),
     "l1ls_submit": (ctypes.c_int, [_P, ctypes.POINTER(GenParams), ctypes.POINTER(SolveOpts), ctypes.c_int,
@@ -419,6 +420,12 @@ class Batch:
         _check(lib.l1ls_batch_get_schedule(self._h, ctypes.byref(b), ctypes.byref(e), ms))
         return {"block": b.value, "entries_per_lane": e.value, "probe_ms": list(ms),
                 "candidates": [(256, 8), (128, 8), (256, 4), (128, 4)]}
+
+    def barrier_selftest(self, max_polls=1 << 12):
+        """Run the bounded-barrier self-test; returns (status, message, seconds)."""
+        sec = ctypes.c_double()
+        st = lib.l1ls_batch_barrier_selftest(self._h, int(max_polls), ctypes.byref(sec))
+        return st, lib.l1ls_last_error().decode(), sec.value
 
     def stats(self):
         """Of the last solve: batch steps run and the device time of their launches (ms)."""

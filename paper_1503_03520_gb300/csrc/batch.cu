@@ -64,7 +64,13 @@ struct BState {
     double k1[3];              // phase-1 sums: ||A x - b||^2, b.r, r.r
     int64_t iter;
     int32_t stop, status, tau_idx, ntau, final_buf, restart;
+    float beta_ff[2], invL_ff[2], thr_ff[2];   // beta, 1/L, tau/L as float-float (set with them)
 };
+
+__host__ __device__ inline void split_ff(double d, float (&out)[2]) {
+    out[0] = (float)d;
+    out[1] = (float)(d - (double)out[0]);
+}
 
 static_assert(sizeof(BState) % 8 == 0, "state is read as 64-bit words");
 
@@ -104,9 +110,14 @@ struct BArgs {
     int* active;
     int64_t step0;
     int steps;
+    uint32_t max_polls;        // the barrier's poll limit (kBarrierPolls in solves)
+    unsigned extra_arrivals;   // 0 in solves; the failure self-test sets 1 (a barrier that never fills)
 };
 
-__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err) {
+// Bounded grid barrier: every block's thread 0 arrives on count; the last one (count reaching
+// gridDim.x + extra, extra = 0 in every solve) bumps gen.  A block that polls gen max_polls
+// times without a change sets *err = 2 and returns false (its block leaves the kernel).
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, uint32_t max_polls, unsigned extra) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -114,14 +125,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, int* e
         const unsigned g = *(volatile unsigned*)gen;
         __threadfence();
         const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == gridDim.x - 1 + extra) {
             atomicExch(count, 0u);
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
             uint32_t polls = 0;
             while (*(volatile unsigned*)gen == g) {
-                if (++polls > kBarrierPolls) {
+                if (++polls > max_polls) {
                     ok = 0;
                     atomicExch(err, 2);
                     break;
@@ -227,6 +238,9 @@ __device__ void finish_step(const BArgs& a, int64_t i, int cur, double gm, doubl
         st.l1_cur = l1n;
         st.iter += 1;
     }
+    split_ff(st.beta, st.beta_ff);
+    split_ff(1.0 / st.L, st.invL_ff);
+    split_ff(st.tau / st.L, st.thr_ff);
     a.state[i] = st;
 }
 
@@ -234,7 +248,7 @@ __device__ void finish_step(const BArgs& a, int64_t i, int cur, double gm, doubl
 // the segment's partials ||A x - b||^2, b.r, r.r in out (lane 0).  Not inlined: the two phases
 // then get their registers allocated separately.
 template <class V, int EPL>
-__device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, double beta_d, int64_t t0, int64_t t1,
+__device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, ff beta, int64_t t0, int64_t t1,
                                          float* wbuf, double* out) {
     const int32_t* rptr = dp->rptr;
     const int32_t* rcol = dp->rcol;
@@ -245,7 +259,6 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
     const float* bv = dp->b;
     float* resf = reinterpret_cast<float*>(dp->res);
     const int64_t npairs = dp->m / 2;
-    const ff beta = ff_from_double(beta_d);
     ff q0 = {0.f, 0.f}, q1 = {0.f, 0.f}, q2 = {0.f, 0.f};
     struct Ops {
         ff axo;
@@ -284,7 +297,7 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
 // One column segment of instance d: K2's product, momentum and shrinkage into x[nxt];
 // returns max |A^T r|, sum |x_{k+1}| and the restart test's partial in out (lane 0).
 template <class V, int EPL>
-__device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, double beta, double L, double tau,
+__device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, ff beta_f, ff invL_f, ff thr_f,
                                          bool rs, int64_t t0, int64_t t1, float* wbuf, double* out) {
     const int32_t* cptr = dp->cptr;
     const int32_t* cpair = dp->cpair;
@@ -295,7 +308,6 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
     float* x0h = dp->xh[cur ^ 1];
     float* x0l = dp->xl[cur ^ 1];
     const int64_t n = dp->n;
-    const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
     float gmax = 0.0f;
     ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
     struct Ops {
@@ -352,14 +364,15 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
             const int64_t sb = dp->s1_begin, ns = dp->ns1;
             const int64_t t0 = (sg - sb) * kSegTiles, t1 = min(dp->n1, t0 + kSegTiles);
             double part[3];
-            row_segment<V, EPL>(dp, cur, __ldcg(&a.state[i].beta), t0, t1, sm.warp_buf(), part);
+            const ff beta = {__ldcg(&a.state[i].beta_ff[0]), __ldcg(&a.state[i].beta_ff[1])};
+            row_segment<V, EPL>(dp, cur, beta, t0, t1, sm.warp_buf(), part);
             if (lane == 0)
                 for (int k = 0; k < 3; ++k) a.part1[3 * sg + k] = part[k];
             double tot[3];
             if (segment_done<3, false>(sb, ns, a.part1, a.instcnt1 + i, tot) && lane == 0)
                 for (int k = 0; k < 3; ++k) a.state[i].k1[k] = tot[k];
         }
-        if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
+        if (!grid_sync(a.bar_count, a.bar_gen, a.err, a.max_polls, a.extra_arrivals)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.fetch[0] = 0u;
         // ---- phase 2: column segments (A^T r, momentum, shrinkage), then the scalar step
         for (;;) {
@@ -373,15 +386,18 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
             const int64_t sb = dp->s2_begin, ns = dp->ns2;
             const int64_t t0 = (sg - sb) * kSegTiles, t1 = min(dp->n2, t0 + kSegTiles);
             double part[3];
-            col_segment<V, EPL>(dp, cur, __ldcg(&a.state[i].beta), __ldcg(&a.state[i].L), __ldcg(&a.state[i].tau),
-                           __ldcg(&a.state[i].restart) != 0, t0, t1, sm.warp_buf(), part);
+            const BState* sp = a.state + i;
+            col_segment<V, EPL>(dp, cur, {__ldcg(&sp->beta_ff[0]), __ldcg(&sp->beta_ff[1])},
+                                {__ldcg(&sp->invL_ff[0]), __ldcg(&sp->invL_ff[1])},
+                                {__ldcg(&sp->thr_ff[0]), __ldcg(&sp->thr_ff[1])}, __ldcg(&sp->restart) != 0, t0, t1,
+                                sm.warp_buf(), part);
             if (lane == 0)
                 for (int k = 0; k < 3; ++k) a.part2[3 * sg + k] = part[k];
             double tot[3];
             if (segment_done<3, true>(sb, ns, a.part2, a.instcnt2 + i, tot) && lane == 0)
                 finish_step(a, i, cur, tot[0], tot[1], tot[2]);
         }
-        if (!grid_sync(a.bar_count, a.bar_gen, a.err)) return;
+        if (!grid_sync(a.bar_count, a.bar_gen, a.err, a.max_polls, a.extra_arrivals)) return;
     }
 }
 
@@ -597,6 +613,9 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
         s.iter = 1;
         s.ntau = ntau;
         s.restart = o->restart;
+        split_ff(0.0, s.beta_ff);
+        split_ff(1.0 / s.L, s.invL_ff);
+        split_ff(s.tau / s.L, s.thr_ff);
     }
     L1LS_CUDA(cudaMemcpyAsync(B->d_state, hs.data(), sizeof(BState) * count, cudaMemcpyHostToDevice, st));
     L1LS_CUDA(cudaMemsetAsync(B->slab, 0, B->slab_bytes, st));
@@ -618,6 +637,8 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
     args.instcnt1 = B->d_cnt;
     args.instcnt2 = B->d_cnt + count;
     args.fetch = B->d_cnt + 2 * count;
+    args.max_polls = kBarrierPolls;
+    args.extra_arrivals = 0;
     args.ninst = count;
     args.ntau_max = ntau;
     args.bar_count = B->d_bar;
@@ -744,4 +765,59 @@ extern "C" l1ls_status l1ls_batch_get_stats(const l1ls_batch* h, int64_t* steps,
     if (steps) *steps = B->last_steps;
     if (device_ms) *device_ms = B->last_ms;
     return L1LS_OK;
+}
+
+extern "C" l1ls_status l1ls_batch_barrier_selftest(l1ls_batch* h, uint32_t max_polls, double* seconds) {
+    if (!h || max_polls < 1) return set_error(L1LS_EINVAL, "bad argument");
+    Batch* B = reinterpret_cast<Batch*>(h);
+    L1LS_CUDA(cudaSetDevice(B->ctx->device));
+    const int count = (int)B->insts.size();
+    cudaStream_t st = nullptr;
+    L1LS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    // every instance stopped (phase 1 has no work), one active so the step starts
+    std::vector<BState> hs(count);
+    for (auto& x : hs) {
+        memset(&x, 0, sizeof(x));
+        x.stop = 1;
+    }
+    const int one = 1;
+    L1LS_CUDA(cudaMemcpyAsync(B->d_state, hs.data(), sizeof(BState) * count, cudaMemcpyHostToDevice, st));
+    L1LS_CUDA(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), st));
+    L1LS_CUDA(cudaMemsetAsync(B->d_err, 0, sizeof(int), st));
+    L1LS_CUDA(cudaMemsetAsync(B->d_cnt, 0, sizeof(unsigned) * (2 * (size_t)count + 2), st));
+    L1LS_CUDA(cudaMemcpyAsync(B->d_active, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    BArgs args{};
+    args.desc = B->d_desc;
+    args.state = B->d_state;
+    args.sinst1 = B->d_sinst1;
+    args.sinst2 = B->d_sinst2;
+    args.nseg1 = B->nseg1;
+    args.nseg2 = B->nseg2;
+    args.part1 = B->d_part1;
+    args.part2 = B->d_part2;
+    args.instcnt1 = B->d_cnt;
+    args.instcnt2 = B->d_cnt + count;
+    args.fetch = B->d_cnt + 2 * count;
+    args.ninst = count;
+    args.ntau_max = 1;
+    args.bar_count = B->d_bar;
+    args.bar_gen = B->d_bar + 1;
+    args.err = B->d_err;
+    args.active = B->d_active;
+    args.step0 = 0;
+    args.steps = 1;
+    args.max_polls = max_polls;
+    args.extra_arrivals = 1;
+    auto t0 = std::chrono::steady_clock::now();
+    L1LS_TRY(launch_any(B, 1, args, st));
+    int err = 0;
+    L1LS_CUDA(cudaMemcpyAsync(&err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    L1LS_CUDA(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), st));
+    L1LS_CUDA(cudaMemsetAsync(B->d_err, 0, sizeof(int), st));
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    cudaStreamDestroy(st);
+    if (err == 2) return set_error(L1LS_ECUDA, "batched FISTA: a bounded grid barrier expired (self-test)");
+    return set_error(L1LS_ECUDA, "self-test: the barrier did not report its expiry (err %d)", err);
 }

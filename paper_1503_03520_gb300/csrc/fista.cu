@@ -49,7 +49,16 @@ struct FistaState {
     unsigned cnt1, cnt2;
     int32_t restart, pad;
     int64_t restarts;
+    // beta, 1/L and tau/L as float-float, refreshed with beta by the scalar step: the FP32
+    // kernels read them instead of every thread converting (two FP64 divisions each)
+    float beta_ff[2], invL_ff[2], thr_ff[2];
 };
+
+// host and device: the float-float scalars of the state
+__host__ __device__ inline void split_ff(double d, float (&out)[2]) {
+    out[0] = (float)d;
+    out[1] = (float)(d - (double)out[0]);
+}
 
 template <class V, class Vec>
 struct K1Args {
@@ -171,6 +180,7 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new, doubl
             st->beta = (t - 1.0) / tn;
             st->t = tn;
         }
+        split_ff(st->beta, st->beta_ff);
         st->l1_cur = l1_new;
         st->iter += 1;
     }
@@ -187,7 +197,8 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<
     constexpr bool rs = RESTART;   // the gradient-restart partial (an instantiation per setting)
     double p[3] = {0.0, 0.0, 0.0};
     if constexpr (sizeof(Vec) == 4) {
-        const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(invL), thr_f = ff_from_double(thr);
+        const ff beta_f = {a.st->beta_ff[0], a.st->beta_ff[1]}, invL_f = {a.st->invL_ff[0], a.st->invL_ff[1]},
+                 thr_f = {a.st->thr_ff[0], a.st->thr_ff[1]};
         float gmax = 0.0f;
         ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
         struct Ops {
@@ -341,9 +352,9 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
     __shared__ CompSmem<kBlock> sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
-    const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
     const bool rs = a.st->restart != 0;
-    const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
+    const ff beta_f = {a.st->beta_ff[0], a.st->beta_ff[1]}, invL_f = {a.st->invL_ff[0], a.st->invL_ff[1]},
+             thr_f = {a.st->thr_ff[0], a.st->thr_ff[1]};
     float gmax = 0.0f;
     ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
     struct Ops {
@@ -488,8 +499,8 @@ __global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
     __shared__ float buf[kMfLen];
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
-    const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
-    const ff beta_f = ff_from_double(beta), invL_f = ff_from_double(1.0 / L), thr_f = ff_from_double(tau / L);
+    const ff beta_f = {a.st->beta_ff[0], a.st->beta_ff[1]}, invL_f = {a.st->invL_ff[0], a.st->invL_ff[1]},
+             thr_f = {a.st->thr_ff[0], a.st->thr_ff[1]};
     float gmax = 0.0f;
     ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
     // persistent blocks take tiles in turn (fewer per-block partials for the last block to sum)
@@ -819,6 +830,9 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     h.status = L1LS_OK;
     h.restart = o->restart;
     h.restarts = 0;
+    split_ff(0.0, h.beta_ff);
+    split_ff(1.0 / h.L, h.invL_ff);
+    split_ff(h.tau / h.L, h.thr_ff);
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (x0) {
         // x0 (device or host FP64) -> FP64 staging -> iterate buffers

@@ -98,3 +98,20 @@ def test_batch_rejects_mixed_or_unpaired(setup):
     finally:
         plain.free()
         f64.free()
+
+
+def test_bounded_barrier_expires_and_the_context_survives(setup):
+    """Failure detection without a GPU fault: the self-test's barrier never fills, every block's
+    bounded wait runs out and the kernel returns; the status reaches the host and the next solve
+    runs normally."""
+    import paper_1503_03520_gb300 as l1
+    ctx, params, refs, insts, taus = setup
+    batch = l1.Batch(ctx, insts[:2])
+    try:
+        st, msg, sec = batch.barrier_selftest(max_polls=1 << 12)
+        assert st == 3 and "barrier expired" in msg
+        assert sec < 30.0
+        res = batch.solve_path(taus[:2], tol=1e-6, max_iter=100000, restart=1)
+        assert all(r["status"] == 0 for rr in res for r in rr)
+    finally:
+        batch.free()
