@@ -63,6 +63,12 @@ class GenParams:
     vartheta: float = float("nan")   # nan: same angle as theta
     g_offsupport: int = 0            # 0: U(-1,1) off the support, 1: zero
     n_nnz_per_col: int = 8           # IGen2: nonzeros per column of N
+    # Sec. 8.9's huge-scale instances: sigma_i alternating (sigma_odd for odd i = 1, 3, ...,
+    # sigma_even for even i), and x* with half of its nonzeros -xstar_hi, the rest +xstar_lo
+    sigma_mode: int = 0              # 0: log-spaced by kappa; 1: alternating
+    sigma_odd: float = 0.1
+    sigma_even: float = 100.0
+    xstar_mode: int = 0              # 0: +-U[lo, hi]; 1: first half of the support -hi, rest +lo
 
     @classmethod
     def from_dict(cls, d):
@@ -193,6 +199,14 @@ def _values_on_pattern(pattern, values):
     return out
 
 
+def sigma_of(p: GenParams, count):
+    """The singular values of the square factor: log-spaced by kappa, or (sigma_mode 1,
+    Sec. 8.9) sigma_i = sigma_odd for odd i and sigma_even for even i (1-based i)."""
+    if p.sigma_mode == 1:
+        return np.where(np.arange(count) % 2 == 0, p.sigma_odd, p.sigma_even).astype(np.float64)
+    return singular_values(p.seed, count, p.kappa)
+
+
 def singular_values(seed, count, kappa):
     """sigma_i = kappa^(-rank_i/(count-1)), ranks from the argsort of random keys."""
     if count == 1:
@@ -219,9 +233,15 @@ def optimal_solution(p: GenParams, ncols_support):
     s = min(s, ncols_support)
     keys = rng.draws(p.seed, rng.TAG_SUPPORT, ncols_support)
     S = np.sort(np.argsort(keys, kind="stable")[:s])
+    xstar = np.zeros(p.n)
+    if p.xstar_mode == 1:
+        # Sec. 8.9: half of the nonzeros (the first in index order) -xstar_hi, the rest +xstar_lo
+        h = len(S) // 2
+        xstar[S[:h]] = -p.xstar_hi
+        xstar[S[h:]] = p.xstar_lo
+        return xstar, S
     mag = p.xstar_lo + (p.xstar_hi - p.xstar_lo) * rng.unit_uniform(rng.draws(p.seed, rng.TAG_XVAL, p.n))
     neg = (rng.draws(p.seed, rng.TAG_XSIGN, p.n) >> np.uint64(63)) == np.uint64(1)
-    xstar = np.zeros(p.n)
     xstar[S] = np.where(neg[S], -mag[S], mag[S])
     return xstar, S
 
@@ -239,7 +259,7 @@ def subgradient(p: GenParams, xstar, count):
 def _square_part(p: GenParams, size, rows):
     """(A0, R, L, sigma, perm) for A0 = L Sigma R^T with ``rows`` >= ``size`` rows."""
     c, s, ct, st = angles(p)
-    sigma = singular_values(p.seed, size, p.kappa)
+    sigma = sigma_of(p, size)
     R = right_factor(size, p.right_stages, c, s)
     perm = row_permutation(p.seed, rows) if p.left_stages > 0 else None
     L = left_factor(rows, p.left_stages, perm, ct, st)
@@ -355,7 +375,7 @@ class Factors:
 def make_factors(p: GenParams) -> Factors:
     if p.m < p.n:
         raise ValueError("make_factors covers IGen (m >= n)")
-    sigma = singular_values(p.seed, p.n, p.kappa)
+    sigma = sigma_of(p, p.n)
     perm = row_permutation(p.seed, p.m) if p.left_stages > 0 else None
     xstar, S = optimal_solution(p, p.n)
     g = subgradient(p, xstar, p.n)

@@ -224,3 +224,23 @@ def test_igen2_step_size_bounds_the_spectrum():
         top = np.linalg.svd(inst.A.toarray(), compute_uv=False)[0]
         assert inst.lipschitz >= top ** 2 * (1 - 1e-12)
         assert inst.lipschitz <= 1.0 + 5.0 * 48
+
+
+def test_sec89_instance_shape():
+    """Sec. 8.9's instances: sigma_i = 0.1 for odd i and 100 for even i, so A^T A = G Sigma^2 G^T
+    has exactly the eigenvalues 0.01 and 1e4, n/2 times each; half of the nonzeros of x* are
+    -1e4 and the rest 0.1; x* is optimal at tau (Eq. bd7, zero gap)."""
+    p = GenParams(m=128, n=64, seed=3, right_stages=2, left_stages=0, theta=2.0 * math.pi / 3.0, sigma_mode=1,
+                  sigma_odd=0.1, sigma_even=100.0, xstar_mode=1, xstar_lo=0.1, xstar_hi=1e4, xstar_frac=1.0 / 8.0)
+    inst = generate(p)
+    assert np.array_equal(inst.sigma[0::2], np.full(32, 0.1)) and np.array_equal(inst.sigma[1::2], np.full(32, 100.0))
+    ev = np.sort(np.linalg.eigvalsh((inst.A.T @ inst.A).toarray()))
+    assert np.allclose(ev[:32], 0.01, rtol=1e-9) and np.allclose(ev[32:], 1e4, rtol=1e-12)
+    S = inst.support
+    assert len(S) == 8 and np.array_equal(inst.xstar[S[:4]], np.full(4, -1e4))
+    assert np.array_equal(inst.xstar[S[4:]], np.full(4, 0.1))
+    assert np.count_nonzero(inst.xstar) == 8
+    assert inst.lipschitz == 1e4
+    assert np.abs(inst.A.T @ inst.e - p.tau * inst.g).max() < 1e-7
+    # b carries A x* with entries near 1e6, so the gap at x* is zero only to FP64 rounding
+    assert abs(certificate(inst.A, inst.b, p.tau, inst.xstar)[3]) < 1e-7

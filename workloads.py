@@ -17,6 +17,7 @@ Workloads (all synthetic; the paper uses no dataset):
           16 tau values 0.9 lambda_max 10^(-3 j / 15).
 * ``c5``  Poisson arrivals; n log-uniform in [2^10, 2^23] (even), m in {n/2, 2n}, kappa
           log-uniform in [1e2, 1e6], x* density U[0.5%, 5%], tau = 10^U[-2,0] lambda_max.
+* ``sec89`` the huge-scale instances of Sec. 8.9 at a size one GPU holds.
 """
 
 import math
@@ -93,6 +94,16 @@ def c5_requests(count, rate, seed=777, log2n_lo=10, log2n_hi=23):
                                            right_stages=2, left_stages=1, value_dtype="f32"),
                         tau_factor=tau_factor, method=method))
     return out
+
+
+def sec89(log2n, value_dtype="f32", seed=0):
+    """The huge-scale instances of Sec. 8.9 at n = 2^log2n: A = Sigma G^T (no left stage),
+    m = 2n, sigma_i = 0.1 (odd i) / 100 (even i), theta = 2 pi / 3, s = n / 2^10 nonzeros of x*,
+    half -1e4 and half 0.1; G = G2 G (two stages, as constructed in Sec. 4.2)."""
+    n = 2 ** log2n
+    return params(m=2 * n, n=n, seed=seed, right_stages=2, left_stages=0, theta=2.0 * math.pi / 3.0,
+                  sigma_mode=1, sigma_odd=0.1, sigma_even=100.0, xstar_mode=1, xstar_lo=0.1, xstar_hi=1e4,
+                  xstar_frac=2.0 ** -10, value_dtype=value_dtype)
 
 
 def random_vector(size, seed):
