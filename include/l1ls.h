@@ -73,6 +73,11 @@ typedef enum { L1LS_F64 = 0, L1LS_F32 = 1, L1LS_BF16 = 2 } l1ls_dtype;
  *   value_dtype   l1ls_dtype in which the nonzeros of A are stored (rounded from FP64).
  *   g_offsupport  0: g_i ~ U(-1,1) off the support of x*; 1: g_i = 0 there.
  *   n_nnz_per_col IGen2 only: nonzeros per column of N.
+ *   sigma_mode    0: sigma_i = kappa^(-rank_i/(n-1)) (log-spaced, random assignment);
+ *                 1: sigma_i = sigma_odd for odd i and sigma_even for even i (1-based), the
+ *                 singular values of the huge-scale instances of Sec. 8.9.
+ *   xstar_mode    0: OsGen magnitudes U[xstar_lo, xstar_hi] with random signs; 1: the first
+ *                 half of the support (index order) -xstar_hi, the rest +xstar_lo (Sec. 8.9).
  *   matrix_free   1: A is not assembled; products apply its factors (Algorithms MvPA /
  *                 MvPAt of Sec. 4: the stages of R, Sigma, the permutation and the left
  *                 rotations), so the instance holds O(m + n) memory.  IGen (m >= n) with
@@ -92,10 +97,13 @@ typedef struct {
     int32_t g_offsupport;
     int32_t n_nnz_per_col;
     int32_t matrix_free;
+    int32_t sigma_mode, xstar_mode;
+    double sigma_odd, sigma_even;
 } l1ls_gen_params;
 
 /* Fill p with the defaults: m = 2048, n = 1024, seed 0, kappa 100, tau 1, frac 0.05,
- * magnitudes [1, 10], w = 1, one left stage, theta = vartheta = 2 pi / 10, FP64 values. */
+ * magnitudes [1, 10], w = 1, one left stage, theta = vartheta = 2 pi / 10, FP64 values,
+ * sigma_mode = xstar_mode = 0 (sigma_odd 0.1, sigma_even 100 for mode 1). */
 void l1ls_gen_params_default(l1ls_gen_params* p);
 
 typedef struct {

@@ -27,7 +27,9 @@ class GenParams(ctypes.Structure):
                 ("xstar_lo", ctypes.c_double), ("xstar_hi", ctypes.c_double), ("theta", ctypes.c_double),
                 ("vartheta", ctypes.c_double), ("right_stages", ctypes.c_int32), ("left_stages", ctypes.c_int32),
                 ("value_dtype", ctypes.c_int32), ("g_offsupport", ctypes.c_int32),
-                ("n_nnz_per_col", ctypes.c_int32), ("matrix_free", ctypes.c_int32)]
+                ("n_nnz_per_col", ctypes.c_int32), ("matrix_free", ctypes.c_int32),
+                ("sigma_mode", ctypes.c_int32), ("xstar_mode", ctypes.c_int32), ("sigma_odd", ctypes.c_double),
+                ("sigma_even", ctypes.c_double)]
 
 
 class InstInfo(ctypes.Structure):

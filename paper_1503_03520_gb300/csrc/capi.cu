@@ -122,6 +122,8 @@ void l1ls_gen_params_default(l1ls_gen_params* p) {
     p->value_dtype = L1LS_F64;
     p->g_offsupport = 0;
     p->n_nnz_per_col = 8;
+    p->sigma_odd = 0.1;
+    p->sigma_even = 100.0;
 }
 
 void l1ls_solve_opts_default(l1ls_solve_opts* o) {

@@ -122,6 +122,36 @@ __global__ void k_xstar_g(uint64_t seed, int64_t n, int64_t nsup, const uint8_t*
     if (i < nsup) g[i] = gi;
 }
 
+// Sec. 8.9's singular values: sigma_odd for odd i, sigma_even for even i (1-based i)
+__global__ void k_sigma_alt(int64_t count, double s_odd, double s_even, double* __restrict__ sigma) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) sigma[j] = (j & 1) ? s_even : s_odd;
+}
+
+// support flags as int32 (for the exclusive scan that ranks the support in index order)
+__global__ void k_flag_i32(const uint8_t* __restrict__ flag, int64_t count, int32_t* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) out[j] = flag[j];
+}
+
+// Sec. 8.9's x*: the first half of the support (index order) -hi, the rest +lo; g = sign(x*)
+__global__ void k_xstar_alt(int64_t n, int64_t nsup, const uint8_t* __restrict__ flag,
+                            const int32_t* __restrict__ rank, int64_t half, double lo, double hi, uint64_t seed,
+                            int goff_mode, double* __restrict__ xstar, double* __restrict__ g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool on = i < nsup && flag[i];
+    double x = 0.0, gi;
+    if (on) {
+        x = rank[i] < half ? -hi : lo;
+        gi = x < 0.0 ? -1.0 : 1.0;
+    } else {
+        gi = goff_mode == 0 ? __dadd_rn(2.0 * u01(sm_output(sm_stream(seed, kTagGOff), (uint64_t)i)), -1.0) : 0.0;
+    }
+    xstar[i] = x;
+    if (i < nsup) g[i] = gi;
+}
+
 // one stage on a vector, in place: transpose ? T^T v : T v
 __global__ void k_stage(double* __restrict__ v, int64_t n, int first, double c, double s, int transpose) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -786,6 +816,14 @@ l1ls_status reorder_pairs(Inst* I, cudaStream_t st) {
     return L1LS_OK;
 }
 
+// sigma_max^2 of the square factor: 1 for the log-spaced values (kappa^0), else the larger of
+// the two alternating values
+double sigma_max2(const l1ls_gen_params* p) {
+    if (p->sigma_mode != 1) return 1.0;
+    const double s = std::min(p->m, p->n) > 1 ? std::max(p->sigma_odd, p->sigma_even) : p->sigma_odd;
+    return s * s;
+}
+
 l1ls_status validate(const l1ls_gen_params* p) {
     if (!p) return set_error(L1LS_EINVAL, "params is NULL");
     if (p->m < 2 || p->n < 2) return set_error(L1LS_EINVAL, "m and n must be >= 2");
@@ -801,6 +839,10 @@ l1ls_status validate(const l1ls_gen_params* p) {
     if (p->left_stages == 1 && (p->m & 1)) return set_error(L1LS_EINVAL, "m must be even with a left stage");
     if (p->value_dtype < L1LS_F64 || p->value_dtype > L1LS_BF16) return set_error(L1LS_EINVAL, "bad value_dtype");
     if (p->matrix_free != 0 && p->matrix_free != 1) return set_error(L1LS_EINVAL, "matrix_free must be 0 or 1");
+    if ((p->sigma_mode != 0 && p->sigma_mode != 1) || (p->xstar_mode != 0 && p->xstar_mode != 1))
+        return set_error(L1LS_EINVAL, "sigma_mode and xstar_mode must be 0 or 1");
+    if (p->sigma_mode == 1 && !(p->sigma_odd > 0.0 && p->sigma_even > 0.0))
+        return set_error(L1LS_EINVAL, "sigma_odd and sigma_even must be > 0");
     if (p->matrix_free && (p->m < p->n || p->value_dtype != L1LS_F32))
         return set_error(L1LS_EINVAL, "matrix_free instances need m >= n and FP32 value_dtype");
     if (!(p->xstar_lo >= 0.0) || !(p->xstar_hi >= p->xstar_lo)) return set_error(L1LS_EINVAL, "bad x* magnitudes");
@@ -872,8 +914,12 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         // singular values: sigma_i = kappa^(-rank_i/(n-1))
         uint32_t* order_n = nullptr;
         GEN_TRY(tmp.get(&order_n, n));
-        GEN_TRY(argsort_stream(p->seed, kTagSigma, nsq, order_n, tmp, st));
-        k_sigma<<<nblk(nsq), 256, 0, st>>>(order_n, nsq, std::log(p->kappa), I->sigma);
+        if (p->sigma_mode == 1) {
+            k_sigma_alt<<<nblk(nsq), 256, 0, st>>>(nsq, p->sigma_odd, p->sigma_even, I->sigma);
+        } else {
+            GEN_TRY(argsort_stream(p->seed, kTagSigma, nsq, order_n, tmp, st));
+            k_sigma<<<nblk(nsq), 256, 0, st>>>(order_n, nsq, std::log(p->kappa), I->sigma);
+        }
         GEN_CUDA(cudaGetLastError());
         // row permutation P (P1 = P2 = P)
         if (p->left_stages == 1) {
@@ -900,8 +946,20 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_TRY(tmp.get(&zb, n));
         GEN_TRY(tmp.get(&ul, n));
         GEN_TRY(tmp.get(&ehat, m));
-        k_xstar_g<<<nblk(n), 256, 0, st>>>(p->seed, n, nsq, flag, p->xstar_lo, p->xstar_hi, p->g_offsupport, I->xstar,
+        if (p->xstar_mode == 1) {
+            int32_t *fi = nullptr, *rank = nullptr;
+            GEN_TRY(tmp.get(&fi, nsq));
+            GEN_TRY(tmp.get(&rank, nsq + 1));
+            k_flag_i32<<<nblk(nsq), 256, 0, st>>>(flag, nsq, fi);
+            GEN_CUDA(cudaGetLastError());
+            int64_t scount = 0;
+            GEN_TRY(exclusive_scan_i32(fi, nsq, rank, &scount, st));
+            k_xstar_alt<<<nblk(n), 256, 0, st>>>(n, nsq, flag, rank, scount / 2, p->xstar_lo, p->xstar_hi, p->seed,
+                                                 p->g_offsupport, I->xstar, gvec);
+        } else {
+            k_xstar_g<<<nblk(n), 256, 0, st>>>(p->seed, n, nsq, flag, p->xstar_lo, p->xstar_hi, p->g_offsupport, I->xstar,
                                             gvec);
+        }
         GEN_CUDA(cudaGetLastError());
         // IGen step 3 by the route of Sec. 4: R^T g and R^T x* (T_w^T first).  IGen2 step 3,
         // e = tau B^{-T} g = tau L Sigma^{-1} R^T g, and b = B x* + e are the same expressions
@@ -977,7 +1035,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
             I->mf_st = (float)g.st;
             I->f_star = p->tau * hred[0] + 0.5 * hred[1];
             I->lam_max = hred[2];
-            I->lipschitz = 1.0;
+            I->lipschitz = sigma_max2(p);
             *out = I;
             return L1LS_OK;
         }
@@ -1099,10 +1157,10 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         I->csc_tile_max = htmax[1];
         I->f_star = p->tau * hred[0] + 0.5 * hred[1];
         I->lam_max = hred[2];
-        I->lipschitz = 1.0;   // sigma_max = kappa^0 = 1
+        I->lipschitz = sigma_max2(p);   // lambda_max(A^T A) = sigma_max^2
         if (igen2) {
             // hred2: [2] max column sum |N~|, [5] max row sum |N~|, [8] max |N~^T b|
-            I->lipschitz = 1.0 + hred2[2] * hred2[5];
+            I->lipschitz = sigma_max2(p) + hred2[2] * hred2[5];
             I->lam_max = std::max(I->lam_max, hred2[8]);
         }
     }

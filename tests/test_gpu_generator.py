@@ -161,3 +161,23 @@ def test_igen2_rejects_bad_column_counts(ctx):
         with pytest.raises(l1.L1LSError) as e:
             ctx.generate(W.params(m=256, n=512, n_nnz_per_col=d))
         assert e.value.status == 1
+
+
+def test_sec89_generator_matches_oracle(ctx):
+    """Sec. 8.9's instance shape (alternating singular values, x* of -1e4 and 0.1) on the device."""
+    params = dict(W.sec89(13, value_dtype="f64"), xstar_frac=2.0 ** -6)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        ex = inst.export()
+        assert np.array_equal(ex["indptr"], ref.A.indptr.astype(np.int64))
+        assert np.array_equal(ex["indices"], ref.A.indices.astype(np.int32))
+        assert np.array_equal(ex["sigma"], ref.sigma)
+        assert np.array_equal(ex["xstar"], ref.xstar)
+        A = csr_from_export(ex, params["m"], params["n"])
+        assert np.abs(A.data - ref.A.data).max() <= 1e-14 * np.abs(ref.A.data).max()
+        assert inst.info["lipschitz"] == ref.lipschitz == 1e4
+        assert inst.info["f_star"] == pytest.approx(ref.f_star, rel=1e-12)
+        assert np.abs(ex["b"] - ref.b).max() <= 1e-12 * np.abs(ref.b).max()
+    finally:
+        inst.free()
