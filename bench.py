@@ -365,6 +365,29 @@ def mf_form(l1, W, log2n, steps, warmup, solve_limit):
     return out
 
 
+def sec89_form(l1, W, log2n, newton_steps):
+    """Sec. 8.9's huge-scale instance shape at n = 2^log2n on one GPU: pdNCG with the paper's
+    mu = 1e-5 (no continuation below it) for a fixed number of Newton steps, reported as the
+    relative error of x and f against the generator's x*, f* (the paper's measure there)."""
+    import numpy as np
+    ctx = l1.Context(0)
+    rows = []
+    for dt in ("f64", "f32"):
+        inst = ctx.generate(W.sec89(log2n, dt))
+        xs = inst.xstar()
+        for k in newton_steps:
+            t = time.perf_counter()
+            x, r = inst.solve_pdncg(tau=1.0, tol=0.0, max_iter=k, mu_min=1e-5, allow=(4, 5))
+            rows.append({"values": dt, "newton": r["iters"], "pcg": r["cg_iters"], "seconds": time.perf_counter() - t,
+                         "rel_err_x": float(np.linalg.norm(x - xs) / np.linalg.norm(xs)),
+                         "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"],
+                         "rel_gap": r["rel_gap"]})
+        inst.free()
+    ctx.close()
+    return {"workload": "sec. 8.9 shape at n=2^%d (m=2n, sigma 0.1/100, theta 2pi/3, x* n/2^10 nonzeros -1e4/0.1), "
+                        "pdNCG with mu = 1e-5" % log2n, "runs": rows}
+
+
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
@@ -501,6 +524,9 @@ def run_ours(args):
         forms["matrix_free"] = mf_form(l1, W, args.log2n, args.steps, args.warmup, args.solve_limit)
     if rank == 0 and not args.no_forms:
         forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_slots)
+    if rank == 0 and args.sec89:
+        forms = forms or {}
+        forms["sec89"] = sec89_form(l1, W, args.sec89_log2n, (8, 16, 32))
     if rank == 0 and args.precision:
         forms = forms or {}
         forms["precision"] = precision_form(l1, W, args.precision_limit)
@@ -556,6 +582,8 @@ def main():
     ap.add_argument("--matrix-free", action="store_true",
                     help="time the iteration on the instance with A not assembled (Algorithms MvPA / MvPAt)")
     ap.add_argument("--precision-limit", type=float, default=8.0, help="c3: time limit per solve (s)")
+    ap.add_argument("--sec89", action="store_true", help="add the Sec. 8.9 pdNCG leg")
+    ap.add_argument("--sec89-log2n", type=int, default=22)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
