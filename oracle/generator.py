@@ -68,7 +68,9 @@ class GenParams:
     sigma_mode: int = 0              # 0: log-spaced by kappa; 1: alternating
     sigma_odd: float = 0.1
     sigma_even: float = 100.0
-    xstar_mode: int = 0              # 0: +-U[lo, hi]; 1: first half of the support -hi, rest +lo
+    xstar_mode: int = 0              # 0: +-U[lo, hi]; 1: first half of the support -hi, rest +lo;
+                                     # 2: Procedure OsGen3 (Sec. 6) with gamma, s1 = s // 2
+    gamma: float = 100.0             # OsGen3's gamma
 
     @classmethod
     def from_dict(cls, d):
@@ -246,6 +248,35 @@ def optimal_solution(p: GenParams, ncols_support):
     return xstar, S
 
 
+def osgen3(p: GenParams, sigma):
+    """Procedure OsGen3 (Sec. 6): x = argmin ||G^T x - gamma (Sigma^T Sigma)^{-1} 1||, which is
+    G (gamma / sigma^2) because G is orthonormal (G = R, the stages applied to the vector one by
+    one, T_1 first); keep the s1 = s // 2 smallest nonzero and the s2 = s - s1 largest |x_i| (ties
+    by index), zero the rest.  IGen only (m >= n).  Returns (x*, sorted support)."""
+    from .operators import rotate   # local import: operators imports this module
+    c, sn, _, _ = angles(p)
+    n = p.n
+    x = p.gamma / (sigma * sigma)
+    for k in range(1, p.right_stages + 1):
+        rotate(x, stage_first(k), c, sn)
+    s = min(support_size(p), n)
+    s1 = s // 2
+    s2 = s - s1
+    order = np.argsort(np.abs(x), kind="stable")
+    nz = order[np.abs(x[order]) > 0.0]
+    keep = np.union1d(nz[:s1], nz[len(nz) - s2:] if s2 > 0 else np.array([], dtype=np.int64))
+    xstar = np.zeros(n)
+    xstar[keep] = x[keep]
+    return xstar, np.sort(keep.astype(np.int64))
+
+
+def kappa_rho(sigma, R, xstar, rho):
+    """Eq. (bd12): ||x*|| / ||P_rho x*||, P_rho the projection on the eigenvectors of A^T A with
+    eigenvalue >= rho; with A^T A = R Sigma^2 R^T that is the mass of R^T x* on sigma_i^2 >= rho."""
+    proj = np.linalg.norm((R.T @ xstar)[sigma * sigma >= rho])
+    return math.inf if proj == 0.0 else float(np.linalg.norm(xstar) / proj)
+
+
 def subgradient(p: GenParams, xstar, count):
     """g in the subdifferential of ||x*||_1 on the first ``count`` coordinates (Eq. bd6)."""
     g = np.zeros(count)
@@ -280,7 +311,7 @@ def generate(p: GenParams) -> Instance:
 def _generate_igen(p: GenParams) -> Instance:
     m, n, tau = p.m, p.n, p.tau
     A, R, L, sigma, perm = _square_part(p, n, m)
-    xstar, S = optimal_solution(p, n)
+    xstar, S = osgen3(p, sigma) if p.xstar_mode == 2 else optimal_solution(p, n)
     g = subgradient(p, xstar, n)
     # IGen step 3 with (A^T A)^{-1} = G (Sigma^T Sigma)^{-1} G^T (end of Sec. 4).
     v = R.T @ g
@@ -340,6 +371,8 @@ def n_columns(p: GenParams, e):
 
 def _generate_igen2(p: GenParams) -> Instance:
     m, n, tau = p.m, p.n, p.tau
+    if p.xstar_mode == 2:
+        raise ValueError("OsGen3 (xstar_mode 2) is defined for m >= n")
     B, R, L, sigma, perm = _square_part(p, m, m)
     xstar, S = optimal_solution(p, m)
     gB = subgradient(p, xstar, m)
@@ -377,7 +410,7 @@ def make_factors(p: GenParams) -> Factors:
         raise ValueError("make_factors covers IGen (m >= n)")
     sigma = sigma_of(p, p.n)
     perm = row_permutation(p.seed, p.m) if p.left_stages > 0 else None
-    xstar, S = optimal_solution(p, p.n)
+    xstar, S = osgen3(p, sigma) if p.xstar_mode == 2 else optimal_solution(p, p.n)
     g = subgradient(p, xstar, p.n)
     return Factors(p, sigma, perm, xstar, S, g)
 

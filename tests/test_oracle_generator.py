@@ -244,3 +244,38 @@ def test_sec89_instance_shape():
     assert np.abs(inst.A.T @ inst.e - p.tau * inst.g).max() < 1e-7
     # b carries A x* with entries near 1e6, so the gap at x* is zero only to FP64 rounding
     assert abs(certificate(inst.A, inst.b, p.tau, inst.xstar)[3]) < 1e-7
+
+
+def test_osgen3_unconstrained_solution_and_selection():
+    """Procedure OsGen3 (Sec. 6): with every component kept, G^T x* = gamma (Sigma^T Sigma)^{-1} 1
+    (the exact least-squares solution, G orthonormal); with s < n the kept components are the
+    s1 smallest nonzero and s2 largest |x_i| of that solution."""
+    from oracle.generator import osgen3
+    full = GenParams(m=96, n=48, seed=5, kappa=30.0, right_stages=3, xstar_mode=2, gamma=100.0, xstar_frac=1.0)
+    inst = generate(full)
+    assert np.allclose(inst.R.T @ inst.xstar, 100.0 / inst.sigma ** 2, rtol=1e-12, atol=0)
+    sparse = GenParams(m=96, n=48, seed=5, kappa=30.0, right_stages=3, xstar_mode=2, gamma=100.0, xstar_frac=0.25)
+    xs, S = osgen3(sparse, inst.sigma)
+    x = inst.xstar                                     # the unconstrained solution of the same G, Sigma
+    order = np.argsort(np.abs(x), kind="stable")
+    assert len(S) == 12
+    assert set(S) == set(order[:6]) | set(order[-6:])
+    assert np.array_equal(xs[S], x[S]) and np.count_nonzero(xs) == 12
+
+
+def test_kappa_rho_against_an_eigendecomposition():
+    """Eq. (bd12) through R and Sigma against the eigenvectors of the assembled A^T A."""
+    from oracle.generator import kappa_rho
+    p = GenParams(m=80, n=40, seed=6, kappa=100.0, right_stages=2, xstar_mode=2, gamma=100.0, xstar_frac=0.2)
+    inst = generate(p)
+    lam, V = np.linalg.eigh((inst.A.T @ inst.A).toarray())
+    for rho in (1e-5, 1e-3, 0.01, 0.1, 0.5, 2.0):
+        Vr = V[:, lam >= rho * (1 - 1e-9)]
+        proj = np.linalg.norm(Vr @ (Vr.T @ inst.xstar))
+        want = math.inf if proj == 0 else np.linalg.norm(inst.xstar) / proj
+        got = kappa_rho(inst.sigma, inst.R, inst.xstar, rho)
+        assert (math.isinf(want) and math.isinf(got)) or math.isclose(got, want, rel_tol=1e-9)
+    assert kappa_rho(inst.sigma, inst.R, inst.xstar, inst.sigma.min() ** 2) == pytest.approx(1.0)
+    assert math.isinf(kappa_rho(inst.sigma, inst.R, inst.xstar, 2.0))
+    # the OsGen3 optimum is optimal at tau (Eq. bd7)
+    assert abs(certificate(inst.A, inst.b, p.tau, inst.xstar)[3]) < 1e-10
