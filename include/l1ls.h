@@ -77,7 +77,10 @@ typedef enum { L1LS_F64 = 0, L1LS_F32 = 1, L1LS_BF16 = 2 } l1ls_dtype;
  *                 1: sigma_i = sigma_odd for odd i and sigma_even for even i (1-based), the
  *                 singular values of the huge-scale instances of Sec. 8.9.
  *   xstar_mode    0: OsGen magnitudes U[xstar_lo, xstar_hi] with random signs; 1: the first
- *                 half of the support (index order) -xstar_hi, the rest +xstar_lo (Sec. 8.9).
+ *                 half of the support (index order) -xstar_hi, the rest +xstar_lo (Sec. 8.9);
+ *                 2: Procedure OsGen3 (Sec. 6): x = G gamma (Sigma^T Sigma)^{-1} 1 with its
+ *                 s1 = s/2 smallest nonzero and s - s1 largest |x_i| kept (m >= n only).
+ *   gamma         OsGen3's gamma (default 100).
  *   matrix_free   1: A is not assembled; products apply its factors (Algorithms MvPA /
  *                 MvPAt of Sec. 4: the stages of R, Sigma, the permutation and the left
  *                 rotations), so the instance holds O(m + n) memory.  IGen (m >= n) with
@@ -99,6 +102,7 @@ typedef struct {
     int32_t matrix_free;
     int32_t sigma_mode, xstar_mode;
     double sigma_odd, sigma_even;
+    double gamma;
 } l1ls_gen_params;
 
 /* Fill p with the defaults: m = 2048, n = 1024, seed 0, kappa 100, tau 1, frac 0.05,
@@ -134,6 +138,12 @@ l1ls_status l1ls_destroy(l1ls_ctx* ctx);
 l1ls_status l1ls_generate(l1ls_ctx* ctx, const l1ls_gen_params* p, void* stream, l1ls_inst** out);
 
 l1ls_status l1ls_inst_free(l1ls_inst* inst);
+/* The conditioning of x* of Eq. (bd12): kappa_rho(x*) = ||x*|| / ||P_rho x*||, P_rho the
+ * projection on the eigenvectors of A^T A with eigenvalue >= rho (with A^T A = R Sigma^2 R^T:
+ * the entries of R^T x* with sigma_i^2 >= rho); +inf when that projection is 0.  IGen (m >= n)
+ * instances.  Synchronous (a stream of its own).  Errors: EINVAL (NULL, an IGen2 instance, rho
+ * NaN), ENOMEM, ECUDA. */
+l1ls_status l1ls_inst_kappa_rho(const l1ls_inst* inst, double rho, double* out);
 l1ls_status l1ls_inst_get_info(const l1ls_inst* inst, l1ls_inst_info* info);
 
 /* Copy an instance to host buffers (any may be NULL).  A is returned in CSR with the

@@ -264,7 +264,7 @@ def osgen3(p: GenParams, sigma):
     s2 = s - s1
     order = np.argsort(np.abs(x), kind="stable")
     nz = order[np.abs(x[order]) > 0.0]
-    keep = np.union1d(nz[:s1], nz[len(nz) - s2:] if s2 > 0 else np.array([], dtype=np.int64))
+    keep = np.union1d(nz[:s1], nz[max(0, len(nz) - s2):] if s2 > 0 else np.array([], dtype=np.int64))
     xstar = np.zeros(n)
     xstar[keep] = x[keep]
     return xstar, np.sort(keep.astype(np.int64))

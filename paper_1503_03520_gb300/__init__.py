@@ -29,7 +29,7 @@ class GenParams(ctypes.Structure):
                 ("value_dtype", ctypes.c_int32), ("g_offsupport", ctypes.c_int32),
                 ("n_nnz_per_col", ctypes.c_int32), ("matrix_free", ctypes.c_int32),
                 ("sigma_mode", ctypes.c_int32), ("xstar_mode", ctypes.c_int32), ("sigma_odd", ctypes.c_double),
-                ("sigma_even", ctypes.c_double)]
+                ("sigma_even", ctypes.c_double), ("gamma", ctypes.c_double)]
 
 
 class InstInfo(ctypes.Structure):
@@ -93,6 +93,7 @@ _sig = {
     "l1ls_generate": (ctypes.c_int, [_P, ctypes.POINTER(GenParams), _P, ctypes.POINTER(_P)]),
     "l1ls_inst_free": (ctypes.c_int, [_P]),
     "l1ls_inst_get_info": (ctypes.c_int, [_P, ctypes.POINTER(InstInfo)]),
+    "l1ls_inst_kappa_rho": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "l1ls_inst_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "l1ls_inst_export_t": (ctypes.c_int, [_P, _P, _P, _P]),
     "l1ls_matvec": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
@@ -304,6 +305,12 @@ class Instance:
         xs = np.zeros(self.n, np.float64)
         _check(lib.l1ls_inst_export(self._h, None, None, None, None, xs.ctypes.data, None, None))
         return xs
+
+    def kappa_rho(self, rho):
+        """kappa_rho(x*) of Eq. (bd12), computed on the device (IGen instances)."""
+        out = ctypes.c_double(0.0)
+        _check(lib.l1ls_inst_kappa_rho(self._h, float(rho), ctypes.byref(out)))
+        return out.value
 
     def export_t(self):
         cp = np.zeros(self.n + 1, np.int64)

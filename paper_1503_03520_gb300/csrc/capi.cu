@@ -124,6 +124,7 @@ void l1ls_gen_params_default(l1ls_gen_params* p) {
     p->n_nnz_per_col = 8;
     p->sigma_odd = 0.1;
     p->sigma_even = 100.0;
+    p->gamma = 100.0;
 }
 
 void l1ls_solve_opts_default(l1ls_solve_opts* o) {
@@ -262,6 +263,13 @@ static l1ls_status values_to_host(const Inst* I, const void* dev, int64_t count,
         }
     }
     return L1LS_OK;
+}
+
+l1ls_status l1ls_inst_kappa_rho(const l1ls_inst* h, double rho, double* out) {
+    if (!h || !out) return set_error(L1LS_EINVAL, "NULL argument");
+    const Inst* I = reinterpret_cast<const Inst*>(h);
+    L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    return kappa_rho(I, rho, out);
 }
 
 l1ls_status l1ls_inst_export(const l1ls_inst* h, int64_t* row_ptr, int32_t* col_idx, double* vals, double* b,

@@ -152,6 +152,43 @@ __global__ void k_xstar_alt(int64_t n, int64_t nsup, const uint8_t* __restrict__
     if (i < nsup) g[i] = gi;
 }
 
+// Procedure OsGen3 (Sec. 6), step 2: x = gamma / sigma^2 (the stages of G follow)
+__global__ void k_gamma_over_sigma2(const double* __restrict__ sigma, int64_t n, double gamma, double* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = __ddiv_rn(gamma, __dmul_rn(sigma[i], sigma[i]));
+}
+// sort keys: the bit pattern of |x| orders non-negative doubles; zeros counted
+__global__ void k_abs_keys(const double* __restrict__ x, int64_t n, uint64_t* __restrict__ keys, int* __restrict__ zeros) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = fabs(x[i]);
+    keys[i] = (uint64_t)__double_as_longlong(a);
+    if (a == 0.0) atomicAdd(zeros, 1);
+}
+// OsGen3, step 3: keep ranks z .. z+s1-1 (the s1 smallest nonzero) and n-s2 .. n-1 (largest)
+__global__ void k_osgen3_flags(const uint32_t* __restrict__ order, int64_t n, const int* __restrict__ zeros, int64_t s1,
+                               int64_t s2, uint8_t* __restrict__ flag) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t z = *zeros;
+    if (r >= z && (r < z + s1 || r >= n - s2)) flag[order[r]] = 1;
+}
+// x* = x on the kept entries (step 4 zeroes the rest); g = sign(x*) there, U(-1,1) elsewhere
+__global__ void k_osgen3_xstar(const double* __restrict__ x, const uint8_t* __restrict__ flag, int64_t n, uint64_t seed,
+                               int goff_mode, double* __restrict__ xstar, double* __restrict__ g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double xi = 0.0, gi;
+    if (flag[i]) {
+        xi = x[i];
+        gi = xi < 0.0 ? -1.0 : 1.0;
+    } else {
+        gi = goff_mode == 0 ? __dadd_rn(2.0 * u01(sm_output(sm_stream(seed, kTagGOff), (uint64_t)i)), -1.0) : 0.0;
+    }
+    xstar[i] = xi;
+    g[i] = gi;
+}
+
 // one stage on a vector, in place: transpose ? T^T v : T v
 __global__ void k_stage(double* __restrict__ v, int64_t n, int first, double c, double s, int transpose) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,6 +254,25 @@ __global__ void k_reduce3(const double* __restrict__ a, int64_t na, const double
         out[0] = tot[0];
         out[1] = tot[1];
         out[2] = tot[2];
+    }
+}
+
+// Eq. (bd12) sums: out[0] = sum x*_i^2, out[1] = sum over sigma_i^2 >= rho of (R^T x*)_i^2
+__global__ void k_kappa_sums(const double* __restrict__ x, const double* __restrict__ z, const double* __restrict__ sigma,
+                             int64_t n, double rho, double* __restrict__ partials, unsigned* __restrict__ counter,
+                             double* __restrict__ out) {
+    __shared__ double smem[2 * 32];
+    double v[2] = {0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        v[0] += x[i] * x[i];
+        if (sigma[i] * sigma[i] >= rho) v[1] += z[i] * z[i];
+    }
+    block_reduce<256, 2>(v, 4u, smem);
+    double tot[2];
+    if (grid_reduce_last<256, 2>(v, 4u, partials, counter, tot, smem) && threadIdx.x == 0) {
+        out[0] = tot[0];
+        out[1] = tot[1];
     }
 }
 
@@ -839,8 +895,10 @@ l1ls_status validate(const l1ls_gen_params* p) {
     if (p->left_stages == 1 && (p->m & 1)) return set_error(L1LS_EINVAL, "m must be even with a left stage");
     if (p->value_dtype < L1LS_F64 || p->value_dtype > L1LS_BF16) return set_error(L1LS_EINVAL, "bad value_dtype");
     if (p->matrix_free != 0 && p->matrix_free != 1) return set_error(L1LS_EINVAL, "matrix_free must be 0 or 1");
-    if ((p->sigma_mode != 0 && p->sigma_mode != 1) || (p->xstar_mode != 0 && p->xstar_mode != 1))
-        return set_error(L1LS_EINVAL, "sigma_mode and xstar_mode must be 0 or 1");
+    if ((p->sigma_mode != 0 && p->sigma_mode != 1) || p->xstar_mode < 0 || p->xstar_mode > 2)
+        return set_error(L1LS_EINVAL, "sigma_mode must be 0 or 1, xstar_mode 0, 1 or 2");
+    if (p->xstar_mode == 2 && (p->m < p->n || !(p->gamma > 0.0)))
+        return set_error(L1LS_EINVAL, "OsGen3 (xstar_mode 2) needs m >= n and gamma > 0");
     if (p->sigma_mode == 1 && !(p->sigma_odd > 0.0 && p->sigma_even > 0.0))
         return set_error(L1LS_EINVAL, "sigma_odd and sigma_even must be > 0");
     if (p->matrix_free && (p->m < p->n || p->value_dtype != L1LS_F32))
@@ -931,12 +989,6 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
             k_identity_perm<<<nblk(m), 256, 0, st>>>(m, I->perm, I->perm_inv);
         }
         GEN_CUDA(cudaGetLastError());
-        // support of x*: the s smallest keys (among the first m columns for IGen2)
-        GEN_TRY(argsort_stream(p->seed, kTagSupport, nsq, order_n, tmp, st));
-        uint8_t* flag = nullptr;
-        GEN_TRY(tmp.get(&flag, n));
-        GEN_CUDA(cudaMemsetAsync(flag, 0, n, st));
-        k_support<<<nblk(s), 256, 0, st>>>(order_n, s, flag);
         double *gvec = nullptr, *vg = nullptr, *vx = nullptr, *ze = nullptr, *zb = nullptr, *ul = nullptr,
                *ehat = nullptr;
         GEN_TRY(tmp.get(&gvec, n));
@@ -946,6 +998,37 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         GEN_TRY(tmp.get(&zb, n));
         GEN_TRY(tmp.get(&ul, n));
         GEN_TRY(tmp.get(&ehat, m));
+        uint8_t* flag = nullptr;
+        GEN_TRY(tmp.get(&flag, n));
+        GEN_CUDA(cudaMemsetAsync(flag, 0, n, st));
+        if (p->xstar_mode == 2) {
+            // Procedure OsGen3 (Sec. 6): x = G gamma (Sigma^T Sigma)^{-1} 1 (G orthonormal), then
+            // the s1 = s/2 smallest nonzero and s - s1 largest |x_i| kept (ties by index)
+            double* xo = vg;   // free until step 3 of IGen
+            uint64_t* keys = nullptr;
+            int* zeros = nullptr;
+            GEN_TRY(tmp.get(&keys, n));
+            GEN_TRY(tmp.get(&zeros, 1));
+            GEN_CUDA(cudaMemsetAsync(zeros, 0, sizeof(int), st));
+            k_gamma_over_sigma2<<<nblk(n), 256, 0, st>>>(I->sigma, n, p->gamma, xo);
+            for (int k = 1; k <= p->right_stages; ++k)
+                k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(xo, n, (k - 1) & 1, g.c, g.s, 0);
+            k_abs_keys<<<nblk(n), 256, 0, st>>>(xo, n, keys, zeros);
+            GEN_CUDA(cudaGetLastError());
+            GEN_TRY(radix_argsort_u64(keys, n, order_n, st));
+            const int64_t s1 = s / 2, s2 = s - s1;
+            k_osgen3_flags<<<nblk(n), 256, 0, st>>>(order_n, n, zeros, s1, s2, flag);
+            k_osgen3_xstar<<<nblk(n), 256, 0, st>>>(xo, flag, n, p->seed, p->g_offsupport, I->xstar, gvec);
+            GEN_CUDA(cudaGetLastError());
+            // kept: ranks [z, z + s1) and [max(z, n - s2), n), i.e. min(s, n - z) entries
+            int hz = 0;
+            GEN_CUDA(cudaMemcpyAsync(&hz, zeros, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GEN_CUDA(cudaStreamSynchronize(st));
+            I->s = std::min<int64_t>(s, n - (int64_t)hz);
+        } else {
+        // support of x*: the s smallest keys (among the first m columns for IGen2)
+        GEN_TRY(argsort_stream(p->seed, kTagSupport, nsq, order_n, tmp, st));
+        k_support<<<nblk(s), 256, 0, st>>>(order_n, s, flag);
         if (p->xstar_mode == 1) {
             int32_t *fi = nullptr, *rank = nullptr;
             GEN_TRY(tmp.get(&fi, nsq));
@@ -961,6 +1044,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
                                             gvec);
         }
         GEN_CUDA(cudaGetLastError());
+        }
         // IGen step 3 by the route of Sec. 4: R^T g and R^T x* (T_w^T first).  IGen2 step 3,
         // e = tau B^{-T} g = tau L Sigma^{-1} R^T g, and b = B x* + e are the same expressions
         // on the square part (x* is zero on the columns of N).
@@ -1168,6 +1252,50 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
 #undef GEN_TRY
 #undef GEN_CUDA
     *out = I;
+    return L1LS_OK;
+}
+
+// kappa_rho(x*) of Eq. (bd12): R^T x* by the stages (T_w^T first), then the two sums
+l1ls_status kappa_rho(const Inst* I, double rho, double* out) {
+    if (I->igen2) return set_error(L1LS_EINVAL, "kappa_rho is defined for IGen instances (m >= n)");
+    if (std::isnan(rho)) return set_error(L1LS_EINVAL, "rho is NaN");
+    const int64_t n = I->n;
+    const l1ls_gen_params& p = I->p;
+    cudaStream_t st = nullptr;
+    L1LS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    double hsum[2] = {0.0, 0.0};
+    l1ls_status rc = L1LS_OK;
+    {
+        TempList tmp(st);
+        double *z = nullptr, *partials = nullptr, *sums = nullptr;
+        unsigned* counter = nullptr;
+        rc = tmp.get(&z, n);
+        if (rc == L1LS_OK) rc = tmp.get(&partials, 2 * 512);
+        if (rc == L1LS_OK) rc = tmp.get(&sums, 2);
+        if (rc == L1LS_OK) rc = tmp.get(&counter, 1);
+        cudaError_t e = cudaSuccess;
+        if (rc == L1LS_OK) {
+            e = cudaMemcpyAsync(z, I->xstar, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+            const double c = std::cos(p.theta), s = std::sin(p.theta);
+            for (int k = p.right_stages; k >= 1 && e == cudaSuccess; --k) {
+                k_stage<<<nblk(n / 2 + 1), 256, 0, st>>>(z, n, (k - 1) & 1, c, s, 1);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                k_kappa_sums<<<512, 256, 0, st>>>(I->xstar, z, I->sigma, n, rho, partials, counter, sums);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hsum, sums, sizeof(hsum), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_error(e, "kappa_rho", __FILE__, __LINE__);
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc != L1LS_OK) return rc;
+    if (e2 != cudaSuccess) return cuda_error(e2, "kappa_rho", __FILE__, __LINE__);
+    *out = hsum[1] == 0.0 ? INFINITY : std::sqrt(hsum[0]) / std::sqrt(hsum[1]);
     return L1LS_OK;
 }
 

@@ -130,6 +130,7 @@ bool is_device_pointer(const void* p);
 // ---- entry points implemented per file ------------------------------------------------
 l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t st, Inst** out,
                               bool stream_ordered = false);
+l1ls_status kappa_rho(const Inst* I, double rho, double* out);
 
 // the serving worker's cancel flag (null elsewhere); solver loops poll it between launches
 extern thread_local const std::atomic<int>* tl_cancel;

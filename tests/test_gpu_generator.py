@@ -181,3 +181,53 @@ def test_sec89_generator_matches_oracle(ctx):
         assert np.abs(ex["b"] - ref.b).max() <= 1e-12 * np.abs(ref.b).max()
     finally:
         inst.free()
+
+
+@pytest.mark.parametrize("m,n,w,frac,kappa", [(8198, 4099, 2, 0.1, 1e3), (2000, 1000, 3, 1.0, 30.0),
+                                             (6002, 3001, 8, 0.37, 1e4), (64, 33, 1, 0.01, 10.0)])
+def test_osgen3_generator_matches_oracle(ctx, m, n, w, frac, kappa):
+    """Procedure OsGen3 (Sec. 6) on the device: the same support as the oracle (both sides sort
+    FP64 |x| values that differ at most by the ulp of exp in sigma, far below the gaps between
+    neighbouring |x_i|), x* and b to 1e-13, f*; kappa_rho of Eq. (bd12) on the device against
+    the oracle's at thresholds between distinct sigma_i^2 and outside the spectrum, to the
+    rounding of R^T x* amplified by kappa_rho itself."""
+    from oracle.generator import kappa_rho
+    params = W.params(m=m, n=n, right_stages=w, left_stages=1, kappa=kappa, value_dtype="f64", seed=11,
+                      xstar_mode=2, gamma=100.0, xstar_frac=frac)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        ex = inst.export()
+        assert np.allclose(ex["sigma"], ref.sigma, rtol=4e-16, atol=0)
+        assert np.array_equal(np.flatnonzero(ex["xstar"]), np.flatnonzero(ref.xstar))
+        assert np.allclose(ex["xstar"], ref.xstar, rtol=1e-13, atol=0)
+        assert inst.info["s"] == np.count_nonzero(ref.xstar)
+        assert np.abs(ex["b"] - ref.b).max() <= 1e-12 * np.abs(ref.b).max()
+        assert inst.info["f_star"] == pytest.approx(ref.f_star, rel=1e-12)
+        s2 = np.unique(ref.sigma ** 2)
+        k = len(s2) // 3
+        for rho in (0.0, 0.5 * s2[0], 0.5 * (s2[k] + s2[k + 1]), 0.5 * (s2[-2] + s2[-1]), 2.0 * s2[-1]):
+            want = kappa_rho(ref.sigma, ref.R, ref.xstar, rho)
+            got = inst.kappa_rho(rho)
+            if np.isinf(want):
+                assert np.isinf(got)
+            else:
+                # ||P_rho x*|| = ||x*|| / kappa_rho: the rounding of R^T x* (about (w + 1) eps ||x*||
+                # per entry, different orders of operations on the two sides) relative to it
+                assert got == pytest.approx(want, rel=1e-12 + 8 * (w + 1) * 2.2e-16 * want)
+    finally:
+        inst.free()
+
+
+def test_kappa_rho_rejections(ctx):
+    import paper_1503_03520_gb300 as l1
+    inst = ctx.generate(W.params(m=300, n=600, value_dtype="f64"))   # IGen2
+    try:
+        with pytest.raises(l1.L1LSError) as e:
+            inst.kappa_rho(1.0)
+        assert e.value.status == 1
+    finally:
+        inst.free()
+    with pytest.raises(l1.L1LSError) as e:
+        ctx.generate(W.params(m=300, n=600, xstar_mode=2))
+    assert e.value.status == 1
