@@ -47,7 +47,7 @@ struct FistaState {
     double P, D, gap, rel;
     int32_t stop, status;
     unsigned cnt1, cnt2;
-    int32_t restart, pad;
+    int32_t restart, stage_err;   // stage_err: kStageTimeout if a stage wait ran out
     int64_t restarts;
     // beta, 1/L and tau/L as float-float, refreshed with beta by the scalar step: the FP32
     // kernels read them instead of every thread converting (two FP64 divisions each)
@@ -94,7 +94,7 @@ struct K2Args {
 template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock, L1LS_K1_MIN_BLOCKS) k_fista_k1(K1Args<V, Vec> a) {
     using Acc = Vec;
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const Vec beta = (Vec)a.st->beta;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kBlock, L1LS_K1_MIN_BLOCKS) k_fista_k1(K1Args<
         Vec axo, bb;
     };
     rows_of<PAIRED, V, Vec, Acc>(
-        a.ptr, a.col, a.val, a.x, a.m, sm.warp_buf(),
+        a.ptr, a.col, a.val, a.x, a.m, sm, &a.st->stage_err,
         [&](int64_t r, bool has) {
             Ops o{Vec(0), Vec(0)};
             if (has) {
@@ -189,7 +189,7 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new, doubl
 template <class V, class Vec, bool PAIRED, bool RESTART>
 __global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const double beta = a.st->beta, L = a.st->L, tau = a.st->tau;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<
             ff x1, x0;
         };
         cols_of<PAIRED, V, Vec, Acc>(
-            a.ptr, a.col, a.val, a.res, a.n, sm.warp_buf(),
+            a.ptr, a.col, a.val, a.res, a.n, sm, &a.st->stage_err,
             [&](int64_t j, bool has) {
                 Ops o{{0.f, 0.f}, {0.f, 0.f}};
                 if (has) {
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<
             double x1, x0;
         };
         cols_of<PAIRED, V, Vec, Acc>(
-            a.ptr, a.col, a.val, a.res, a.n, sm.warp_buf(),
+            a.ptr, a.col, a.val, a.res, a.n, sm, &a.st->stage_err,
             [&](int64_t j, bool has) {
                 Ops o{0.0, 0.0};
                 if (has) {
@@ -937,6 +937,8 @@ l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_stat
     L1LS_CUDA(cudaStreamSynchronize(st));
     const FistaState& f = *w->host_st;
     if (final_status == L1LS_OK) final_status = f.stop ? (l1ls_status)f.status : L1LS_ENOCONV;
+    if (f.stage_err && final_status == L1LS_OK)
+        final_status = set_error(L1LS_ECUDA, "a bulk-copy stage wait ran out of polls (sums read directly)");
     if (x_out) {
         const int c = (int)(f.cert_iter & 1);
         if (w->X[c]) {

@@ -34,7 +34,7 @@ struct PdState {
     double tau, tol, mu, mu_target, mu_min, pcg_rtol, armijo, stall;
     int64_t max_newton, pcg_max, ls_max;
     double P, D, gap, rel, prev_gap;
-    int32_t prev_full, pad0;
+    int32_t prev_full, stage_err;   // stage_err: kStageTimeout if a stage wait ran out
     double k1[2];
     double gnorm2, rz, rz0, alpha, beta;
     int32_t cg_done, pad1;
@@ -57,12 +57,12 @@ __global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__
                                                      const Vec* __restrict__ b, Vec* __restrict__ r, int64_t m,
                                                      double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     double p[2] = {0.0, 0.0};
     rows_of<PAIRED, V, X, Acc>(
-        ptr, col, val, x, m, sm.warp_buf(), [&](int64_t i, bool has) { return has ? b[i] : Vec(0); },
+        ptr, col, val, x, m, sm, &st->stage_err, [&](int64_t i, bool has) { return has ? b[i] : Vec(0); },
         [&](int64_t i, Acc u, const Vec& bb) {
             const Vec rr = bb - u;
             r[i] = rr;
@@ -84,12 +84,12 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
                                                    const double* __restrict__ x, double* __restrict__ atr, int64_t n,
                                                    double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     double p[2] = {0.0, 0.0};
     cols_of<PAIRED, V, Vec, Acc>(
-        ptr, col, val, r, n, sm.warp_buf(), [&](int64_t j, bool has) { return has ? x[j] : 0.0; },
+        ptr, col, val, r, n, sm, &st->stage_err, [&](int64_t j, bool has) { return has ? x[j] : 0.0; },
         [&](int64_t j, Acc a, const double& xj) {
             atr[j] = (double)a;
             p[0] = fmax(p[0], fabs((double)a));
@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ pt
                                                   Vec* __restrict__ out, const Vec* __restrict__ r, int64_t m,
                                                   double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     if (!LS && *(volatile int32_t*)&st->cg_done) return;
     double p[2] = {0.0, 0.0};
     rows_of<PAIRED, V, X, Acc>(
-        ptr, col, val, x, m, sm.warp_buf(), [&](int64_t i, bool has) { return (LS && has) ? r[i] : Vec(0); },
+        ptr, col, val, x, m, sm, &st->stage_err, [&](int64_t i, bool has) { return (LS && has) ? r[i] : Vec(0); },
         [&](int64_t i, Acc u, const Vec& ri) {
             out[i] = u;
             if (LS) {
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ pt
                                                   const double* __restrict__ hd, const double* __restrict__ p,
                                                   double* __restrict__ hp, int64_t n, double* partials, PdState* st) {
     using Acc = Vec;
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[32];
     if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
     double q[1] = {0.0};
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ pt
         double pj, h;
     };
     cols_of<PAIRED, V, Vec, Acc>(
-        ptr, col, val, ap, n, sm.warp_buf(),
+        ptr, col, val, ap, n, sm, &st->stage_err,
         [&](int64_t j, bool has) {
             Ops o{0.0, 0.0};
             if (has) {
@@ -517,6 +517,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         L1LS_CUDA(cudaGetLastError());
     }
     const PdState& f = *w->host;
+    if (f.stage_err && final_status == L1LS_OK)
+        final_status = set_error(L1LS_ECUDA, "a bulk-copy stage wait ran out of polls (sums read directly)");
     if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X, sizeof(double) * n, cudaMemcpyDefault, s));
     L1LS_CUDA(cudaStreamSynchronize(s));
     if (res) {

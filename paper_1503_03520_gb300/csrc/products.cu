@@ -17,15 +17,15 @@ constexpr int kBlock = 256;
 template <class V, class X, class Acc, bool PAIRED, bool COLS>
 __global__ void __launch_bounds__(kBlock) k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                  const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
-                                                 const int32_t* __restrict__ out_perm, X* __restrict__ y) {
-    __shared__ TraversalSmem<Acc, kBlock> sm;
+                                                 const int32_t* __restrict__ out_perm, X* __restrict__ y, int* err) {
+    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     auto pre = [&](int64_t, bool) { return NoOps{}; };
     auto epi = [&](int64_t r, Acc acc, const NoOps&) {
         const int64_t dst = out_perm ? out_perm[r] : r;
         y[dst] = (X)acc;
     };
-    if constexpr (COLS) cols_of<PAIRED, V, X, Acc>(ptr, col, val, x, nrows, sm.warp_buf(), pre, epi);
-    else rows_of<PAIRED, V, X, Acc>(ptr, col, val, x, nrows, sm.warp_buf(), pre, epi);
+    if constexpr (COLS) cols_of<PAIRED, V, X, Acc>(ptr, col, val, x, nrows, sm, err, pre, epi);
+    else rows_of<PAIRED, V, X, Acc>(ptr, col, val, x, nrows, sm, err, pre, epi);
 }
 
 template <class X>
@@ -49,15 +49,15 @@ l1ls_status launch_spmv(const Inst* I, bool transpose, const X* x, X* y, const i
         const int32_t* col = transpose ? I->pcol_pair : I->prow_col;
         const V* val = static_cast<const V*>(transpose ? I->pcol_val : I->prow_val);
         if (transpose)
-            k_spmv<V, X, Acc, true, true><<<grid_for(I, nrows), kBlock, 0, st>>>(ptr, col, val, x, nrows, out_perm, y);
+            k_spmv<V, X, Acc, true, true><<<grid_for(I, nrows), kBlock, 0, st>>>(ptr, col, val, x, nrows, out_perm, y, I->dev_err);
         else
             k_spmv<V, X, Acc, true, false><<<grid_for(I, nrows / 2), kBlock, 0, st>>>(ptr, col, val, x, nrows,
-                                                                                      out_perm, y);
+                                                                                      out_perm, y, I->dev_err);
     } else {
         const int32_t* ptr = transpose ? I->csc_ptr : I->csr_ptr;
         const int32_t* col = transpose ? I->csc_row : I->csr_col;
         const V* val = static_cast<const V*>(transpose ? I->csc_val : I->csr_val);
-        k_spmv<V, X, Acc, false, false><<<grid_for(I, nrows), kBlock, 0, st>>>(ptr, col, val, x, nrows, out_perm, y);
+        k_spmv<V, X, Acc, false, false><<<grid_for(I, nrows), kBlock, 0, st>>>(ptr, col, val, x, nrows, out_perm, y, I->dev_err);
     }
     L1LS_CUDA(cudaGetLastError());
     return L1LS_OK;

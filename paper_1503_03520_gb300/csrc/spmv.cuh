@@ -13,6 +13,8 @@
 // Nonzero arrays must be allocated with kPad entries of slack after nnz (vector tails).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace l1ls {
@@ -124,6 +126,18 @@ template <class T> struct Two;
 template <> struct Two<float> { using type = float2; };
 template <> struct Two<double> { using type = double2; };
 
+// the two values of one paired entry as one load
+template <class V> struct ValPair;
+template <> struct ValPair<float> { using type = float2; };
+template <> struct ValPair<double> { using type = double2; };
+template <> struct ValPair<__nv_bfloat16> { using type = __nv_bfloat162; };
+template <class Acc> __device__ __forceinline__ void pair_to_acc(float2 v, Acc& a, Acc& b) { a = v.x; b = v.y; }
+template <class Acc> __device__ __forceinline__ void pair_to_acc(double2 v, Acc& a, Acc& b) { a = v.x; b = v.y; }
+template <class Acc> __device__ __forceinline__ void pair_to_acc(__nv_bfloat162 v, Acc& a, Acc& b) {
+    a = __bfloat162float(v.x);
+    b = __bfloat162float(v.y);
+}
+
 template <class T, int N>
 __device__ __forceinline__ void load_span(const T* __restrict__ p, T (&out)[N]) {
     constexpr int kVecs = (int)(N * sizeof(T) / 16);
@@ -135,151 +149,289 @@ __device__ __forceinline__ void load_span(const T* __restrict__ p, T (&out)[N]) 
     memcpy(out, w, sizeof(w));
 }
 
-// ROWS = true : npairs row pairs; x gathered at the column index; pre / epi are called per
-//               row (2p and 2p+1) exactly as for warp_csr.
-// ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
-// wbuf: this warp's 2 * kWarpChunk accumulators.
-// One tile t (32 row pairs, or 32 columns) of the paired traversal whose row extents rb, re
-// (this lane's row) are already loaded; see warp_pcsr.
-template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
-__device__ __forceinline__ void pcsr_tile_body(int64_t t, int32_t rb, int32_t re, const int32_t* __restrict__ idx,
-                                               const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
-                                               Acc* __restrict__ wbuf, Pre& pre, Epi& epi) {
-    const int lane = threadIdx.x & 31;
-    Acc* w0 = wbuf;
-    Acc* w1 = wbuf + kWarpChunk;
-    const int64_t r = (t << 5) + lane;
-    const bool has = r < nrows;
-    auto ops0 = pre(ROWS ? 2 * r : r, has);
-    auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
-    const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
-    const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
-    const int32_t e1 = __shfl_sync(0xffffffffu, re, last);
-    Acc a0 = Acc(0), a1 = Acc(0);
-    for (int32_t c = e0 & ~(kPEPL - 1); c < e1; c += 32 * kPEPL) {
-        const int32_t base = c + lane * kPEPL;
-        Acc p0[kPEPL], p1[kPEPL];
-        if (base < e1) {
-            int32_t ij[kPEPL];
-            V vv[2 * kPEPL];
-            load_span<int32_t, kPEPL>(idx + base, ij);
-            load_span<V, 2 * kPEPL>(val2 + 2 * (int64_t)base, vv);
+// ---- bulk-copy staging of the nonzero stream -----------------------------------------------
+// Each warp owns two stages in shared memory.  While it works on tile t, one lane has already
+// issued the bulk copies (cp.async.bulk, completion counted in bytes on the stage's mbarrier)
+// of the index and value spans of its next tile t + nwarps into the other stage, so the
+// stream of A arrives while the current tile's gathers are in flight: a tile costs one memory
+// round trip (the gathers) instead of two (stream, then gathers).  A span starts at the
+// 16-byte boundary at or below the tile's first entry and ends at the one at or above its
+// last; a tile longer than one stage is staged in consecutive pieces.  The copies carry an
+// L2 evict-first policy (A is read once per product).  Each wait polls at most kStagePolls
+// times; if one runs out the warp records kStageTimeout in *err and reads the rest of its
+// tiles directly from global memory (same sums, same order).
+
+constexpr uint32_t kStagePolls = 1u << 20;
+constexpr int kStageTimeout = 1 << 30;
+constexpr int kStageBytes = 2880;   // per stage and warp (two stages x 8 warps fit 48 KB)
+
+template <class V> struct StageGeom {
+    static constexpr int kCap = (kStageBytes / (4 + 2 * (int)sizeof(V))) & ~3;   // entries per stage
+};
+
+template <class V, int BLOCK> struct PairedSmem {
+    static constexpr int kWarps = BLOCK / 32;
+    static constexpr int kCap = StageGeom<V>::kCap;
+    alignas(16) int32_t idx[kWarps][2][kCap];
+    alignas(16) V val[kWarps][2][2 * kCap];
+    alignas(8) uint64_t bar[kWarps][2];
+};
+static_assert(StageGeom<float>::kCap % 4 == 0 && StageGeom<double>::kCap % 4 == 0, "stage spans of 16 bytes");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+// the stage of entries [lo, hi) (lo, hi multiples of 4): lane 0 arms the barrier and issues
+template <class V>
+__device__ __forceinline__ void stage_issue(int32_t* sidx, V* sval, uint64_t* bar, const int32_t* __restrict__ idx,
+                                            const V* __restrict__ val2, int32_t lo, int32_t hi, uint64_t policy) {
+    if ((threadIdx.x & 31) == 0) {
+        const uint32_t cnt = (uint32_t)(hi - lo);
+        const uint32_t bi = 4u * cnt, bv = 2u * (uint32_t)sizeof(V) * cnt;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of this stage
+        mbar_expect_tx(bar, bi + bv);
+        bulk_load(sidx, idx + lo, bi, bar, policy);
+        bulk_load(sval, val2 + 2 * (int64_t)lo, bv, bar, policy);
+    }
+}
+
+// bounded wait for a stage; false (warp-uniform) if some lane ran out of polls
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity) {
+    bool done = false;
+    for (uint32_t k = 0; k < kStagePolls && !done; ++k) done = mbar_try_wait(bar, parity);
+    return __all_sync(0xffffffffu, done);
+}
+
+// this lane's entries [eb, ee) of its row (ROWS: row pair, a0 / a1 for rows 2p / 2p+1) or
+// column (a0), read from ib[e - off], vb[e - off] (shared stage or global arrays), in entry
+// order, four entries' loads at a time
+template <bool ROWS, class V, class X, class Acc>
+__device__ __forceinline__ void lane_entries(const int32_t* ib, const typename ValPair<V>::type* vb, int32_t off,
+                                             int32_t eb, int32_t ee, const X* __restrict__ x, Acc& a0, Acc& a1) {
+    for (int32_t e = eb; e < ee; e += 4) {
+        Acc v0[4], v1[4], g0[4], g1[4];
 #pragma unroll
-            for (int k = 0; k < kPEPL; ++k) {
-                const int32_t e = base + k;
-                const bool in = e >= e0 && e < e1;
-                const Acc v0 = val_to_acc<Acc>(vv[2 * k]), v1 = val_to_acc<Acc>(vv[2 * k + 1]);
+        for (int k = 0; k < 4; ++k) {
+            v0[k] = v1[k] = g0[k] = g1[k] = Acc(0);
+            if (e + k < ee) {
+                const int32_t j = ib[e + k - off];
+                pair_to_acc<Acc>(vb[e + k - off], v0[k], v1[k]);
                 if (ROWS) {
-                    const Acc xv = in ? vec_to_acc<Acc>(__ldg(x + ij[k])) : Acc(0);
-                    p0[k] = v0 * xv;
-                    p1[k] = v1 * xv;
+                    g0[k] = vec_to_acc<Acc>(__ldg(x + j));
                 } else {
-                    Acc g0 = Acc(0), g1 = Acc(0);
-                    if (in) {
-                        const typename Two<X>::type g = __ldg(reinterpret_cast<const typename Two<X>::type*>(x) + ij[k]);
-                        g0 = vec_to_acc<Acc>(g.x);
-                        g1 = vec_to_acc<Acc>(g.y);
-                    }
-                    p0[k] = v0 * g0 + v1 * g1;
-                    p1[k] = Acc(0);
+                    const typename Two<X>::type g = __ldg(reinterpret_cast<const typename Two<X>::type*>(x) + j);
+                    g0[k] = vec_to_acc<Acc>(g.x);
+                    g1[k] = vec_to_acc<Acc>(g.y);
                 }
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < kPEPL; ++k) p0[k] = p1[k] = Acc(0);
         }
 #pragma unroll
-        for (int k = 0; k < kPEPL; ++k) {
-            w0[k * 32 + lane] = p0[k];
-            if (ROWS) w1[k * 32 + lane] = p1[k];
-        }
-        __syncwarp();
-        const int32_t lo = max(rb, c), hi = min(re, c + 32 * kPEPL);
-        for (int32_t e = lo; e < hi; ++e) {
-            const int32_t i = e - c;
-            const int32_t q = (i & (kPEPL - 1)) * 32 + (i / kPEPL);
-            a0 += w0[q];
-            if (ROWS) a1 += w1[q];
-        }
-        __syncwarp();
-    }
-    if (has) {
-        if (ROWS) {
-            epi(2 * r, a0, ops0);
-            epi(2 * r + 1, a1, ops1);
-        } else {
-            epi(r, a0, ops0);
+        for (int k = 0; k < 4; ++k) {
+            if (e + k < ee) {
+                if (ROWS) {
+                    a0 += v0[k] * g0[k];
+                    a1 += v1[k] * g0[k];
+                } else {
+                    a0 += v0[k] * g0[k] + v1[k] * g1[k];
+                }
+            }
         }
     }
 }
 
-template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
-__device__ __forceinline__ void pcsr_tile(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                          const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
-                                          Acc* __restrict__ wbuf, Pre& pre, Epi& epi) {
+// row extents of this lane's row of tile t (0, 0 past the end)
+__device__ __forceinline__ void tile_extents(const int32_t* __restrict__ ptr, int64_t t, int64_t nrows, int32_t& rb,
+                                             int32_t& re) {
     const int64_t r = (t << 5) + (threadIdx.x & 31);
-    int32_t rb = 0, re = 0;
+    rb = re = 0;
     if (r < nrows) {
         rb = __ldcs(ptr + r);
         re = __ldcs(ptr + r + 1);
     }
-    pcsr_tile_body<ROWS, V, X, Acc>(t, rb, re, idx, val2, x, nrows, wbuf, pre, epi);
 }
 
-// ROWS = true : npairs row pairs; x gathered at the column index; pre / epi are called per
-//               row (2p and 2p+1) exactly as for warp_csr.
-// ROWS = false: nrows columns; x gathered at (2p, 2p+1); pre / epi per column.
-// wbuf: this warp's 2 * kWarpChunk accumulators.
-template <bool ROWS, class V, class X, class Acc, class Pre, class Epi>
+// first entry, end and the first stage piece [lo, hi) of the tile whose lane extents are (rb, re)
+__device__ __forceinline__ void tile_span(int64_t t, int64_t nrows, int32_t rb, int32_t re, int cap, int32_t& e1,
+                                          int32_t& lo, int32_t& hi) {
+    const int last = (int)min((int64_t)31, nrows - 1 - (t << 5));
+    const int32_t e0 = __shfl_sync(0xffffffffu, rb, 0);
+    e1 = __shfl_sync(0xffffffffu, re, last);
+    if (e1 <= e0) {
+        lo = hi = e1;   // no entries
+        return;
+    }
+    lo = e0 & ~3;
+    hi = min(lo + cap, (e1 + 3) & ~3);
+}
+
+// Lane l owns row pair (ROWS) or column t*32 + l; it sums its own entries in nonzero order from
+// the staged stream, so every sum has a fixed order.  ROWS = true: npairs row pairs, x gathered
+// at the column index, pre / epi called per row (2p and 2p+1).  ROWS = false: nrows columns,
+// x gathered at (2p, 2p+1), pre / epi per column.  Warps walk tiles warp_id + k * total_warps.
+template <bool ROWS, class V, class X, class Acc, int BLOCK, class Pre, class Epi>
 __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                           const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
-                                          Acc* __restrict__ wbuf, Pre pre, Epi epi) {
-    // the row extents of the warp's next tile are loaded before the current tile is processed,
-    // so the pointer round trip overlaps the previous tile's work
+                                          PairedSmem<V, BLOCK>& sm, int* err, Pre pre, Epi epi) {
+    using VP = typename ValPair<V>::type;
+    constexpr int kCap = PairedSmem<V, BLOCK>::kCap;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ntiles = (nrows + 31) >> 5;
-    const int lane = threadIdx.x & 31;
-    int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int32_t nb = 0, ne = 0;
-    if (t < ntiles && (t << 5) + lane < nrows) {
-        nb = __ldcs(ptr + (t << 5) + lane);
-        ne = __ldcs(ptr + (t << 5) + lane + 1);
+    int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (t >= ntiles) return;
+    uint64_t* bar = sm.bar[wid];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
     }
+    __syncwarp();
+    const uint64_t policy = l2_evict_first_policy();
+    uint32_t parity = 0;    // bit s: parity of stage s's next phase
+    // false after a wait ran out (warp-uniform); never on for arrays off 16-byte boundaries
+    bool staging = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(val2)) & 15u) == 0;
+
+    int32_t rb, re, nb, ne;
+    tile_extents(ptr, t, nrows, rb, re);
+    tile_extents(ptr, t + nwarps, nrows, nb, ne);
+    int s = 0;
+    int32_t e1, lo, hi;
+    tile_span(t, nrows, rb, re, kCap, e1, lo, hi);
+    bool issued = staging && hi > lo;
+    if (issued) stage_issue<V>(sm.idx[wid][0], sm.val[wid][0], &bar[0], idx, val2, lo, hi, policy);
+
     for (; t < ntiles; t += nwarps) {
-        const int32_t rb = nb, re = ne;
+        // the next tile's first piece into the other stage, then the extents of the one after
         const int64_t tn = t + nwarps;
-        nb = ne = 0;
-        if (tn < ntiles && (tn << 5) + lane < nrows) {
-            nb = __ldcs(ptr + (tn << 5) + lane);
-            ne = __ldcs(ptr + (tn << 5) + lane + 1);
+        int32_t e1n = 0, lon = 0, hin = 0;
+        bool issued_n = false;
+        if (tn < ntiles) {
+            tile_span(tn, nrows, nb, ne, kCap, e1n, lon, hin);
+            issued_n = staging && hin > lon;
+            if (issued_n) stage_issue<V>(sm.idx[wid][s ^ 1], sm.val[wid][s ^ 1], &bar[s ^ 1], idx, val2, lon, hin, policy);
         }
-        pcsr_tile_body<ROWS, V, X, Acc>(t, rb, re, idx, val2, x, nrows, wbuf, pre, epi);
+        int32_t nb2, ne2;
+        tile_extents(ptr, tn + nwarps, nrows, nb2, ne2);
+
+        const int64_t r = (t << 5) + lane;
+        const bool has = r < nrows;
+        auto ops0 = pre(ROWS ? 2 * r : r, has);
+        auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
+        Acc a0 = Acc(0), a1 = Acc(0);
+        const int32_t end = (e1 + 3) & ~3;
+        bool staged = issued && staging;
+        for (;;) {
+            if (staged) {
+                const bool ok = stage_wait(&bar[s], (parity >> s) & 1u);
+                parity ^= 1u << s;
+                if (!ok) {   // record, wait once more (bounded) for the copies in flight, read directly
+                    staging = staged = false;
+                    if (lane == 0 && err) atomicOr(err, kStageTimeout);
+                    stage_wait(&bar[s], ((parity >> s) & 1u) ^ 1u);
+                    if (issued_n) stage_wait(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
+                }
+            }
+            const int32_t eb = max(rb, lo), ee = min(re, hi);
+            if (staged)
+                lane_entries<ROWS, V, X, Acc>(sm.idx[wid][s], reinterpret_cast<const VP*>(sm.val[wid][s]), lo, eb, ee, x,
+                                              a0, a1);
+            else
+                lane_entries<ROWS, V, X, Acc>(idx, reinterpret_cast<const VP*>(val2), 0, eb, ee, x, a0, a1);
+            if (hi >= e1) break;
+            // a tile longer than one stage: its next piece into the same stage
+            __syncwarp();
+            lo = hi;
+            hi = min(lo + kCap, end);
+            staged = staging;
+            if (staged) stage_issue<V>(sm.idx[wid][s], sm.val[wid][s], &bar[s], idx, val2, lo, hi, policy);
+        }
+        __syncwarp();   // every lane is done with stage s before it is refilled
+        if (has) {
+            if (ROWS) {
+                epi(2 * r, a0, ops0);
+                epi(2 * r + 1, a1, ops1);
+            } else {
+                epi(r, a0, ops0);
+            }
+        }
+        rb = nb;
+        re = ne;
+        nb = nb2;
+        ne = ne2;
+        e1 = e1n;
+        lo = lon;
+        hi = hin;
+        issued = issued_n;
+        s ^= 1;
     }
 }
 
-// Row traversal of A (nrows rows) in plain or paired storage.
-template <bool PAIRED, class V, class X, class Acc, class Pre, class Epi>
+// Row traversal of A (nrows rows) in plain or paired storage; `sm` is the kernel's
+// TraversalSmem, `err` receives kStageTimeout if a stage wait ran out (may be NULL).
+template <bool PAIRED, class V, class X, class Acc, class Smem, class Pre, class Epi>
 __device__ __forceinline__ void rows_of(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                        const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
-                                        Acc* __restrict__ wbuf, Pre pre, Epi epi) {
-    if constexpr (PAIRED) warp_pcsr<true, V, X, Acc>(ptr, idx, val, x, nrows / 2, wbuf, pre, epi);
-    else warp_csr<V, X, Acc>(ptr, idx, val, x, nrows, wbuf, pre, epi);
+                                        const V* __restrict__ val, const X* __restrict__ x, int64_t nrows, Smem& sm,
+                                        int* err, Pre pre, Epi epi) {
+    if constexpr (PAIRED) warp_pcsr<true, V, X, Acc>(ptr, idx, val, x, nrows / 2, sm, err, pre, epi);
+    else warp_csr<V, X, Acc>(ptr, idx, val, x, nrows, sm.warp_buf(), pre, epi);
 }
 
 // Column traversal of A (rows of A^T, ncols of them) in plain or paired storage.
-template <bool PAIRED, class V, class X, class Acc, class Pre, class Epi>
+template <bool PAIRED, class V, class X, class Acc, class Smem, class Pre, class Epi>
 __device__ __forceinline__ void cols_of(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                        const V* __restrict__ val, const X* __restrict__ x, int64_t ncols,
-                                        Acc* __restrict__ wbuf, Pre pre, Epi epi) {
-    if constexpr (PAIRED) warp_pcsr<false, V, X, Acc>(ptr, idx, val, x, ncols, wbuf, pre, epi);
-    else warp_csr<V, X, Acc>(ptr, idx, val, x, ncols, wbuf, pre, epi);
+                                        const V* __restrict__ val, const X* __restrict__ x, int64_t ncols, Smem& sm,
+                                        int* err, Pre pre, Epi epi) {
+    if constexpr (PAIRED) warp_pcsr<false, V, X, Acc>(ptr, idx, val, x, ncols, sm, err, pre, epi);
+    else warp_csr<V, X, Acc>(ptr, idx, val, x, ncols, sm.warp_buf(), pre, epi);
 }
 
-// shared accumulators per block for either storage
-template <class Acc, int BLOCK> struct TraversalSmem {
-    Acc buf[(BLOCK / 32) * 2 * kWarpChunk];
-    __device__ Acc* warp_buf() { return buf + (threadIdx.x >> 5) * 2 * kWarpChunk; }
+// shared memory of one traversal kernel: the two stages per warp (paired storage) or the
+// chunk accumulators per warp (plain CSR)
+template <class Acc, int BLOCK> struct CsrSmem {
+    Acc buf[(BLOCK / 32) * kWarpChunk];
+    __device__ Acc* warp_buf() { return buf + (threadIdx.x >> 5) * kWarpChunk; }
 };
+template <class V, class Acc, int BLOCK, bool PAIRED>
+using TraversalSmem = typename std::conditional<PAIRED, PairedSmem<V, BLOCK>, CsrSmem<Acc, BLOCK>>::type;
 
 // Matrix operands of one orientation
 template <class V> struct Csr {
@@ -299,7 +451,8 @@ namespace l1ls {
 // about 44 bits, enough for the residual b - A y of a nearly fitted row (a small difference of
 // large terms) and for A^T r at a small tau, where plain FP32 holds the duality-gap
 // certificate above 1e-6 (the floor grows as tau, and with it the objective, shrinks along a
-// path).  The tile structure is that of pcsr_tile; the warp buffer holds high and low words.
+// path).  The tile structure is that of warp_csr (lane runs of EPL entries, sums through a
+// warp buffer), which holds high and low words here.
 //
 // Inputs: the row traversal gathers a float-float vector kept as two FP32 arrays (high and low
 // words).  The column traversal gathers the residual: in paired storage the residual of row
@@ -406,16 +559,6 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
     }
 }
 
-// row extents of this lane's row of tile t (0, 0 past the end)
-__device__ __forceinline__ void tile_extents(const int32_t* __restrict__ ptr, int64_t t, int64_t nrows, int32_t& rb,
-                                             int32_t& re) {
-    const int64_t r = (t << 5) + (threadIdx.x & 31);
-    rb = re = 0;
-    if (r < nrows) {
-        rb = __ldcs(ptr + r);
-        re = __ldcs(ptr + r + 1);
-    }
-}
 
 template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
 __device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
