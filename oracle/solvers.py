@@ -16,6 +16,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   A^T r at y_k (which supplies a dual point); x_{k-1} is returned as soon as
   P(x_{k-1}) - max_{j<=k} D(y_j) is within the tolerance.  A y_k is formed by linearity
   from A x_{k-1} and A x_{k-2}.
+* FISTA with backtracking on L (Beck & Teboulle, Sec. 4 of their paper; the paper's TFOCS
+  runs use a dynamic L): see fista_bt.
 * pdNCG (Sec. 8.1 and 8.3): Newton-CG on f^mu_tau(x) = tau psi_mu(x) + 1/2||Ax - b||^2 with
   the pseudo-Huber psi_mu of Eq. (pseudoHuber), mu = 1e-5.  The Newton system of the model
   (bd4) is solved by PCG with the inverse diagonal of its matrix as preconditioner, stopped
@@ -50,7 +52,8 @@ import numpy as np
 TINY = 1e-300
 
 STATUS_OK = 0
-STATUS_NOCONV = 6
+STATUS_NOCONV = 5      # the library's L1LS_ENOCONV
+STATUS_NUMERIC = 6     # L1LS_ENUMERIC
 
 
 def objective(A, b, tau, x):
@@ -125,6 +128,78 @@ def fista(A, b, tau, L, tol, max_iter, x0=None, restart=False):
             t = t_new
         x_old, x_cur = x_cur, x_new
         Ax_old = u
+        k += 1
+
+
+def sufficient_decrease(Ad, d, L):
+    """The backtracking test of FISTA with backtracking for the quadratic smooth part
+    h(x) = 1/2 ||A x - b||^2: h(x) <= h(y) + grad h(y)^T d + L/2 ||d||^2 with d = x - y.  Since
+    h(y + d) - h(y) - grad h(y)^T d = 1/2 ||A d||^2 exactly, the test is ||A d||^2 <= L ||d||^2;
+    evaluated in this form it has no cancellation (the difference of the two objective values
+    near the optimum is below their rounding)."""
+    return float(Ad @ Ad) <= L * float(d @ d)
+
+
+def fista_bt(A, b, tau, L0, eta, tol, max_iter, x0=None, max_trials=60, trace=False):
+    """FISTA with backtracking on L (Beck & Teboulle 2009, "A fast iterative shrinkage-
+    thresholding algorithm for linear inverse problems", Sec. 4): the step constant of
+    iteration k is the smallest L = eta^i L_{k-1} (i >= 0) for which the prox-gradient point
+    x = S_{tau/L}(y_k + g/L), g = A^T (b - A y_k), passes sufficient_decrease with
+    d = x - y_k and A d = A x - A y_k.  L never decreases.  The momentum is FISTA's.
+    Iteration k certifies its own output x_k by P(x_k) - max_{j<=k} D(theta(y_j)).  A y_k is
+    formed by linearity from A x_{k-1} and A x_{k-2}.
+
+    Returns dict(x, iters, products, P, D, gap, rel_gap, status, L, backtracks) and, with
+    trace, hist = [(P(x_k), L_k)] per iteration."""
+    n = A.shape[1]
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)   # x_{k-1}
+    x_prev = x.copy()                                                             # x_{k-2}
+    Ax = A @ x
+    Ax_prev = Ax.copy()
+    products = 1
+    t = 1.0
+    beta = 0.0
+    L = float(L0)
+    best_D = -math.inf
+    backtracks = 0
+    hist = []
+    k = 1
+    while True:
+        y = x + beta * (x - x_prev)
+        Ay = Ax + beta * (Ax - Ax_prev)
+        r = b - Ay
+        g = A.T @ r
+        products += 1
+        best_D = max(best_D, dual_value(b, r, g, tau))
+        trials = 0
+        while True:
+            x_new = soft_threshold(y + g / L, tau / L)
+            Ax_new = A @ x_new
+            products += 1
+            if sufficient_decrease(Ax_new - Ay, x_new - y, L):
+                break
+            trials += 1
+            if trials > max_trials:
+                return dict(x=x, iters=k - 1, products=products, P=math.nan, D=best_D, gap=math.nan,
+                            rel_gap=math.nan, status=STATUS_NUMERIC, L=L, backtracks=backtracks, hist=hist)
+            L *= eta
+            backtracks += 1
+        res_new = Ax_new - b
+        P = tau * float(np.abs(x_new).sum()) + 0.5 * float(res_new @ res_new)
+        gap = P - best_D
+        rel = gap / max(abs(P), TINY)
+        hist.append((P, L))
+        if rel <= tol or k >= max_iter:
+            out = dict(x=x_new, iters=k, products=products, P=P, D=best_D, gap=gap, rel_gap=rel,
+                       status=STATUS_OK if rel <= tol else STATUS_NOCONV, L=L, backtracks=backtracks)
+            if trace:
+                out["hist"] = hist
+            return out
+        t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
+        beta = (t - 1.0) / t_new
+        t = t_new
+        x_prev, x = x, x_new
+        Ax_prev, Ax = Ax, Ax_new
         k += 1
 
 
