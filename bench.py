@@ -388,6 +388,67 @@ def sec89_form(l1, W, log2n, newton_steps):
                         "pdNCG with mu = 1e-5" % log2n, "runs": rows}
 
 
+def variants_form(l1, W, log2n, limit_s):
+    """FISTA variants on the C2 recipe at n = 2^log2n (FP32 values, tau = 1, gap 1e-6): the
+    paper's fixed L (= sigma_max^2 = 1, known exactly for these instances), the gradient
+    restart, and backtracking on L from L0 = 1e-2 (factor 2; FP64 vectors, one host decision
+    per trial)."""
+    ctx = l1.Context(0)
+    inst = ctx.generate(W.c2_scaled(log2n))
+    f_star = inst.info["f_star"]
+    rows = []
+    for name, call in (("fixed_L", lambda: inst.solve_fista(tau=1.0, tol=W.C2_TOL, max_iter=10 ** 6,
+                                                             time_limit_s=limit_s, allow=(4, 5))),
+                       ("restart", lambda: inst.solve_fista(tau=1.0, tol=W.C2_TOL, max_iter=10 ** 6, restart=1,
+                                                             time_limit_s=limit_s, allow=(4, 5))),
+                       ("backtracking", lambda: inst.solve_fista_bt(1e-2, 2.0, tau=1.0, tol=W.C2_TOL,
+                                                                     max_iter=10 ** 6, time_limit_s=limit_s,
+                                                                     allow=(4, 5)))):
+        t = time.perf_counter()
+        _, r = call()
+        el = time.perf_counter() - t
+        row = {"variant": name, "status": r["status_name"], "iters": r["iters"], "products": r["products"],
+               "seconds": el, "ms_per_iter": 1e3 * el / max(r["iters"], 1), "rel_gap": r["rel_gap"],
+               "rel_err_f": abs(r["f"] - f_star) / f_star}
+        if name == "backtracking":
+            row.update({"L0": 1e-2, "eta": 2.0, "increases": r["ls_trials"], "L_final": r["L"]})
+        rows.append(row)
+    inst.free()
+    ctx.close()
+    return {"workload": "c2 recipe at m=2^%d, n=2^%d, tau=1, gap 1e-6, %g s limit" % (log2n + 1, log2n, limit_s),
+            "runs": rows}
+
+
+def osgen3_form(l1, W, log2n, limit_s):
+    """Sec. 8.5's instances: x* by Procedure OsGen3 (gamma = 100, s1 = s2 = s/2, s = n/2^7),
+    A = Sigma G^T (L = I, G = G2 G), n = 2^log2n, m = 2n, kappa(A^T A) = 1e2 .. 1e8, rotation
+    angles 2 pi/10 and 2 pi/10^3: device generation time, kappa_rho(x*) at rho = 10 sigma_min^2
+    (the paper's rho = 0.1 with its singular values shifted by 0.1), and FISTA to the 1e-6 gap."""
+    import math
+    ctx = l1.Context(0)
+    rows = []
+    for theta in (2 * math.pi / 10, 2 * math.pi / 1e3):
+        for kappa in (10.0, 1e2, 1e3, 1e4):
+            n = 2 ** log2n
+            params = W.params(m=2 * n, n=n, seed=5, kappa=kappa, right_stages=2, left_stages=0, theta=theta,
+                              xstar_frac=2.0 ** -7, xstar_mode=2, gamma=100.0, value_dtype="f32")
+            t = time.perf_counter()
+            inst = ctx.generate(params)
+            gen_s = time.perf_counter() - t
+            krho = inst.kappa_rho(10.0 / kappa ** 2)
+            t = time.perf_counter()
+            _, r = inst.solve_fista(tau=1.0, tol=W.C2_TOL, max_iter=10 ** 6, time_limit_s=limit_s, allow=(4, 5))
+            el = time.perf_counter() - t
+            rows.append({"theta": theta, "kappa_AtA": kappa ** 2, "s": inst.info["s"], "generate_s": gen_s,
+                         "kappa_rho": krho, "fista_status": r["status_name"], "fista_iters": r["iters"],
+                         "fista_s": el, "rel_gap": r["rel_gap"],
+                         "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]})
+            inst.free()
+    ctx.close()
+    return {"workload": "sec. 8.5 shape: OsGen3 x* (gamma 100, s = n/2^7), A = Sigma G^T, m=2^%d, n=2^%d, FP32 "
+                        "values, FISTA %g s limit" % (log2n + 1, log2n, limit_s), "runs": rows}
+
+
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
@@ -524,6 +585,11 @@ def run_ours(args):
         forms["matrix_free"] = mf_form(l1, W, args.log2n, args.steps, args.warmup, args.solve_limit)
     if rank == 0 and not args.no_forms:
         forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_slots)
+    if rank == 0 and not args.no_forms:
+        forms["fista_variants"] = variants_form(l1, W, args.variants_log2n, args.solve_limit)
+    if rank == 0 and args.osgen3:
+        forms = forms or {}
+        forms["osgen3"] = osgen3_form(l1, W, args.osgen3_log2n, args.osgen3_limit)
     if rank == 0 and args.sec89:
         forms = forms or {}
         forms["sec89"] = sec89_form(l1, W, args.sec89_log2n, (8, 16, 32))
@@ -582,6 +648,10 @@ def main():
     ap.add_argument("--matrix-free", action="store_true",
                     help="time the iteration on the instance with A not assembled (Algorithms MvPA / MvPAt)")
     ap.add_argument("--precision-limit", type=float, default=8.0, help="c3: time limit per solve (s)")
+    ap.add_argument("--variants-log2n", type=int, default=22, help="FISTA variants leg: log2 n")
+    ap.add_argument("--osgen3", action="store_true", help="add the Sec. 8.5 OsGen3 leg")
+    ap.add_argument("--osgen3-log2n", type=int, default=22)
+    ap.add_argument("--osgen3-limit", type=float, default=10.0, help="Sec. 8.5 leg: FISTA time limit (s)")
     ap.add_argument("--sec89", action="store_true", help="add the Sec. 8.9 pdNCG leg")
     ap.add_argument("--sec89-log2n", type=int, default=22)
     args = ap.parse_args()

@@ -221,6 +221,7 @@ typedef struct {
     int32_t reserved;
     double queue_s;           /* serving (l1ls_poll): submission to admission, seconds         */
     double latency_s;         /* serving (l1ls_poll): submission to completion, seconds        */
+    double L;                 /* l1ls_solve_fista_bt: the final step constant                 */
 } l1ls_result;
 
 /* FISTA (Sec. 8.1; Beck & Teboulle) with fixed L = info.lipschitz from x0 (NULL: 0).  Stops
@@ -230,6 +231,20 @@ typedef struct {
  * filled when a limit is hit, ENUMERIC on NaN/Inf.  Blocking. */
 l1ls_status l1ls_solve_fista(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
                              l1ls_result* res, void* stream);
+
+/* FISTA with backtracking on L (Beck & Teboulle's FISTA with backtracking; the paper runs
+ * FISTA through TFOCS, whose L is dynamic, Sec. 8.1).  Starts from L = L0 (> 0); in every
+ * iteration the prox-gradient trial x = S_{tau/L}(y_k + A^T r_k / L) is accepted when
+ * ||A (x - y_k)||^2 <= L ||x - y_k||^2 (the sufficient-decrease test of 1/2 ||Ax - b||^2),
+ * otherwise L is multiplied by eta (> 1) and the trial repeated, at most o->ls_max times per
+ * iteration (then ENUMERIC).  L never decreases.  Each trial costs one product with A, each
+ * iteration one with A^T.  The certificate is that of l1ls_solve_fista evaluated at the
+ * iteration's own output x_k.  FP64 vectors; assembled matrices only (EINVAL for
+ * matrix_free).  res->ls_trials counts the increases of L, res->L is the final L.  Other
+ * arguments, statuses and the stopping rule as for l1ls_solve_fista (o->restart and
+ * o->accum are ignored).  Blocking. */
+l1ls_status l1ls_solve_fista_bt(l1ls_inst* inst, const l1ls_solve_opts* o, double L0, double eta, const double* x0,
+                                double* x_out, l1ls_result* res, void* stream);
 
 /* FISTA in steps, for callers that drive the iteration themselves (benchmarks, schedulers):
  *   l1ls_fista_begin  sets up the state of l1ls_solve_fista at x0 (NULL: 0) and enqueues it;

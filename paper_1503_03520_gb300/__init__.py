@@ -53,7 +53,7 @@ class Result(ctypes.Structure):
                 ("ls_trials", ctypes.c_int64), ("f", ctypes.c_double), ("dual", ctypes.c_double),
                 ("gap", ctypes.c_double), ("rel_gap", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("mu", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+                ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("L", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -100,6 +100,8 @@ _sig = {
     "l1ls_rmatvec": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "l1ls_rmatvec_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "l1ls_solve_fista": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Result), _P]),
+    "l1ls_solve_fista_bt": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), ctypes.c_double, ctypes.c_double, _P, _P,
+                                           ctypes.POINTER(Result), _P]),
     "l1ls_solve_pdncg": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Result), _P]),
     "l1ls_fista_begin": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), _P, _P]),
     "l1ls_fista_step": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
@@ -364,6 +366,11 @@ class Instance:
     def solve_fista(self, x0=None, x_out=None, stream=None, allow=(4, 5), **opts):
         """FISTA to the duality-gap tolerance; returns (x, result dict)."""
         return self._solve(lib.l1ls_solve_fista, x0, x_out, stream, opts, allow)
+
+    def solve_fista_bt(self, L0, eta=2.0, x0=None, x_out=None, stream=None, allow=(4, 5), **opts):
+        """FISTA with backtracking on L from L0 (factor eta); returns (x, result dict)."""
+        fn = lambda h, o, p0, pout, r, s: lib.l1ls_solve_fista_bt(h, o, float(L0), float(eta), p0, pout, r, s)
+        return self._solve(fn, x0, x_out, stream, opts, allow)
 
     def fista_begin(self, x0=None, stream=None, **opts):
         o = solve_opts(**opts)

@@ -11,7 +11,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libl1ls.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["capi.cu", "prims.cu", "gen.cu", "products.cu", "fista.cu", "pdncg.cu", "batch.cu", "serve.cu", "mfree.cu"]
+SOURCES = ["capi.cu", "prims.cu", "gen.cu", "products.cu", "fista.cu", "pdncg.cu", "batch.cu", "serve.cu", "mfree.cu", "fista_bt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -204,3 +204,58 @@ def test_fista_compensated_products_in_plain_storage(ctx, case, frac):
         assert abs(r["f"] - o["P"]) <= 2e-6 * o["P"]
     finally:
         inst.free()
+
+
+@pytest.mark.parametrize("L0,tau_rel", [(1e-3, None), (0.3, 0.2), (4.0, 0.5)])
+def test_fista_backtracking_matches_oracle(ctx, L0, tau_rel):
+    """FISTA with backtracking on L (FP64 values and vectors) against the oracle's: the same
+    increases of L (each a decision ||A d||^2 <= L ||d||^2 taken on both sides in FP64), the
+    same final L, the iteration count within 2%, and the certified x."""
+    params = W.params(m=4096, n=2048, right_stages=2, left_stages=1, kappa=100.0, value_dtype="f64", seed=21,
+                      xstar_frac=0.05)
+    ref = oracle_instance(params)
+    tau = 1.0 if tau_rel is None else tau_rel * ref.lam_max
+    inst = ctx.generate(params)
+    try:
+        x, r = inst.solve_fista_bt(L0, 2.0, tau=tau, tol=1e-8, max_iter=50000)
+        o = solvers.fista_bt(ref.A, ref.b, tau, L0, 2.0, 1e-8, 50000)
+        assert o["status"] == 0 and r["status"] == 0 and r["rel_gap"] <= 1e-8
+        assert r["ls_trials"] == o["backtracks"] and r["L"] == o["L"], (r["ls_trials"], o["backtracks"], r["L"], o["L"])
+        assert abs(r["iters"] - o["iters"]) <= max(2, 0.02 * o["iters"]), (r["iters"], o["iters"])
+        assert r["products"] == 1 + 2 * r["iters"] + r["ls_trials"]
+        assert o["products"] == 1 + 2 * o["iters"] + o["backtracks"]
+        assert solvers.certificate(ref.A, ref.b, tau, x)[3] <= 2e-8
+        if tau_rel is None:   # strong convexity: ||x - x*||^2 <= 2 gap / sigma_min^2
+            assert float((x - ref.xstar) @ (x - ref.xstar)) <= 2.0 * r["gap"] * 100.0 ** 2
+    finally:
+        inst.free()
+
+
+def test_fista_backtracking_fp32_values(ctx):
+    """FP32 values (FP32 sums in the products): the C2 recipe at n = 2^16 from L0 = 1e-2 reaches
+    the 1e-6 gap; L ends within [L0, 2 L_f] (L_f = sigma_max^2 = 1)."""
+    params = W.c2_scaled(16)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        x, r = inst.solve_fista_bt(1e-2, 2.0, tau=1.0, tol=1e-6, max_iter=50000)
+        assert r["status"] == 0 and r["rel_gap"] <= 1e-6
+        assert 1e-2 < r["L"] <= 2.0 and r["ls_trials"] >= 6
+        assert solvers.certificate(ref.A, ref.b, 1.0, x)[3] <= 1e-5
+    finally:
+        inst.free()
+
+
+def test_fista_backtracking_rejections(ctx):
+    import paper_1503_03520_gb300 as l1
+    inst = ctx.generate(W.params(m=512, n=256, value_dtype="f32"))
+    mf = ctx.generate(W.params(m=512, n=256, value_dtype="f32", matrix_free=1))
+    try:
+        for call in (lambda: inst.solve_fista_bt(0.0, 2.0), lambda: inst.solve_fista_bt(1.0, 1.0),
+                     lambda: inst.solve_fista_bt(float("nan"), 2.0), lambda: mf.solve_fista_bt(1.0, 2.0)):
+            with pytest.raises(l1.L1LSError) as e:
+                call()
+            assert e.value.status == 1
+    finally:
+        inst.free()
+        mf.free()
