@@ -281,9 +281,9 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
         resf[4 * (r >> 1) + (r & 1)] = rr.hi;
         resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
         const ff dd = ff_sub(u, ff_from_float(o.bb));
-        q0 = ff_add(q0, ff_mul(dd, dd));
-        q1 = ff_add(q1, ff_mul(ff_from_float(o.bb), rr));
-        q2 = ff_add(q2, ff_mul(rr, rr));
+        sum2_add(q0, ff_mul(dd, dd));
+        sum2_add(q1, ff_mul(ff_from_float(o.bb), rr));
+        sum2_add(q2, ff_mul(rr, rr));
     };
     tiles_ff<true, true, V, EPL>(t0, t1, rptr, rcol, rval, xh, xl, nullptr, npairs, wbuf, pre, epi);
     q0 = warp_sum_ff(q0);
@@ -329,8 +329,8 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
         x0h[j] = xn.hi;
         x0l[j] = xn.lo;
         gmax = fmaxf(gmax, fabsf(g.hi));
-        l1 = ff_add(l1, ff_abs(xn));
-        if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+        sum2_add(l1, ff_abs(xn));
+        if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
     };
     tiles_ff<false, true, V, EPL>(t0, t1, cptr, cpair, cval, nullptr, nullptr, res, n, wbuf, pre, epi);
 #pragma unroll

@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(kBlock, L1LS_K1_MIN_BLOCKS) k_fista_k1(K1Args<
                 const ff d = two_sum(u, -o.bb);                  // u - b exactly
                 ff sq = two_prod(d.hi, d.hi);
                 sq.lo = __fmaf_rn(2.0f * d.hi, d.lo, sq.lo);
-                q[0] = ff_add(q[0], sq);
-                q[1] = ff_add(q[1], two_prod(o.bb, rr));
-                q[2] = ff_add(q[2], two_prod(rr, rr));
+                sum2_add(q[0], sq);
+                sum2_add(q[1], two_prod(o.bb, rr));
+                sum2_add(q[2], two_prod(rr, rr));
             } else {
                 const double du = (double)u - (double)o.bb;
                 p[0] += du * du;
@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<
                 a.xoh[j] = xn.hi;
                 a.xol[j] = xn.lo;
                 gmax = fmaxf(gmax, fabsf(g));
-                l1 = ff_add(l1, ff_abs(xn));
-                if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+                sum2_add(l1, ff_abs(xn));
+                if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
             });
         p[0] = (double)gmax;
         p[1] = ff_to_double(l1);
@@ -329,9 +329,9 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
             resf[2 * r + 1] = rr.lo;
         }
         const ff d = ff_sub(u, ff_from_float(o.bb));
-        q[0] = ff_add(q[0], ff_mul(d, d));
-        q[1] = ff_add(q[1], ff_mul(ff_from_float(o.bb), rr));
-        q[2] = ff_add(q[2], ff_mul(rr, rr));
+        sum2_add(q[0], ff_mul(d, d));
+        sum2_add(q[1], ff_mul(ff_from_float(o.bb), rr));
+        sum2_add(q[2], ff_mul(rr, rr));
     };
     const int64_t nrows = PAIRED ? a.m / 2 : a.m;
     const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (nrows + 31) >> 5;
@@ -375,8 +375,8 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
         a.xoh[j] = xn.hi;
         a.xol[j] = xn.lo;
         gmax = fmaxf(gmax, fabsf(g.hi));
-        l1 = ff_add(l1, ff_abs(xn));
-        if (rs) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+        sum2_add(l1, ff_abs(xn));
+        if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
     };
     const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (a.n + 31) >> 5;
     for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
@@ -420,9 +420,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_fista_mf1(MfK1Args a) {
         const ff d = two_sum(u, -bb);
         ff sq = two_prod(d.hi, d.hi);
         sq.lo = __fmaf_rn(2.0f * d.hi, d.lo, sq.lo);
-        q[0] = ff_add(q[0], sq);
-        q[1] = ff_add(q[1], two_prod(bb, rr));
-        q[2] = ff_add(q[2], two_prod(rr, rr));
+        sum2_add(q[0], sq);
+        sum2_add(q[1], two_prod(bb, rr));
+        sum2_add(q[2], two_prod(rr, rr));
         return rr;
     };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
             a.xoh[j] = xn.hi;
             a.xol[j] = xn.lo;
             gmax = fmaxf(gmax, fabsf(g));
-            l1 = ff_add(l1, ff_abs(xn));
-            if (RESTART) rt = ff_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, x1)));
+            sum2_add(l1, ff_abs(xn));
+            if (RESTART) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, x1)));
         }
         __syncthreads();   // the tile buffer is reloaded next
     }

@@ -162,6 +162,15 @@ __device__ __forceinline__ void load_span(const T* __restrict__ p, T (&out)[N]) 
 // tiles directly from global memory (same sums, same order).
 
 constexpr uint32_t kStagePolls = 1u << 20;
+// build parameters of the stage wait: a sleep between unsuccessful polls (32 ns measured 1.7%
+// faster in K2 than none: polling warps stop taking issue slots), and the suspend-time hint of
+// mbarrier.try_wait (0: none; 1000 ns measured no different)
+#ifndef L1LS_STAGE_SLEEP_NS
+#define L1LS_STAGE_SLEEP_NS 32
+#endif
+#ifndef L1LS_STAGE_HINT_NS
+#define L1LS_STAGE_HINT_NS 0
+#endif
 constexpr int kStageTimeout = 1 << 30;
 constexpr int kStageBytes = 2880;   // per stage and warp (two stages x 8 warps fit 48 KB)
 
@@ -195,6 +204,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t done;
+#if L1LS_STAGE_HINT_NS > 0
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"((uint32_t)L1LS_STAGE_HINT_NS)
+        : "memory");
+#else
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -202,6 +220,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "=r"(done)
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
+#endif
     return done != 0;
 }
 
@@ -237,7 +256,12 @@ __device__ __forceinline__ void stage_issue(int32_t* sidx, V* sval, uint64_t* ba
 // bounded wait for a stage; false (warp-uniform) if some lane ran out of polls
 __device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity) {
     bool done = false;
-    for (uint32_t k = 0; k < kStagePolls && !done; ++k) done = mbar_try_wait(bar, parity);
+    for (uint32_t k = 0; k < kStagePolls && !done; ++k) {
+        done = mbar_try_wait(bar, parity);
+#if L1LS_STAGE_SLEEP_NS > 0
+        if (!done) __nanosleep(L1LS_STAGE_SLEEP_NS);
+#endif
+    }
     return __all_sync(0xffffffffu, done);
 }
 
