@@ -323,8 +323,8 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
     };
     auto epi = [&](int64_t j, ff g, const Ops& o) {
         // y = x_k + beta (x_k - x_{k-1}); x_{k+1} = S_{tau/L}(y + A^T r / L) (Sec. 8.1)
-        const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
-        const ff v = ff_add(y, ff_mul(g, invL_f));
+        const ff y = ff_add_sloppy(o.x1, ff_mul(beta_f, ff_add_sloppy(o.x1, ff_neg(o.x0))));
+        const ff v = ff_add_sloppy(y, ff_mul(g, invL_f));
         const ff xn = ff_soft_threshold(v, thr_f);
         x0h[j] = xn.hi;
         x0l[j] = xn.lo;

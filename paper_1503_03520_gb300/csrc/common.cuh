@@ -178,6 +178,15 @@ __device__ __forceinline__ void sum2_add(ff& acc, ff p) {
     acc.hi = t.hi;
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(t.lo, p.lo));
 }
+// Double-word addition without the TwoSum of the low words (Dekker's "sloppy" addition,
+// 11 FP32 operations instead of 20): the absolute error stays within a few units of
+// 2^-48 (|a| + |b|), but under cancellation it is not small relative to the result.  Used for
+// the FISTA iterate update, whose accuracy is absolute (relative to |x|) in any case.
+__device__ __forceinline__ ff ff_add_sloppy(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {

@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<
                 return o;
             },
             [&](int64_t j, Acc g, const Ops& o) {
-                const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
-                const ff v = ff_add(y, ff_mul(ff_from_float(g), invL_f));
+                const ff y = ff_add_sloppy(o.x1, ff_mul(beta_f, ff_add_sloppy(o.x1, ff_neg(o.x0))));
+                const ff v = ff_add_sloppy(y, ff_mul(ff_from_float(g), invL_f));
                 const ff xn = ff_soft_threshold(v, thr_f);
                 a.xoh[j] = xn.hi;
                 a.xol[j] = xn.lo;
@@ -369,8 +369,8 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
         return o;
     };
     auto epi = [&](int64_t j, ff g, const Ops& o) {
-        const ff y = ff_add(o.x1, ff_mul(beta_f, ff_sub(o.x1, o.x0)));
-        const ff v = ff_add(y, ff_mul(g, invL_f));
+        const ff y = ff_add_sloppy(o.x1, ff_mul(beta_f, ff_add_sloppy(o.x1, ff_neg(o.x0))));
+        const ff v = ff_add_sloppy(y, ff_mul(g, invL_f));
         const ff xn = ff_soft_threshold(v, thr_f);
         a.xoh[j] = xn.hi;
         a.xol[j] = xn.lo;
@@ -514,8 +514,8 @@ __global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
             if (j >= a.R.n) break;
             const float g = buf[kMfHalo + p];
             const ff x1 = {a.xch[j], a.xcl[j]}, x0 = {a.xoh[j], a.xol[j]};
-            const ff y = ff_add(x1, ff_mul(beta_f, ff_sub(x1, x0)));
-            const ff v = ff_add(y, ff_mul(ff_from_float(g), invL_f));
+            const ff y = ff_add_sloppy(x1, ff_mul(beta_f, ff_add_sloppy(x1, ff_neg(x0))));
+            const ff v = ff_add_sloppy(y, ff_mul(ff_from_float(g), invL_f));
             const ff xn = ff_soft_threshold(v, thr_f);
             a.xoh[j] = xn.hi;
             a.xol[j] = xn.lo;
