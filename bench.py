@@ -452,6 +452,36 @@ def osgen3_form(l1, W, log2n, limit_s):
                         "values, FISTA (float-float products) %g s limit" % (log2n + 1, log2n, limit_s), "runs": rows}
 
 
+def sweep_form(l1, W, stored_log2n, mf_log2n, steps, warmup):
+    """C2's size sweep: the FISTA iteration on the C2 recipe at n = 2^k for the stored matrix
+    (up to 2^27, the largest n whose nonzeros fit 32-bit offsets) and for the matrix-free
+    products (up to 2^29): device time per iteration (CUDA events), algorithmic GB/s and the
+    fraction of the measured HBM copy peak, and the instance's device memory."""
+    import torch
+    peak, _ = measured_hbm_peak()
+    rows = []
+    ctx = l1.Context(0)
+    for mf, sizes in ((0, stored_log2n), (1, mf_log2n)):
+        for k in sizes:
+            inst = ctx.generate(dict(W.c2_scaled(k), matrix_free=mf))
+            m, n, nnz = inst.m, inst.n, inst.nnz
+            k1b, k2b = mf_bytes_per_iteration(m, n) if mf else bytes_per_iteration(m, n, nnz)
+            stream = torch.cuda.current_stream()
+            inst.fista_begin(tau=1.0, tol=0.0, max_iter=10 ** 12, stream=stream)
+            inst.fista_step(warmup, stream=stream)
+            torch.cuda.synchronize()
+            kms = inst.fista_step(steps, timed=True, stream=stream)
+            inst.fista_end(stream=stream, allow=(4, 5))
+            it_ms = (kms[0] + kms[1]) / steps
+            rows.append({"storage": "matrix-free" if mf else "stored", "log2n": k, "nnz": nnz,
+                         "device_bytes": inst.info["device_bytes"], "iteration_ms": it_ms,
+                         "gbs": (k1b + k2b) / (it_ms * 1e-3) / 1e9,
+                         "frac": (k1b + k2b) / (it_ms * 1e-3) / 1e9 / peak})
+            inst.free()
+    ctx.close()
+    return {"workload": "c2 recipe (m = 2n, ~8/col, FP32 values) at n = 2^k", "peak_gbs": peak, "runs": rows}
+
+
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
@@ -590,6 +620,9 @@ def run_ours(args):
         forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_slots)
     if rank == 0 and not args.no_forms:
         forms["fista_variants"] = variants_form(l1, W, args.variants_log2n, args.solve_limit)
+    if rank == 0 and args.sweep:
+        forms = forms or {}
+        forms["size_sweep"] = sweep_form(l1, W, range(20, 28), range(24, 30), 20, 3)
     if rank == 0 and args.osgen3:
         forms = forms or {}
         forms["osgen3"] = osgen3_form(l1, W, args.osgen3_log2n, args.osgen3_limit)
@@ -652,6 +685,8 @@ def main():
                     help="time the iteration on the instance with A not assembled (Algorithms MvPA / MvPAt)")
     ap.add_argument("--precision-limit", type=float, default=8.0, help="c3: time limit per solve (s)")
     ap.add_argument("--variants-log2n", type=int, default=22, help="FISTA variants leg: log2 n")
+    ap.add_argument("--sweep", action="store_true", help="add the size sweep (n = 2^20 .. 2^27 stored, "
+                                                         "2^24 .. 2^29 matrix-free)")
     ap.add_argument("--osgen3", action="store_true", help="add the Sec. 8.5 OsGen3 leg")
     ap.add_argument("--osgen3-log2n", type=int, default=22)
     ap.add_argument("--osgen3-limit", type=float, default=10.0, help="Sec. 8.5 leg: FISTA time limit (s)")

@@ -22,6 +22,7 @@
 namespace l1ls {
 
 l1ls_status exclusive_scan_i32(const int32_t* in, int64_t count, int32_t* out, int64_t* total, cudaStream_t st);
+l1ls_status sum_i32(const int32_t* in, int64_t count, int64_t* total, cudaStream_t st);
 l1ls_status radix_argsort_u64(const uint64_t* keys, int64_t count, uint32_t* order, cudaStream_t st);
 
 namespace {
@@ -1076,14 +1077,12 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
             // A stays in factored form: FP32 copies of the factors for the products; the rows are
             // kept in the order of the left rotations (row i of A is row perm[i] of it)
             int32_t* cnt = nullptr;
-            int32_t* ptr = nullptr;
             GEN_TRY(tmp.get(&cnt, n));
-            GEN_TRY(tmp.get(&ptr, n + 1));
             k_csc_count<<<nblk(n), 256, 0, st>>>(g, I->perm_inv, cnt);
             GEN_CUDA(cudaGetLastError());
             int64_t nnz = 0;
-            GEN_TRY(exclusive_scan_i32(cnt, n, ptr, &nnz, st));
-            I->nnz = nnz;                         // of the matrix the factors represent
+            GEN_TRY(sum_i32(cnt, n, &nnz, st));
+            I->nnz = nnz;                         // of the matrix the factors represent (may exceed 2^31)
             GEN_TRY(I->alloc_n(&I->sigma32, pad32(n)));
             GEN_CUDA(cudaMemsetAsync(I->sigma32, 0, sizeof(float) * pad32(n), st));
             k_to_f32<<<nblk(n), 256, 0, st>>>(I->sigma, n, I->sigma32);

@@ -157,6 +157,26 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t count) {
 
 // Exclusive scan of `count` int32 values into out[0..count] (out[count] = total).
 // Fails with EINVAL when the total does not fit in int32.
+// the 64-bit sum of count int32 values (no 32-bit limit: the counts of a matrix that is never
+// assembled)
+l1ls_status sum_i32(const int32_t* in, int64_t count, int64_t* total, cudaStream_t st) {
+    const int64_t ntiles = (count + kScanTile - 1) / kScanTile;
+    int64_t* sums = nullptr;
+    L1LS_CUDA(cudaMallocAsync((void**)&sums, sizeof(int64_t) * (ntiles + 1), st));
+    if (ntiles > 0) {
+        k_scan_tile_sums<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, count, sums);
+        L1LS_CUDA(cudaGetLastError());
+    }
+    k_scan_top<<<1, kScanBlock, 0, st>>>(sums, ntiles);
+    L1LS_CUDA(cudaGetLastError());
+    int64_t tot = 0;
+    L1LS_CUDA(cudaMemcpyAsync(&tot, sums + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    L1LS_CUDA(cudaFreeAsync(sums, st));
+    L1LS_CUDA(cudaStreamSynchronize(st));
+    *total = tot;
+    return L1LS_OK;
+}
+
 l1ls_status exclusive_scan_i32(const int32_t* in, int64_t count, int32_t* out, int64_t* total, cudaStream_t st) {
     const int64_t ntiles = (count + kScanTile - 1) / kScanTile;
     int64_t* sums = nullptr;
