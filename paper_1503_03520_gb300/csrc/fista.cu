@@ -37,6 +37,13 @@ constexpr int kBlock = 256;
 #ifndef L1LS_K2_MIN_BLOCKS
 #define L1LS_K2_MIN_BLOCKS 4
 #endif
+// the same for the float-float kernels K1C / K2C (K2C at 64 registers spills; 3 blocks allow 85)
+#ifndef L1LS_K1C_MIN_BLOCKS
+#define L1LS_K1C_MIN_BLOCKS 4
+#endif
+#ifndef L1LS_K2C_MIN_BLOCKS
+#define L1LS_K2C_MIN_BLOCKS 3
+#endif
 
 struct FistaState {
     double tau, L, tol;
@@ -91,8 +98,9 @@ struct K2Args {
     int64_t n;
 };
 
+// (FP64 vectors need more than 64 registers: 3 blocks per SM for them)
 template <class V, class Vec, bool PAIRED>
-__global__ void __launch_bounds__(kBlock, L1LS_K1_MIN_BLOCKS) k_fista_k1(K1Args<V, Vec> a) {
+__global__ void __launch_bounds__(kBlock, sizeof(Vec) == 8 ? 3 : L1LS_K1_MIN_BLOCKS) k_fista_k1(K1Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[3 * 32];
@@ -186,8 +194,9 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new, doubl
     }
 }
 
+// (the gradient-restart partial needs more than 64 registers: 3 blocks per SM for that variant)
 template <class V, class Vec, bool PAIRED, bool RESTART>
-__global__ void __launch_bounds__(kBlock, L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<V, Vec> a) {
+__global__ void __launch_bounds__(kBlock, RESTART ? 3 : L1LS_K2_MIN_BLOCKS) k_fista_k2(K2Args<V, Vec> a) {
     using Acc = Vec;
     __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[3 * 32];
@@ -297,8 +306,9 @@ struct K2CArgs {
 };
 
 template <class V, bool PAIRED>
-__global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
-    __shared__ CompSmem<kBlock> sm;
+__global__ void __launch_bounds__(kBlock, L1LS_K1C_MIN_BLOCKS) k_fista_k1c(K1CArgs<V> a) {
+    // paired storage: the staged traversal with float-float sums; plain CSR: lane runs
+    __shared__ typename std::conditional<PAIRED, PairedSmem<V, kBlock>, CompSmem<kBlock>>::type sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const ff beta = ff_from_double(a.st->beta);
@@ -334,9 +344,14 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
         sum2_add(q[2], ff_mul(rr, rr));
     };
     const int64_t nrows = PAIRED ? a.m / 2 : a.m;
-    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (nrows + 31) >> 5;
-    for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
-        tile_ff<true, PAIRED, V>(t, a.ptr, a.col, a.val, a.xh, a.xl, nullptr, nrows, sm.warp_buf(), pre, epi);
+    if constexpr (PAIRED) {
+        warp_pcsr<true, V>(a.ptr, a.col, a.val, nrows, sm, &a.st->stage_err, FFSum<true, V>{a.xh, a.xl, nullptr}, pre,
+                           epi);
+    } else {
+        const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (nrows + 31) >> 5;
+        for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
+            tile_ff<true, false, V>(t, a.ptr, a.col, a.val, a.xh, a.xl, nullptr, nrows, sm.warp_buf(), pre, epi);
+    }
     double p[3] = {ff_to_double(q[0]), ff_to_double(q[1]), ff_to_double(q[2])};
     block_reduce<kBlock, 3>(p, 0u, red);
     double tot[3];
@@ -348,8 +363,8 @@ __global__ void __launch_bounds__(kBlock) k_fista_k1c(K1CArgs<V> a) {
 }
 
 template <class V, bool PAIRED>
-__global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
-    __shared__ CompSmem<kBlock> sm;
+__global__ void __launch_bounds__(kBlock, L1LS_K2C_MIN_BLOCKS) k_fista_k2c(K2CArgs<V> a) {
+    __shared__ typename std::conditional<PAIRED, PairedSmem<V, kBlock>, CompSmem<kBlock>>::type sm;
     __shared__ double red[3 * 32];
     if (*(volatile int32_t*)&a.st->stop) return;
     const bool rs = a.st->restart != 0;
@@ -378,9 +393,14 @@ __global__ void __launch_bounds__(kBlock) k_fista_k2c(K2CArgs<V> a) {
         sum2_add(l1, ff_abs(xn));
         if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
     };
-    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (a.n + 31) >> 5;
-    for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
-        tile_ff<false, PAIRED, V>(t, a.ptr, a.pair, a.val, nullptr, nullptr, a.res, a.n, sm.warp_buf(), pre, epi);
+    if constexpr (PAIRED) {
+        warp_pcsr<false, V>(a.ptr, a.pair, a.val, a.n, sm, &a.st->stage_err,
+                            FFSum<false, V>{nullptr, nullptr, reinterpret_cast<const float4*>(a.res)}, pre, epi);
+    } else {
+        const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (a.n + 31) >> 5;
+        for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
+            tile_ff<false, false, V>(t, a.ptr, a.pair, a.val, nullptr, nullptr, a.res, a.n, sm.warp_buf(), pre, epi);
+    }
     double p[3] = {(double)gmax, ff_to_double(l1), ff_to_double(rt)};
     block_reduce<kBlock, 3>(p, 1u, red);
     double tot[3];
@@ -587,6 +607,7 @@ struct FistaWork {
     FistaState* st = nullptr;
     FistaState* host_st = nullptr;   // host copy of the state
     int grid1 = 0, grid2 = 0;
+    int grid2r = 0;                      // K2 with the gradient-restart partial (more registers)
     cudaGraphExec_t exec = nullptr;
     int exec_chunk = 0;
     int64_t enqueued = 0;           // iterations enqueued since begin (parity of the next one)
@@ -650,10 +671,10 @@ l1ls_status enqueue_k2(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
         a2.ptr = I->pcol_ptr;
         a2.col = I->pcol_pair;
         a2.val = static_cast<const V*>(I->pcol_val);
-        if (w->restart) k_fista_k2<V, Vec, true, true><<<w->grid2, kBlock, 0, st>>>(a2);
+        if (w->restart) k_fista_k2<V, Vec, true, true><<<w->grid2r, kBlock, 0, st>>>(a2);
         else k_fista_k2<V, Vec, true, false><<<w->grid2, kBlock, 0, st>>>(a2);
     } else {
-        if (w->restart) k_fista_k2<V, Vec, false, true><<<w->grid2, kBlock, 0, st>>>(a2);
+        if (w->restart) k_fista_k2<V, Vec, false, true><<<w->grid2r, kBlock, 0, st>>>(a2);
         else k_fista_k2<V, Vec, false, false><<<w->grid2, kBlock, 0, st>>>(a2);
     }
     return L1LS_OK;
@@ -787,9 +808,11 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         } else if (I->paired) {
             w->grid1 = grid_of(I, k_fista_k1<V, Vec, true>, m / 2);
             w->grid2 = grid_of(I, k_fista_k2<V, Vec, true, false>, n);
+            w->grid2r = grid_of(I, k_fista_k2<V, Vec, true, true>, n);
         } else {
             w->grid1 = grid_of(I, k_fista_k1<V, Vec, false>, m);
             w->grid2 = grid_of(I, k_fista_k2<V, Vec, false, false>, n);
+            w->grid2r = grid_of(I, k_fista_k2<V, Vec, false, true>, n);
         }
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
         L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 3 + 1024));

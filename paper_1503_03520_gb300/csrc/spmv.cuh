@@ -302,6 +302,23 @@ __device__ __forceinline__ void lane_entries(const int32_t* ib, const typename V
     }
 }
 
+// Summation policies of the staged traversal: how a lane gathers the vector for its entries
+// and accumulates its row (column).
+//   PlainSum: products and sums in Acc (FP64 for FP64 values, FP32 otherwise).
+template <bool ROWS, class V, class X, class Acc> struct PlainSum {
+    using acc_t = Acc;
+    const X* x;
+    __device__ __forceinline__ Acc zero() const { return Acc(0); }
+    __device__ __forceinline__ void entries(const int32_t* ib, const typename ValPair<V>::type* vb, int32_t off,
+                                            int32_t eb, int32_t ee, Acc& a0, Acc& a1) const {
+        lane_entries<ROWS, V, X, Acc>(ib, vb, off, eb, ee, x, a0, a1);
+    }
+    __device__ __forceinline__ Acc finish(Acc a) const { return a; }
+};
+
+// Forward declaration: the float-float policy (FFSum) is defined with the float-float kernels.
+template <bool ROWS, class V> struct FFSum;
+
 // row extents of this lane's row of tile t (0, 0 past the end)
 __device__ __forceinline__ void tile_extents(const int32_t* __restrict__ ptr, int64_t t, int64_t nrows, int32_t& rb,
                                              int32_t& re) {
@@ -331,11 +348,13 @@ __device__ __forceinline__ void tile_span(int64_t t, int64_t nrows, int32_t rb, 
 // the staged stream, so every sum has a fixed order.  ROWS = true: npairs row pairs, x gathered
 // at the column index, pre / epi called per row (2p and 2p+1).  ROWS = false: nrows columns,
 // x gathered at (2p, 2p+1), pre / epi per column.  Warps walk tiles warp_id + k * total_warps.
-template <bool ROWS, class V, class X, class Acc, int BLOCK, class Pre, class Epi>
+// `sum` (PlainSum or FFSum) gathers and accumulates a lane's entries.
+template <bool ROWS, class V, int BLOCK, class Sum, class Pre, class Epi>
 __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                          const V* __restrict__ val2, const X* __restrict__ x, int64_t nrows,
-                                          PairedSmem<V, BLOCK>& sm, int* err, Pre pre, Epi epi) {
+                                          const V* __restrict__ val2, int64_t nrows, PairedSmem<V, BLOCK>& sm,
+                                          int* err, const Sum& sum, Pre pre, Epi epi) {
     using VP = typename ValPair<V>::type;
+    using Acc = typename Sum::acc_t;
     constexpr int kCap = PairedSmem<V, BLOCK>::kCap;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -380,7 +399,7 @@ __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const
         const bool has = r < nrows;
         auto ops0 = pre(ROWS ? 2 * r : r, has);
         auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
-        Acc a0 = Acc(0), a1 = Acc(0);
+        Acc a0 = sum.zero(), a1 = sum.zero();
         const int32_t end = (e1 + 3) & ~3;
         bool staged = issued && staging;
         for (;;) {
@@ -396,10 +415,9 @@ __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const
             }
             const int32_t eb = max(rb, lo), ee = min(re, hi);
             if (staged)
-                lane_entries<ROWS, V, X, Acc>(sm.idx[wid][s], reinterpret_cast<const VP*>(sm.val[wid][s]), lo, eb, ee, x,
-                                              a0, a1);
+                sum.entries(sm.idx[wid][s], reinterpret_cast<const VP*>(sm.val[wid][s]), lo, eb, ee, a0, a1);
             else
-                lane_entries<ROWS, V, X, Acc>(idx, reinterpret_cast<const VP*>(val2), 0, eb, ee, x, a0, a1);
+                sum.entries(idx, reinterpret_cast<const VP*>(val2), 0, eb, ee, a0, a1);
             if (hi >= e1) break;
             // a tile longer than one stage: its next piece into the same stage
             __syncwarp();
@@ -411,10 +429,10 @@ __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const
         __syncwarp();   // every lane is done with stage s before it is refilled
         if (has) {
             if (ROWS) {
-                epi(2 * r, a0, ops0);
-                epi(2 * r + 1, a1, ops1);
+                epi(2 * r, sum.finish(a0), ops0);
+                epi(2 * r + 1, sum.finish(a1), ops1);
             } else {
-                epi(r, a0, ops0);
+                epi(r, sum.finish(a0), ops0);
             }
         }
         rb = nb;
@@ -435,7 +453,7 @@ template <bool PAIRED, class V, class X, class Acc, class Smem, class Pre, class
 __device__ __forceinline__ void rows_of(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                         const V* __restrict__ val, const X* __restrict__ x, int64_t nrows, Smem& sm,
                                         int* err, Pre pre, Epi epi) {
-    if constexpr (PAIRED) warp_pcsr<true, V, X, Acc>(ptr, idx, val, x, nrows / 2, sm, err, pre, epi);
+    if constexpr (PAIRED) warp_pcsr<true, V>(ptr, idx, val, nrows / 2, sm, err, PlainSum<true, V, X, Acc>{x}, pre, epi);
     else warp_csr<V, X, Acc>(ptr, idx, val, x, nrows, sm.warp_buf(), pre, epi);
 }
 
@@ -444,7 +462,7 @@ template <bool PAIRED, class V, class X, class Acc, class Smem, class Pre, class
 __device__ __forceinline__ void cols_of(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                         const V* __restrict__ val, const X* __restrict__ x, int64_t ncols, Smem& sm,
                                         int* err, Pre pre, Epi epi) {
-    if constexpr (PAIRED) warp_pcsr<false, V, X, Acc>(ptr, idx, val, x, ncols, sm, err, pre, epi);
+    if constexpr (PAIRED) warp_pcsr<false, V>(ptr, idx, val, ncols, sm, err, PlainSum<false, V, X, Acc>{x}, pre, epi);
     else warp_csr<V, X, Acc>(ptr, idx, val, x, ncols, sm.warp_buf(), pre, epi);
 }
 
@@ -619,6 +637,63 @@ __device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restric
                                              float* __restrict__ wbuf, Pre& pre, Epi& epi) {
     tile_ff<ROWS, true, V, EPL>(t, ptr, idx, val2, xh, xl, r4, nrows, wbuf, pre, epi);
 }
+
+// The float-float policy of the staged traversal (paired storage): each product is
+// TwoProduct(a, hi) with a * lo added to its low word, and the lane's running sum is kept by
+// Algorithm Sum2 of Ogita, Rump & Oishi (TwoSum on the high word, the errors and low words in
+// one FP32 word), which is as accurate as a sum in twice the working precision; the row sum
+// is renormalised by TwoSum at the end.  ROWS gathers the float-float vector (xh, xl) at the
+// column index; otherwise the residual float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} at the pair.
+template <bool ROWS, class V> struct FFSum {
+    using acc_t = ff;
+    const float* xh;
+    const float* xl;
+    const float4* r4;
+    __device__ __forceinline__ ff zero() const { return {0.0f, 0.0f}; }
+    __device__ __forceinline__ void entries(const int32_t* ib, const typename ValPair<V>::type* vb, int32_t off,
+                                            int32_t eb, int32_t ee, ff& a0, ff& a1) const {
+        for (int32_t e = eb; e < ee; e += 4) {
+            float v0[4], v1[4], g0[4], g1[4], h0[4], h1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v0[k] = v1[k] = g0[k] = g1[k] = h0[k] = h1[k] = 0.0f;
+                if (e + k < ee) {
+                    const int32_t j = ib[e + k - off];
+                    pair_to_acc<float>(vb[e + k - off], v0[k], v1[k]);
+                    if (ROWS) {
+                        g0[k] = __ldg(xh + j);
+                        h0[k] = __ldg(xl + j);
+                    } else {
+                        const float4 g = __ldg(r4 + j);
+                        g0[k] = g.x;
+                        g1[k] = g.y;
+                        h0[k] = g.z;
+                        h1[k] = g.w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e + k < ee) {
+                    ff p0 = two_prod(v0[k], g0[k]);
+                    p0.lo = __fmaf_rn(v0[k], h0[k], p0.lo);
+                    if (ROWS) {
+                        ff p1 = two_prod(v1[k], g0[k]);
+                        p1.lo = __fmaf_rn(v1[k], h0[k], p1.lo);
+                        sum2_add(a0, p0);
+                        sum2_add(a1, p1);
+                    } else {
+                        ff p1 = two_prod(v1[k], g1[k]);
+                        p1.lo = __fmaf_rn(v1[k], h1[k], p1.lo);
+                        sum2_add(a0, p0);
+                        sum2_add(a0, p1);
+                    }
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ ff finish(ff a) const { return two_sum(a.hi, a.lo); }
+};
 
 template <int BLOCK> struct CompSmem {
     float buf[(BLOCK / 32) * 4 * kWarpChunk];
