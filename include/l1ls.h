@@ -286,9 +286,10 @@ l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const do
  *                       certified solution at the last tau.  An instance's results do not depend
  *                       on the other instances of the batch or on the kernel schedule.  Blocking.
  *   l1ls_batch_get_schedule  schedule chosen by the built-in autotuner (0 before the first
- *                       solve): threads per block and entries per lane of the traversal, and
- *                       tune_ms (4 doubles, may be NULL): the time of the four probe steps of
- *                       each candidate (256, 8), (128, 8), (256, 4), (128, 4), in ms.
+ *                       solve): threads per block and entries per lane of the traversal (0: the
+ *                       staged stream, where each lane sums its own row from shared memory),
+ *                       and tune_ms (4 doubles, may be NULL): the time of the four probe steps
+ *                       of each candidate (256, 0), (128, 0), (256, 8), (128, 8), in ms.
  *   l1ls_batch_get_stats  of the last solve: batch steps run (each one FISTA step of every
  *                       active instance) and the device time of its launches in ms (CUDA
  *                       events on the solve's stream around the launch loop).

@@ -435,7 +435,7 @@ class Batch:
         ms = (ctypes.c_double * 4)()
         _check(lib.l1ls_batch_get_schedule(self._h, ctypes.byref(b), ctypes.byref(e), ms))
         return {"block": b.value, "entries_per_lane": e.value, "probe_ms": list(ms),
-                "candidates": [(256, 8), (128, 8), (256, 4), (128, 4)]}
+                "candidates": [(256, 0), (128, 0), (256, 8), (128, 8)]}
 
     def barrier_selftest(self, max_polls=1 << 12):
         """Run the bounded-barrier self-test; returns (status, message, seconds)."""

@@ -247,9 +247,9 @@ __device__ void finish_step(const BArgs& a, int64_t i, int cur, double gm, doubl
 // One row-pair segment (tiles t0 .. t1-1) of instance d: K1's product and epilogue; returns
 // the segment's partials ||A x - b||^2, b.r, r.r in out (lane 0).  Not inlined: the two phases
 // then get their registers allocated separately.
-template <class V, int EPL>
+template <class V, int EPL, int BLOCK, class Smem>
 __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, ff beta, int64_t t0, int64_t t1,
-                                         float* wbuf, double* out) {
+                                         Smem& sm, StageState& ss, int* err, double* out) {
     const int32_t* rptr = dp->rptr;
     const int32_t* rcol = dp->rcol;
     const V* rval = static_cast<const V*>(dp->rval);
@@ -285,7 +285,11 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
         sum2_add(q1, ff_mul(ff_from_float(o.bb), rr));
         sum2_add(q2, ff_mul(rr, rr));
     };
-    tiles_ff<true, true, V, EPL>(t0, t1, rptr, rcol, rval, xh, xl, nullptr, npairs, wbuf, pre, epi);
+    if constexpr (EPL == 0)
+        staged_tiles<true, V, BLOCK>(t0, 1, t1, rptr, rcol, rval, npairs, sm, ss, err, FFSum<true, V>{xh, xl, nullptr},
+                                     pre, epi);
+    else
+        tiles_ff<true, true, V, EPL>(t0, t1, rptr, rcol, rval, xh, xl, nullptr, npairs, sm.warp_buf(), pre, epi);
     q0 = warp_sum_ff(q0);
     q1 = warp_sum_ff(q1);
     q2 = warp_sum_ff(q2);
@@ -296,9 +300,10 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
 
 // One column segment of instance d: K2's product, momentum and shrinkage into x[nxt];
 // returns max |A^T r|, sum |x_{k+1}| and the restart test's partial in out (lane 0).
-template <class V, int EPL>
+template <class V, int EPL, int BLOCK, class Smem>
 __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, ff beta_f, ff invL_f, ff thr_f,
-                                         bool rs, int64_t t0, int64_t t1, float* wbuf, double* out) {
+                                         bool rs, int64_t t0, int64_t t1, Smem& sm, StageState& ss, int* err,
+                                         double* out) {
     const int32_t* cptr = dp->cptr;
     const int32_t* cpair = dp->cpair;
     const V* cval = static_cast<const V*>(dp->cval);
@@ -332,7 +337,11 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
         sum2_add(l1, ff_abs(xn));
         if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
     };
-    tiles_ff<false, true, V, EPL>(t0, t1, cptr, cpair, cval, nullptr, nullptr, res, n, wbuf, pre, epi);
+    if constexpr (EPL == 0)
+        staged_tiles<false, V, BLOCK>(t0, 1, t1, cptr, cpair, cval, n, sm, ss, err, FFSum<false, V>{nullptr, nullptr, res},
+                                      pre, epi);
+    else
+        tiles_ff<false, true, V, EPL>(t0, t1, cptr, cpair, cval, nullptr, nullptr, res, n, sm.warp_buf(), pre, epi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_down_sync(0xffffffffu, gmax, o));
     l1 = warp_sum_ff(l1);
@@ -342,10 +351,20 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
     out[2] = ff_to_double(rt);
 }
 
+// EPL = 0: the staged stream (each lane sums its own row from shared memory); 4 or 8: lane
+// runs of EPL entries summed through a warp buffer.  Registers are sized for
+// L1LS_BATCH_WARPS_PER_SM resident warps (a build parameter: 16 needs no spills, 24 caps a
+// thread at 80 registers with about 100 bytes of spills and measured 4% faster on C4).
+#ifndef L1LS_BATCH_WARPS_PER_SM
+#define L1LS_BATCH_WARPS_PER_SM 24
+#endif
 template <int BLOCK, int EPL, class V>
-__global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
-    __shared__ CompSmem<BLOCK> sm;   // 4 * kWarpChunk floats per warp; phase 2 uses half
+__global__ void __launch_bounds__(BLOCK, L1LS_BATCH_WARPS_PER_SM * 32 / BLOCK) k_batch(BArgs a) {
+    using Smem = typename std::conditional<EPL == 0, PairedSmem<V, BLOCK>, CompSmem<BLOCK>>::type;
+    __shared__ Smem sm;
     const int lane = threadIdx.x & 31;
+    StageState ss{0, 0, false};
+    if constexpr (EPL == 0) stage_init(sm, ss);
     for (int s = 0; s < a.steps; ++s) {
         if (*(volatile int*)a.active == 0) return;
         const int64_t step = a.step0 + s;
@@ -365,7 +384,7 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
             const int64_t t0 = (sg - sb) * kSegTiles, t1 = min(dp->n1, t0 + kSegTiles);
             double part[3];
             const ff beta = {__ldcg(&a.state[i].beta_ff[0]), __ldcg(&a.state[i].beta_ff[1])};
-            row_segment<V, EPL>(dp, cur, beta, t0, t1, sm.warp_buf(), part);
+            row_segment<V, EPL, BLOCK>(dp, cur, beta, t0, t1, sm, ss, a.err, part);
             if (lane == 0)
                 for (int k = 0; k < 3; ++k) a.part1[3 * sg + k] = part[k];
             double tot[3];
@@ -387,10 +406,10 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BArgs a) {
             const int64_t t0 = (sg - sb) * kSegTiles, t1 = min(dp->n2, t0 + kSegTiles);
             double part[3];
             const BState* sp = a.state + i;
-            col_segment<V, EPL>(dp, cur, {__ldcg(&sp->beta_ff[0]), __ldcg(&sp->beta_ff[1])},
+            col_segment<V, EPL, BLOCK>(dp, cur, {__ldcg(&sp->beta_ff[0]), __ldcg(&sp->beta_ff[1])},
                                 {__ldcg(&sp->invL_ff[0]), __ldcg(&sp->invL_ff[1])},
                                 {__ldcg(&sp->thr_ff[0]), __ldcg(&sp->thr_ff[1])}, __ldcg(&sp->restart) != 0, t0, t1,
-                                sm.warp_buf(), part);
+                                sm, ss, a.err, part);
             if (lane == 0)
                 for (int k = 0; k < 3; ++k) a.part2[3 * sg + k] = part[k];
             double tot[3];
@@ -448,9 +467,10 @@ struct Batch {
 
 namespace {
 
-// Schedules: (threads per block, entries per lane and chunk) of the persistent kernel.
+// Schedules: (threads per block, entries per lane and chunk) of the persistent kernel; 0
+// entries per lane = the staged stream.
 constexpr int kSchedBlock[4] = {256, 128, 256, 128};
-constexpr int kSchedEPL[4] = {8, 8, 4, 4};
+constexpr int kSchedEPL[4] = {0, 0, 8, 8};
 
 template <int BLOCK, int EPL, class V>
 l1ls_status launch_batch(Batch* B, BArgs& args, cudaStream_t st, int* grid_out) {
@@ -469,10 +489,10 @@ template <class V>
 l1ls_status launch_sched(Batch* B, int sched, BArgs& args, cudaStream_t st) {
     int grid = 0;
     switch (sched) {
-        case 0: return launch_batch<256, 8, V>(B, args, st, &grid);
-        case 1: return launch_batch<128, 8, V>(B, args, st, &grid);
-        case 2: return launch_batch<256, 4, V>(B, args, st, &grid);
-        default: return launch_batch<128, 4, V>(B, args, st, &grid);
+        case 0: return launch_batch<256, 0, V>(B, args, st, &grid);
+        case 1: return launch_batch<128, 0, V>(B, args, st, &grid);
+        case 2: return launch_batch<256, 8, V>(B, args, st, &grid);
+        default: return launch_batch<128, 8, V>(B, args, st, &grid);
     }
 }
 
@@ -683,7 +703,9 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
         L1LS_CUDA(cudaMemcpyAsync(&err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         L1LS_CUDA(cudaStreamSynchronize(st));
         if (err) {
-            final_status = set_error(L1LS_ECUDA, "batched FISTA: a bounded grid barrier expired");
+            final_status = err == kStageTimeout
+                               ? set_error(L1LS_ECUDA, "batched FISTA: a bulk-copy stage wait ran out of polls")
+                               : set_error(L1LS_ECUDA, "batched FISTA: a bounded grid barrier expired");
             break;
         }
         if (active == 0) break;

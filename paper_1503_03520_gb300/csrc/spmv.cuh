@@ -344,56 +344,71 @@ __device__ __forceinline__ void tile_span(int64_t t, int64_t nrows, int32_t rb, 
     hi = min(lo + cap, (e1 + 3) & ~3);
 }
 
-// Lane l owns row pair (ROWS) or column t*32 + l; it sums its own entries in nonzero order from
-// the staged stream, so every sum has a fixed order.  ROWS = true: npairs row pairs, x gathered
-// at the column index, pre / epi called per row (2p and 2p+1).  ROWS = false: nrows columns,
-// x gathered at (2p, 2p+1), pre / epi per column.  Warps walk tiles warp_id + k * total_warps.
-// `sum` (PlainSum or FFSum) gathers and accumulates a lane's entries.
+// A warp's staging state across calls: the L2 policy of its copies, the parity of each
+// stage's next mbarrier phase, and whether staging is on (off after a wait ran out).
+struct StageState {
+    uint64_t policy;
+    uint32_t parity;
+    bool staging;
+};
+
+// Once per kernel and warp, before the warp's first staged_tiles (warp-uniform).
+template <class V, int BLOCK>
+__device__ __forceinline__ void stage_init(PairedSmem<V, BLOCK>& sm, StageState& ss) {
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(&sm.bar[wid][0], 1);
+        mbar_init(&sm.bar[wid][1], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    ss.policy = l2_evict_first_policy();
+    ss.parity = 0;
+    ss.staging = true;
+}
+
+// Tiles t, t + step, ... (< tend) of one matrix in paired storage: lane l owns row pair (ROWS)
+// or column tile*32 + l and sums its own entries in nonzero order from the staged stream, so
+// every sum has a fixed order.  ROWS = true: nrows row pairs, pre / epi called per row (2p and
+// 2p+1); ROWS = false: nrows columns, pre / epi per column.  `sum` (PlainSum or FFSum) gathers
+// and accumulates a lane's entries.  Every copy issued here is waited for here, so calls can
+// follow each other on the same state.  Warp-uniform arguments.
 template <bool ROWS, class V, int BLOCK, class Sum, class Pre, class Epi>
-__device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                          const V* __restrict__ val2, int64_t nrows, PairedSmem<V, BLOCK>& sm,
-                                          int* err, const Sum& sum, Pre pre, Epi epi) {
+__device__ __forceinline__ void staged_tiles(int64_t t, int64_t step, int64_t tend, const int32_t* __restrict__ ptr,
+                                             const int32_t* __restrict__ idx, const V* __restrict__ val2,
+                                             int64_t nrows, PairedSmem<V, BLOCK>& sm, StageState& ss, int* err,
+                                             const Sum& sum, Pre& pre, Epi& epi) {
     using VP = typename ValPair<V>::type;
     using Acc = typename Sum::acc_t;
     constexpr int kCap = PairedSmem<V, BLOCK>::kCap;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t ntiles = (nrows + 31) >> 5;
-    int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-    if (t >= ntiles) return;
+    if (t >= tend) return;
     uint64_t* bar = sm.bar[wid];
-    if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
-    }
-    __syncwarp();
-    const uint64_t policy = l2_evict_first_policy();
-    uint32_t parity = 0;    // bit s: parity of stage s's next phase
-    // false after a wait ran out (warp-uniform); never on for arrays off 16-byte boundaries
-    bool staging = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(val2)) & 15u) == 0;
+    // arrays off 16-byte boundaries never stage
+    const bool aligned = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(val2)) & 15u) == 0;
 
     int32_t rb, re, nb, ne;
     tile_extents(ptr, t, nrows, rb, re);
-    tile_extents(ptr, t + nwarps, nrows, nb, ne);
+    tile_extents(ptr, t + step, nrows, nb, ne);
     int s = 0;
     int32_t e1, lo, hi;
     tile_span(t, nrows, rb, re, kCap, e1, lo, hi);
-    bool issued = staging && hi > lo;
-    if (issued) stage_issue<V>(sm.idx[wid][0], sm.val[wid][0], &bar[0], idx, val2, lo, hi, policy);
+    bool issued = aligned && ss.staging && hi > lo;
+    if (issued) stage_issue<V>(sm.idx[wid][0], sm.val[wid][0], &bar[0], idx, val2, lo, hi, ss.policy);
 
-    for (; t < ntiles; t += nwarps) {
+    for (; t < tend; t += step) {
         // the next tile's first piece into the other stage, then the extents of the one after
-        const int64_t tn = t + nwarps;
+        const int64_t tn = t + step;
         int32_t e1n = 0, lon = 0, hin = 0;
         bool issued_n = false;
-        if (tn < ntiles) {
+        if (tn < tend) {
             tile_span(tn, nrows, nb, ne, kCap, e1n, lon, hin);
-            issued_n = staging && hin > lon;
-            if (issued_n) stage_issue<V>(sm.idx[wid][s ^ 1], sm.val[wid][s ^ 1], &bar[s ^ 1], idx, val2, lon, hin, policy);
+            issued_n = aligned && ss.staging && hin > lon;
+            if (issued_n)
+                stage_issue<V>(sm.idx[wid][s ^ 1], sm.val[wid][s ^ 1], &bar[s ^ 1], idx, val2, lon, hin, ss.policy);
         }
         int32_t nb2, ne2;
-        tile_extents(ptr, tn + nwarps, nrows, nb2, ne2);
+        tile_extents(ptr, tn + step, nrows, nb2, ne2);
 
         const int64_t r = (t << 5) + lane;
         const bool has = r < nrows;
@@ -401,16 +416,16 @@ __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const
         auto ops1 = pre(ROWS ? 2 * r + 1 : r, ROWS && has);
         Acc a0 = sum.zero(), a1 = sum.zero();
         const int32_t end = (e1 + 3) & ~3;
-        bool staged = issued && staging;
+        bool staged = issued && ss.staging;
         for (;;) {
             if (staged) {
-                const bool ok = stage_wait(&bar[s], (parity >> s) & 1u);
-                parity ^= 1u << s;
+                const bool ok = stage_wait(&bar[s], (ss.parity >> s) & 1u);
+                ss.parity ^= 1u << s;
                 if (!ok) {   // record, wait once more (bounded) for the copies in flight, read directly
-                    staging = staged = false;
+                    ss.staging = staged = false;
                     if (lane == 0 && err) atomicOr(err, kStageTimeout);
-                    stage_wait(&bar[s], ((parity >> s) & 1u) ^ 1u);
-                    if (issued_n) stage_wait(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u);
+                    stage_wait(&bar[s], ((ss.parity >> s) & 1u) ^ 1u);
+                    if (issued_n) stage_wait(&bar[s ^ 1], (ss.parity >> (s ^ 1)) & 1u);
                 }
             }
             const int32_t eb = max(rb, lo), ee = min(re, hi);
@@ -423,8 +438,8 @@ __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const
             __syncwarp();
             lo = hi;
             hi = min(lo + kCap, end);
-            staged = staging;
-            if (staged) stage_issue<V>(sm.idx[wid][s], sm.val[wid][s], &bar[s], idx, val2, lo, hi, policy);
+            staged = aligned && ss.staging;
+            if (staged) stage_issue<V>(sm.idx[wid][s], sm.val[wid][s], &bar[s], idx, val2, lo, hi, ss.policy);
         }
         __syncwarp();   // every lane is done with stage s before it is refilled
         if (has) {
@@ -445,6 +460,20 @@ __device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const
         issued = issued_n;
         s ^= 1;
     }
+}
+
+// The whole matrix, tiles dealt round-robin: warp w of the grid takes tiles w, w + W, ...
+template <bool ROWS, class V, int BLOCK, class Sum, class Pre, class Epi>
+__device__ __forceinline__ void warp_pcsr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                          const V* __restrict__ val2, int64_t nrows, PairedSmem<V, BLOCK>& sm,
+                                          int* err, const Sum& sum, Pre pre, Epi epi) {
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t ntiles = (nrows + 31) >> 5;
+    const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    StageState ss;
+    stage_init(sm, ss);
+    staged_tiles<ROWS, V, BLOCK>(t, nwarps, ntiles, ptr, idx, val2, nrows, sm, ss, err, sum, pre, epi);
 }
 
 // Row traversal of A (nrows rows) in plain or paired storage; `sm` is the kernel's
@@ -554,13 +583,12 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
                         p1[k] = {0.f, 0.f};
                     }
                 } else if (PAIRED) {
+                    // the two terms of a column entry, summed in turn below (as FFSum does)
                     const float4 g = in ? __ldg(static_cast<const float4*>(rin) + ij[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    ff q0 = two_prod(v0, g.x);
-                    q0.lo = __fmaf_rn(v0, g.z, q0.lo);
-                    ff q1 = two_prod(v1, g.y);
-                    q1.lo = __fmaf_rn(v1, g.w, q1.lo);
-                    p0[k] = ff_add(q0, q1);
-                    p1[k] = {0.f, 0.f};
+                    p0[k] = two_prod(v0, g.x);
+                    p0[k].lo = __fmaf_rn(v0, g.z, p0[k].lo);
+                    p1[k] = two_prod(v1, g.y);
+                    p1[k].lo = __fmaf_rn(v1, g.w, p1[k].lo);
                 } else {
                     const float2 g = in ? __ldg(static_cast<const float2*>(rin) + ij[k]) : make_float2(0.f, 0.f);
                     p0[k] = two_prod(v0, g.x);
@@ -576,27 +604,30 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
         for (int k = 0; k < EPL; ++k) {
             w0h[k * 32 + lane] = p0[k].hi;
             w0l[k * 32 + lane] = p0[k].lo;
-            if (kTwoRows) {
+            if (PAIRED) {
                 w1h[k * 32 + lane] = p1[k].hi;
                 w1l[k * 32 + lane] = p1[k].lo;
             }
         }
         __syncwarp();
+        // running sums by Sum2 in entry order (for a paired column: term of row 2p, then 2p+1),
+        // the same operations as the staged traversal's FFSum, so both give the same bits
         const int32_t lo = max(rb, c), hi = min(re, c + kChunk);
         for (int32_t e = lo; e < hi; ++e) {
             const int32_t i = e - c;
             const int32_t q = (i & (EPL - 1)) * 32 + (i / EPL);
-            a0 = ff_add(a0, {w0h[q], w0l[q]});
-            if (kTwoRows) a1 = ff_add(a1, {w1h[q], w1l[q]});
+            sum2_add(a0, {w0h[q], w0l[q]});
+            if (kTwoRows) sum2_add(a1, {w1h[q], w1l[q]});
+            else if (PAIRED) sum2_add(a0, {w1h[q], w1l[q]});
         }
         __syncwarp();
     }
     if (has) {
         if (kTwoRows) {
-            epi(2 * r, a0, ops0);
-            epi(2 * r + 1, a1, ops1);
+            epi(2 * r, two_sum(a0.hi, a0.lo), ops0);
+            epi(2 * r + 1, two_sum(a1.hi, a1.lo), ops1);
         } else {
-            epi(r, a0, ops0);
+            epi(r, two_sum(a0.hi, a0.lo), ops0);
         }
     }
 }
