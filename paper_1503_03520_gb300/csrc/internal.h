@@ -145,9 +145,8 @@ l1ls_status spmv_plain(const Inst* I, bool transpose, const void* x, int vec_dty
 // z: n floats of scratch
 l1ls_status mf_product(const Inst* I, bool transpose, const float* in, float* out, const int32_t* map, float* z,
                        cudaStream_t st);
-// the first launch of each product alone (FISTA fuses the second with its epilogues)
+// z = Sigma R^T x, the first launch of A x alone (FISTA fuses the second with its epilogues)
 l1ls_status mf_apply_rt(const Inst* I, const float* x, float* z, cudaStream_t st);
-l1ls_status mf_apply_left_t(const Inst* I, const float* y, float* z, cudaStream_t st);
 
 l1ls_status fista_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
                         cudaStream_t st);

@@ -74,13 +74,6 @@ l1ls_status mf_apply_rt(const Inst* I, const float* x, float* z, cudaStream_t st
     return L1LS_OK;
 }
 
-// z = the first n entries of P2^T G~^T y, y in the stored row order (the first launch of A^T y)
-l1ls_status mf_apply_left_t(const Inst* I, const float* y, float* z, cudaStream_t st) {
-    const int64_t units = I->p.left_stages ? I->m / 2 : I->m;
-    k_mf_scatter<<<blocks_of(units, 256), 256, 0, st>>>(mf_left(I), y, nullptr, z);
-    return L1LS_OK;
-}
-
 // transpose = false: out (m) = A in (n); true: out (n) = A^T in (m).  The m-vector's row h of
 // the stored order is entry map[h] (map NULL: h).  z: n floats of scratch.
 l1ls_status mf_product(const Inst* I, bool transpose, const float* in, float* out, const int32_t* map, float* z,

@@ -22,12 +22,6 @@ namespace l1ls {
 constexpr int kEPL = 8;       // nonzeros per lane per chunk
 constexpr int kPad = kEPL;    // slack entries after the nonzero arrays
 constexpr int kWarpChunk = 32 * kEPL;
-// nonzeros per lane and chunk of the paired traversal (a build parameter, 4 or 8)
-#ifndef L1LS_PAIRED_EPL
-#define L1LS_PAIRED_EPL 8
-#endif
-constexpr int kPEPL = L1LS_PAIRED_EPL;
-static_assert(kPEPL == 4 || kPEPL == 8, "paired traversal: 4 or 8 nonzeros per lane");
 
 template <class Acc, class V> __device__ __forceinline__ Acc val_to_acc(V v);
 template <> __device__ __forceinline__ double val_to_acc<double, double>(double v) { return v; }
@@ -658,15 +652,6 @@ __device__ __forceinline__ void tiles_ff(int64_t t0, int64_t t1, const int32_t* 
         if (t + 1 < t1) tile_extents(ptr, t + 1, nrows, nb, ne);
         tile_ff_body<ROWS, PAIRED, V, EPL>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
     }
-}
-
-// paired storage (the form the batched kernel uses)
-template <bool ROWS, class V, int EPL = kEPL, class Pre, class Epi>
-__device__ __forceinline__ void pcsr_tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                             const V* __restrict__ val2, const float* __restrict__ xh,
-                                             const float* __restrict__ xl, const float4* __restrict__ r4, int64_t nrows,
-                                             float* __restrict__ wbuf, Pre& pre, Epi& epi) {
-    tile_ff<ROWS, true, V, EPL>(t, ptr, idx, val2, xh, xl, r4, nrows, wbuf, pre, epi);
 }
 
 // The float-float policy of the staged traversal (paired storage): each product is
