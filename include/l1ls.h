@@ -186,7 +186,7 @@ l1ls_status l1ls_rmatvec_noalloc(const l1ls_inst* inst, const void* y, l1ls_dtyp
 /* Solver options.  Defaults (l1ls_solve_opts_default): tau 1, rel_gap_tol 1e-6,
  * max_iter 100000 (FISTA iterations; Newton steps for pdNCG), no time limit, mu 1e-5,
  * mu_min 1e-14, mu_start 1, pcg_rtol 0.1, pcg_max 1000, ls_max 50, armijo 1e-4,
- * check_every 32.  pdNCG only: mu (the paper's smoothing parameter, Sec. 8.3) is reached by
+ * check_every 32, f_target -inf.  pdNCG only: mu (the paper's smoothing parameter, Sec. 8.3) is reached by
  * continuation from mu_start (divided by 10 after each full Newton step); below mu it is
  * divided by 10 again, down to mu_min, when a full step fails to halve the gap. */
 typedef struct {
@@ -204,6 +204,10 @@ typedef struct {
                                  summed in float-float (about 44 bits), for gaps below the FP32
                                  floor at small tau or large kappa.  EINVAL with FP64 values.
                                  Batches always use 1.                                         */
+    double f_target;          /* FISTA, FISTA with backtracking, pdNCG: also stop (status OK) as
+                                 soon as the certified objective f(x_k) <= f_target, the rule by
+                                 which the paper ends its comparison solvers (Sec. 8.3); -inf
+                                 (the default): off.  Batches ignore it.                       */
 } l1ls_solve_opts;
 
 void l1ls_solve_opts_default(l1ls_solve_opts* o);

@@ -85,9 +85,11 @@ def soft_threshold(v, t):
     return np.sign(v) * np.maximum(np.abs(v) - t, 0.0)
 
 
-def fista(A, b, tau, L, tol, max_iter, x0=None, restart=False):
+def fista(A, b, tau, L, tol, max_iter, x0=None, restart=False, f_target=-math.inf):
     """FISTA with the certificate above.  Returns dict(x, x_next, iters, products, P, D, gap,
-    rel_gap, status, restarts).
+    rel_gap, status, restarts).  It also stops (status OK) at the first certified x_{k-1} with
+    P(x_{k-1}) <= f_target: the paper ends its comparison solvers once their objective is
+    below pdNCG's (Sec. 8.3).
 
     restart=True adds the gradient restart of O'Donoghue & Candes (2015, "Adaptive restart for
     accelerated gradient schemes"), not used by the paper: when (y_k - x_k)^T (x_k - x_{k-1}) > 0
@@ -114,10 +116,11 @@ def fista(A, b, tau, L, tol, max_iter, x0=None, restart=False):
         gap = P - best_D
         rel = gap / max(abs(P), TINY)
         x_new = soft_threshold(y + g / L, tau / L)
-        if rel <= tol or k - 1 >= max_iter:
+        if rel <= tol or P <= f_target or k - 1 >= max_iter:
             # x_next: the prox-gradient step from y_k, one past the certified iterate
+            ok = rel <= tol or P <= f_target
             return dict(x=x_cur, x_next=x_new, iters=k - 1, products=products, P=P, D=best_D, gap=gap,
-                        rel_gap=rel, status=STATUS_OK if rel <= tol else STATUS_NOCONV, restarts=restarts)
+                        rel_gap=rel, status=STATUS_OK if ok else STATUS_NOCONV, restarts=restarts)
         if restart and float((y - x_new) @ (x_new - x_cur)) > 0.0:
             t = 1.0
             beta = 0.0
@@ -140,7 +143,7 @@ def sufficient_decrease(Ad, d, L):
     return float(Ad @ Ad) <= L * float(d @ d)
 
 
-def fista_bt(A, b, tau, L0, eta, tol, max_iter, x0=None, max_trials=60, trace=False):
+def fista_bt(A, b, tau, L0, eta, tol, max_iter, x0=None, max_trials=60, trace=False, f_target=-math.inf):
     """FISTA with backtracking on L (Beck & Teboulle 2009, "A fast iterative shrinkage-
     thresholding algorithm for linear inverse problems", Sec. 4): the step constant of
     iteration k is the smallest L = eta^i L_{k-1} (i >= 0) for which the prox-gradient point
@@ -150,7 +153,7 @@ def fista_bt(A, b, tau, L0, eta, tol, max_iter, x0=None, max_trials=60, trace=Fa
     formed by linearity from A x_{k-1} and A x_{k-2}.
 
     Returns dict(x, iters, products, P, D, gap, rel_gap, status, L, backtracks) and, with
-    trace, hist = [(P(x_k), L_k)] per iteration."""
+    trace, hist = [(P(x_k), L_k)] per iteration.  f_target as for fista."""
     n = A.shape[1]
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)   # x_{k-1}
     x_prev = x.copy()                                                             # x_{k-2}
@@ -189,9 +192,10 @@ def fista_bt(A, b, tau, L0, eta, tol, max_iter, x0=None, max_trials=60, trace=Fa
         gap = P - best_D
         rel = gap / max(abs(P), TINY)
         hist.append((P, L))
-        if rel <= tol or k >= max_iter:
+        if rel <= tol or P <= f_target or k >= max_iter:
+            ok = rel <= tol or P <= f_target
             out = dict(x=x_new, iters=k, products=products, P=P, D=best_D, gap=gap, rel_gap=rel,
-                       status=STATUS_OK if rel <= tol else STATUS_NOCONV, L=L, backtracks=backtracks)
+                       status=STATUS_OK if ok else STATUS_NOCONV, L=L, backtracks=backtracks)
             if trace:
                 out["hist"] = hist
             return out

@@ -45,7 +45,7 @@ class SolveOpts(ctypes.Structure):
                 ("time_limit_s", ctypes.c_double), ("mu", ctypes.c_double), ("mu_min", ctypes.c_double),
                 ("mu_start", ctypes.c_double), ("pcg_rtol", ctypes.c_double), ("armijo", ctypes.c_double), ("ls_max", ctypes.c_int32),
                 ("pcg_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("accum", ctypes.c_int32)]
+                ("accum", ctypes.c_int32), ("f_target", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):

@@ -132,6 +132,7 @@ void l1ls_solve_opts_default(l1ls_solve_opts* o) {
     memset(o, 0, sizeof(*o));
     o->tau = 1.0;
     o->rel_gap_tol = 1e-6;
+    o->f_target = -INFINITY;
     o->max_iter = 100000;
     o->time_limit_s = 0.0;
     o->mu = 1e-5;

@@ -59,6 +59,7 @@ struct FistaState {
     // beta, 1/L and tau/L as float-float, refreshed with beta by the scalar step: the FP32
     // kernels read them instead of every thread converting (two FP64 divisions each)
     float beta_ff[2], invL_ff[2], thr_ff[2];
+    double f_target;   // stop once P(x_{k-1}) <= f_target (-inf: off)
 };
 
 // host and device: the float-float scalars of the state
@@ -171,7 +172,7 @@ __device__ void fista_finalize(FistaState* st, double amax, double l1_new, doubl
     if (!isfinite(P) || !isfinite(D)) {
         st->status = L1LS_ENUMERIC;
         st->stop = 1;
-    } else if (rel <= st->tol) {
+    } else if (rel <= st->tol || P <= st->f_target) {
         st->status = L1LS_OK;
         st->stop = 1;
     } else if (st->iter - 1 >= st->max_iter) {
@@ -843,6 +844,7 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     h.tau = o->tau;
     h.L = I->lipschitz;
     h.tol = o->rel_gap_tol;
+    h.f_target = o->f_target;
     h.max_iter = o->max_iter;
     h.t = 1.0;
     h.beta = 0.0;

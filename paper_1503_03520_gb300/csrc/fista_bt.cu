@@ -205,7 +205,7 @@ l1ls_status solve_bt(Inst* I, const l1ls_solve_opts* o, double L0, double eta, c
         std::swap(x, xn);
         std::swap(axp, ax);
         std::swap(ax, axn);
-        if (rel <= o->rel_gap_tol) break;
+        if (rel <= o->rel_gap_tol || P <= o->f_target) break;
         if (k >= o->max_iter) {
             status = L1LS_ENOCONV;
             break;

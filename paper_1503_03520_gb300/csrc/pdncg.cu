@@ -45,6 +45,7 @@ struct PdState {
     int32_t stop, status;
     int64_t iter, products, cg_total, ls_total;
     unsigned cnt[8];
+    double f_target;   // stop once P(x) <= f_target (-inf: off)
 };
 
 
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
         if (!isfinite(P) || !isfinite(D)) {
             st->status = L1LS_ENUMERIC;
             st->stop = 1;
-        } else if (rel <= st->tol) {
+        } else if (rel <= st->tol || P <= st->f_target) {
             st->status = L1LS_OK;
             st->stop = 1;
         } else if (st->iter >= st->max_newton) {
@@ -436,6 +437,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     memset(&h, 0, sizeof(h));
     h.tau = o->tau;
     h.tol = o->rel_gap_tol;
+    h.f_target = o->f_target;
     h.mu = o->mu_start > o->mu ? o->mu_start : o->mu;
     h.mu_target = o->mu;
     h.mu_min = o->mu_min;

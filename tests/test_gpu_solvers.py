@@ -259,3 +259,30 @@ def test_fista_backtracking_rejections(ctx):
     finally:
         inst.free()
         mf.free()
+
+
+def test_objective_target_matches_oracle(ctx):
+    """f_target (the paper's rule for ending its comparison solvers, Sec. 8.3): FISTA and FISTA
+    with backtracking stop at the same iteration as the oracle's; pdNCG stops below the target."""
+    params = W.params(m=4096, n=2048, right_stages=2, left_stages=1, kappa=100.0, value_dtype="f64", seed=23,
+                      xstar_frac=0.05)
+    ref = oracle_instance(params)
+    f0 = 0.5 * float(ref.b @ ref.b)             # the objective at x = 0
+    target = ref.f_star + 1e-4 * (f0 - ref.f_star)
+    inst = ctx.generate(params)
+    try:
+        runs = ((lambda: inst.solve_fista(tau=1.0, tol=0.0, max_iter=100000, f_target=target),
+                 lambda: solvers.fista(ref.A, ref.b, 1.0, ref.lipschitz, 0.0, 100000, f_target=target)),
+                (lambda: inst.solve_fista_bt(1e-2, 2.0, tau=1.0, tol=0.0, max_iter=100000, f_target=target),
+                 lambda: solvers.fista_bt(ref.A, ref.b, 1.0, 1e-2, 2.0, 0.0, 100000, f_target=target)))
+        for dev, orc in runs:
+            x, r = dev()
+            o = orc()
+            assert r["status"] == 0 and o["status"] == 0 and o["iters"] >= 5
+            assert r["iters"] == o["iters"] and r["f"] <= target, (r["iters"], o["iters"])
+            assert solvers.objective(ref.A, ref.b, 1.0, x) <= target * (1.0 + 1e-12)
+        x, r = inst.solve_pdncg(tau=1.0, tol=0.0, max_iter=200, f_target=target)
+        assert r["status"] == 0 and r["f"] <= target
+        assert solvers.objective(ref.A, ref.b, 1.0, x) <= target * (1.0 + 1e-12)
+    finally:
+        inst.free()

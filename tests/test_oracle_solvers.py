@@ -224,3 +224,18 @@ def test_planted_factor_error_in_the_backtracking_test_is_caught(monkeypatch):
     with np.errstate(all="ignore"):   # the planted test lets the iteration diverge
         r = solvers.fista_bt(inst.A, inst.b, 0.5, 0.3, 2.0, 1e-12, 10000)
     assert r["L"] != 0.3 * 2.0 * 2.0
+
+
+def test_objective_target_stops_at_the_first_iterate_below_it():
+    """f_target (the paper's rule for ending its comparison solvers, Sec. 8.3): the returned
+    iterate is the first certified one with P <= f_target, against a written-out trace."""
+    inst = generate(GenParams(m=256, n=128, seed=9, kappa=100.0, right_stages=2, xstar_frac=0.05))
+    A, b = inst.A, inst.b
+    trace = [solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, k)["P"] for k in range(0, 40)]
+    target = inst.f_star + 1e-2 * (trace[0] - inst.f_star)
+    first = next(k for k, P in enumerate(trace) if P <= target)
+    assert first >= 3
+    r = solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, 100000, f_target=target)
+    assert r["status"] == 0 and r["iters"] == first and r["P"] <= target
+    q = solvers.fista_bt(A, b, 1.0, inst.lipschitz, 2.0, 0.0, 100000, f_target=target)
+    assert q["status"] == 0 and q["P"] <= target and q["iters"] == first   # no increase of L: FISTA's iterates
