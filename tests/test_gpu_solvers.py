@@ -144,15 +144,18 @@ def test_fista_restart_matches_oracle(ctx, tau):
         inst.free()
 
 
-@pytest.mark.parametrize("restart,tau_exp", [(0, 0.5), (1, 2.0)])
-def test_fista_compensated_products_reach_small_gaps_at_small_tau(ctx, restart, tau_exp):
+@pytest.mark.parametrize("restart,tau_exp,w,dt", [(0, 0.5, 2, "f32"), (1, 2.0, 2, "f32"), (1, 1.0, 8, "f32"),
+                                                  (1, 1.0, 8, "bf16")])
+def test_fista_compensated_products_reach_small_gaps_at_small_tau(ctx, restart, tau_exp, w, dt):
     """accum = 1 (float-float products) against the oracle's FP64 FISTA on the stored FP32
     problem, down to a tau (1e-2 of lambda_max) where FP32 sums of the products stall above
-    the 1e-6 gap.  (Without the restart FISTA needs more than 1e5 iterations there.)"""
-    params = W.params(m=2000, n=1000, right_stages=2, left_stages=1, kappa=10.0 ** 2.2, seed=41, xstar_frac=0.02,
-                      value_dtype="f32")
+    the 1e-6 gap.  (Without the restart FISTA needs more than 1e5 iterations there.)  With
+    w = 8 a tile of 32 row pairs holds about 18 entries per pair, more than one shared-memory
+    stage: the staged float-float traversal then streams each tile in pieces."""
+    params = W.params(m=2000, n=1000, right_stages=w, left_stages=1, kappa=10.0 ** 2.2, seed=41, xstar_frac=0.02,
+                      value_dtype=dt)
     ref = oracle_instance(params)
-    A = stored_values(ref.A, "f32")
+    A = stored_values(ref.A, dt)
     b = ref.b.astype(np.float32).astype(np.float64)
     tau = 0.9 * ref.lam_max * 10.0 ** -tau_exp
     inst = ctx.generate(params)
@@ -284,5 +287,27 @@ def test_objective_target_matches_oracle(ctx):
         x, r = inst.solve_pdncg(tau=1.0, tol=0.0, max_iter=200, f_target=target)
         assert r["status"] == 0 and r["f"] <= target
         assert solvers.objective(ref.A, ref.b, 1.0, x) <= target * (1.0 + 1e-12)
+    finally:
+        inst.free()
+
+
+@pytest.mark.parametrize("factor", [1.0, 1.5])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_tau_at_or_above_lambda_max_gives_zero(ctx, factor, dt):
+    """The degenerate case of Eq. (prob1): for tau >= lambda_max = ||A^T b||_inf the minimiser is
+    x = 0, and at x = 0 the dual point theta = b is feasible with D = P = ||b||^2 / 2, so every
+    solver certifies the start without an iteration (lambda_max checked against the oracle)."""
+    params = W.params(m=1024, n=512, right_stages=2, kappa=30.0, seed=4, xstar_frac=0.05, value_dtype=dt)
+    ref = oracle_instance(params)
+    inst = ctx.generate(params)
+    try:
+        assert inst.info["lam_max"] == pytest.approx(float(np.abs(ref.A.T @ ref.b).max()), rel=1e-12)
+        # FP32 products: step just above the device's own lambda_max by their rounding
+        tau = factor * inst.info["lam_max"] * (1.0 if dt == "f64" else 1.0 + 1e-5)
+        for fn in (inst.solve_fista, inst.solve_pdncg):
+            x, r = fn(tau=tau, tol=1e-12, max_iter=100)
+            assert r["status"] == 0 and r["iters"] == 0 and not np.any(x)
+        x, r = inst.solve_fista_bt(1e-2, 2.0, tau=tau, tol=1e-12, max_iter=100)
+        assert r["status"] == 0 and not np.any(x)
     finally:
         inst.free()
