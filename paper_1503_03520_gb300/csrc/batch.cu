@@ -328,14 +328,12 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
     };
     auto epi = [&](int64_t j, ff g, const Ops& o) {
         // y = x_k + beta (x_k - x_{k-1}); x_{k+1} = S_{tau/L}(y + A^T r / L) (Sec. 8.1)
-        const ff y = ff_add_sloppy(o.x1, ff_mul(beta_f, ff_add_sloppy(o.x1, ff_neg(o.x0))));
-        const ff v = ff_add_sloppy(y, ff_mul(g, invL_f));
-        const ff xn = ff_soft_threshold(v, thr_f);
-        x0h[j] = xn.hi;
-        x0l[j] = xn.lo;
+        const FfStep f = ff_fista_step(o.x1, o.x0, g, beta_f, invL_f, thr_f);
+        x0h[j] = f.x.hi;
+        x0l[j] = f.x.lo;
         gmax = fmaxf(gmax, fabsf(g.hi));
-        sum2_add(l1, ff_abs(xn));
-        if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+        sum2_add(l1, f.mag);
+        if (rs) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, o.x1)));
     };
     if constexpr (EPL == 0)
         staged_tiles<false, V, BLOCK>(t0, 1, t1, cptr, cpair, cval, n, sm, ss, err, FFSum<false, V>{nullptr, nullptr, res},

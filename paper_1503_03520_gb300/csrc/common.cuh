@@ -201,11 +201,27 @@ __device__ __forceinline__ ff ff_from_double(double d) {   // FP64 pipe: use out
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ ff ff_abs(ff a) { return a.hi < 0.0f ? ff_neg(a) : a; }
-// shrinkage S_t(v) of Sec. 2 in float-float: sign(v) max(|v| - t, 0)
-__device__ __forceinline__ ff ff_soft_threshold(ff v, ff t) {
-    const ff a = ff_sub(ff_abs(v), t);
-    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
-    return v.hi < 0.0f ? ff_neg(a) : a;
+// FISTA's step in float-float for one coordinate (Sec. 8.1): y = x1 + beta (x1 - x0),
+// x = S_thr(y + g invL) with the shrinkage S_t(v) = sign(v) max(|v| - t, 0) of Sec. 2; also |x|
+// for the l1 norm.  Additions without the low-word TwoSum
+// (absolute errors of a few units of 2^-48 |x|: the iterate's own accuracy).
+struct FfStep {
+    ff y, x, mag;
+};
+__device__ __forceinline__ FfStep ff_fista_step(ff x1, ff x0, ff g, ff beta, ff invL, ff thr) {
+    FfStep o;
+    o.y = ff_add_sloppy(x1, ff_mul(beta, ff_add_sloppy(x1, ff_neg(x0))));
+    ff gl = two_prod(g.hi, invL.hi);
+    gl.lo = __fmaf_rn(g.hi, invL.lo, __fmaf_rn(g.lo, invL.hi, gl.lo));
+    const ff v = ff_add_sloppy(o.y, fast_two_sum(gl.hi, gl.lo));
+    const ff a = ff_add_sloppy(ff_abs(v), ff_neg(thr));
+    if (a.hi > 0.0f) {
+        o.mag = a;
+        o.x = v.hi < 0.0f ? ff_neg(a) : a;
+    } else {
+        o.mag = o.x = {0.0f, 0.0f};
+    }
+    return o;
 }
 
 }  // namespace l1ls

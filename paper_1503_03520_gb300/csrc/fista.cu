@@ -225,14 +225,12 @@ __global__ void __launch_bounds__(kBlock, RESTART ? 3 : L1LS_K2_MIN_BLOCKS) k_fi
                 return o;
             },
             [&](int64_t j, Acc g, const Ops& o) {
-                const ff y = ff_add_sloppy(o.x1, ff_mul(beta_f, ff_add_sloppy(o.x1, ff_neg(o.x0))));
-                const ff v = ff_add_sloppy(y, ff_mul(ff_from_float(g), invL_f));
-                const ff xn = ff_soft_threshold(v, thr_f);
-                a.xoh[j] = xn.hi;
-                a.xol[j] = xn.lo;
+                const FfStep f = ff_fista_step(o.x1, o.x0, ff_from_float(g), beta_f, invL_f, thr_f);
+                a.xoh[j] = f.x.hi;
+                a.xol[j] = f.x.lo;
                 gmax = fmaxf(gmax, fabsf(g));
-                sum2_add(l1, ff_abs(xn));
-                if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+                sum2_add(l1, f.mag);
+                if (rs) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, o.x1)));
             });
         p[0] = (double)gmax;
         p[1] = ff_to_double(l1);
@@ -385,14 +383,12 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2C_MIN_BLOCKS) k_fista_k2c(K2CAr
         return o;
     };
     auto epi = [&](int64_t j, ff g, const Ops& o) {
-        const ff y = ff_add_sloppy(o.x1, ff_mul(beta_f, ff_add_sloppy(o.x1, ff_neg(o.x0))));
-        const ff v = ff_add_sloppy(y, ff_mul(g, invL_f));
-        const ff xn = ff_soft_threshold(v, thr_f);
-        a.xoh[j] = xn.hi;
-        a.xol[j] = xn.lo;
+        const FfStep f = ff_fista_step(o.x1, o.x0, g, beta_f, invL_f, thr_f);
+        a.xoh[j] = f.x.hi;
+        a.xol[j] = f.x.lo;
         gmax = fmaxf(gmax, fabsf(g.hi));
-        sum2_add(l1, ff_abs(xn));
-        if (rs) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, o.x1)));
+        sum2_add(l1, f.mag);
+        if (rs) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, o.x1)));
     };
     if constexpr (PAIRED) {
         warp_pcsr<false, V>(a.ptr, a.pair, a.val, a.n, sm, &a.st->stage_err,
@@ -535,14 +531,12 @@ __global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
             if (j >= a.R.n) break;
             const float g = buf[kMfHalo + p];
             const ff x1 = {a.xch[j], a.xcl[j]}, x0 = {a.xoh[j], a.xol[j]};
-            const ff y = ff_add_sloppy(x1, ff_mul(beta_f, ff_add_sloppy(x1, ff_neg(x0))));
-            const ff v = ff_add_sloppy(y, ff_mul(ff_from_float(g), invL_f));
-            const ff xn = ff_soft_threshold(v, thr_f);
-            a.xoh[j] = xn.hi;
-            a.xol[j] = xn.lo;
+            const FfStep f = ff_fista_step(x1, x0, ff_from_float(g), beta_f, invL_f, thr_f);
+            a.xoh[j] = f.x.hi;
+            a.xol[j] = f.x.lo;
             gmax = fmaxf(gmax, fabsf(g));
-            sum2_add(l1, ff_abs(xn));
-            if (RESTART) sum2_add(rt, ff_mul(ff_sub(y, xn), ff_sub(xn, x1)));
+            sum2_add(l1, f.mag);
+            if (RESTART) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, x1)));
         }
         __syncthreads();   // the tile buffer is reloaded next
     }
