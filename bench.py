@@ -482,6 +482,39 @@ def sweep_form(l1, W, stored_log2n, mf_log2n, steps, warmup):
     return {"workload": "c2 recipe (m = 2n, ~8/col, FP32 values) at n = 2^k", "peak_gbs": peak, "runs": rows}
 
 
+def c1_form(l1, W):
+    """C1 (m = 2048, n = 1024, FP64, tol 1e-8): the latency-bound case.  FISTA through
+    l1ls_solve_fista (CUDA graphs of 32 iterations between host checks) against the same
+    iterations launched one kernel at a time (l1ls_fista_begin / step / end), and pdNCG."""
+    import torch
+    ctx = l1.Context(0)
+    inst = ctx.generate(W.C1)
+    out = {"workload": "c1: m=2048, n=1024, kappa 1e2, x* 5%, FP64 values, tau=1, gap 1e-8"}
+    for rep in range(2):          # the first round warms up (module load, graph build)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, r = inst.solve_fista(tau=1.0, tol=W.C1_TOL, max_iter=200000)
+        graph = time.perf_counter() - t
+        t = time.perf_counter()
+        inst.fista_begin(tau=1.0, tol=W.C1_TOL, max_iter=200000)
+        inst.fista_step(r["iters"] + 2)
+        _, g = inst.fista_end(allow=(4, 5))
+        stepped = time.perf_counter() - t
+        t = time.perf_counter()
+        _, q = inst.solve_pdncg(tau=1.0, tol=W.C1_TOL, max_iter=200)
+        pd = time.perf_counter() - t
+    out["fista_graphs"] = {"seconds": graph, "iters": r["iters"], "us_per_iter": 1e6 * graph / r["iters"],
+                           "rel_gap": r["rel_gap"], "status": r["status_name"]}
+    out["fista_kernel_by_kernel"] = {"seconds": stepped, "iters": g["iters"],
+                                     "us_per_iter": 1e6 * stepped / max(g["iters"], 1), "rel_gap": g["rel_gap"],
+                                     "status": g["status_name"]}
+    out["pdncg"] = {"seconds": pd, "iters": q["iters"], "cg_iters": q["cg_iters"], "rel_gap": q["rel_gap"],
+                    "status": q["status_name"]}
+    inst.free()
+    ctx.close()
+    return out
+
+
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
@@ -653,6 +686,7 @@ def run_ours(args):
         forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_slots)
     if rank == 0 and not args.no_forms:
         forms["fista_variants"] = variants_form(l1, W, args.variants_log2n, args.solve_limit)
+        forms["c1"] = c1_form(l1, W)
     if rank == 0 and args.sweep:
         forms = forms or {}
         forms["size_sweep"] = sweep_form(l1, W, range(20, 28), range(24, 30), 20, 3)
