@@ -44,6 +44,8 @@ int main(void) {
          sizeof(l1ls_result));
   printf("%zu %zu %zu\n", offsetof(l1ls_gen_params, right_stages), offsetof(l1ls_solve_opts, ls_max),
          offsetof(l1ls_result, status));
+  printf("%zu %zu %zu %zu\n", offsetof(l1ls_gen_params, gamma), offsetof(l1ls_solve_opts, f_target),
+         offsetof(l1ls_result, L), offsetof(l1ls_inst_info, device_bytes));
   return 0;
 }
 """
@@ -59,6 +61,8 @@ int main(void) {
     assert sizes[4] == l1.GenParams.right_stages.offset
     assert sizes[5] == l1.SolveOpts.ls_max.offset
     assert sizes[6] == l1.Result.status.offset
+    assert sizes[7:] == [l1.GenParams.gamma.offset, l1.SolveOpts.f_target.offset, l1.Result.L.offset,
+                         l1.InstInfo.device_bytes.offset]
 
 
 def test_defaults_without_gpu():
@@ -67,6 +71,22 @@ def test_defaults_without_gpu():
     assert p.m == 64 and p.n == 32 and p.value_dtype == 1 and p.right_stages == 1 and p.left_stages == 1
     o = l1.solve_opts(tol=1e-8)
     assert o.rel_gap_tol == 1e-8 and o.mu == 1e-5 and o.ls_max == 50 and o.pcg_rtol == 0.1
+    assert o.f_target == float("-inf") and o.restart == 0 and o.accum == 0
+    q = l1.gen_params({})
+    assert q.gamma == 100.0 and q.xstar_mode == 0 and q.sigma_mode == 0 and q.matrix_free == 0
+
+
+def test_footprint_is_monotone_without_gpu():
+    """The serving admission estimate (host arithmetic only): larger instances, more stages,
+    wider values and pdNCG's larger work space never lower it."""
+    import paper_1503_03520_gb300 as l1
+    base = {"m": 4096, "n": 2048, "right_stages": 2, "value_dtype": "f32"}
+    f0 = l1.footprint(base)
+    assert f0 > 0
+    assert l1.footprint(dict(base, m=8192, n=4096)) > f0
+    assert l1.footprint(dict(base, right_stages=4)) > f0
+    assert l1.footprint(dict(base, value_dtype="f64")) > f0
+    assert l1.footprint(base, "pdncg") >= f0
 
 
 def test_create_fails_cleanly_without_device():
