@@ -96,3 +96,30 @@ def test_create_fails_cleanly_without_device():
         pytest.skip("a GPU is present")
     with pytest.raises(l1.L1LSError):
         l1.Context(0)
+
+
+def test_binding_refuses_to_import_without_the_library():
+    """No fallback: a copy of the binding next to no libl1ls.so raises ImportError on import."""
+    import sys
+    src = os.path.join(ROOT, "paper_1503_03520_gb300", "__init__.py")
+    with tempfile.TemporaryDirectory() as d:
+        pkg = os.path.join(d, "l1ls_nolib")
+        os.makedirs(pkg)
+        with open(src) as f, open(os.path.join(pkg, "__init__.py"), "w") as g:
+            g.write(f.read())
+        r = subprocess.run([sys.executable, "-c", "import l1ls_nolib"], cwd=d, capture_output=True, text=True)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libl1ls.so is not built" in r.stderr
+
+
+def test_product_sources_do_not_reach_the_oracle():
+    """The package (binding, build script, CUDA sources) never names the oracle package."""
+    pkg = os.path.join(ROOT, "paper_1503_03520_gb300")
+    hits = []
+    for dirpath, _dirs, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, name)).read()
+                if re.search(r"\boracle\b", text):
+                    hits.append(name)
+    assert not hits, hits
