@@ -239,3 +239,42 @@ def test_objective_target_stops_at_the_first_iterate_below_it():
     assert r["status"] == 0 and r["iters"] == first and r["P"] <= target
     q = solvers.fista_bt(A, b, 1.0, inst.lipschitz, 2.0, 0.0, 100000, f_target=target)
     assert q["status"] == 0 and q["P"] <= target and q["iters"] == first   # no increase of L: FISTA's iterates
+
+
+def test_pseudo_huber_terms_against_high_precision():
+    """Eq. (pseudoHuber) term by term, sqrt(mu^2 + x^2) - mu and its difference along a step,
+    against 60-digit arithmetic: the oracle's cancellation-free forms keep a few ulps of
+    relative error down to x ~ 1e-12 mu and up to x ~ 1e12 mu (the plain formula loses all
+    digits at the small end)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    rng = np.random.default_rng(3)
+    for mu in (1e-5, 1e-2, 1.0):
+        x = np.concatenate([[0.0], mu * 10.0 ** rng.uniform(-12, 12, 64) * rng.choice([-1.0, 1.0], 64)])
+        d = rng.standard_normal(x.size) * np.maximum(np.abs(x), mu)
+        alpha = 0.37
+        got = solvers.psi_terms(x, mu)
+        got_diff = solvers.psi_diff_terms(x, d, alpha, mu)
+        for i in range(x.size):
+            ref = mpmath.sqrt(mpmath.mpf(mu) ** 2 + mpmath.mpf(x[i]) ** 2) - mu
+            assert abs(got[i] - float(ref)) <= 4e-16 * float(ref) + 1e-300, (mu, x[i])
+            xt = mpmath.mpf(x[i]) + mpmath.mpf(alpha * d[i])  # the oracle forms alpha*d in FP64 first
+            ref_d = (mpmath.sqrt(mpmath.mpf(mu) ** 2 + xt ** 2) - mpmath.sqrt(mpmath.mpf(mu) ** 2 + mpmath.mpf(x[i]) ** 2))
+            scale = abs(float(ref_d)) + 1e-300
+            # x + alpha*d is rounded once in FP64 before the quotient: an error of about one ulp
+            # of |x + alpha d| times the slope |xt| / sqrt(mu^2 + xt^2) <= 1
+            tol = 8e-16 * scale + 2.3e-16 * abs(x[i] + alpha * d[i])
+            assert abs(got_diff[i] - float(ref_d)) <= tol, (mu, x[i], d[i])
+
+
+def test_pseudo_huber_slope_and_curvature():
+    """The derivatives pdNCG builds on, checked by differences of the oracle's terms:
+    psi' = x / sqrt(mu^2 + x^2) and psi'' = mu^2 / (mu^2 + x^2)^{3/2} (Eq. (pseudoHuber))."""
+    mu, h = 0.5, 1e-4
+    x = np.array([-3.0, -0.4, 0.0, 0.1, 2.0])
+    w = np.sqrt(mu * mu + x * x)
+    slope = (solvers.psi_terms(x + h, mu) - solvers.psi_terms(x - h, mu)) / (2 * h)
+    assert np.allclose(slope, x / w, rtol=1e-7, atol=1e-10)
+    curv = (solvers.psi_diff_terms(x, np.ones_like(x), h, mu)
+            + solvers.psi_diff_terms(x, -np.ones_like(x), h, mu)) / (h * h)
+    assert np.allclose(curv, mu * mu / w ** 3, rtol=1e-6)
