@@ -44,3 +44,33 @@ def test_single_process_needs_no_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5, None) == 3.5
+
+
+def _bench(args, env_extra, timeout):
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=timeout)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """--impl reference under torchrun: ranks other than 0 exit 0 without work or output."""
+    r = _bench(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"],
+               {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, 60)
+    assert r.returncode == 0 and r.stdout == ""
+
+
+def test_reference_arm_json_line():
+    """Rank 0 prints one JSON line carrying the contract's keys, with the oracle as the arm."""
+    import json
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"], {"RANK": "0", "WORLD_SIZE": "1"}, 600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
