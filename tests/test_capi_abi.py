@@ -123,3 +123,49 @@ def test_product_sources_do_not_reach_the_oracle():
                 if re.search(r"\boracle\b", text):
                     hits.append(name)
     assert not hits, hits
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) for every function prototype in the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \t]*?\**)\s*\b(l1ls_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+        ps = [p.strip() for p in " ".join(params.split()).split(",") if p.strip()]
+        if ps == ["void"]:
+            ps = []
+        types = []
+        for p in ps:
+            p = re.sub(r"\bconst\b", "", p)
+            m = re.match(r"(.*?)([A-Za-z_]\w*)$", p.strip())       # drop the parameter name
+            t = (m.group(1) if m and ("*" in m.group(1) or m.group(1).strip()) else p)
+            types.append(" ".join(t.replace("*", " * ").split()))
+        out[name] = (" ".join(re.sub(r"\bconst\b", "", ret).replace("*", " * ").split()), types)
+    return out
+
+
+def test_binding_signatures_match_header_prototypes():
+    """Every header prototype has a ctypes signature in the binding with the same arity and the
+    same scalar widths, and every pointer parameter is a pointer on the Python side."""
+    import paper_1503_03520_gb300 as l1
+    scalars = {"double": ctypes.c_double, "int": ctypes.c_int, "int32_t": ctypes.c_int32,
+               "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64, "uint32_t": ctypes.c_uint32,
+               "size_t": ctypes.c_size_t, "l1ls_dtype": ctypes.c_int, "l1ls_status": ctypes.c_int}
+    protos = _prototypes()
+    assert len(protos) == len(_declared_functions())
+    for name, (ret, params) in protos.items():
+        assert name in l1._sig, name
+        res, args = l1._sig[name]
+        assert len(args) == len(params), (name, params)
+        if ret == "void":
+            assert res is None, name
+        elif ret == "char *":
+            assert res is ctypes.c_char_p, name
+        else:
+            assert ctypes.sizeof(res) == ctypes.sizeof(scalars[ret]), name
+        for t, a in zip(params, args):
+            if t.endswith("*"):
+                assert a is ctypes.c_void_p or issubclass(a, ctypes._Pointer), (name, t)
+            else:
+                assert ctypes.sizeof(a) == ctypes.sizeof(scalars[t]), (name, t)
+                assert issubclass(a, ctypes.c_double) == (t == "double"), (name, t)
