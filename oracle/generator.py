@@ -313,12 +313,12 @@ def _generate_igen(p: GenParams) -> Instance:
     A, R, L, sigma, perm = _square_part(p, n, m)
     xstar, S = osgen3(p, sigma) if p.xstar_mode == 2 else optimal_solution(p, n)
     g = subgradient(p, xstar, n)
-    # IGen step 3 with (A^T A)^{-1} = G (Sigma^T Sigma)^{-1} G^T (end of Sec. 4).
+    # IGen's e = tau A (A^T A)^{-1} g (Sec. 3.1) with (A^T A)^{-1} = G (Sigma^T Sigma)^{-1} G^T (end of Sec. 4).
     v = R.T @ g
     v = v / (sigma * sigma)
     v = R @ v
     e = tau * (A @ v)
-    # IGen step 4.
+    # IGen's b = A x* + e (Sec. 3.1).
     b = A @ xstar + e
     f_star = tau * np.abs(xstar).sum() + 0.5 * float(e @ e)
     lam_max = float(np.abs(A.T @ b).max())
@@ -327,7 +327,7 @@ def _generate_igen(p: GenParams) -> Instance:
 
 
 def n_columns(p: GenParams, e):
-    """IGen2 columns N_i (i = 0 .. n-m-1) and the scaled N~_i of step 4.
+    """IGen2 columns N_i (i = 0 .. n-m-1) and the scaled N~_i (Sec. 3.2).
 
     Column i takes the first ``n_nnz_per_col`` distinct rows among the candidates
     draw(NROW, i*4096 + t) mod m, t = 0, 1, ...; the value of the k-th accepted row is
@@ -376,7 +376,7 @@ def _generate_igen2(p: GenParams) -> Instance:
     B, R, L, sigma, perm = _square_part(p, m, m)
     xstar, S = optimal_solution(p, m)
     gB = subgradient(p, xstar, m)
-    # IGen2 step 3: e = tau B^{-T} g with B^{-T} = L Sigma^{-1} R^T.
+    # IGen2's e = tau B^{-T} g with B^{-T} = L Sigma^{-1} R^T.
     v = R.T @ gB
     v = v / sigma
     e = tau * (L @ v)

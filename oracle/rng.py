@@ -29,13 +29,13 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # Stream tags.  Each random quantity of the generator draws from its own stream.
 TAG_SIGMA = 1     # keys whose ranks assign the singular values to indices
 TAG_PERM = 2      # keys whose argsort is the row permutation P (P1 = P2 = P, Sec. 4.1)
-TAG_SUPPORT = 3   # keys whose s smallest select the support S of x* (OsGen step 2)
+TAG_SUPPORT = 3   # keys whose s smallest select the support S of x* (OsGen, Sec. 6)
 TAG_XVAL = 4      # magnitudes of the nonzeros of x*
 TAG_XSIGN = 5     # signs of the nonzeros of x*
-TAG_GOFF = 6      # subgradient entries g_i off the support (IGen step 2)
+TAG_GOFF = 6      # subgradient entries g_i off the support (IGen, Sec. 3.1)
 TAG_NROW = 7      # IGen2: row indices of the columns of N
 TAG_NVAL = 8      # IGen2: values of the columns of N
-TAG_XI = 9        # IGen2: the scalars xi of step 4
+TAG_XI = 9        # IGen2: the scalars xi (Sec. 3.2)
 
 
 def mix64(z):

@@ -153,7 +153,7 @@ __global__ void k_xstar_alt(int64_t n, int64_t nsup, const uint8_t* __restrict__
     if (i < nsup) g[i] = gi;
 }
 
-// Procedure OsGen3 (Sec. 6), step 2: x = gamma / sigma^2 (the stages of G follow)
+// Procedure OsGen3 (Sec. 6): the least-squares solution starts as gamma / sigma^2 (the stages of G follow)
 __global__ void k_gamma_over_sigma2(const double* __restrict__ sigma, int64_t n, double gamma, double* __restrict__ x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = __ddiv_rn(gamma, __dmul_rn(sigma[i], sigma[i]));
@@ -166,7 +166,7 @@ __global__ void k_abs_keys(const double* __restrict__ x, int64_t n, uint64_t* __
     keys[i] = (uint64_t)__double_as_longlong(a);
     if (a == 0.0) atomicAdd(zeros, 1);
 }
-// OsGen3, step 3: keep ranks z .. z+s1-1 (the s1 smallest nonzero) and n-s2 .. n-1 (largest)
+// OsGen3's selection (Sec. 6): keep ranks z .. z+s1-1 (the s1 smallest nonzero) and n-s2 .. n-1 (largest)
 __global__ void k_osgen3_flags(const uint32_t* __restrict__ order, int64_t n, const int* __restrict__ zeros, int64_t s1,
                                int64_t s2, uint8_t* __restrict__ flag) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,7 +174,7 @@ __global__ void k_osgen3_flags(const uint32_t* __restrict__ order, int64_t n, co
     const int64_t z = *zeros;
     if (r >= z && (r < z + s1 || r >= n - s2)) flag[order[r]] = 1;
 }
-// x* = x on the kept entries (step 4 zeroes the rest); g = sign(x*) there, U(-1,1) elsewhere
+// x* = x on the kept entries (zero elsewhere); g = sign(x*) there, U(-1,1) elsewhere
 __global__ void k_osgen3_xstar(const double* __restrict__ x, const uint8_t* __restrict__ flag, int64_t n, uint64_t seed,
                                int goff_mode, double* __restrict__ xstar, double* __restrict__ g) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -637,7 +637,7 @@ __global__ void k_colnorm2(const int32_t* __restrict__ ptr, const V* __restrict_
 constexpr int kNMax = 64;           // nonzeros per column of N
 constexpr int kNTries = 4096;       // candidate rows drawn per column before giving up
 
-// Column i of N~ (step 4): the first d distinct rows among draw(NROW, i*4096 + t) mod m
+// Column i of N~ (IGen2, Sec. 3.2): the first d distinct rows among draw(NROW, i*4096 + t) mod m
 // (t = 0, 1, ...), the k-th accepted row with value 2 U(draw(NVAL, i*d + k)) - 1; then, in
 // ascending row order, dot = N_i^T e and N~_i = xi_i tau / |dot| N_i (unscaled when dot = 0,
 // where |N~_i^T e| <= tau holds anyway).  e and b are read in the stored row order
@@ -1005,7 +1005,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         if (p->xstar_mode == 2) {
             // Procedure OsGen3 (Sec. 6): x = G gamma (Sigma^T Sigma)^{-1} 1 (G orthonormal), then
             // the s1 = s/2 smallest nonzero and s - s1 largest |x_i| kept (ties by index)
-            double* xo = vg;   // free until step 3 of IGen
+            double* xo = vg;   // free until IGen's e is formed
             uint64_t* keys = nullptr;
             int* zeros = nullptr;
             GEN_TRY(tmp.get(&keys, n));
@@ -1046,7 +1046,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         }
         GEN_CUDA(cudaGetLastError());
         }
-        // IGen step 3 by the route of Sec. 4: R^T g and R^T x* (T_w^T first).  IGen2 step 3,
+        // IGen's e (Sec. 3.1) by the route of Sec. 4: R^T g and R^T x* (T_w^T first).  IGen2's e,
         // e = tau B^{-T} g = tau L Sigma^{-1} R^T g, and b = B x* + e are the same expressions
         // on the square part (x* is zero on the columns of N).
         GEN_CUDA(cudaMemcpyAsync(vg, gvec, sizeof(double) * nsq, cudaMemcpyDeviceToDevice, st));
@@ -1146,7 +1146,7 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
         double *col_abs = nullptr, *col_atb = nullptr, *row_abs = nullptr, *red2 = nullptr;
         int* err_n = nullptr;
         if (igen2) {
-            // IGen2 step 4: the columns of N~ after those of B
+            // IGen2 (Sec. 3.2): the columns of N~ after those of B
             GEN_TRY(tmp.get(&col_abs, n - nsq));
             GEN_TRY(tmp.get(&col_atb, n - nsq));
             GEN_TRY(tmp.get(&err_n, 1));
