@@ -113,7 +113,7 @@ void l1ls_gen_params_default(l1ls_gen_params* p);
 typedef struct {
     uint64_t m, n, nnz, s;
     double f_star;        /* f_tau(x*) at tau = tau_gen                                       */
-    double lipschitz;     /* upper bound of lambda_max(A^T A) used by FISTA                    */
+    double lipschitz;     /* L >= lambda_max(A^T A), the step constant FISTA uses              */
     double lam_max;       /* ||A^T b||_inf: every tau >= lam_max has minimiser 0               */
     double tau_gen;
     int32_t value_dtype, right_stages, left_stages, igen2;

@@ -15,7 +15,7 @@ Follows, in the paper's order:
 * Procedure OsGen (Sec. 6): a random support S with |S| = s and random nonzeros.
 * Procedure IGen (Sec. 3.1): g in the subdifferential of ||x*||_1 (Eq. bd6),
                          e = tau A (A^T A)^{-1} g with (A^T A)^{-1} = G (Sigma^T Sigma)^{-1} G^T
-                         (end of Sec. 4: two products with G and a diagonal scaling),
+                         (end of Sec. 4: a diagonal scaling between a product with G^T and one with G),
                          b = A x* + e.
 * Procedure IGen2 (Sec. 3.2): for m < n, A = [B, N~] with B square (built as above with
                          n = m), e = tau B^{-T} g, N~_i = xi tau / |N_i^T e| N_i.
@@ -94,7 +94,7 @@ class Instance:
     Lmat: sp.csr_matrix               # left factor (m x m)
     f_star: float                     # f_tau(x*) at tau = params.tau
     lam_max: float                    # ||A^T b||_inf
-    lipschitz: float                  # an upper bound of lambda_max(A^T A)
+    lipschitz: float                  # L >= lambda_max(A^T A)
     extra: dict = field(default_factory=dict)
 
 

@@ -11,7 +11,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   y = x = x* it is zero (Sec. 3.1: A^T e = tau g).  rel_gap = gap / max(P, tiny).
 * FISTA (Sec. 8.1; Beck & Teboulle): x_k = S_{tau/L}(y_k - A^T(A y_k - b) / L),
   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, y_{k+1} = x_k + ((t_k - 1)/t_{k+1})(x_k - x_{k-1}),
-  y_1 = x_0, t_1 = 1, L an upper bound of lambda_max(A^T A) (fixed, not TFOCS' dynamic L).
+  y_1 = x_0, t_1 = 1, L >= lambda_max(A^T A) (fixed, not TFOCS' dynamic L).
   Iteration k evaluates A x_{k-1} (which certifies x_{k-1} through P(x_{k-1})) and
   A^T r at y_k (which supplies a dual point); x_{k-1} is returned as soon as
   P(x_{k-1}) - max_{j<=k} D(y_j) is within the tolerance.  A y_k is formed by linearity
