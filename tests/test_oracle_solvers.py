@@ -278,3 +278,16 @@ def test_pseudo_huber_slope_and_curvature():
     curv = (solvers.psi_diff_terms(x, np.ones_like(x), h, mu)
             + solvers.psi_diff_terms(x, -np.ones_like(x), h, mu)) / (h * h)
     assert np.allclose(curv, mu * mu / w ** 3, rtol=1e-6)
+
+
+@pytest.mark.parametrize("tau", [0.05, 1.4, 1.9, 2.5])
+def test_brute_force_on_orthonormal_columns_is_shrinkage(tau):
+    """A with orthonormal columns (a random Q of a QR factorisation, m = 9, n = 6): the unique
+    minimiser of Eq. (prob1) is the soft threshold S_tau(A^T b), independent of the generator."""
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(rng.standard_normal((9, 6)))
+    b = rng.standard_normal(9) * 1.5
+    xb, fb = brute_force(Q, b, tau)
+    xs = solvers.soft_threshold(Q.T @ b, tau)
+    assert np.allclose(xb, xs, atol=1e-12)
+    assert math.isclose(fb, solvers.objective(Q, b, tau, xs), rel_tol=1e-12)
