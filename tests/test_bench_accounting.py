@@ -1,0 +1,66 @@
+"""Host-side accounting of bench.py: the algorithmic bytes of the FISTA iteration on the C2
+recipe (m = 2n, one left rotation so rows pair up, nnz = 8n - 8) and their agreement with the
+committed ncu traffic summary."""
+
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _counted(m, n, nnz):
+    """K1 / K2 bytes counted array by array (FP32 values and vectors, int32 indices and
+    pointers, float-float iterates): each orientation of the paired storage holds nnz / 2
+    indices and nnz values."""
+    idx, val = 4 * (nnz // 2), 4 * nnz
+    k1 = idx + val + 4 * (m // 2 + 1) + 4 * n + 4 * m * 4      # row pairs; x; A x_{k-2}, b, A x_{k-1}, r
+    k2 = idx + val + 4 * (n + 1) + 4 * m + 3 * 8 * n           # columns; r; x_{k-1}, x_{k-2}, x_k
+    return k1, k2
+
+
+def test_c2_bytes_per_iteration():
+    n = 2 ** 24
+    assert bench.bytes_per_iteration(2 * n, n, 8 * n - 8) == _counted(2 * n, n, 8 * n - 8)
+    k1, k2 = bench.bytes_per_iteration(2 * n, n, 8 * n - 8)
+    assert round(k1 / 1e9, 3) == 1.476 and round(k2 / 1e9, 3) == 1.409
+
+
+def test_unpaired_storage_counts_one_index_per_entry():
+    m, n, nnz = 1000, 500, 3000
+    k1, k2 = bench.bytes_per_iteration(m, n, nnz, paired=False)
+    assert k1 == nnz * 8 + 4 * (m + 1) + 4 * n + 16 * m
+    assert k2 == nnz * 8 + 4 * (n + 1) + 4 * m + 24 * n
+
+
+def test_traffic_summary_uses_the_same_accounting():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        d = json.load(f)
+    n = 2 ** 24
+    k1, k2 = bench.bytes_per_iteration(2 * n, n, 8 * n - 8)
+    assert d["algorithmic_bytes_per_launch"] == {"k_fista_k1": k1, "k_fista_k2": k2}
+    h1, h2 = bench.bytes_per_iteration(2 ** 24, 2 ** 23, 8 * 2 ** 23 - 8)
+    assert d["n23"]["k_fista_k1"]["algorithmic"] == h1 and d["n23"]["k_fista_k2"]["algorithmic"] == h2
+    for k in ("k_fista_k1", "k_fista_k2"):
+        assert d["bytes_per_launch"][k] == 2 * d["n23"][k]["dram"]      # scaled by the units processed
+        assert 0.8 <= d["n23"][k]["dram"] / d["n23"][k]["algorithmic"] <= 1.2
+
+
+def test_measured_peak_is_read_from_the_peaks_file():
+    peak, kind = bench.measured_hbm_peak()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert kind == "measured" and peak > 1000
+    else:
+        assert kind == "fallback"
+
+
+def test_matrix_free_accounting_matches_the_summary():
+    """K1 = 20n + 16m and K2 = 32n bytes (the factors' O(m + n) vectors only)."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        d = json.load(f)["matrix_free_n23"]
+    n = 2 ** 23
+    assert bench.mf_bytes_per_iteration(2 * n, n) == (20 * n + 32 * n, 32 * n)
+    assert (d["k1_algorithmic"], d["k2_algorithmic"]) == bench.mf_bytes_per_iteration(2 * n, n)
