@@ -64,3 +64,34 @@ def test_matrix_free_accounting_matches_the_summary():
     n = 2 ** 23
     assert bench.mf_bytes_per_iteration(2 * n, n) == (20 * n + 32 * n, 32 * n)
     assert (d["k1_algorithmic"], d["k2_algorithmic"]) == bench.mf_bytes_per_iteration(2 * n, n)
+
+
+def test_clock_sampler_parses_samples_and_reasons(tmp_path, monkeypatch):
+    """The clocks record from a fake nvidia-smi: median SM clock under load, the maximum, and
+    the throttle reasons seen Active in any sample."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 1965, 2070, 1101.5, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 1980, 2070, 1190.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 1950, 2070, 1188.2, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo 'garbled line'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    for _ in range(100):
+        if len(s.lines) >= 4:
+            break
+        time.sleep(0.05)
+    rec = s.stop()
+    assert rec["sm_mhz"] == 1965.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
