@@ -15,6 +15,7 @@ import numpy as np
 
 
 def brute_force(A, b, tau, slack=1e-9):
+    """Minimiser of Eq. (prob1) and its objective, by enumeration of all sign patterns."""
     A = np.asarray(A.todense() if hasattr(A, "todense") else A, dtype=np.float64)
     m, n = A.shape
     if n > 12:

@@ -74,7 +74,8 @@ class GenParams:
 
     @classmethod
     def from_dict(cls, d):
-        """Build from a parameter dict, ignoring keys that only the CUDA path reads."""
+        """Build from a parameter dict (the generator parameters of Sec. 3-6), ignoring keys
+        that only the CUDA path reads."""
         names = set(cls.__dataclass_fields__)
         return cls(**{k: v for k, v in d.items() if k in names})
 
@@ -99,13 +100,15 @@ class Instance:
 
 
 def support_size(p: GenParams) -> int:
-    """s = floor(frac * n + 0.5), clamped to [1, min(m, n)]."""
+    """Number s of nonzeros of x* (Procedure OsGen, Sec. 6, takes s as given):
+    s = floor(frac * n + 0.5), clamped to [1, min(m, n)]."""
     s = int(math.floor(p.xstar_frac * p.n + 0.5))
     return max(1, min(s, p.m, p.n))
 
 
 def angles(p: GenParams):
-    """(c, s, c~, s~) of the right and left rotations, by the host libm."""
+    """(c, s, c~, s~) of the right and left rotations (angles theta and vartheta of the Givens
+    matrices of Sec. 4 and 4.1), by the host libm."""
     vt = p.theta if math.isnan(p.vartheta) else p.vartheta
     return math.cos(p.theta), math.sin(p.theta), math.cos(vt), math.sin(vt)
 
@@ -121,13 +124,14 @@ def givens(size, i, j, c, s):
 
 
 def stage_pairs(size, first):
-    """Planes of one stage: (first, first+1), (first+2, first+3), ... inside [0, size)."""
+    """Planes of one stage (Sec. 4.1 for G, Sec. 4.2 for G2): (first, first+1),
+    (first+2, first+3), ... inside [0, size)."""
     i = np.arange(first, size - 1, 2, dtype=np.int64)
     return i, i + 1
 
 
 def stage_matrix(size, first, c, s):
-    """Composition of the rotations of one stage.
+    """Composition of the rotations of one stage (G of Sec. 4.1, G2 of Sec. 4.2).
 
     The rotations of a stage act on disjoint planes, so their product is the block
     diagonal matrix with a 2x2 block [[c, -s], [s, c]] on each plane and 1 on every
@@ -144,12 +148,14 @@ def stage_matrix(size, first, c, s):
 
 
 def stage_first(k):
-    """Kind of the k-th stage (1-based): odd stages are G (first plane 0), even are G2."""
+    """Kind of the k-th stage (1-based, Sec. 4.2 alternates them): odd stages are G (first
+    plane 0), even are G2."""
     return (k - 1) % 2
 
 
 def right_factor(size, stages, c, s):
-    """R = T_w ... T_2 T_1 (T_1 applied first to a vector)."""
+    """Right singular vectors of Eq. (bd8): R = T_w ... T_2 T_1 (T_1 applied first to a
+    vector), the products of stages of Sec. 4.2."""
     R = sp.identity(size, format="csr")
     for k in range(1, stages + 1):
         R = stage_matrix(size, stage_first(k), c, s) @ R
@@ -157,13 +163,14 @@ def right_factor(size, stages, c, s):
 
 
 def perm_matrix(perm):
-    """Permutation matrix with (P v)_i = v_{perm[i]}."""
+    """The random permutation matrix P of Sec. 4.1, with (P v)_i = v_{perm[i]}."""
     size = len(perm)
     return sp.csr_matrix((np.ones(size), (np.arange(size), perm)), shape=(size, size))
 
 
 def left_factor(size, stages, perm, ct, st):
-    """L = P (T~_l ... T~_1) P, or the identity when there is no left stage."""
+    """Left singular vectors of Eq. (bd8): L = P (T~_l ... T~_1) P (Sec. 4.1), or the
+    identity when there is no left stage (the A = Sigma G^T of Sec. 8)."""
     if stages == 0:
         return sp.identity(size, format="csr")
     Gt = right_factor(size, stages, ct, st)
@@ -210,7 +217,9 @@ def sigma_of(p: GenParams, count):
 
 
 def singular_values(seed, count, kappa):
-    """sigma_i = kappa^(-rank_i/(count-1)), ranks from the argsort of random keys."""
+    """Diagonal of Sigma (Sec. 4) with kappa(A) = sigma_max / sigma_min = kappa: the paper
+    fixes the condition number, not the spacing; here sigma_i = kappa^(-rank_i/(count-1)),
+    ranks from the argsort of random keys."""
     if count == 1:
         return np.ones(1)
     keys = rng.draws(seed, rng.TAG_SIGMA, count)
@@ -221,7 +230,8 @@ def singular_values(seed, count, kappa):
 
 
 def row_permutation(seed, m):
-    """perm = stable argsort of random keys; P[i, perm[i]] = 1."""
+    """The random row permutation of Sec. 4.1: perm = stable argsort of random keys;
+    P[i, perm[i]] = 1."""
     return np.argsort(rng.draws(seed, rng.TAG_PERM, m), kind="stable").astype(np.int64)
 
 
@@ -406,6 +416,8 @@ class Factors:
 
 
 def make_factors(p: GenParams) -> Factors:
+    """The factors of Eq. (bd8) and the x*, g of Procedures OsGen / OsGen3 (Sec. 6) and IGen
+    (Eq. bd6), without assembling A (m >= n)."""
     if p.m < p.n:
         raise ValueError("make_factors covers IGen (m >= n)")
     sigma = sigma_of(p, p.n)

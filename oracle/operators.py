@@ -16,7 +16,8 @@ from .generator import angles, stage_first, stage_pairs
 
 
 def rotate(v, first, c, s):
-    """v <- T v for one stage: (v_i, v_j) <- (c v_i - s v_j, s v_i + c v_j)."""
+    """v <- T v for one stage (the rotation step of Algorithms MvPA / MvPAt, Sec. 4):
+    (v_i, v_j) <- (c v_i - s v_j, s v_i + c v_j)."""
     i, j = stage_pairs(len(v), first)
     vi = v[i].copy()
     vj = v[j].copy()
@@ -26,7 +27,8 @@ def rotate(v, first, c, s):
 
 
 def rotate_t(v, first, c, s):
-    """v <- T^T v for one stage: (v_i, v_j) <- (c v_i + s v_j, -s v_i + c v_j)."""
+    """v <- T^T v for one stage (Algorithms MvPA / MvPAt, Sec. 4):
+    (v_i, v_j) <- (c v_i + s v_j, -s v_i + c v_j)."""
     i, j = stage_pairs(len(v), first)
     vi = v[i].copy()
     vj = v[j].copy()

@@ -39,7 +39,7 @@ TAG_XI = 9        # IGen2: the scalars xi (Sec. 3.2)
 
 
 def mix64(z):
-    """SplitMix64 finaliser applied elementwise to a uint64 array (wraps mod 2^64)."""
+    """SplitMix64 (Steele, Lea & Flood 2014) finaliser applied elementwise to a uint64 array (wraps mod 2^64)."""
     z = np.asarray(z, dtype=np.uint64)
     with np.errstate(over="ignore"):
         z = (z ^ (z >> np.uint64(30))) * _M1
@@ -48,7 +48,8 @@ def mix64(z):
 
 
 def splitmix_output(state0, index):
-    """The ``index``-th output (0-based) of SplitMix64 started at ``state0``."""
+    """The ``index``-th output (0-based) of SplitMix64 (Steele, Lea & Flood 2014) started at
+    ``state0``: the state advances by the golden-ratio increment, then the finaliser."""
     idx = np.asarray(index, dtype=np.uint64)
     with np.errstate(over="ignore"):
         state = np.uint64(state0) + (idx + np.uint64(1)) * GAMMA
@@ -56,7 +57,8 @@ def splitmix_output(state0, index):
 
 
 def stream_key(seed, tag):
-    """Starting state of stream ``tag`` of ``seed``."""
+    """Starting state of stream ``tag`` of ``seed`` (one stream per quantity the paper draws at
+    random without naming a generator: keys of Sec. 4.1 and 6, magnitudes, signs)."""
     return np.uint64(splitmix_output(np.uint64(seed), np.array([tag], dtype=np.uint64))[0])
 
 
@@ -67,6 +69,7 @@ def draws(seed, tag, count, start=0):
 
 
 def unit_uniform(u):
-    """Map uint64 draws to doubles in [0, 1) with 53 random bits."""
+    """Map uint64 draws to doubles in [0, 1) with 53 random bits (the uniform draws of
+    Sec. 3-6)."""
     u = np.asarray(u, dtype=np.uint64)
     return (u >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)

@@ -63,14 +63,17 @@ def objective(A, b, tau, x):
 
 
 def dual_value(b, r, atr, tau):
-    """D(theta) at theta = s r, s = min(1, tau/||A^T r||_inf)."""
+    """Lagrange dual of Eq. (prob1), D(theta) = b^T theta - 1/2 ||theta||^2 over
+    ||A^T theta||_inf <= tau, at theta = s r, s = min(1, tau/||A^T r||_inf).  The paper states
+    no stopping test; this certificate is the reading used on both sides."""
     amax = float(np.abs(atr).max()) if len(atr) else 0.0
     s = 1.0 if amax <= tau else tau / amax
     return s * float(b @ r) - 0.5 * s * s * float(r @ r)
 
 
 def certificate(A, b, tau, x):
-    """(P, D, gap, rel_gap) at x with the dual point built from r = b - A x."""
+    """(P, D, gap, rel_gap) at x with the dual point built from r = b - A x; zero gap exactly
+    at the minimisers of Eq. (prob1), whose optimality condition is Eq. (bd7)."""
     r = b - A @ x
     atr = A.T @ r
     P = tau * np.abs(x).sum() + 0.5 * float(r @ r)
@@ -135,7 +138,7 @@ def fista(A, b, tau, L, tol, max_iter, x0=None, restart=False, f_target=-math.in
 
 
 def sufficient_decrease(Ad, d, L):
-    """The backtracking test of FISTA with backtracking for the quadratic smooth part
+    """The backtracking test of FISTA with backtracking (Beck & Teboulle 2009) for the quadratic smooth part
     h(x) = 1/2 ||A x - b||^2: h(x) <= h(y) + grad h(y)^T d + L/2 ||d||^2 with d = x - y.  Since
     h(y + d) - h(y) - grad h(y)^T d = 1/2 ||A d||^2 exactly, the test is ||A d||^2 <= L ||d||^2;
     evaluated in this form it has no cancellation (the difference of the two objective values
@@ -213,14 +216,15 @@ def psi_terms(x, mu):
 
 
 def psi_diff_terms(x, d, alpha, mu):
-    """Per-coordinate psi(x + alpha d) - psi(x), cancellation-free."""
+    """Per-coordinate psi(x + alpha d) - psi(x) of Eq. (pseudoHuber), cancellation-free."""
     xt = x + alpha * d
     return (alpha * d) * (x + xt) / (np.sqrt(mu * mu + xt * xt) + np.sqrt(mu * mu + x * x))
 
 
 def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, pcg_max=1000,
           ls_max=50, armijo=1e-4, stall=0.5, x0=None, mu_start=1.0):
-    """Primal-dual Newton-CG with the certificate above.
+    """Primal-dual Newton-CG (pdNCG, Sec. 8.1) on f_tau^mu of Eq. (prob2) with the pseudo-Huber
+    smoothing of Eq. (pseudoHuber), stopped by the certificate above.
 
     Returns dict(x, iters, products, cg_iters, ls_trials, P, D, gap, rel_gap, mu, status).
     """
