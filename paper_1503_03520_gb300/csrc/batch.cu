@@ -356,6 +356,8 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
 #ifndef L1LS_BATCH_WARPS_PER_SM
 #define L1LS_BATCH_WARPS_PER_SM 24
 #endif
+// The tau path of Sec. 8.8 for a batch of instances: FISTA (Sec. 8.1) with warm starts along
+// each path, all instances in one persistent kernel.
 template <int BLOCK, int EPL, class V>
 __global__ void __launch_bounds__(BLOCK, L1LS_BATCH_WARPS_PER_SM * 32 / BLOCK) k_batch(BArgs a) {
     using Smem = typename std::conditional<EPL == 0, PairedSmem<V, BLOCK>, CompSmem<BLOCK>>::type;

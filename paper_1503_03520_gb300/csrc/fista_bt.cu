@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kBtBlock = 256;
 
+// FISTA with backtracking (Beck & Teboulle 2009), one iteration in four kernels.
 // r = b - A y with A y = A x + beta (A x - A x_prev); writes A y and r; sums b.r, r.r
 __global__ void __launch_bounds__(kBtBlock) k_bt_residual(const double* __restrict__ ax, const double* __restrict__ axp,
                                                         const double* __restrict__ b, double beta, int64_t m,

@@ -75,6 +75,7 @@ __global__ void k_keys(uint64_t seed, uint64_t tag, int64_t count, uint64_t* __r
     if (i < count) keys[i] = sm_output(sm_stream(seed, tag), (uint64_t)i);
 }
 
+// Sigma of Sec. 4: sigma_i = kappa^(-rank_i/(n-1)) (kappa(A) = kappa, sigma_max = 1)
 __global__ void k_sigma(const uint32_t* __restrict__ order, int64_t count, double logk, double* __restrict__ sigma) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= count) return;
@@ -98,6 +99,7 @@ __global__ void k_identity_perm(int64_t count, int32_t* __restrict__ perm, int32
     perm_inv[i] = (int32_t)i;
 }
 
+// support S of x* (Procedure OsGen, Sec. 6): the s smallest keys
 __global__ void k_support(const uint32_t* __restrict__ order, int64_t s, uint8_t* __restrict__ flag) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r < s) flag[order[r]] = 1;
@@ -190,7 +192,7 @@ __global__ void k_osgen3_xstar(const double* __restrict__ x, const uint8_t* __re
     g[i] = gi;
 }
 
-// one stage on a vector, in place: transpose ? T^T v : T v
+// one stage (Sec. 4.1-4.2) on a vector, in place: transpose ? T^T v : T v
 __global__ void k_stage(double* __restrict__ v, int64_t n, int first, double c, double s, int transpose) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = first + 2 * t;
@@ -205,7 +207,7 @@ __global__ void k_stage(double* __restrict__ v, int64_t n, int first, double c, 
     }
 }
 
-// z = Sigma^{-1}-scaled vectors: ze = tau vg / sigma, zb = sigma vx + tau vg / sigma (length n)
+// IGen's e and b (Sec. 3.1) by the route of Sec. 4, Sigma step: ze = tau vg / sigma, zb = sigma vx + tau vg / sigma (length n)
 __global__ void k_scale(const double* __restrict__ vg, const double* __restrict__ vx, const double* __restrict__ sigma,
                         int64_t n, double tau, double* __restrict__ ze, double* __restrict__ zb,
                         double* __restrict__ u_lam) {
@@ -219,7 +221,8 @@ __global__ void k_scale(const double* __restrict__ vg, const double* __restrict_
     u_lam[k] = __dadd_rn(__dmul_rn(__dmul_rn(sg, sg), vx[k]), __dmul_rn(tau, vg[k]));
 }
 
-// ehat = G~ P2 [ze; 0], bhat = G~ P2 [zb; 0] in the relabelled row order
+// left factor of Eq. (bd8) (Sec. 4.1): ehat = G~ P2 [ze; 0], bhat = G~ P2 [zb; 0] in the
+// relabelled row order
 __global__ void k_left(const double* __restrict__ ze, const double* __restrict__ zb, const int32_t* __restrict__ perm,
                        Geo g, double* __restrict__ ehat, double* __restrict__ bhat) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

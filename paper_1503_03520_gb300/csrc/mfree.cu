@@ -8,6 +8,7 @@ namespace l1ls {
 
 namespace {
 
+// Algorithms MvPA / MvPAt (Sec. 4): the stages of the right factor applied to a vector
 __global__ void __launch_bounds__(kMfThreads) k_mf_rt(const float* __restrict__ x, const float* __restrict__ sigma,
                                                       MfRight R, float* __restrict__ z) {
     __shared__ float buf[kMfLen];
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(kMfThreads) k_mf_r(const float* __restrict__ z
     }
 }
 
-// rows of A x: row h (stored order) written to y[map[h]] (map NULL: y[h])
+// rows of A x (MvPA, Sec. 4: the left factor's rotations): row h (stored order) written to y[map[h]] (map NULL: y[h])
 __global__ void k_mf_rows(MfLeft L, const float* __restrict__ z, const int32_t* __restrict__ map, float* __restrict__ y) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t units = L.left ? L.m / 2 : L.m;

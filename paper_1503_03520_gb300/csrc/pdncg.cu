@@ -51,7 +51,7 @@ struct PdState {
 
 __device__ __forceinline__ bool halted(const PdState* st) { return *(volatile const int32_t*)&st->stop != 0; }
 
-// ---- N1: r = b - A x --------------------------------------------------------------------
+// ---- N1 (Newton step of pdNCG, Sec. 8.1): r = b - A x --------------------------------------------------------------------
 template <class V, class Vec, class X, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                      const V* __restrict__ val, const X* __restrict__ x,
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ pt
     }
 }
 
-// ---- C2: Hp = h p + A^T Ap, alpha ------------------------------------------------------
+// ---- C2 (PCG product, Sec. 8.1): Hp = h p + A^T Ap, alpha ------------------------------------------------------
 template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                   const V* __restrict__ val, const Vec* __restrict__ ap,
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_pupd(double* __restrict__ p, PX* 
     }
 }
 
-// ---- LT: Armijo trials -------------------------------------------------------------------
+// ---- LT: Armijo trials on f_tau^mu of Eq. (prob2) -------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ x, const double* __restrict__ d,
                                                      const double* __restrict__ grad, int64_t n, double* partials,
                                                      PdState* st) {

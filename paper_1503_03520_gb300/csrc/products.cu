@@ -14,6 +14,7 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// y = A x (COLS = false) or x = A^T y (COLS = true) on the assembled A of Eq. (bd8)
 template <class V, class X, class Acc, bool PAIRED, bool COLS>
 __global__ void __launch_bounds__(kBlock) k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                  const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
