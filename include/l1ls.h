@@ -166,17 +166,20 @@ l1ls_status l1ls_matvec(const l1ls_inst* inst, const void* x, l1ls_dtype vec_dty
 /* x = A^T y (Algorithm MvPAt).  y: m entries, x: n entries, as for l1ls_matvec. */
 l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dtype, void* x, void* stream);
 
-/* x = A^T y like l1ls_rmatvec, for callers that cannot allocate device memory: code that runs
- * while a CUDA graph is being captured, real-time loops that must not block on the
- * device-wide synchronisation cudaMalloc / cudaFree may imply, hosts that give the library a
- * fixed memory budget.  (The paper has no counterpart; this is an interface of this library.)
- *   y, x: DEVICE pointers only (m and n entries of vec_dtype, L1LS_F64 or L1LS_F32).
+/* x = A^T y like l1ls_rmatvec, for callers that cannot allocate device memory: real-time
+ * loops that must not stall on the device-wide synchronisation cudaMalloc / cudaFree may
+ * imply, and host applications that own all device memory (a fixed budget handed out up
+ * front, libraries not allowed to allocate).  (The paper has no counterpart; this is an
+ * interface of this library.)
+ *   y, x: DEVICE pointers only (m and n entries of vec_dtype, L1LS_F64 or L1LS_F32); a host
+ *   pointer is refused with L1LS_EINVAL before anything is enqueued.
  *   The one m-vector of scratch the product needs lives in a fixed array compiled into the
  *   library: 2^20 doubles (8 MiB) held by every GPU that loads the library until the process
  *   exits.  Instances with m > 2^20 are rejected with L1LS_EINVAL.
  *   No cudaMalloc, cudaFree or other allocating call is made.  The first call on a device
  *   looks up the array's device address (cudaGetSymbolAddress) with that device current;
- *   make that first call before any stream capture.
+ *   make that first call before any stream capture.  The address is kept for the life of the
+ *   process, which assumes the device's primary context is never reset (cudaDeviceReset).
  *   All calls share the array and it keeps the last call's contents (every entry used is
  *   written before it is read, so nothing needs clearing).  Calls whose work overlaps on the
  *   GPU (different streams, or different threads) race on the array: order them.
@@ -311,7 +314,6 @@ l1ls_status l1ls_batch_get_stats(const l1ls_batch* batch, int64_t* steps, double
 l1ls_status l1ls_batch_barrier_selftest(l1ls_batch* batch, uint32_t max_polls, double* seconds);
 l1ls_status l1ls_batch_free(l1ls_batch* batch);
 
-/* Thread-local message describing the last non-OK status returned on this thread. */
 /* Serving: solve requests admitted by device-memory footprint and run concurrently.
  * A request is (generator parameters, solver options, method): the instance is generated on
  * the device, solved to o->rel_gap_tol at o->tau, and freed; the caller receives x (n
@@ -353,6 +355,7 @@ l1ls_status l1ls_poll(l1ls_ctx* ctx, uint64_t ticket, int wait_ms, l1ls_result* 
 l1ls_status l1ls_cancel(l1ls_ctx* ctx, uint64_t ticket);
 l1ls_status l1ls_serve_stats(l1ls_ctx* ctx, l1ls_serve_info* info);
 
+/* Thread-local message describing the last non-OK status returned on this thread. */
 const char* l1ls_last_error(void);
 
 /* Library version string. */

@@ -221,6 +221,21 @@ def psi_diff_terms(x, d, alpha, mu):
     return (alpha * d) * (x + xt) / (np.sqrt(mu * mu + xt * xt) + np.sqrt(mu * mu + x * x))
 
 
+def pd_curvature(x, gd, mu, tau):
+    """Diagonal of the primal-dual Newton matrix, tau (1 - g_i x_i / w_i) / w_i with
+    w_i = sqrt(mu^2 + x_i^2): the Newton system of the conditions tau g + A^T(Ax - b) = 0 and
+    g_i w_i = x_i (pdNCG, Sec. 8.1) after eliminating dg.  Returns (h, w)."""
+    w = np.sqrt(mu * mu + x * x)
+    return tau * (1.0 - gd * x / w) / w, w
+
+
+def pd_dual_step(x, gd, d, mu):
+    """Newton step of the dual estimate g for the primal step d, from the linearised
+    condition g_i w_i = x_i: dg = (x + (1 - g x / w) d) / w - g."""
+    w = np.sqrt(mu * mu + x * x)
+    return (x + (1.0 - gd * x / w) * d) / w - gd
+
+
 def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, pcg_max=1000,
           ls_max=50, armijo=1e-4, stall=0.5, x0=None, mu_start=1.0):
     """Primal-dual Newton-CG (pdNCG, Sec. 8.1) on f_tau^mu of Eq. (prob2) with the pseudo-Huber
@@ -257,9 +272,8 @@ def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, 
         elif prev_full and gap > stall * prev_gap:
             mu = max(mu * 0.1, mu_min)
         prev_gap = gap
-        w = np.sqrt(mu * mu + x * x)
+        hdiag, w = pd_curvature(x, gd, mu, tau)                     # primal-dual psi curvature
         grad = tau * x / w - atr                                    # grad f^mu
-        hdiag = tau * (1.0 - gd * x / w) / w                        # primal-dual psi curvature
         minv = 1.0 / (hdiag + colnorm2)
         # PCG on (diag(hdiag) + A^T A) d = -grad from d = 0.
         d = np.zeros(n)
@@ -298,7 +312,7 @@ def pdncg(A, b, tau, tol, max_newton=200, mu0=1e-5, mu_min=1e-14, pcg_rtol=0.1, 
             if df <= armijo * step * slope or trial == ls_max - 1:
                 break                                               # the last trial is accepted
             step *= 0.5
-        dg = (x + (1.0 - gd * x / w) * d) / w - gd
+        dg = pd_dual_step(x, gd, d, mu)
         x = x + step * d
         gd = np.clip(gd + dg, -1.0, 1.0)
         prev_full = step == 1.0

@@ -172,6 +172,13 @@ def _vec_ptr(v):
     return ctypes.c_void_p(a.ctypes.data), code, a
 
 
+def _numel(v):
+    n = getattr(v, "numel", None)
+    if callable(n):
+        return int(n())
+    return int(np.asarray(v).size)
+
+
 def gen_params(d):
     """GenParams from a parameter dict (keys of ``l1ls_gen_params``; value_dtype may be a name)."""
     p = GenParams()
@@ -321,7 +328,15 @@ class Instance:
         _check(lib.l1ls_inst_export_t(self._h, cp.ctypes.data, ri.ctypes.data, va.ctypes.data))
         return dict(indptr=cp, indices=ri, data=va)
 
-    def _product(self, fn, vin, vout, nout, stream):
+    def _product(self, fn, vin, vout, nin, nout, stream, device_only=False):
+        if device_only:
+            for v in (vin, vout):
+                if not (hasattr(v, "is_cuda") and v.is_cuda):
+                    raise ValueError("this product takes CUDA tensors for its input and output")
+        if _numel(vin) != nin:
+            raise ValueError("input vector has %d entries, the product needs %d" % (_numel(vin), nin))
+        if vout is not None and _numel(vout) != nout:
+            raise ValueError("output vector has %d entries, the product writes %d" % (_numel(vout), nout))
         pin, code, keep_in = _vec_ptr(vin)
         if vout is None:
             try:
@@ -340,15 +355,15 @@ class Instance:
 
     def matvec(self, x, y=None, stream=None):
         """y = A x."""
-        return self._product(lib.l1ls_matvec, x, y, self.m, stream)
+        return self._product(lib.l1ls_matvec, x, y, self.n, self.m, stream)
 
     def rmatvec(self, y, x=None, stream=None):
         """x = A^T y."""
-        return self._product(lib.l1ls_rmatvec, y, x, self.n, stream)
+        return self._product(lib.l1ls_rmatvec, y, x, self.m, self.n, stream)
 
     def rmatvec_noalloc(self, y, x, stream=None):
-        """x = A^T y with device buffers and no allocation (fixed scratch, m <= 2^20)."""
-        return self._product(lib.l1ls_rmatvec_noalloc, y, x, self.n, stream)
+        """x = A^T y with CUDA tensors and no allocation (fixed scratch, m <= 2^20)."""
+        return self._product(lib.l1ls_rmatvec_noalloc, y, x, self.m, self.n, stream, device_only=True)
 
     def _solve(self, fn, x0, x_out, stream, opts, allow):
         o = opts if isinstance(opts, SolveOpts) else solve_opts(**opts)

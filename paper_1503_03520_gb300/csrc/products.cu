@@ -144,11 +144,12 @@ extern "C" l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_d
 }
 
 // ---- x = A^T y without any allocation -------------------------------------------------------
-// For callers that cannot allocate device memory: code running while a CUDA graph is being
-// captured, real-time loops that must not synchronise the device (cudaMalloc / cudaFree can),
-// and hosts that hand the library a fixed memory budget.  l1ls_rmatvec needs one m-vector of
-// scratch (y gathered into the stored row order); here that scratch is a fixed-size array
-// in the device image of the library instead of a context staging buffer.
+// For callers that cannot allocate device memory: real-time loops that must not stall on the
+// device-wide synchronisation cudaMalloc / cudaFree may imply, and host applications that own
+// all device memory themselves (a fixed budget handed out up front, libraries not allowed to
+// allocate).  l1ls_rmatvec needs one m-vector of scratch (y gathered into the stored row
+// order); here that scratch is a fixed-size array in the device image of the library instead
+// of a context staging buffer.
 namespace l1ls {
 namespace {
 
@@ -159,7 +160,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on `device` (the current device), looked up once.
+// Device address of the scratch array on `device` (the current device), looked up once per
+// device and kept for the life of the process: this assumes the device's primary context is
+// never reset (cudaDeviceReset unloads the module, and a cached address would then dangle).
 l1ls_status noalloc_scratch(int device, void** out) {
     if (device < 0 || device >= kMaxDevices) return set_error(L1LS_EINVAL, "device %d out of range", device);
     std::lock_guard<std::mutex> g(g_noalloc_mu);
@@ -187,6 +190,9 @@ extern "C" l1ls_status l1ls_rmatvec_noalloc(const l1ls_inst* inst, const void* y
         return set_error(L1LS_EINVAL, "l1ls_rmatvec_noalloc supports m <= %lld rows (instance has m = %lld)",
                          (long long)kNoAllocMaxRows, (long long)I->m);
     L1LS_CUDA(cudaSetDevice(I->ctx->device));
+    // cudaPointerGetAttributes allocates nothing; a host pointer is refused before any launch
+    if (!is_device_pointer(y) || !is_device_pointer(x))
+        return set_error(L1LS_EINVAL, "l1ls_rmatvec_noalloc takes device pointers for y and x");
     void* scratch = nullptr;
     L1LS_TRY(noalloc_scratch(I->ctx->device, &scratch));
     cudaStream_t st = (cudaStream_t)stream;

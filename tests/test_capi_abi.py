@@ -169,3 +169,35 @@ def test_binding_signatures_match_header_prototypes():
             else:
                 assert ctypes.sizeof(a) == ctypes.sizeof(scalars[t]), (name, t)
                 assert issubclass(a, ctypes.c_double) == (t == "double"), (name, t)
+
+
+def _unbound_instance(m, n):
+    """An Instance object with sizes only: the checks below fire before any library call."""
+    import paper_1503_03520_gb300 as l1
+    inst = object.__new__(l1.Instance)
+    inst._h = None
+    inst.m, inst.n, inst.nnz = m, n, 0
+    return inst
+
+
+def test_binding_checks_vector_lengths_without_gpu():
+    import numpy as np
+    inst = _unbound_instance(10, 5)
+    with pytest.raises(ValueError):
+        inst.matvec(np.zeros(4))                      # A x needs n = 5 entries
+    with pytest.raises(ValueError):
+        inst.matvec(np.zeros(5), np.zeros(9))        # and writes m = 10
+    with pytest.raises(ValueError):
+        inst.rmatvec(np.zeros(5))                     # A^T y needs m = 10
+    with pytest.raises(ValueError):
+        inst.rmatvec(np.zeros(10), np.zeros(4))
+
+
+def test_noalloc_binding_refuses_host_vectors_without_gpu():
+    import numpy as np
+    import torch
+    inst = _unbound_instance(10, 5)
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        inst.rmatvec_noalloc(np.zeros(10), np.zeros(5))
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        inst.rmatvec_noalloc(torch.zeros(10), torch.zeros(5))

@@ -115,3 +115,47 @@ def test_bounded_barrier_expires_and_the_context_survives(setup):
         assert all(r["status"] == 0 for rr in res for r in rr)
     finally:
         batch.free()
+
+
+def test_batch_with_more_segments_than_warps():
+    """Six C2-recipe instances at n = 2^18: 6 x 1024 segments of 8 tiles per phase against at
+    most 152 SMs x 24 warps = 3648 warps, so warps draw several segments from the phase counters
+    and run the staged traversal over several tiles each.  Both sides run at most 30 FISTA
+    iterations at each of two tau (the caps end every tau) from x = 0 with the same warm start;
+    the batch's float-float products (about 44 bits) against the oracle's FP64 FISTA on the
+    stored FP32 problem.  One instance alone equals itself in the batch bit for bit."""
+    import paper_1503_03520_gb300 as l1
+    ctx = l1.Context(0)
+    insts = []
+    try:
+        params = [W.c2_scaled(18, seed=70 + k, kappa=10.0 ** (2 + 0.5 * k)) for k in range(6)]
+        refs = [oracle_instance(p) for p in params]
+        insts = [ctx.generate(p) for p in params]
+        taus = np.array([[0.9 * r.lam_max, 0.3 * r.lam_max] for r in refs])
+        batch = l1.Batch(ctx, insts)
+        xs = [np.zeros(i.n) for i in insts]
+        res = batch.solve_path(taus, x_out=xs, tol=0.0, max_iter=30, restart=0)
+        batch.free()
+        for k, ref in enumerate(refs):
+            A = stored_values(ref.A, "f32")
+            b = ref.b.astype(np.float32).astype(np.float64)
+            x0 = None
+            for j in range(2):
+                o = solvers.fista(A, b, taus[k, j], 1.0, 0.0, 30, x0=x0)
+                r = res[k][j]
+                assert r["status"] == 5 and r["iters"] == 30, (k, j, r)
+                assert abs(r["f"] - o["P"]) <= 1e-9 * o["P"], (k, j, r["f"], o["P"])
+                x0 = o["x_next"]
+            assert np.abs(xs[k] - o["x"]).max() <= 1e-6 * max(1.0, np.abs(o["x"]).max()), k
+        alone = l1.Batch(ctx, [insts[4]])
+        x_alone = [np.zeros(insts[4].n)]
+        res_alone = alone.solve_path(taus[4:5], x_out=x_alone, tol=0.0, max_iter=30, restart=0)
+        alone.free()
+        for j in range(2):
+            a, f = res_alone[0][j], res[4][j]
+            assert (a["iters"], a["f"], a["gap"]) == (f["iters"], f["f"], f["gap"])
+        assert np.array_equal(x_alone[0], xs[4])
+    finally:
+        for i in insts:
+            i.free()
+        ctx.close()

@@ -291,3 +291,81 @@ def test_brute_force_on_orthonormal_columns_is_shrinkage(tau):
     xs = solvers.soft_threshold(Q.T @ b, tau)
     assert np.allclose(xb, xs, atol=1e-12)
     assert math.isclose(fb, solvers.objective(Q, b, tau, xs), rel_tol=1e-12)
+
+
+def test_pd_curvature_at_g_equal_x_over_w_is_the_hessian_of_bd4():
+    """At g = x / w the primal-dual matrix diag(h) + A^T A equals the Hessian of the smoothed
+    objective of Eq. (prob2), tau psi_mu'' + A^T A (the model bd4): psi_mu'' is taken here by
+    symbolic differentiation of Eq. (pseudoHuber), independently of the oracle's formula."""
+    sympy = pytest.importorskip("sympy")
+    xs, ms = sympy.symbols("x mu", real=True)
+    d2 = sympy.lambdify((xs, ms), sympy.diff(sympy.sqrt(ms ** 2 + xs ** 2) - ms, xs, 2), "mpmath")
+    rng = np.random.default_rng(5)
+    for mu in (1e-5, 1e-2, 1.0):
+        x = mu * 10.0 ** rng.uniform(-3, 6, 40) * rng.choice([-1.0, 1.0], 40)
+        w = np.sqrt(mu * mu + x * x)
+        for tau in (0.3, 1.0):
+            h, w2 = solvers.pd_curvature(x, x / w, mu, tau)
+            assert np.array_equal(w2, w)
+            ref = np.array([tau * float(d2(xi, mu)) for xi in x])
+            # 1 - g x / w cancels when |x| >> mu: a few ulps of 1 relative to mu^2 / w^2
+            tol = 1e-13 * ref + 8 * 2.3e-16 * tau / w
+            assert np.all(np.abs(h - ref) <= tol), mu
+
+
+def _pd_newton_step(A, b, x, g, mu, tau, dual_step=None):
+    h, w = solvers.pd_curvature(x, g, mu, tau)
+    grad = tau * x / w + A.T @ (A @ x - b)
+    dx = np.linalg.solve(A.T @ A + np.diag(h), -grad)
+    dg = (dual_step or solvers.pd_dual_step)(x, g, dx, mu)
+    return dx, dg
+
+
+def _pd_conditions(A, b, x, g, mu, tau):
+    """The two conditions pdNCG's Newton step linearises: tau g + A^T (A x - b) = 0 and
+    g_i sqrt(mu^2 + x_i^2) - x_i = 0 (complex arguments allowed)."""
+    return tau * g + A.T @ (A @ x - b), g * np.sqrt(mu * mu + x * x) - x
+
+
+def _check_pd_step_is_newton(A, b, x, g, mu, tau, dx, dg):
+    # the first condition is linear in (x, g): a Newton step zeroes it exactly
+    F1, _ = _pd_conditions(A, b, x + dx, g + dg, mu, tau)
+    scale = tau + np.abs(A.T) @ (np.abs(A) @ (np.abs(x) + np.abs(dx)) + np.abs(b))
+    ok1 = np.all(np.abs(F1) <= 1e-12 * scale)
+    # the second: F2 + J2 (dx, dg) = 0, with J2 (dx, dg) the directional derivative taken by
+    # the complex step (exact to rounding for an analytic function)
+    hstep = 1e-30
+    _, F2 = _pd_conditions(A, b, x, g, mu, tau)
+    _, F2c = _pd_conditions(A, b, x + 1j * hstep * dx, g + 1j * hstep * dg, mu, tau)
+    J2 = np.imag(F2c) / hstep
+    w = np.sqrt(mu * mu + x * x)
+    scale2 = np.abs(x) + w * (np.abs(g) + np.abs(dg)) + np.abs(dx)
+    ok2 = np.all(np.abs(F2 + J2) <= 1e-12 * scale2)
+    return ok1 and ok2
+
+
+def test_pd_direction_and_dual_step_are_a_newton_step():
+    """With dx from the oracle's primal-dual matrix (solved exactly) and dg from its dual step,
+    (dx, dg) is Newton's step on the pair of conditions of pdNCG's primal-dual formulation at
+    any (x, g), not only at g = x / w: the linear condition holds at (x + dx, g + dg) and the
+    other's linearisation, taken by the complex step, vanishes."""
+    rng = np.random.default_rng(9)
+    for trial in range(6):
+        A = rng.standard_normal((14, 9))
+        b = rng.standard_normal(14)
+        x = rng.standard_normal(9) * 10.0 ** rng.uniform(-3, 1, 9)
+        g = rng.uniform(-1.0, 1.0, 9)
+        for mu, tau in ((1e-2, 0.7), (1.0, 2.0)):
+            dx, dg = _pd_newton_step(A, b, x, g, mu, tau)
+            assert _check_pd_step_is_newton(A, b, x, g, mu, tau, dx, dg), (trial, mu)
+
+
+def test_planted_sign_error_in_the_dual_step_is_caught():
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((14, 9))
+    b = rng.standard_normal(14)
+    x = rng.standard_normal(9)
+    g = rng.uniform(-1.0, 1.0, 9)
+    wrong = lambda x, g, d, mu: (x - (1.0 - g * x / np.sqrt(mu * mu + x * x)) * d) / np.sqrt(mu * mu + x * x) - g
+    dx, dg = _pd_newton_step(A, b, x, g, 0.1, 1.0, dual_step=wrong)
+    assert not _check_pd_step_is_newton(A, b, x, g, 0.1, 1.0, dx, dg)
