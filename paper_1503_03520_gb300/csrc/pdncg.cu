@@ -7,13 +7,15 @@
 //       certificate at x, stop test, mu-continuation (mu /= 10 after a full Newton step
 //       until the paper's mu; below it when a full step failed to halve the gap)
 //   N3  w = sqrt(mu^2 + x^2), grad = tau x / w - a, h = tau (1 - g x / w) / w (primal-dual
-//       curvature with the dual estimate g), M^{-1} = 1 / (h + diag(A^T A)), PCG start
+//       curvature with the dual estimate g = clip(a / tau, -1, 1): the linear condition
+//       tau g + A^T (A x - b) = 0 solved for g at the current x and projected onto the box),
+//       M^{-1} = 1 / (h + diag(A^T A)), PCG start
 //   PCG iteration (stopped when the residual in the preconditioner's norm falls to
 //   pcg_rtol of its start, or at pcg_max):
 //   C1  Ap = A p          C2  Hp = h p + A^T Ap, alpha = rz / p.Hp
 //   C3  d += alpha p, res -= alpha Hp, beta    C4  p = M^{-1} res + beta p
 //   L1  Ad = A d (r.Ad, ||Ad||^2);  LT  Armijo trials, four halvings per pass, per-coordinate
-//       psi differences;  L3  x += alpha d, g <- clip(g + dg, -1, 1)
+//       psi differences;  L3  x += alpha d
 // Vectors of length n and every reduction are FP64; with FP32 / BF16 values the products
 // run in FP32 with FP32 shadows of x and p for the gathers.
 #include <chrono>
@@ -129,8 +131,8 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
 
 // ---- N3: gradient, primal-dual curvature, preconditioner, PCG start --------------------
 template <class PX>
-__global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x, const double* __restrict__ gd,
-                                                    const double* __restrict__ atr, const double* __restrict__ cn2,
+__global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x, const double* __restrict__ atr,
+                                                    const double* __restrict__ cn2,
                                                     double* __restrict__ grad, double* __restrict__ hd,
                                                     double* __restrict__ minv, double* __restrict__ rcg,
                                                     double* __restrict__ p, PX* __restrict__ p_g, double* __restrict__ d,
@@ -140,10 +142,11 @@ __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x
     const double mu = st->mu, tau = st->tau;
     double q[2] = {0.0, 0.0};
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-        const double xj = x[j];
+        const double xj = x[j], aj = atr[j];
         const double w = sqrt(mu * mu + xj * xj);
-        const double gr = tau * xj / w - atr[j];
-        const double h = tau * (1.0 - gd[j] * xj / w) / w;
+        const double gr = tau * xj / w - aj;
+        const double gj = fmin(1.0, fmax(-1.0, aj / tau));
+        const double h = tau * (1.0 - gj * xj / w) / w;
         const double mi = 1.0 / (h + cn2[j]);
         const double rc = -gr;
         const double z = mi * rc;
@@ -332,19 +335,13 @@ __global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ 
     }
 }
 
-// ---- L3: x += step d, dual estimate update -----------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, double* __restrict__ gd,
-                                                     const double* __restrict__ d, int64_t n, PdState* st) {
+// ---- L3: x += step d (the dual estimate is recomputed from A^T r at the next N3) ----------
+__global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, const double* __restrict__ d, int64_t n,
+                                                     PdState* st) {
     if (halted(st)) return;
-    const double mu = st->mu, step = st->step;
-    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-        const double xj = x[j], dj = d[j], gj = gd[j];
-        const double w = sqrt(mu * mu + xj * xj);
-        const double dg = (xj + (1.0 - gj * xj / w) * dj) / w - gj;
-        const double xn = xj + step * dj;
-        x[j] = xn;
-        gd[j] = fmin(1.0, fmax(-1.0, gj + dg));
-    }
+    const double step = st->step;
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock)
+        x[j] += step * d[j];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->prev_full = step == 1.0 ? 1 : 0;
         st->iter += 1;
@@ -361,7 +358,7 @@ int grid_for(const Inst* I, K kernel, int64_t rows) {
 }
 
 struct PdWork {
-    double *X = nullptr, *gd = nullptr, *atr = nullptr, *grad = nullptr, *hd = nullptr, *minv = nullptr,
+    double *X = nullptr, *atr = nullptr, *grad = nullptr, *hd = nullptr, *minv = nullptr,
            *rcg = nullptr, *p = nullptr, *hp = nullptr, *d = nullptr;
     float* p32 = nullptr;   // FP32 shadow of p for the gathers of C1
     void *r = nullptr, *ap = nullptr, *ad = nullptr;
@@ -416,7 +413,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         w = new PdWork();
         I->pd_work = w;
         I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
-        for (double** v : {&w->X, &w->gd, &w->atr, &w->grad, &w->hd, &w->minv, &w->rcg, &w->p, &w->hp, &w->d})
+        for (double** v : {&w->X, &w->atr, &w->grad, &w->hd, &w->minv, &w->rcg, &w->p, &w->hp, &w->d})
             L1LS_TRY(I->alloc_n(v, n));
         if (sizeof(Vec) == 4) L1LS_TRY(I->alloc_n(&w->p32, n));
         L1LS_TRY(I->alloc(&w->r, sizeof(Vec) * pad32(m)));
@@ -432,7 +429,6 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
-    L1LS_CUDA(cudaMemsetAsync(w->gd, 0, sizeof(double) * n, s));
     PdState h;
     memset(&h, 0, sizeof(h));
     h.tau = o->tau;
@@ -496,7 +492,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
             final_status = L1LS_ECANCELLED;
             break;
         }
-        k_pd_init<float><<<w->gv, kBlock, 0, s>>>(w->X, w->gd, w->atr, I->colnorm2, w->grad, w->hd, w->minv, w->rcg,
+        k_pd_init<float><<<w->gv, kBlock, 0, s>>>(w->X, w->atr, I->colnorm2, w->grad, w->hd, w->minv, w->rcg,
                                                   w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->d, n, w->part, w->st);
         L1LS_CUDA(cudaGetLastError());
         const int64_t max_cg_launches = o->pcg_max / chunk + 3;
@@ -515,7 +511,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
                                                                        (const Vec*)w->r, m, w->part, w->st);
         for (int t = 0; t < ls_passes; ++t)
             k_pd_trial<<<w->gv, kBlock, 0, s>>>(w->X, w->d, w->grad, n, w->part, w->st);
-        k_pd_apply<<<w->gv, kBlock, 0, s>>>(w->X, w->gd, w->d, n, w->st);
+        k_pd_apply<<<w->gv, kBlock, 0, s>>>(w->X, w->d, n, w->st);
         L1LS_CUDA(cudaGetLastError());
     }
     const PdState& f = *w->host;

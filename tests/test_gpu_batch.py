@@ -131,17 +131,20 @@ def test_batch_with_more_segments_than_warps():
         params = [W.c2_scaled(18, seed=70 + k, kappa=10.0 ** (2 + 0.5 * k)) for k in range(6)]
         refs = [oracle_instance(p) for p in params]
         insts = [ctx.generate(p) for p in params]
-        taus = np.array([[0.9 * r.lam_max, 0.3 * r.lam_max] for r in refs])
+        # at these tau 30 iterations leave gaps far above the tolerance, so the caps end both
+        # sides' runs (a gap rounded to <= 0 would end a run at tol = 0)
+        taus = np.array([[0.3 * r.lam_max, 0.1 * r.lam_max] for r in refs])
         batch = l1.Batch(ctx, insts)
         xs = [np.zeros(i.n) for i in insts]
-        res = batch.solve_path(taus, x_out=xs, tol=0.0, max_iter=30, restart=0)
+        res = batch.solve_path(taus, x_out=xs, tol=1e-12, max_iter=30, restart=0)
         batch.free()
         for k, ref in enumerate(refs):
             A = stored_values(ref.A, "f32")
             b = ref.b.astype(np.float32).astype(np.float64)
             x0 = None
             for j in range(2):
-                o = solvers.fista(A, b, taus[k, j], 1.0, 0.0, 30, x0=x0)
+                o = solvers.fista(A, b, taus[k, j], 1.0, 1e-12, 30, x0=x0)
+                assert o["status"] == 5
                 r = res[k][j]
                 assert r["status"] == 5 and r["iters"] == 30, (k, j, r)
                 assert abs(r["f"] - o["P"]) <= 1e-9 * o["P"], (k, j, r["f"], o["P"])
@@ -149,7 +152,7 @@ def test_batch_with_more_segments_than_warps():
             assert np.abs(xs[k] - o["x"]).max() <= 1e-6 * max(1.0, np.abs(o["x"]).max()), k
         alone = l1.Batch(ctx, [insts[4]])
         x_alone = [np.zeros(insts[4].n)]
-        res_alone = alone.solve_path(taus[4:5], x_out=x_alone, tol=0.0, max_iter=30, restart=0)
+        res_alone = alone.solve_path(taus[4:5], x_out=x_alone, tol=1e-12, max_iter=30, restart=0)
         alone.free()
         for j in range(2):
             a, f = res_alone[0][j], res[4][j]

@@ -369,3 +369,18 @@ def test_planted_sign_error_in_the_dual_step_is_caught():
     wrong = lambda x, g, d, mu: (x - (1.0 - g * x / np.sqrt(mu * mu + x * x)) * d) / np.sqrt(mu * mu + x * x) - g
     dx, dg = _pd_newton_step(A, b, x, g, 0.1, 1.0, dual_step=wrong)
     assert not _check_pd_step_is_newton(A, b, x, g, 0.1, 1.0, dx, dg)
+
+
+def test_residual_dual_equals_the_newton_update_after_an_exact_full_step():
+    """The reading behind pdNCG's dual estimate: the first condition tau g + A^T(Ax - b) = 0 is
+    linear, so Newton's g + dg after an exact full step is A^T r(x + dx) / tau, the dual the
+    oracle recomputes from the residual at the accepted point."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((16, 10))
+    b = rng.standard_normal(16)
+    x = rng.standard_normal(10)
+    g = rng.uniform(-1.0, 1.0, 10)
+    for mu, tau in ((1e-3, 0.5), (0.3, 1.5)):
+        dx, dg = _pd_newton_step(A, b, x, g, mu, tau)
+        xn = x + dx
+        assert np.allclose(g + dg, A.T @ (b - A @ xn) / tau, rtol=1e-10, atol=1e-10)
