@@ -143,33 +143,49 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_iterations(log2n, warmup, steps, budget_s):
-    """Time oracle FISTA iterations in a fresh single-threaded Python process."""
-    code = r"""
+CPU_SAMPLE_LOG2N = 20     # the oracle's sample of the C2 recipe: n = 2^20, m = 2^21
+
+_ORACLE_TIMING = r"""
 import json, os, sys, time
-sys.path.insert(0, %r)
+sys.path.insert(0, %(root)r)
 import workloads as W
 from oracle.generator import GenParams, generate
 from oracle import solvers
-p = W.c2_scaled(%d)
+p = W.c2_scaled(%(log2n)d, seed=%(seed)d)
 t0 = time.time()
 inst = generate(GenParams.from_dict(p))
 tgen = time.time() - t0
 A, b = inst.A, inst.b
-solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, %d)
-steps = %d
+solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, %(warmup)d)
+steps = %(steps)d
 if steps <= 0:
     t = time.time(); solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, 2); one = (time.time() - t) / 2
-    steps = max(3, int(%f / max(one, 1e-6)))
+    steps = max(3, int(%(budget)f / max(one, 1e-6)))
+go = %(go)r
+if go:
+    open(os.path.join(go, "ready.%%d" %% os.getpid()), "w").close()
+    while not os.path.exists(os.path.join(go, "go")):
+        time.sleep(0.01)
 t = time.time()
 r = solvers.fista(A, b, 1.0, inst.lipschitz, 0.0, steps)
-el = time.time() - t
-print(json.dumps(dict(m=A.shape[0], n=A.shape[1], nnz=int(A.nnz), steps=steps, seconds=el, gen_seconds=tgen)))
-""" % (ROOT, log2n, max(warmup, 1), steps, budget_s)
+t1 = time.time()
+print(json.dumps(dict(m=A.shape[0], n=A.shape[1], nnz=int(A.nnz), steps=steps, seconds=t1 - t, start=t, end=t1,
+                      gen_seconds=tgen)))
+"""
+
+
+def _oracle_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    return env
+
+
+def cpu_oracle_iterations(log2n, warmup, steps, budget_s):
+    """Time oracle FISTA iterations in a fresh single-threaded Python process."""
+    code = _ORACLE_TIMING % dict(root=ROOT, log2n=log2n, seed=0, warmup=max(warmup, 1), steps=steps,
+                                 budget=budget_s, go="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_oracle_env(), timeout=900)
     if out.returncode != 0:
         raise RuntimeError("oracle timing failed: " + out.stderr[-2000:])
     d = json.loads(out.stdout.strip().splitlines()[-1])
@@ -177,25 +193,87 @@ print(json.dumps(dict(m=A.shape[0], n=A.shape[1], nnz=int(A.nnz), steps=steps, s
     per_iter = d["seconds"] / d["steps"]
     d["value"] = (k1 + k2) / per_iter / 1e9
     d["ms_per_step"] = per_iter * 1e3
+    d["cores"] = 1
     return d
+
+
+def host_cores_for_oracle(bytes_per_process=1.6e9):
+    """Host cores the all-cores oracle uses: every core, bounded by the available memory (one
+    single-threaded oracle process per core, each holding its own instance)."""
+    cores = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(l.split()[1]) * 1024 for l in f if l.startswith("MemAvailable"))
+        cores = max(1, min(cores, int(0.6 * avail / bytes_per_process)))
+    except Exception:
+        pass
+    return cores
+
+
+def cpu_oracle_all_cores(log2n, warmup, steps, budget_s, cores=None):
+    """The oracle as it stands on all host cores: one single-threaded oracle process per core,
+    each on its own seeded instance of the sample (independent replicas, as the GPU ranks are),
+    released together once every process has generated its instance and warmed up.  value =
+    the algorithmic bytes of all processes' iterations / (last end - first start)."""
+    import tempfile
+    cores = cores or host_cores_for_oracle()
+    with tempfile.TemporaryDirectory() as go:
+        procs = []
+        for c in range(cores):
+            code = _ORACLE_TIMING % dict(root=ROOT, log2n=log2n, seed=c, warmup=max(warmup, 1), steps=steps,
+                                         budget=budget_s, go=go)
+            procs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                          stderr=subprocess.PIPE, text=True, env=_oracle_env()))
+        t0 = time.time()
+        while sum(f.startswith("ready.") for f in os.listdir(go)) < cores:
+            if any(p.poll() not in (None, 0) for p in procs) or time.time() - t0 > 900:
+                for p in procs:
+                    p.kill()
+                raise RuntimeError("all-cores oracle timing failed before the start")
+            time.sleep(0.05)
+        open(os.path.join(go, "go"), "w").close()
+        rows = []
+        for p in procs:
+            out, err = p.communicate(timeout=900)
+            if p.returncode != 0:
+                raise RuntimeError("all-cores oracle timing failed: " + err[-2000:])
+            rows.append(json.loads(out.strip().splitlines()[-1]))
+    k1, k2 = bytes_per_iteration(rows[0]["m"], rows[0]["n"], rows[0]["nnz"])
+    span = max(r["end"] for r in rows) - min(r["start"] for r in rows)
+    total_steps = sum(r["steps"] for r in rows)
+    return {"value": (k1 + k2) * total_steps / span / 1e9, "cores": cores, "steps": total_steps,
+            "seconds": span, "ms_per_step": span / max(r["steps"] for r in rows) * 1e3, "m": rows[0]["m"],
+            "n": rows[0]["n"], "nnz": rows[0]["nnz"]}
+
+
+def cpu_baseline_line(single, multi, log2n):
+    what = ("oracle FISTA iterations (numpy + scipy.sparse, FP64) on the n=2^%d, m=2^%d instance of the same "
+            "recipe" % (log2n, log2n + 1))
+    return {"value": multi["value"], "unit": UNIT, "cores": multi["cores"], "kind": "oracle",
+            "sample": "%s: %d single-threaded processes, one per host core, each on its own seeded instance, "
+                      "%d iterations in %.1f s together" % (what, multi["cores"], multi["steps"], multi["seconds"]),
+            "single_thread": {"value": single["value"], "unit": UNIT, "cores": 1,
+                              "sample": "%s: %d iterations in %.1f s, one thread" % (what, single["steps"],
+                                                                                      single["seconds"])}}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    log2n = 22
-    d = cpu_oracle_iterations(log2n, args.warmup, args.steps, 0.0)
-    sample = "one oracle FISTA iteration (numpy + scipy.sparse, FP64) per step on the n=2^%d, m=2^%d instance " \
-             "of the same recipe; %d timed steps after %d warm-up" % (log2n, log2n + 1, d["steps"], args.warmup)
-    line = {"metric": METRIC, "value": d["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": d["steps"],
-            "warmup": args.warmup, "ms_per_step": d["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+    log2n = CPU_SAMPLE_LOG2N
+    steps = args.steps
+    single = cpu_oracle_iterations(log2n, args.warmup, steps, 0.0)
+    multi = cpu_oracle_all_cores(log2n, args.warmup, steps, 0.0)
+    line = {"metric": METRIC, "value": multi["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": multi["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (generator of Sec. 3-6)",
             "impl": "reference",
             "config": {"workload": "c2: m=2^25, n=2^24, ~8 nnz/col, FP32 values, kappa(A)=1e4, x* 1%, tau=1",
-                       "sample": "n=2^%d" % log2n, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": d["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                       "sample": "n=2^%d, one oracle FISTA iteration per step and process" % log2n,
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": cpu_baseline_line(single, multi, log2n),
+            "e2e": {"value": multi["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -703,12 +781,10 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            log2n = 20
-            d = cpu_oracle_iterations(log2n, 1, 0, args.cpu_budget)
-            cpu = {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "%d oracle FISTA iterations (numpy + scipy.sparse, FP64, single thread) on the "
-                             "n=2^%d, m=2^%d instance of the same recipe, %.1f s" % (d["steps"], log2n, log2n + 1,
-                                                                                     d["seconds"])}
+            log2n = CPU_SAMPLE_LOG2N
+            single = cpu_oracle_iterations(log2n, 1, 0, args.cpu_budget)
+            multi = cpu_oracle_all_cores(log2n, 1, single["steps"], 0.0)
+            cpu = cpu_baseline_line(single, multi, log2n)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (generator of Sec. 3-6, seeded)",
