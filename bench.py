@@ -342,13 +342,22 @@ def batch_form(l1, W, ctx, iters_per_tau):
             "speedup_instance_iterations": rate / rate_one}
 
 
-def serve_form(l1, W, count, rate, log2n_hi, slots=16):
-    """C5: Poisson arrivals into the serving loop (`slots` slots, FP32 values) against the same
-    requests served FIFO one at a time with FP64 values (one slot)."""
-    import numpy as np
-    reqs = W.c5_requests(count, rate, log2n_hi=log2n_hi)
+SERVE_RATES = (10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0)
 
-    def run(dtype, slots, accum):
+
+def serve_form(l1, W, count, rates, log2n_hi, slots=16):
+    """C5: Poisson arrivals into the serving loop (`slots` slots, FP32 values, float-float FISTA
+    products) against the same requests served FIFO one at a time with FP64 values (one slot),
+    at each arrival rate.  The request sequence is the same at every rate (arrival times of the
+    unit-rate sequence divided by the rate).  Both arms stop a request at the same iteration
+    caps (no time limits), so a request is certified in both or fails in both up to the
+    rounding of its certificate; certified solves per second count requests certified to the
+    1e-6 gap over the span from the first arrival to the last completion; latency is from
+    arrival to completion."""
+    import numpy as np
+    reqs = W.c5_requests(count, 1.0, log2n_hi=log2n_hi)
+
+    def run(dtype, slots, accum, rate):
         ctx = l1.Context(0)
         ctx.serve_config(slots=slots)
         # iteration caps, not time limits: the same requests finish (or stop) in both runs
@@ -357,9 +366,10 @@ def serve_form(l1, W, count, rate, log2n_hi, slots=16):
         t0 = time.perf_counter()
         tickets = []
         for r in reqs:
+            due = r["t"] / rate
             now = time.perf_counter() - t0
-            if r["t"] > now:
-                time.sleep(r["t"] - now)
+            if due > now:
+                time.sleep(due - now)
             o = of if r["method"] == "fista" else op
             tickets.append(ctx.submit(dict(r["params"], value_dtype=dtype), method=r["method"], tau=-r["tau_factor"],
                                       **o))
@@ -370,25 +380,29 @@ def serve_form(l1, W, count, rate, log2n_hi, slots=16):
                 if o is not None:
                     out.append(o)
                     break
-        el = time.perf_counter() - t0
+        el = time.perf_counter() - t0 - reqs[0]["t"] / rate
         st = ctx.serve_stats()
         ctx.close()
         lat = np.array([o[1]["latency_s"] for o in out])
         ok = int(sum(o[0] == 0 for o in out))
-        return {"seconds": el, "certified": ok, "of": len(out), "certified_per_s": ok / el,
-                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                "peak_running": st["peak_running"],
+        return {"seconds": el, "certified": ok, "of": len(out), "fraction_certified": ok / len(out),
+                "certified_per_s": ok / el, "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "peak_running": st["peak_running"],
                 "statuses": {l1.STATUS.get(k, str(k)): int(v) for k, v in
                              enumerate(np.bincount([o[0] for o in out], minlength=10)) if v}}
 
-    served = run("f32", slots, 1)
-    fifo = run("f64", 1, 0)
-    return {"workload": "c5: %d Poisson requests at %g/s, n = 2^U[10,%d], m in {n/2, 2n}, kappa 10^U[2,6], "
+    table = []
+    for rate in rates:
+        served = run("f32", slots, 1, rate)
+        fifo = run("f64", 1, 0, rate)
+        table.append({"rate_per_s": rate, "served": served, "fifo_fp64": fifo,
+                      "speedup_certified_per_s": served["certified_per_s"] / max(fifo["certified_per_s"], 1e-12)})
+    return {"workload": "c5: %d Poisson requests per rate, n = 2^U[10,%d], m in {n/2, 2n}, kappa 10^U[2,6], "
                         "x* 0.5-5%%, tau = 10^U[-2,0] lambda_max, FISTA (kappa <= 1e3, restart, at most 5000 "
                         "iterations) or pdNCG (at most 30 Newton steps of at most 300 PCG iterations), tol 1e-6"
-                        % (count, rate, log2n_hi),
-            "slots": slots, "served": served, "fifo_fp64": fifo,
-            "speedup_certified_per_s": served["certified_per_s"] / max(fifo["certified_per_s"], 1e-12)}
+                        % (count, log2n_hi),
+            "slots": slots, "rates": table,
+            "best_speedup_certified_per_s": max(r["speedup_certified_per_s"] for r in table)}
 
 
 def mf_bytes_per_iteration(m, n, left=True):
@@ -596,7 +610,8 @@ def c1_form(l1, W):
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
-    BF16) to a 1e-6 gap (1e-4 for BF16), against the FP64 optimum x*, f* of the generator."""
+    BF16) and pdNCG, each to a 1e-6 gap (1e-4 for BF16) within `limit_s`, against the FP64
+    optimum x*, f* of the generator."""
     import numpy as np
     ctx = l1.Context(0)
     rows = []
@@ -605,18 +620,23 @@ def precision_form(l1, W, limit_s):
             inst = ctx.generate(W.c3(kappa, dt))
             xs = inst.xstar()
             tol = 1e-4 if dt == "bf16" else 1e-6
-            t = time.perf_counter()
-            x, r = inst.solve_fista(tau=1.0, tol=tol, max_iter=10 ** 6, restart=1, accum=0 if dt == "f64" else 1,
-                                    time_limit_s=limit_s, allow=(4, 5))
-            el = time.perf_counter() - t
             f_star = inst.info["f_star"]
-            rows.append({"kappa": kappa, "values": dt, "tol": tol, "status": r["status_name"], "iters": r["iters"],
-                         "seconds": el, "rel_gap": r["rel_gap"], "rel_err_f": abs(r["f"] - f_star) / f_star,
-                         "rel_err_x": float(np.linalg.norm(x - xs) / np.linalg.norm(xs))})
+            for method in ("fista", "pdncg"):
+                t = time.perf_counter()
+                if method == "fista":
+                    x, r = inst.solve_fista(tau=1.0, tol=tol, max_iter=10 ** 6, restart=1,
+                                            accum=0 if dt == "f64" else 1, time_limit_s=limit_s, allow=(4, 5))
+                else:
+                    x, r = inst.solve_pdncg(tau=1.0, tol=tol, max_iter=200, time_limit_s=limit_s, allow=(4, 5))
+                el = time.perf_counter() - t
+                rows.append({"kappa": kappa, "values": dt, "method": method, "tol": tol, "status": r["status_name"],
+                             "iters": r["iters"], "cg_iters": r["cg_iters"], "seconds": el, "rel_gap": r["rel_gap"],
+                             "rel_err_f": abs(r["f"] - f_star) / f_star,
+                             "rel_err_x": float(np.linalg.norm(x - xs) / np.linalg.norm(xs))})
             inst.free()
     ctx.close()
-    return {"workload": "c3: m=2^22, n=2^21, ~16/col, x* 2%%, tau=1, FISTA with restart, %g s limit" % limit_s,
-            "runs": rows}
+    return {"workload": "c3: m=2^22, n=2^21, ~16/col, x* 2%%, tau=1, FISTA with restart and pdNCG, %g s limit "
+                        "per solve" % limit_s, "runs": rows}
 
 
 def run_ours(args):
@@ -761,7 +781,8 @@ def run_ours(args):
     if rank == 0 and not args.no_forms:
         forms["matrix_free"] = mf_form(l1, W, args.log2n, args.steps, args.warmup, args.solve_limit)
     if rank == 0 and not args.no_forms:
-        forms["serve"] = serve_form(l1, W, args.serve_count, args.serve_rate, args.serve_log2n, args.serve_slots)
+        rates = SERVE_RATES if args.serve_rate is None else (args.serve_rate,)
+        forms["serve"] = serve_form(l1, W, args.serve_count, rates, args.serve_log2n, args.serve_slots)
     if rank == 0 and not args.no_forms:
         forms["fista_variants"] = variants_form(l1, W, args.variants_log2n, args.solve_limit)
         forms["c1"] = c1_form(l1, W)
@@ -774,7 +795,7 @@ def run_ours(args):
     if rank == 0 and args.sec89:
         forms = forms or {}
         forms["sec89"] = sec89_form(l1, W, args.sec89_log2n, (8, 16, 32))
-    if rank == 0 and args.precision:
+    if rank == 0 and not args.no_forms and not args.no_precision:
         forms = forms or {}
         forms["precision"] = precision_form(l1, W, args.precision_limit)
 
@@ -819,14 +840,15 @@ def main():
     ap.add_argument("--solve-limit", type=float, default=30.0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched (c4) and serving (c5) legs")
     ap.add_argument("--batch-iters", type=int, default=300, help="c4: FISTA iterations per tau at most")
-    ap.add_argument("--serve-count", type=int, default=32)
-    ap.add_argument("--serve-rate", type=float, default=300.0)
-    ap.add_argument("--serve-log2n", type=int, default=20, help="c5: largest log2 n of a request")
+    ap.add_argument("--serve-count", type=int, default=48, help="c5: requests per arrival rate")
+    ap.add_argument("--serve-rate", type=float, default=None, help="c5: one arrival rate (default: the sweep "
+                                                                   "10, 30, 100, 300, 1000, 2000 per s)")
+    ap.add_argument("--serve-log2n", type=int, default=23, help="c5: largest log2 n of a request")
     ap.add_argument("--serve-slots", type=int, default=16, help="c5: serving slots")
-    ap.add_argument("--precision", action="store_true", help="add the c3 precision sweep (about 1-2 min)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the c3 precision sweep (about 30 s)")
     ap.add_argument("--matrix-free", action="store_true",
                     help="time the iteration on the instance with A not assembled (Algorithms MvPA / MvPAt)")
-    ap.add_argument("--precision-limit", type=float, default=8.0, help="c3: time limit per solve (s)")
+    ap.add_argument("--precision-limit", type=float, default=6.0, help="c3: time limit per solve (s)")
     ap.add_argument("--variants-log2n", type=int, default=22, help="FISTA variants leg: log2 n")
     ap.add_argument("--sweep", action="store_true", help="add the size sweep (n = 2^20 .. 2^27 stored, "
                                                          "2^24 .. 2^29 matrix-free)")

@@ -549,21 +549,35 @@ __global__ void __launch_bounds__(kMfThreads) k_fista_mf2(MfK2Args a) {
     ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
     // persistent blocks take tiles in turn (fewer per-block partials for the last block to sum)
     const int64_t ntiles = (a.R.n + kMfTile - 1) / kMfTile;
+    constexpr int kPer = kMfTile / kMfThreads;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t a0 = tile * kMfTile;
+        // this thread's iterates of the tile, loaded before the stage sweep so that their
+        // latency overlaps the sweep (the new iterate overwrites x0 only after all are read)
+        ff x1[kPer], x0[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int64_t j = a0 + (int)threadIdx.x + u * kMfThreads;
+            x1[u] = x0[u] = ff{0.0f, 0.0f};
+            if (j < a.R.n) {
+                x1[u] = ff{__ldcs(a.xch + j), __ldcs(a.xcl + j)};
+                x0[u] = ff{__ldcs(a.xoh + j), __ldcs(a.xol + j)};
+            }
+        }
         mf_load<true>(buf, a.z, a.sigma, a0 - kMfHalo, a.R.n);
         mf_stages<false>(buf, a0 - kMfHalo, a.R);
-        for (int p = threadIdx.x; p < kMfTile; p += blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int p = (int)threadIdx.x + u * kMfThreads;
             const int64_t j = a0 + p;
             if (j >= a.R.n) break;
             const float g = buf[kMfHalo + p];
-            const ff x1 = {a.xch[j], a.xcl[j]}, x0 = {a.xoh[j], a.xol[j]};
-            const FfStep f = ff_fista_step(x1, x0, ff_from_float(g), beta_f, invL_f, thr_f);
+            const FfStep f = ff_fista_step(x1[u], x0[u], ff_from_float(g), beta_f, invL_f, thr_f);
             a.xoh[j] = f.x.hi;
             a.xol[j] = f.x.lo;
             gmax = fmaxf(gmax, fabsf(g));
             sum2_add(l1, f.mag);
-            if (RESTART) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, x1)));
+            if (RESTART) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, x1[u])));
         }
         __syncthreads();   // the tile buffer is reloaded next
     }

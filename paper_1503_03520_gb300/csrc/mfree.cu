@@ -12,12 +12,21 @@ namespace {
 __global__ void __launch_bounds__(kMfThreads) k_mf_rt(const float* __restrict__ x, const float* __restrict__ sigma,
                                                       MfRight R, float* __restrict__ z) {
     __shared__ float buf[kMfLen];
+    constexpr int kPer = kMfTile / kMfThreads;
     const int64_t a = (int64_t)blockIdx.x * kMfTile;
+    float sg[kPer];   // sigma of this thread's outputs, loaded before the sweep
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int64_t i = a + (int)threadIdx.x + u * kMfThreads;
+        sg[u] = i < R.n ? __ldg(sigma + i) : 0.0f;
+    }
     mf_load<false>(buf, x, sigma, a - kMfHalo, R.n);
     mf_stages<true>(buf, a - kMfHalo, R);
-    for (int p = threadIdx.x; p < kMfTile; p += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int p = (int)threadIdx.x + u * kMfThreads;
         const int64_t i = a + p;
-        if (i < R.n) z[i] = buf[kMfHalo + p] * __ldg(sigma + i);
+        if (i < R.n) z[i] = buf[kMfHalo + p] * sg[u];
     }
 }
 
@@ -27,7 +36,7 @@ __global__ void __launch_bounds__(kMfThreads) k_mf_r(const float* __restrict__ z
     const int64_t a = (int64_t)blockIdx.x * kMfTile;
     mf_load<true>(buf, z, sigma, a - kMfHalo, R.n);
     mf_stages<false>(buf, a - kMfHalo, R);
-    for (int p = threadIdx.x; p < kMfTile; p += blockDim.x) {
+    for (int p = threadIdx.x; p < kMfTile; p += kMfThreads) {
         const int64_t i = a + p;
         if (i < R.n) x[i] = buf[kMfHalo + p];
     }

@@ -37,18 +37,30 @@ struct MfLeft {
     const int32_t* perm;   // row pair t (stored order) of the left stage takes z_perm[2t], z_perm[2t+1]
 };
 
+// Every block that uses these helpers has kMfThreads threads: the loops below stride by the
+// constant so that each thread's loads of a tile are unrolled and all in flight at once.
+constexpr int kMfPerThread = (kMfLen + kMfThreads - 1) / kMfThreads;
+
 // buf[p] = v[g0 + p] (0 outside [0, n)), scaled by sigma when SCALE; g0 = a - kMfHalo
 template <bool SCALE>
 __device__ __forceinline__ void mf_load(float* buf, const float* __restrict__ v, const float* __restrict__ sigma,
                                         int64_t g0, int64_t n) {
-    for (int p = threadIdx.x; p < kMfLen; p += blockDim.x) {
+    float xv[kMfPerThread], sv[kMfPerThread];
+#pragma unroll
+    for (int u = 0; u < kMfPerThread; ++u) {
+        const int p = (int)threadIdx.x + u * kMfThreads;
         const int64_t i = g0 + p;
-        float x = 0.0f;
-        if (i >= 0 && i < n) {
-            x = __ldcs(v + i);
-            if (SCALE) x *= __ldg(sigma + i);
+        xv[u] = 0.0f;
+        sv[u] = 1.0f;
+        if (p < kMfLen && i >= 0 && i < n) {
+            xv[u] = __ldcs(v + i);
+            if (SCALE) sv[u] = __ldg(sigma + i);
         }
-        buf[p] = x;
+    }
+#pragma unroll
+    for (int u = 0; u < kMfPerThread; ++u) {
+        const int p = (int)threadIdx.x + u * kMfThreads;
+        if (p < kMfLen) buf[p] = SCALE ? xv[u] * sv[u] : xv[u];
     }
     __syncthreads();
 }
@@ -61,7 +73,7 @@ __device__ __forceinline__ void mf_stages(float* buf, int64_t g0, const MfRight&
         const int k = TRANS ? R.w - q : q + 1;
         const int first = (k - 1) & 1;
         const int p0 = (int)(((first - g0) % 2 + 2) % 2);   // first local index with i = first (mod 2)
-        for (int p = p0 + 2 * (int)threadIdx.x; p + 1 < kMfLen; p += 2 * (int)blockDim.x) {
+        for (int p = p0 + 2 * (int)threadIdx.x; p + 1 < kMfLen; p += 2 * kMfThreads) {
             const int64_t i = g0 + p;
             if (i < 0 || i + 1 >= R.n) continue;
             const float a = buf[p], b = buf[p + 1];

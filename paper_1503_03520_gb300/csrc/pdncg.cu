@@ -11,13 +11,22 @@
 //       tau g + A^T (A x - b) = 0 solved for g at the current x and projected onto the box),
 //       M^{-1} = 1 / (h + diag(A^T A)), PCG start
 //   PCG iteration (stopped when the residual in the preconditioner's norm falls to
-//   pcg_rtol of its start, or at pcg_max):
-//   C1  Ap = A p          C2  Hp = h p + A^T Ap, alpha = rz / p.Hp
-//   C3  d += alpha p, res -= alpha Hp, beta    C4  p = M^{-1} res + beta p
+//   pcg_rtol of its start, or at pcg_max), three kernels: the update of the search direction
+//   p = z + beta p (z = M^{-1} res) is folded into the products, A p = A z + beta (A p_old),
+//   so no pass of its own is needed:
+//   C1  Ap = A z + beta Ap                     C2  p = z + beta p, Hp = h p + A^T Ap,
+//                                                  alpha = rz / p.Hp
+//   C3  d += alpha p, res -= alpha Hp, z = M^{-1} res, rz, beta
 //   L1  Ad = A d (r.Ad, ||Ad||^2);  LT  Armijo trials, four halvings per pass, per-coordinate
 //       psi differences;  L3  x += alpha d
-// Vectors of length n and every reduction are FP64; with FP32 / BF16 values the products
-// run in FP32 with FP32 shadows of x and p for the gathers.
+// Precision: the iterate x, A^T r, the gradient and every reduction across blocks (the
+// certificate, the CG inner products) are FP64.  The other CG vectors (h, M^{-1}, z, p, Hp,
+// d) are held in the product precision: FP32 with FP32 / BF16 values, FP64 with FP64 values.
+// The CG residual res is FP64 with FP64 values and float-float (hi, lo; about 48 bits) with
+// FP32 / BF16 values, where its update and the per-thread sums of the inner products run as
+// float-float arithmetic on the FP32 pipes: this GPU's FP64 pipe has a small fraction of the
+// FP32 rate, and FP64 arithmetic per entry (with the conversions to and from FP32) made the
+// vector update the slowest kernel of the iteration.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -130,35 +139,48 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
 }
 
 // ---- N3: gradient, primal-dual curvature, preconditioner, PCG start --------------------
-template <class PX>
+// the CG residual: FP64 with FP64 vectors, float-float pairs with FP32 vectors
+template <class CV> struct CgRes { using type = double; };
+template <> struct CgRes<float> { using type = float2; };
+
+template <class CV>
 __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x, const double* __restrict__ atr,
                                                     const double* __restrict__ cn2,
-                                                    double* __restrict__ grad, double* __restrict__ hd,
-                                                    double* __restrict__ minv, double* __restrict__ rcg,
-                                                    double* __restrict__ p, PX* __restrict__ p_g, double* __restrict__ d,
+                                                    double* __restrict__ grad, CV* __restrict__ hd,
+                                                    CV* __restrict__ minv, typename CgRes<CV>::type* __restrict__ rcg,
+                                                    CV* __restrict__ z, CV* __restrict__ d,
                                                     int64_t n, double* partials, PdState* st) {
     __shared__ double red[2 * 32];
     if (halted(st)) return;
-    const double mu = st->mu, tau = st->tau;
+    const double mu = st->mu, tau = st->tau, itau = 1.0 / tau;
     double q[2] = {0.0, 0.0};
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
         const double xj = x[j], aj = atr[j];
-        const double w = sqrt(mu * mu + xj * xj);
-        const double gr = tau * xj / w - aj;
-        const double gj = fmin(1.0, fmax(-1.0, aj / tau));
-        const double h = tau * (1.0 - gj * xj / w) / w;
-        const double mi = 1.0 / (h + cn2[j]);
+        // one reciprocal square root instead of a square root and three divisions (FP64 pipe)
+        const double iw = rsqrt(mu * mu + xj * xj);
+        const double xw = xj * iw;
+        const double gr = tau * xw - aj;
+        const double gj = fmin(1.0, fmax(-1.0, aj * itau));
+        const double h = tau * (1.0 - gj * xw) * iw;
+        // the preconditioner needs only the precision of the CG vectors
+        CV mi;
+        if constexpr (sizeof(CV) == 8) mi = 1.0 / (h + cn2[j]);
+        else mi = __frcp_rn((float)(h + cn2[j]));
         const double rc = -gr;
-        const double z = mi * rc;
+        const CV zj = (CV)((double)mi * rc);
         grad[j] = gr;
-        hd[j] = h;
+        hd[j] = (CV)h;
         minv[j] = mi;
-        rcg[j] = rc;
-        p[j] = z;
-        if (p_g) p_g[j] = (PX)z;
-        d[j] = 0.0;
+        if constexpr (sizeof(CV) == 8) {
+            rcg[j] = rc;
+        } else {
+            const ff r = ff_from_double(rc);
+            rcg[j] = make_float2(r.hi, r.lo);
+        }
+        z[j] = zj;
+        d[j] = CV(0);
         q[0] += gr * gr;
-        q[1] += rc * z;
+        q[1] += rc * (double)zj;
     }
     block_reduce<kBlock, 2>(q, 0u, red);
     double tot[2];
@@ -166,12 +188,13 @@ __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x
         st->gnorm2 = tot[0];
         st->rz = tot[1];
         st->rz0 = tot[1];
+        st->beta = 0.0;
         st->cg_done = 0;
         st->cg_it = 0;
     }
 }
 
-// ---- C1: Ap = A p (also L1: Ad = A d with partials) -------------------------------------
+// ---- C1: Ap = A z + beta Ap, i.e. A p for p = z + beta p (also L1: Ad = A d with partials)
 template <class V, class Vec, class X, bool LS, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                   const V* __restrict__ val, const X* __restrict__ x,
@@ -182,14 +205,19 @@ __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ pt
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     if (!LS && *(volatile int32_t*)&st->cg_done) return;
+    // beta = 0 (first CG iteration): out holds no previous A p, and is not read
+    const Vec beta = LS ? Vec(0) : (Vec)st->beta;
     double p[2] = {0.0, 0.0};
     rows_of<PAIRED, V, X, Acc>(
-        ptr, col, val, x, m, sm, &st->stage_err, [&](int64_t i, bool has) { return (LS && has) ? r[i] : Vec(0); },
+        ptr, col, val, x, m, sm, &st->stage_err,
+        [&](int64_t i, bool has) { return !has ? Vec(0) : LS ? r[i] : (beta != Vec(0) ? out[i] : Vec(0)); },
         [&](int64_t i, Acc u, const Vec& ri) {
-            out[i] = u;
             if (LS) {
+                out[i] = u;
                 p[0] += (double)ri * (double)u;
                 p[1] += (double)u * (double)u;
+            } else {
+                out[i] = beta != Vec(0) ? u + beta * ri : u;
             }
         });
     if (!LS) return;
@@ -205,35 +233,41 @@ __global__ void __launch_bounds__(kBlock) k_pd_ax(const int32_t* __restrict__ pt
     }
 }
 
-// ---- C2 (PCG product, Sec. 8.1): Hp = h p + A^T Ap, alpha ------------------------------------------------------
+// ---- C2 (PCG product, Sec. 8.1): p = z + beta p, Hp = h p + A^T Ap, alpha ---------------------------------------
 template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                   const V* __restrict__ val, const Vec* __restrict__ ap,
-                                                  const double* __restrict__ hd, const double* __restrict__ p,
-                                                  double* __restrict__ hp, int64_t n, double* partials, PdState* st) {
+                                                  const Vec* __restrict__ hd, const Vec* __restrict__ z,
+                                                  Vec* __restrict__ p, Vec* __restrict__ hp, int64_t n,
+                                                  double* partials, PdState* st) {
     using Acc = Vec;
     __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
     __shared__ double red[32];
     if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
+    const Vec beta = (Vec)st->beta;
     double q[1] = {0.0};
+    ff qf = {0.0f, 0.0f};   // FP32 vectors: p.Hp summed in float-float (Sum2)
     struct Ops {
-        double pj, h;
+        Vec pj, h;
     };
     cols_of<PAIRED, V, Vec, Acc>(
         ptr, col, val, ap, n, sm, &st->stage_err,
         [&](int64_t j, bool has) {
-            Ops o{0.0, 0.0};
+            Ops o{Vec(0), Vec(0)};
             if (has) {
-                o.pj = p[j];
+                o.pj = beta != Vec(0) ? z[j] + beta * p[j] : z[j];
                 o.h = hd[j];
             }
             return o;
         },
         [&](int64_t j, Acc a, const Ops& o) {
-            const double h = o.h * o.pj + (double)a;
+            const Vec h = o.h * o.pj + a;
+            p[j] = o.pj;
             hp[j] = h;
-            q[0] += o.pj * h;
+            if constexpr (sizeof(Vec) == 8) q[0] += o.pj * h;
+            else sum2_add(qf, two_prod(o.pj, h));
         });
+    if constexpr (sizeof(Vec) == 4) q[0] = ff_to_double(qf);
     block_reduce<kBlock, 1>(q, 0u, red);
     double tot[1];
     if (grid_reduce_last<kBlock, 1>(q, 0u, partials, &st->cnt[4], tot, red) && threadIdx.x == 0) {
@@ -248,21 +282,45 @@ __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ pt
     }
 }
 
-// ---- C3: d += alpha p, res -= alpha Hp ------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_pd_cgupd(double* __restrict__ d, double* __restrict__ rcg,
-                                                     const double* __restrict__ p, const double* __restrict__ hp,
-                                                     const double* __restrict__ minv, int64_t n, double* partials,
-                                                     PdState* st) {
+// ---- C3: d += alpha p, res -= alpha Hp, z = M^{-1} res ---------------------------------
+template <class CV>
+__global__ void __launch_bounds__(kBlock) k_pd_cgupd(CV* __restrict__ d, typename CgRes<CV>::type* __restrict__ rcg,
+                                                     const CV* __restrict__ p, const CV* __restrict__ hp,
+                                                     const CV* __restrict__ minv, CV* __restrict__ z, int64_t n,
+                                                     double* partials, PdState* st) {
     __shared__ double red[2 * 32];
     if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
-    const double alpha = st->alpha;
     double q[2] = {0.0, 0.0};
-    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-        d[j] += alpha * p[j];
-        const double rc = rcg[j] - alpha * hp[j];
-        rcg[j] = rc;
-        q[0] += rc * rc;
-        q[1] += rc * (minv[j] * rc);
+    if constexpr (sizeof(CV) == 8) {
+        const double alpha = st->alpha;
+        for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+            const double pj = p[j];
+            d[j] += alpha * pj;
+            const double rc = rcg[j] - alpha * hp[j];
+            rcg[j] = rc;
+            const double zj = minv[j] * rc;
+            z[j] = zj;
+            q[1] += rc * zj;
+        }
+    } else {
+        // alpha as float-float; res -= alpha Hp and res.z in float-float on the FP32 pipes
+        const ff alpha = ff_from_double(st->alpha);
+        ff rz = {0.0f, 0.0f};
+        for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+            const float pj = p[j], hj = hp[j];
+            d[j] = __fmaf_rn(alpha.hi, pj, d[j]);
+            const float2 r2 = rcg[j];
+            ff ah = two_prod(alpha.hi, hj);
+            ah.lo = __fmaf_rn(alpha.lo, hj, ah.lo);
+            const ff r = ff_sub(ff{r2.x, r2.y}, ah);
+            rcg[j] = make_float2(r.hi, r.lo);
+            const float zj = minv[j] * r.hi;
+            z[j] = zj;
+            ff t = two_prod(r.hi, zj);
+            t.lo = __fmaf_rn(r.lo, zj, t.lo);
+            sum2_add(rz, t);
+        }
+        q[1] = ff_to_double(rz);
     }
     block_reduce<kBlock, 2>(q, 0u, red);
     double tot[2];
@@ -278,24 +336,15 @@ __global__ void __launch_bounds__(kBlock) k_pd_cgupd(double* __restrict__ d, dou
     }
 }
 
-// ---- C4: p = M^{-1} res + beta p --------------------------------------------------------
-template <class PX>
-__global__ void __launch_bounds__(kBlock) k_pd_pupd(double* __restrict__ p, PX* __restrict__ p_g,
-                                                    const double* __restrict__ rcg, const double* __restrict__ minv,
-                                                    int64_t n, const PdState* st) {
-    if (halted(st) || *(volatile const int32_t*)&st->cg_done) return;
-    const double beta = st->beta;
-    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-        const double v = minv[j] * rcg[j] + beta * p[j];
-        p[j] = v;
-        if (p_g) p_g[j] = (PX)v;
-    }
-}
-
 // ---- LT: Armijo trials on f_tau^mu of Eq. (prob2) -------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ x, const double* __restrict__ d,
+// NT trials per pass: the first pass tries the full step alone (most Newton steps take it),
+// later passes four halvings each; every trial costs a square root and a division per entry
+// on the FP64 pipe
+template <class CV, int NT>
+__global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ x, const CV* __restrict__ d,
                                                      const double* __restrict__ grad, int64_t n, double* partials,
                                                      PdState* st) {
+    constexpr int kTrialsPerPass = NT;
     __shared__ double red[(kTrialsPerPass + 1) * 32];
     if (halted(st) || *(volatile int32_t*)&st->ls_done) return;
     const double mu = st->mu, step0 = st->step;
@@ -303,7 +352,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ 
 #pragma unroll
     for (int t = 0; t <= kTrialsPerPass; ++t) q[t] = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-        const double xj = x[j], dj = d[j];
+        const double xj = x[j], dj = (double)d[j];
         const double w0 = sqrt(mu * mu + xj * xj);
         double a = step0;
 #pragma unroll
@@ -336,12 +385,13 @@ __global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ 
 }
 
 // ---- L3: x += step d (the dual estimate is recomputed from A^T r at the next N3) ----------
-__global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, const double* __restrict__ d, int64_t n,
+template <class CV>
+__global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, const CV* __restrict__ d, int64_t n,
                                                      PdState* st) {
     if (halted(st)) return;
     const double step = st->step;
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock)
-        x[j] += step * d[j];
+        x[j] += step * (double)d[j];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->prev_full = step == 1.0 ? 1 : 0;
         st->iter += 1;
@@ -358,9 +408,9 @@ int grid_for(const Inst* I, K kernel, int64_t rows) {
 }
 
 struct PdWork {
-    double *X = nullptr, *atr = nullptr, *grad = nullptr, *hd = nullptr, *minv = nullptr,
-           *rcg = nullptr, *p = nullptr, *hp = nullptr, *d = nullptr;
-    float* p32 = nullptr;   // FP32 shadow of p for the gathers of C1
+    double *X = nullptr, *atr = nullptr, *grad = nullptr;
+    void *hd = nullptr, *minv = nullptr, *z = nullptr, *p = nullptr, *hp = nullptr, *d = nullptr;   // CG vectors
+    void* rcg = nullptr;   // CG residual (CgRes)
     void *r = nullptr, *ap = nullptr, *ad = nullptr;
     double* part = nullptr;
     PdState* st = nullptr;
@@ -390,16 +440,13 @@ template <class V, class Vec, bool PAIRED>
 void enqueue_cg(Inst* I, PdWork* w, cudaStream_t s) {
     Csr<V> R, C;
     views<V, PAIRED>(I, R, C);
-    if constexpr (sizeof(Vec) == 8)
-        k_pd_ax<V, Vec, double, false, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->p, (Vec*)w->ap,
-                                                                        nullptr, I->m, w->part, w->st);
-    else
-        k_pd_ax<V, Vec, float, false, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->p32, (Vec*)w->ap,
-                                                                       nullptr, I->m, w->part, w->st);
-    k_pd_hp<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->ap, w->hd, w->p, w->hp,
-                                                     I->n, w->part, w->st);
-    k_pd_cgupd<<<w->gv, kBlock, 0, s>>>(w->d, w->rcg, w->p, w->hp, w->minv, I->n, w->part, w->st);
-    k_pd_pupd<float><<<w->gv, kBlock, 0, s>>>(w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->rcg, w->minv, I->n, w->st);
+    k_pd_ax<V, Vec, Vec, false, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, (const Vec*)w->z, (Vec*)w->ap,
+                                                                 nullptr, I->m, w->part, w->st);
+    k_pd_hp<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->ap, (const Vec*)w->hd,
+                                                     (const Vec*)w->z, (Vec*)w->p, (Vec*)w->hp, I->n, w->part, w->st);
+    k_pd_cgupd<Vec><<<w->gv, kBlock, 0, s>>>((Vec*)w->d, (typename CgRes<Vec>::type*)w->rcg, (const Vec*)w->p,
+                                             (const Vec*)w->hp,
+                                             (const Vec*)w->minv, (Vec*)w->z, I->n, w->part, w->st);
 }
 
 template <class V, class Vec, bool PAIRED>
@@ -413,9 +460,9 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         w = new PdWork();
         I->pd_work = w;
         I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
-        for (double** v : {&w->X, &w->atr, &w->grad, &w->hd, &w->minv, &w->rcg, &w->p, &w->hp, &w->d})
-            L1LS_TRY(I->alloc_n(v, n));
-        if (sizeof(Vec) == 4) L1LS_TRY(I->alloc_n(&w->p32, n));
+        for (double** v : {&w->X, &w->atr, &w->grad}) L1LS_TRY(I->alloc_n(v, n));
+        L1LS_TRY(I->alloc(&w->rcg, sizeof(typename CgRes<Vec>::type) * pad32(n)));
+        for (void** v : {&w->hd, &w->minv, &w->z, &w->p, &w->hp, &w->d}) L1LS_TRY(I->alloc(v, sizeof(Vec) * pad32(n)));
         L1LS_TRY(I->alloc(&w->r, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->ap, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->ad, sizeof(Vec) * pad32(m)));
@@ -469,7 +516,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         cudaStreamDestroy(cap);
         w->cg_chunk = chunk;
     }
-    const int ls_passes = (o->ls_max + kTrialsPerPass - 1) / kTrialsPerPass;
+    const int ls_passes = (o->ls_max - 1 + kTrialsPerPass - 1) / kTrialsPerPass;   // after the full-step pass
     for (;;) {
         // N1 gathers the FP64 iterate (once per Newton step)
         k_pd_resid<V, Vec, double, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->X, bvec, (Vec*)w->r, m,
@@ -492,8 +539,9 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
             final_status = L1LS_ECANCELLED;
             break;
         }
-        k_pd_init<float><<<w->gv, kBlock, 0, s>>>(w->X, w->atr, I->colnorm2, w->grad, w->hd, w->minv, w->rcg,
-                                                  w->p, sizeof(Vec) == 8 ? nullptr : w->p32, w->d, n, w->part, w->st);
+        k_pd_init<Vec><<<w->gv, kBlock, 0, s>>>(w->X, w->atr, I->colnorm2, w->grad, (Vec*)w->hd, (Vec*)w->minv,
+                                                (typename CgRes<Vec>::type*)w->rcg, (Vec*)w->z, (Vec*)w->d, n,
+                                                w->part, w->st);
         L1LS_CUDA(cudaGetLastError());
         const int64_t max_cg_launches = o->pcg_max / chunk + 3;
         for (int64_t launch = 0;; ++launch) {
@@ -507,11 +555,13 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
             if (w->host->cg_done) break;
         }
         if (final_status != L1LS_OK) break;
-        k_pd_ax<V, Vec, double, true, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->d, (Vec*)w->ad,
-                                                                       (const Vec*)w->r, m, w->part, w->st);
+        k_pd_ax<V, Vec, Vec, true, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, (const Vec*)w->d,
+                                                                    (Vec*)w->ad, (const Vec*)w->r, m, w->part, w->st);
+        k_pd_trial<Vec, 1><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n, w->part, w->st);
         for (int t = 0; t < ls_passes; ++t)
-            k_pd_trial<<<w->gv, kBlock, 0, s>>>(w->X, w->d, w->grad, n, w->part, w->st);
-        k_pd_apply<<<w->gv, kBlock, 0, s>>>(w->X, w->d, n, w->st);
+            k_pd_trial<Vec, kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n, w->part,
+                                                                     w->st);
+        k_pd_apply<Vec><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, n, w->st);
         L1LS_CUDA(cudaGetLastError());
     }
     const PdState& f = *w->host;
