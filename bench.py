@@ -313,6 +313,7 @@ def batch_form(l1, W, ctx, iters_per_tau):
     b.free()
     it = sum(r["iters"] for rr in res for r in rr)
     ok = sum(r["status"] == 0 for rr in res for r in rr)
+    ok_by_tau = [sum(rr[j]["status"] == 0 for rr in res) for j in range(taus.shape[1])]
     for i in insts:
         i.free()
     sub = list(range(0, 256, 16))
@@ -329,17 +330,21 @@ def batch_form(l1, W, ctx, iters_per_tau):
         t_one += time.perf_counter() - t
         inst.free()
     rate, rate_one = it / el, it_one / t_one
+    cert_rate, cert_rate_one = ok / el, ok_one / t_one
     return {"workload": "c4: 256 instances, n = 2^U[12,18], m = 2n, ~8/col, kappa 10^U[2,5], x* 1%%, 16 taus "
                         "0.9 lambda_max .. 1e-3, warm-started, tol 1e-6, at most %d FISTA iterations per tau"
                         % iters_per_tau,
             "batched": {"seconds": el, "instance_iterations": it, "instance_iterations_per_s": rate,
-                        "certified": ok, "of": 256 * 16, "steps": st["steps"],
+                        "certified": ok, "of": 256 * 16, "certified_per_s": cert_rate,
+                        "certified_by_tau_index": ok_by_tau, "steps": st["steps"],
                         "ms_per_step": st["device_ms"] / max(1, st["steps"]), "schedule": sched,
                         "values": "FP32, float-float products and iterates"},
             "one_at_a_time_fp64": {"seconds": t_one, "instances": len(sub), "instance_iterations": it_one,
                                    "instance_iterations_per_s": rate_one, "certified": ok_one,
-                                   "of": len(sub) * 16, "api": "l1ls_solve_fista per instance and tau"},
-            "speedup_instance_iterations": rate / rate_one}
+                                   "of": len(sub) * 16, "certified_per_s": cert_rate_one,
+                                   "api": "l1ls_solve_fista per instance and tau"},
+            "speedup_instance_iterations": rate / rate_one,
+            "speedup_certified_per_s": cert_rate / max(cert_rate_one, 1e-12)}
 
 
 SERVE_RATES = (10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0)
@@ -362,7 +367,7 @@ def serve_form(l1, W, count, rates, log2n_hi, slots=16):
         ctx.serve_config(slots=slots)
         # iteration caps, not time limits: the same requests finish (or stop) in both runs
         of = dict(tol=1e-6, max_iter=5000, restart=1, accum=accum)
-        op = dict(tol=1e-6, max_iter=30, pcg_max=300)
+        op = dict(tol=1e-6, max_iter=30, pcg_max=300, accum=accum)
         t0 = time.perf_counter()
         tickets = []
         for r in reqs:
@@ -610,8 +615,8 @@ def c1_form(l1, W):
 def precision_form(l1, W, limit_s):
     """C3: A stored as FP64 / FP32 / BF16 at kappa 1e2, 1e4, 1e6 (m = 2^22, n = 2^21, 16 per
     column, x* 2%, tau = tau_gen = 1): FISTA (gradient restart; float-float products for FP32 /
-    BF16) and pdNCG, each to a 1e-6 gap (1e-4 for BF16) within `limit_s`, against the FP64
-    optimum x*, f* of the generator."""
+    BF16) and pdNCG (float-float gradient products for FP32 / BF16), each to a 1e-6 gap (1e-4 for
+    BF16) within `limit_s`, against the FP64 optimum x*, f* of the generator."""
     import numpy as np
     ctx = l1.Context(0)
     rows = []
@@ -627,7 +632,8 @@ def precision_form(l1, W, limit_s):
                     x, r = inst.solve_fista(tau=1.0, tol=tol, max_iter=10 ** 6, restart=1,
                                             accum=0 if dt == "f64" else 1, time_limit_s=limit_s, allow=(4, 5))
                 else:
-                    x, r = inst.solve_pdncg(tau=1.0, tol=tol, max_iter=200, time_limit_s=limit_s, allow=(4, 5))
+                    x, r = inst.solve_pdncg(tau=1.0, tol=tol, max_iter=200, accum=0 if dt == "f64" else 1,
+                                            time_limit_s=limit_s, allow=(4, 5))
                 el = time.perf_counter() - t
                 rows.append({"kappa": kappa, "values": dt, "method": method, "tol": tol, "status": r["status_name"],
                              "iters": r["iters"], "cg_iters": r["cg_iters"], "seconds": el, "rel_gap": r["rel_gap"],

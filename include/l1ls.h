@@ -206,7 +206,10 @@ typedef struct {
                                  default); 1 = products of the float-float iterate and residual
                                  summed in float-float (about 44 bits), for gaps below the FP32
                                  floor at small tau or large kappa.  EINVAL with FP64 values.
-                                 Batches always use 1.                                         */
+                                 Batches always use 1.  pdNCG, FP32 / BF16 values: 1 = the
+                                 two products of each Newton step that give the gradient and
+                                 the certificate (r = b - A x, A^T r) in float-float, the PCG
+                                 products in FP32; ignored with FP64 values.                   */
     double f_target;          /* FISTA, FISTA with backtracking, pdNCG: also stop (status OK) as
                                  soon as the certified objective f(x_k) <= f_target, the rule by
                                  which the paper ends its comparison solvers (Sec. 8.3); -inf

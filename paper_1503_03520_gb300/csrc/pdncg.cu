@@ -89,6 +89,36 @@ __global__ void __launch_bounds__(kBlock) k_pd_resid(const int32_t* __restrict__
     }
 }
 
+// Certificate at x from ||r||^2, b.r (st->k1) and tot = {max |A^T r|, ||x||_1}, the stop test
+// and the mu-continuation (last CTA of N2, thread 0)
+__device__ void pd_certify(PdState* st, const double (&tot)[2]) {
+    const double tau = st->tau;
+    const double P = __dadd_rn(__dmul_rn(tau, tot[1]), __dmul_rn(0.5, st->k1[0]));
+    const double s = tot[0] <= tau ? 1.0 : tau / tot[0];
+    const double D = __dadd_rn(__dmul_rn(s, st->k1[1]), -__dmul_rn(__dmul_rn(__dmul_rn(0.5, s), s), st->k1[0]));
+    const double gap = P - D;
+    const double rel = gap / fmax(fabs(P), 1e-300);
+    st->P = P;
+    st->D = D;
+    st->gap = gap;
+    st->rel = rel;
+    st->products += 2;
+    if (!isfinite(P) || !isfinite(D)) {
+        st->status = L1LS_ENUMERIC;
+        st->stop = 1;
+    } else if (rel <= st->tol || P <= st->f_target) {
+        st->status = L1LS_OK;
+        st->stop = 1;
+    } else if (st->iter >= st->max_newton) {
+        st->status = L1LS_ENOCONV;
+        st->stop = 1;
+    } else {
+        if (st->prev_full && st->mu > st->mu_target) st->mu = fmax(st->mu * 0.1, st->mu_target);
+        else if (st->prev_full && gap > st->stall * st->prev_gap) st->mu = fmax(st->mu * 0.1, st->mu_min);
+        st->prev_gap = gap;
+    }
+}
+
 // ---- N2: a = A^T r, certificate ---------------------------------------------------------
 template <class V, class Vec, bool PAIRED>
 __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
@@ -109,32 +139,93 @@ __global__ void __launch_bounds__(kBlock) k_pd_atr(const int32_t* __restrict__ p
         });
     block_reduce<kBlock, 2>(p, 1u, red);
     double tot[2];
-    if (grid_reduce_last<kBlock, 2>(p, 1u, partials, &st->cnt[1], tot, red) && threadIdx.x == 0) {
-        const double tau = st->tau;
-        const double P = __dadd_rn(__dmul_rn(tau, tot[1]), __dmul_rn(0.5, st->k1[0]));
-        const double s = tot[0] <= tau ? 1.0 : tau / tot[0];
-        const double D = __dadd_rn(__dmul_rn(s, st->k1[1]), -__dmul_rn(__dmul_rn(__dmul_rn(0.5, s), s), st->k1[0]));
-        const double gap = P - D;
-        const double rel = gap / fmax(fabs(P), 1e-300);
-        st->P = P;
-        st->D = D;
-        st->gap = gap;
-        st->rel = rel;
-        st->products += 2;
-        if (!isfinite(P) || !isfinite(D)) {
-            st->status = L1LS_ENUMERIC;
-            st->stop = 1;
-        } else if (rel <= st->tol || P <= st->f_target) {
-            st->status = L1LS_OK;
-            st->stop = 1;
-        } else if (st->iter >= st->max_newton) {
-            st->status = L1LS_ENOCONV;
-            st->stop = 1;
+    if (grid_reduce_last<kBlock, 2>(p, 1u, partials, &st->cnt[1], tot, red) && threadIdx.x == 0) pd_certify(st, tot);
+}
+
+// ---- N1 / N2 with float-float products (accum = 1; FP32 / BF16 values) ----------------
+// At large kappa the residual b - A x is a small difference of large terms (e reaches
+// 1 / sigma_min) and FP32 sums of A^T r lose the gradient to rounding; as in FISTA's
+// compensated kernels, x is gathered as a float-float pair, A x and the residual are kept in
+// float-float (paired storage: one float4 {hi, hi, lo, lo} per row pair; plain: float2 per
+// row) and A^T r is summed in float-float.  The high words of r also go to the FP32 residual
+// that the line search reads.
+template <class V, bool PAIRED>
+__global__ void __launch_bounds__(kBlock) k_pd_resid_ff(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                        const V* __restrict__ val, const float* __restrict__ xh,
+                                                        const float* __restrict__ xl, const float* __restrict__ b,
+                                                        float* __restrict__ rff, float* __restrict__ r, int64_t m,
+                                                        double* partials, PdState* st) {
+    __shared__ typename std::conditional<PAIRED, PairedSmem<V, kBlock>, CompSmem<kBlock>>::type sm;
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    ff q0 = {0.0f, 0.0f}, q1 = {0.0f, 0.0f};
+    auto pre = [&](int64_t i, bool has) { return has ? b[i] : 0.0f; };
+    auto epi = [&](int64_t i, ff u, const float& bb) {
+        const ff rr = ff_sub(ff_from_float(bb), u);
+        if (PAIRED) {
+            rff[4 * (i >> 1) + (i & 1)] = rr.hi;
+            rff[4 * (i >> 1) + 2 + (i & 1)] = rr.lo;
         } else {
-            if (st->prev_full && st->mu > st->mu_target) st->mu = fmax(st->mu * 0.1, st->mu_target);
-            else if (st->prev_full && gap > st->stall * st->prev_gap) st->mu = fmax(st->mu * 0.1, st->mu_min);
-            st->prev_gap = gap;
+            rff[2 * i] = rr.hi;
+            rff[2 * i + 1] = rr.lo;
         }
+        r[i] = rr.hi;
+        sum2_add(q0, ff_mul(rr, rr));
+        sum2_add(q1, ff_mul(ff_from_float(bb), rr));
+    };
+    const int64_t nrows = PAIRED ? m / 2 : m;
+    if constexpr (PAIRED) {
+        warp_pcsr<true, V>(ptr, col, val, nrows, sm, &st->stage_err, FFSum<true, V>{xh, xl, nullptr}, pre, epi);
+    } else {
+        const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (nrows + 31) >> 5;
+        for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
+            tile_ff<true, false, V>(t, ptr, col, val, xh, xl, nullptr, nrows, sm.warp_buf(), pre, epi);
+    }
+    double p[2] = {ff_to_double(q0), ff_to_double(q1)};
+    block_reduce<kBlock, 2>(p, 0u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(p, 0u, partials, &st->cnt[0], tot, red) && threadIdx.x == 0) {
+        st->k1[0] = tot[0];
+        st->k1[1] = tot[1];
+    }
+}
+
+template <class V, bool PAIRED>
+__global__ void __launch_bounds__(kBlock) k_pd_atr_ff(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                      const V* __restrict__ val, const float* __restrict__ rff,
+                                                      const double* __restrict__ x, double* __restrict__ atr,
+                                                      int64_t n, double* partials, PdState* st) {
+    __shared__ typename std::conditional<PAIRED, PairedSmem<V, kBlock>, CompSmem<kBlock>>::type sm;
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    double p[2] = {0.0, 0.0};
+    auto pre = [&](int64_t j, bool has) { return has ? x[j] : 0.0; };
+    auto epi = [&](int64_t j, ff g, const double& xj) {
+        const double a = ff_to_double(g);
+        atr[j] = a;
+        p[0] = fmax(p[0], fabs(a));
+        p[1] += fabs(xj);
+    };
+    if constexpr (PAIRED) {
+        warp_pcsr<false, V>(ptr, col, val, n, sm, &st->stage_err,
+                            FFSum<false, V>{nullptr, nullptr, reinterpret_cast<const float4*>(rff)}, pre, epi);
+    } else {
+        const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (n + 31) >> 5;
+        for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
+            tile_ff<false, false, V>(t, ptr, col, val, nullptr, nullptr, rff, n, sm.warp_buf(), pre, epi);
+    }
+    block_reduce<kBlock, 2>(p, 1u, red);
+    double tot[2];
+    if (grid_reduce_last<kBlock, 2>(p, 1u, partials, &st->cnt[1], tot, red) && threadIdx.x == 0) pd_certify(st, tot);
+}
+
+// x as a float-float pair for the compensated N1
+__global__ void __launch_bounds__(kBlock) k_pd_split(const double* __restrict__ x, float* __restrict__ xh,
+                                                     float* __restrict__ xl, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const ff v = ff_from_double(x[j]);
+        xh[j] = v.hi;
+        xl[j] = v.lo;
     }
 }
 
@@ -387,11 +478,18 @@ __global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ 
 // ---- L3: x += step d (the dual estimate is recomputed from A^T r at the next N3) ----------
 template <class CV>
 __global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, const CV* __restrict__ d, int64_t n,
-                                                     PdState* st) {
+                                                     float* __restrict__ xh, float* __restrict__ xl, PdState* st) {
     if (halted(st)) return;
     const double step = st->step;
-    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock)
-        x[j] += step * (double)d[j];
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const double v = x[j] + step * (double)d[j];
+        x[j] = v;
+        if (xh) {   // the float-float copy that the compensated N1 gathers
+            const ff f = ff_from_double(v);
+            xh[j] = f.hi;
+            xl[j] = f.lo;
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->prev_full = step == 1.0 ? 1 : 0;
         st->iter += 1;
@@ -412,10 +510,11 @@ struct PdWork {
     void *hd = nullptr, *minv = nullptr, *z = nullptr, *p = nullptr, *hp = nullptr, *d = nullptr;   // CG vectors
     void* rcg = nullptr;   // CG residual (CgRes)
     void *r = nullptr, *ap = nullptr, *ad = nullptr;
+    float *xh = nullptr, *xl = nullptr, *rff = nullptr;   // compensated N1 / N2 (accum = 1)
     double* part = nullptr;
     PdState* st = nullptr;
     PdState* host = nullptr;
-    int gm = 0, gn = 0, gv = 0;
+    int gm = 0, gn = 0, gv = 0, gmf = 0, gnf = 0;
     cudaGraphExec_t cg_exec = nullptr;
     int cg_chunk = 0;
     ~PdWork() {
@@ -469,13 +568,29 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         w->gm = grid_for(I, k_pd_resid<V, Vec, double, PAIRED>, PAIRED ? m / 2 : m);
         w->gn = grid_for(I, k_pd_atr<V, Vec, PAIRED>, n);
         w->gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)I->ctx->num_sms * 8));
-        const int gmax = std::max(w->gm, std::max(w->gn, w->gv));
+        int gmax = std::max(w->gm, std::max(w->gn, w->gv));
+        if constexpr (sizeof(Vec) == 4) {
+            w->gmf = grid_for(I, k_pd_resid_ff<V, PAIRED>, PAIRED ? m / 2 : m);
+            w->gnf = grid_for(I, k_pd_atr_ff<V, PAIRED>, n);
+            gmax = std::max(gmax, std::max(w->gmf, w->gnf));
+        }
         L1LS_TRY(I->alloc_n(&w->part, (int64_t)gmax * (kTrialsPerPass + 1)));
         L1LS_TRY(I->alloc_n(&w->st, 1));
         w->host = new PdState();   // pageable: no allocation that synchronises the device
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
+    // accum = 1 with FP32 / BF16 values: the gradient's products N1 / N2 in float-float
+    const bool comp = sizeof(Vec) == 4 && o->accum == 1;
+    if (comp) {
+        if (!w->xh) {
+            L1LS_TRY(I->alloc_n(&w->xh, pad32(n)));
+            L1LS_TRY(I->alloc_n(&w->xl, pad32(n)));
+            L1LS_TRY(I->alloc_n(&w->rff, 2 * pad32(m)));
+        }
+        k_pd_split<<<w->gv, kBlock, 0, s>>>(w->X, w->xh, w->xl, n);
+        L1LS_CUDA(cudaGetLastError());
+    }
     PdState h;
     memset(&h, 0, sizeof(h));
     h.tau = o->tau;
@@ -518,11 +633,21 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     }
     const int ls_passes = (o->ls_max - 1 + kTrialsPerPass - 1) / kTrialsPerPass;   // after the full-step pass
     for (;;) {
-        // N1 gathers the FP64 iterate (once per Newton step)
-        k_pd_resid<V, Vec, double, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->X, bvec, (Vec*)w->r, m,
-                                                                    w->part, w->st);
-        k_pd_atr<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->r, w->X, w->atr, n,
-                                                          w->part, w->st);
+        // N1 gathers the FP64 iterate (once per Newton step), or its float-float copy
+        if constexpr (sizeof(Vec) == 4) {
+            if (comp) {
+                k_pd_resid_ff<V, PAIRED><<<w->gmf, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->xh, w->xl, I->bhat32, w->rff,
+                                                                   (float*)w->r, m, w->part, w->st);
+                k_pd_atr_ff<V, PAIRED><<<w->gnf, kBlock, 0, s>>>(C.ptr, C.idx, C.val, w->rff, w->X, w->atr, n, w->part,
+                                                                 w->st);
+            }
+        }
+        if (!comp) {
+            k_pd_resid<V, Vec, double, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->X, bvec, (Vec*)w->r, m,
+                                                                        w->part, w->st);
+            k_pd_atr<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->r, w->X, w->atr, n,
+                                                              w->part, w->st);
+        }
         L1LS_CUDA(cudaGetLastError());
         L1LS_CUDA(cudaMemcpyAsync(w->host, w->st, sizeof(PdState), cudaMemcpyDeviceToHost, s));
         L1LS_CUDA(cudaStreamSynchronize(s));
@@ -561,7 +686,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         for (int t = 0; t < ls_passes; ++t)
             k_pd_trial<Vec, kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n, w->part,
                                                                      w->st);
-        k_pd_apply<Vec><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, n, w->st);
+        k_pd_apply<Vec><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, n, comp ? w->xh : nullptr,
+                                                 comp ? w->xl : nullptr, w->st);
         L1LS_CUDA(cudaGetLastError());
     }
     const PdState& f = *w->host;

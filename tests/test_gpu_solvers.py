@@ -311,3 +311,28 @@ def test_tau_at_or_above_lambda_max_gives_zero(ctx, factor, dt):
         assert r["status"] == 0 and not np.any(x)
     finally:
         inst.free()
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e6])
+def test_pdncg_compensated_gradient_at_large_kappa(ctx, kappa):
+    """accum = 1: pdNCG's gradient products (r = b - A x, A^T r) in float-float, the PCG in FP32.
+    The C3 recipe (16 per column, x* 2%) at n = 2^14 with FP32 values: at kappa = 1e6 the
+    residual's entries reach 1 / sigma_min = 1e6 and FP32 sums of A^T r lose the gradient.  The
+    oracle re-certifies the device's x on the stored problem, and its own pdNCG on that problem
+    bounds the Newton count (the two part only through rounding in the line search)."""
+    params = W.params(m=2 ** 15, n=2 ** 14, seed=0, kappa=kappa, xstar_frac=0.02, right_stages=4,
+                      left_stages=1, value_dtype="f32")
+    ref = oracle_instance(params)
+    A = stored_values(ref.A, "f32")
+    b = ref.b.astype(np.float32).astype(np.float64)
+    inst = ctx.generate(params)
+    try:
+        x, r = inst.solve_pdncg(tau=1.0, tol=1e-6, max_iter=200, accum=1)
+        assert r["status"] == 0 and r["rel_gap"] <= 1e-6
+        P, D, gap, rel = solvers.certificate(A, b, 1.0, x)
+        assert rel <= 2e-5
+        o = solvers.pdncg(A, b, 1.0, 1e-6)
+        assert o["status"] == 0
+        assert r["iters"] <= 2 * o["iters"] + 3, (r["iters"], o["iters"])
+    finally:
+        inst.free()
