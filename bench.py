@@ -288,6 +288,47 @@ def max_over_ranks(value, dist, device="cuda"):
     return float(t.item())
 
 
+def pcg_bytes_per_iteration(m, n, nnz):
+    """Algorithmic bytes of one pdNCG PCG iteration with FP32 values in paired storage: C1 (the
+    row pairs, z gathered, A p read and written), C2 (the columns, A p gathered as one float2 per
+    row pair, z, p and the curvature read, p and Hp written), C3 (d, p, Hp, M^-1 read and the
+    float-float residual read; d, z written and the residual written)."""
+    mat = (nnz // 2) * 12
+    c1 = mat + (m // 2 + 1) * 4 + 4 * n + 8 * m
+    c2 = mat + (n + 1) * 4 + 4 * m + 12 * n + 8 * n
+    c3 = 16 * n + 8 * n + 8 * n + 8 * n
+    return c1 + c2 + c3
+
+
+def pcg_iteration_timing(inst, m, n, nnz, lo=16, hi=144):
+    """Time per PCG iteration of pdNCG: one Newton step from a point near x* with the relative
+    residual target 1e-30 (PCG runs to its cap) at two caps; the difference of the two solve
+    times over the difference of the iteration counts (whole CUDA-graph chunks of 16, so the
+    host checks cancel)."""
+    import numpy as np
+    xs = inst.xstar()
+    rng = np.random.default_rng(0)
+    x0 = xs * (1.0 + 0.01 * rng.standard_normal(xs.size)) + 1e-3 * rng.standard_normal(xs.size)
+    out = {}
+    for k in (lo, hi):
+        best = None
+        for _ in range(3):
+            t = time.perf_counter()
+            _, r = inst.solve_pdncg(x0=x0, tau=1.0, tol=0.0, max_iter=1, pcg_max=k, pcg_rtol=1e-30, mu_start=1e-5,
+                                    check_every=16, allow=(4, 5))
+            el = time.perf_counter() - t
+            best = el if best is None else min(best, el)
+        out[k] = (best, r["cg_iters"])
+    iters = out[hi][1] - out[lo][1]
+    if iters <= 0:
+        return None
+    ms = (out[hi][0] - out[lo][0]) / iters * 1e3
+    b = pcg_bytes_per_iteration(m, n, nnz)
+    peak, src = measured_hbm_peak()
+    return {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak,
+            "peak_source": src, "method": "(t(%d) - t(%d)) / %d PCG iterations of one Newton step" % (hi, lo, iters)}
+
+
 def rank_workload(log2n, rank):
     """The instance each rank times: the same recipe, its own seed (replicas, no collective)."""
     import workloads as W
@@ -787,6 +828,8 @@ def run_ours(args):
                                     "cg_iters": r["cg_iters"], "products": r["products"], "rel_gap": r["rel_gap"],
                                     "status": r["status_name"],
                                     "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]}
+        if not args.matrix_free:
+            solves["pdncg"]["pcg_iteration"] = pcg_iteration_timing(inst, m, n, nnz)
 
     inst.free()
     forms = None

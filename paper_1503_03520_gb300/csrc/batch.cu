@@ -49,8 +49,8 @@ struct BDesc {
     const float* b;
     float2* ax;                // A x_{k-1}, float-float per row
     float4* res;               // b - A y_k per row pair {hi(2p), hi(2p+1), lo(2p), lo(2p+1)}
-    float* xh[2];              // iterates x_{k-1}, x_{k-2} (alternating), float-float:
-    float* xl[2];              //   high and low words
+    float2* x[2];              // iterates x_{k-1}, x_{k-2} (alternating), float-float {hi, lo}
+                               //   pairs: the row phase gathers both words with one load
     int64_t m, n;
     int64_t s1_begin, s2_begin;    // first segment of the instance in each segment list
     int64_t n1, n2;                // tiles of the instance: row-pair tiles, column tiles
@@ -253,8 +253,8 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
     const int32_t* rptr = dp->rptr;
     const int32_t* rcol = dp->rcol;
     const V* rval = static_cast<const V*>(dp->rval);
-    const float* xh = dp->xh[cur];
-    const float* xl = dp->xl[cur];
+    const float* xh = reinterpret_cast<const float*>(dp->x[cur]);   // interleaved pairs
+    const float* xl = nullptr;
     float2* ax = dp->ax;
     const float* bv = dp->b;
     float* resf = reinterpret_cast<float*>(dp->res);
@@ -308,29 +308,27 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
     const int32_t* cpair = dp->cpair;
     const V* cval = static_cast<const V*>(dp->cval);
     const float4* res = dp->res;
-    const float* x1h = dp->xh[cur];
-    const float* x1l = dp->xl[cur];
-    float* x0h = dp->xh[cur ^ 1];
-    float* x0l = dp->xl[cur ^ 1];
+    const float2* x1p = dp->x[cur];
+    float2* x0p = dp->x[cur ^ 1];
     const int64_t n = dp->n;
     float gmax = 0.0f;
     ff l1 = {0.0f, 0.0f}, rt = {0.0f, 0.0f};
     struct Ops {
         ff x1, x0;
     };
-    auto pre = [x1h, x1l, x0h, x0l](int64_t j, bool has) {
+    auto pre = [x1p, x0p](int64_t j, bool has) {
         Ops o{{0.f, 0.f}, {0.f, 0.f}};
         if (has) {
-            o.x1 = {x1h[j], x1l[j]};
-            o.x0 = {x0h[j], x0l[j]};
+            const float2 a = x1p[j], b = x0p[j];
+            o.x1 = {a.x, a.y};
+            o.x0 = {b.x, b.y};
         }
         return o;
     };
     auto epi = [&](int64_t j, ff g, const Ops& o) {
         // y = x_k + beta (x_k - x_{k-1}); x_{k+1} = S_{tau/L}(y + A^T r / L) (Sec. 8.1)
         const FfStep f = ff_fista_step(o.x1, o.x0, g, beta_f, invL_f, thr_f);
-        x0h[j] = f.x.hi;
-        x0l[j] = f.x.lo;
+        x0p[j] = make_float2(f.x.hi, f.x.lo);
         gmax = fmaxf(gmax, fabsf(g.hi));
         sum2_add(l1, f.mag);
         if (rs) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, o.x1)));
@@ -420,9 +418,9 @@ __global__ void __launch_bounds__(BLOCK, L1LS_BATCH_WARPS_PER_SM * 32 / BLOCK) k
     }
 }
 
-__global__ void k_ff2d_b(const float* __restrict__ hi, const float* __restrict__ lo, int64_t n, double* __restrict__ out) {
+__global__ void k_ff2d_b(const float2* __restrict__ x, int64_t n, double* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = ff_to_double({hi[i], lo[i]});
+    if (i < n) out[i] = ff_to_double({x[i].x, x[i].y});
 }
 
 }  // namespace
@@ -553,10 +551,8 @@ extern "C" l1ls_status l1ls_batch_create(l1ls_ctx* hctx, int count, l1ls_inst* c
         d.res = reinterpret_cast<float4*>(slab + off);
         off += 2 * (size_t)pad32(I->m);
         for (int k = 0; k < 2; ++k) {
-            d.xh[k] = slab + off;
-            off += pad32(I->n);
-            d.xl[k] = slab + off;
-            off += pad32(I->n);
+            d.x[k] = reinterpret_cast<float2*>(slab + off);
+            off += 2 * (size_t)pad32(I->n);
         }
         d.m = I->m;
         d.n = I->n;
@@ -758,7 +754,7 @@ extern "C" l1ls_status l1ls_batch_solve_path(l1ls_batch* h, const double* taus, 
             const int fb = hs[i].final_buf;
             double* tmp = nullptr;
             L1LS_CUDA(cudaMallocAsync((void**)&tmp, sizeof(double) * d.n, st));
-            k_ff2d_b<<<(unsigned)((d.n + 255) / 256), 256, 0, st>>>(d.xh[fb], d.xl[fb], d.n, tmp);
+            k_ff2d_b<<<(unsigned)((d.n + 255) / 256), 256, 0, st>>>(d.x[fb], d.n, tmp);
             L1LS_CUDA(cudaGetLastError());
             L1LS_CUDA(cudaMemcpyAsync(x_out[i], tmp, sizeof(double) * d.n, cudaMemcpyDefault, st));
             L1LS_CUDA(cudaFreeAsync(tmp, st));

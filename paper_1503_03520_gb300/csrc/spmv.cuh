@@ -520,7 +520,7 @@ namespace l1ls {
 // warp buffer), which holds high and low words here.
 //
 // Inputs: the row traversal gathers a float-float vector kept as two FP32 arrays (high and low
-// words).  The column traversal gathers the residual: in paired storage the residual of row
+// words), or, when the low-word array is NULL, as one array of interleaved {hi, lo} pairs.  The column traversal gathers the residual: in paired storage the residual of row
 // pair p is one float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} (both rows with one 16-byte load),
 // in plain storage one float2 {hi, lo} per row.
 
@@ -566,8 +566,17 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
                 const float v0 = val_to_acc<float>(vv[kVals * k]);
                 const float v1 = PAIRED ? val_to_acc<float>(vv[kVals * k + kVals - 1]) : 0.f;
                 if (ROWS) {
-                    const float hx = in ? __ldg(xh + ij[k]) : 0.f;
-                    const float lx = in ? __ldg(xl + ij[k]) : 0.f;
+                    float hx = 0.f, lx = 0.f;
+                    if (in) {
+                        if (xl) {
+                            hx = __ldg(xh + ij[k]);
+                            lx = __ldg(xl + ij[k]);
+                        } else {   // interleaved {hi, lo} pairs: one 8-byte gather
+                            const float2 g = __ldg(reinterpret_cast<const float2*>(xh) + ij[k]);
+                            hx = g.x;
+                            lx = g.y;
+                        }
+                    }
                     p0[k] = two_prod(v0, hx);
                     p0[k].lo = __fmaf_rn(v0, lx, p0[k].lo);
                     if (PAIRED) {
@@ -659,7 +668,7 @@ __device__ __forceinline__ void tiles_ff(int64_t t0, int64_t t1, const int32_t* 
 // Algorithm Sum2 of Ogita, Rump & Oishi (TwoSum on the high word, the errors and low words in
 // one FP32 word), which is as accurate as a sum in twice the working precision; the row sum
 // is renormalised by TwoSum at the end.  ROWS gathers the float-float vector (xh, xl) at the
-// column index; otherwise the residual float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} at the pair.
+// column index (xl NULL: xh holds interleaved {hi, lo} pairs); otherwise the residual float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} at the pair.
 template <bool ROWS, class V> struct FFSum {
     using acc_t = ff;
     const float* xh;
@@ -677,8 +686,14 @@ template <bool ROWS, class V> struct FFSum {
                     const int32_t j = ib[e + k - off];
                     pair_to_acc<float>(vb[e + k - off], v0[k], v1[k]);
                     if (ROWS) {
-                        g0[k] = __ldg(xh + j);
-                        h0[k] = __ldg(xl + j);
+                        if (xl) {
+                            g0[k] = __ldg(xh + j);
+                            h0[k] = __ldg(xl + j);
+                        } else {   // interleaved {hi, lo} pairs: one 8-byte gather
+                            const float2 g = __ldg(reinterpret_cast<const float2*>(xh) + j);
+                            g0[k] = g.x;
+                            h0[k] = g.y;
+                        }
                     } else {
                         const float4 g = __ldg(r4 + j);
                         g0[k] = g.x;

@@ -95,3 +95,19 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     s = bench.ClockSampler(0)
     s.start()
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_pcg_iteration_bytes_counted_array_by_array():
+    """One pdNCG PCG iteration (FP32 values, paired storage), array by array: both orientations
+    of the matrix with their pointers; C1 gathers z (n floats) and reads and writes A p (m
+    floats each); C2 gathers A p (m floats), reads z, p, h and writes p, Hp (n floats each); C3
+    reads d, p, Hp, M^-1 (n floats each) and the float-float residual (n pairs), writes d, z and
+    the residual."""
+    n = 2 ** 24
+    m, nnz = 2 * n, 8 * n - 8
+    mats = 2 * (4 * (nnz // 2) + 4 * nnz) + 4 * (m // 2 + 1) + 4 * (n + 1)
+    c1 = 4 * n + 4 * m + 4 * m
+    c2 = 4 * m + 3 * 4 * n + 2 * 4 * n
+    c3 = 4 * 4 * n + 8 * n + 2 * 4 * n + 8 * n
+    assert bench.pcg_bytes_per_iteration(m, n, nnz) == mats + c1 + c2 + c3
+    assert round(bench.pcg_bytes_per_iteration(m, n, nnz) / 1e9, 2) == 3.22
