@@ -114,38 +114,6 @@ struct BArgs {
     unsigned extra_arrivals;   // 0 in solves; the failure self-test sets 1 (a barrier that never fills)
 };
 
-// Bounded grid barrier: every block's thread 0 arrives on count; the last one (count reaching
-// gridDim.x + extra, extra = 0 in every solve) bumps gen.  A block that polls gen max_polls
-// times without a change sets *err = 2 and returns false (its block leaves the kernel).
-__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, uint32_t max_polls, unsigned extra) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned g = *(volatile unsigned*)gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1 + extra) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            uint32_t polls = 0;
-            while (*(volatile unsigned*)gen == g) {
-                if (++polls > max_polls) {
-                    ok = 0;
-                    atomicExch(err, 2);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 __device__ __forceinline__ ff warp_sum_ff(ff v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -286,10 +254,10 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
         sum2_add(q2, ff_mul(rr, rr));
     };
     if constexpr (EPL == 0)
-        staged_tiles<true, V, BLOCK>(t0, 1, t1, rptr, rcol, rval, npairs, sm, ss, err, FFSum<true, V>{xh, xl, nullptr},
+        staged_tiles<true, V, BLOCK>(t0, 1, t1, rptr, rcol, rval, npairs, sm, ss, err, FFSum<true, V, true>{xh, xl, nullptr},
                                      pre, epi);
     else
-        tiles_ff<true, true, V, EPL>(t0, t1, rptr, rcol, rval, xh, xl, nullptr, npairs, sm.warp_buf(), pre, epi);
+        tiles_ff<true, true, V, EPL, true>(t0, t1, rptr, rcol, rval, xh, xl, nullptr, npairs, sm.warp_buf(), pre, epi);
     q0 = warp_sum_ff(q0);
     q1 = warp_sum_ff(q1);
     q2 = warp_sum_ff(q2);
@@ -334,10 +302,10 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
         if (rs) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, o.x1)));
     };
     if constexpr (EPL == 0)
-        staged_tiles<false, V, BLOCK>(t0, 1, t1, cptr, cpair, cval, n, sm, ss, err, FFSum<false, V>{nullptr, nullptr, res},
+        staged_tiles<false, V, BLOCK>(t0, 1, t1, cptr, cpair, cval, n, sm, ss, err, FFSum<false, V, true>{nullptr, nullptr, res},
                                       pre, epi);
     else
-        tiles_ff<false, true, V, EPL>(t0, t1, cptr, cpair, cval, nullptr, nullptr, res, n, sm.warp_buf(), pre, epi);
+        tiles_ff<false, true, V, EPL, true>(t0, t1, cptr, cpair, cval, nullptr, nullptr, res, n, sm.warp_buf(), pre, epi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_down_sync(0xffffffffu, gmax, o));
     l1 = warp_sum_ff(l1);

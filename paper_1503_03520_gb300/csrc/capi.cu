@@ -167,8 +167,30 @@ l1ls_status l1ls_create(int device, size_t budget, l1ls_ctx** out) {
         return cuda_error(e, "cudaMemGetInfo", __FILE__, __LINE__);
     }
     c->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+    if (cudaHostAlloc((void**)&c->pinned, Ctx::kPinnedSlots * Ctx::kPinnedSlotBytes, cudaHostAllocDefault) ==
+        cudaSuccess) {
+        for (int i = Ctx::kPinnedSlots - 1; i >= 0; --i) c->pinned_free.push_back(i);
+    } else {
+        cudaGetLastError();
+        c->pinned = nullptr;   // read-backs use pageable memory
+    }
     *out = reinterpret_cast<l1ls_ctx*>(c);
     return L1LS_OK;
+}
+
+void* Ctx::pinned_get(size_t bytes) {
+    if (!pinned || bytes > kPinnedSlotBytes) return nullptr;
+    std::lock_guard<std::mutex> g(pinned_mu);
+    if (pinned_free.empty()) return nullptr;
+    const int i = pinned_free.back();
+    pinned_free.pop_back();
+    return pinned + (size_t)i * kPinnedSlotBytes;
+}
+
+void Ctx::pinned_put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(pinned_mu);
+    pinned_free.push_back((int)((static_cast<char*>(p) - pinned) / (ptrdiff_t)kPinnedSlotBytes));
 }
 
 l1ls_status l1ls_destroy(l1ls_ctx* h) {
@@ -188,6 +210,7 @@ l1ls_status l1ls_destroy(l1ls_ctx* h) {
     }
     for (int i = 0; i < Ctx::kStages; ++i)
         if (c->stage[i]) cudaFree(c->stage[i]);
+    if (c->pinned) cudaFreeHost(c->pinned);
     delete c;
     return L1LS_OK;
 }

@@ -224,4 +224,38 @@ __device__ __forceinline__ FfStep ff_fista_step(ff x1, ff x0, ff g, ff beta, ff 
     return o;
 }
 
+// Bounded grid barrier: every block's thread 0 arrives on count; the last one (count reaching
+// gridDim.x + extra, extra = 0 in every solve) bumps gen.  A block that polls gen max_polls
+// times without a change (sleeping sleep_ns between polls) sets *err = 2 and returns false
+// (its block leaves the kernel).
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, uint32_t max_polls, unsigned extra,
+                                          unsigned sleep_ns = 64) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g = *(volatile unsigned*)gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1 + extra) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            uint32_t polls = 0;
+            while (*(volatile unsigned*)gen == g) {
+                if (++polls > max_polls) {
+                    ok = 0;
+                    atomicExch(err, 2);
+                    break;
+                }
+                if (sleep_ns) __nanosleep(sleep_ns);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 }  // namespace l1ls

@@ -71,6 +71,7 @@ struct FistaState {
     float beta_ff[2], invL_ff[2], thr_ff[2];
     double f_target;   // stop once P(x_{k-1}) <= f_target (-inf: off)
 };
+static_assert(sizeof(FistaState) <= Ctx::kPinnedSlotBytes, "the state read-back fits a pinned slot");
 
 // host and device: the float-float scalars of the state
 __host__ __device__ inline void split_ff(double d, float (&out)[2]) {
@@ -649,9 +650,11 @@ struct FistaWork {
     int64_t enqueued = 0;           // iterations enqueued since begin (parity of the next one)
     bool active = false;
     cudaEvent_t ev[2][3] = {};
+    Ctx* pin_ctx = nullptr;   // host_st is a pinned slot of this context (else pageable)
     ~FistaWork() {
         if (exec) cudaGraphExecDestroy(exec);
-        delete host_st;
+        if (pin_ctx) pin_ctx->pinned_put(host_st);
+        else delete host_st;
         for (auto& row : ev)
             for (auto& e : row)
                 if (e) cudaEventDestroy(e);
@@ -853,7 +856,13 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         L1LS_TRY(I->alloc_n(&w->part1, (int64_t)w->grid1 * 3));
         L1LS_TRY(I->alloc_n(&w->part2, (int64_t)w->grid2 * 3 + 1024));
         L1LS_TRY(I->alloc_n(&w->st, 1));
-        w->host_st = new FistaState();   // pageable: no allocation that synchronises the device
+        // the state read back at every host check: a pinned slot of the context, else pageable
+        if (void* slot = I->ctx->pinned_get(sizeof(FistaState))) {
+            w->host_st = new (slot) FistaState();
+            w->pin_ctx = I->ctx;
+        } else {
+            w->host_st = new FistaState();
+        }
         for (int k = 0; k < 2; ++k) {
             L1LS_CUDA(cudaEventCreate(&w->ev[k][0]));
             L1LS_CUDA(cudaEventCreate(&w->ev[k][1]));
@@ -917,8 +926,9 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
             L1LS_TRY(spmv_plain(I, false, xsrc, sizeof(Vec) == 8 ? L1LS_F64 : L1LS_F32, w->ax, false, st));
             h.products = 1;
         }
+        L1LS_CUDA(cudaMemcpyAsync(&w->host_st->l1_cur, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost, st));
         L1LS_CUDA(cudaStreamSynchronize(st));
-        L1LS_CUDA(cudaMemcpy(&h.l1_cur, &w->st->l1_cur, sizeof(double), cudaMemcpyDeviceToHost));
+        h.l1_cur = w->host_st->l1_cur;
     } else {
         if (sizeof(Vec) == 8) {
             L1LS_CUDA(cudaMemsetAsync(w->X[0], 0, sizeof(double) * n, st));

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,18 @@ struct Ctx {
     l1ls_status alloc(void** p, size_t bytes, cudaStream_t st = nullptr, bool stream_ordered = false);
     void release(void* p, size_t bytes, cudaStream_t st = nullptr, bool stream_ordered = false);
     l1ls_status staging(int which, size_t bytes, void** out);
+    // Pinned host slots for the solvers' per-step state read-backs.  A copy into pageable
+    // memory is staged through a buffer the driver shares between host threads, which
+    // serialised the serving loop's concurrent requests; pinned slots are allocated once with
+    // the context.  pinned_get returns NULL when every slot is taken (callers then fall back
+    // to pageable memory).
+    static constexpr int kPinnedSlots = 512;
+    static constexpr size_t kPinnedSlotBytes = 1024;
+    char* pinned = nullptr;
+    std::vector<int> pinned_free;
+    std::mutex pinned_mu;
+    void* pinned_get(size_t bytes);
+    void pinned_put(void* p);
     // serving loop (created by the first l1ls_submit or l1ls_serve_config)
     void* server = nullptr;
     void (*server_stop)(void*) = nullptr;

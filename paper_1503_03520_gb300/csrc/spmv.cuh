@@ -46,10 +46,18 @@ __device__ __forceinline__ void load_run(const T* __restrict__ p, T (&out)[kEPL]
     memcpy(out, w, sizeof(w));
 }
 
+// Gather of a vector entry: the read-only non-coherent path (__ldg) where the vector is not
+// written during the kernel, an L2 load (__ldcg) in persistent kernels whose later phases gather
+// what earlier phases of the same launch wrote (the non-coherent path may return stale lines).
+template <bool COH, class T> __device__ __forceinline__ T gather_load(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // Traverse all rows of a CSR matrix; `pre(row, valid)` returns the epilogue operands of a
 // row (loaded before the nonzeros), `epi(row, sum, operands)` consumes the row sum.
 // `wbuf` is this warp's shared buffer of kWarpChunk accumulators.
-template <class V, class X, class Acc, class Pre, class Epi>
+template <class V, class X, class Acc, bool COH = false, class Pre, class Epi>
 __device__ __forceinline__ void warp_csr(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                          const V* __restrict__ val, const X* __restrict__ x, int64_t nrows,
                                          Acc* __restrict__ wbuf, Pre pre, Epi epi) {
@@ -80,7 +88,7 @@ __device__ __forceinline__ void warp_csr(const int32_t* __restrict__ ptr, const 
 #pragma unroll
                 for (int k = 0; k < kEPL; ++k) {
                     const int32_t e = base + k;
-                    p[k] = (e >= e0 && e < e1) ? val_to_acc<Acc>(vv[k]) * vec_to_acc<Acc>(__ldg(x + cj[k])) : Acc(0);
+                    p[k] = (e >= e0 && e < e1) ? val_to_acc<Acc>(vv[k]) * vec_to_acc<Acc>(gather_load<COH>(x + cj[k])) : Acc(0);
                 }
             } else {
 #pragma unroll
@@ -262,7 +270,7 @@ __device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity) {
 // this lane's entries [eb, ee) of its row (ROWS: row pair, a0 / a1 for rows 2p / 2p+1) or
 // column (a0), read from ib[e - off], vb[e - off] (shared stage or global arrays), in entry
 // order, four entries' loads at a time
-template <bool ROWS, class V, class X, class Acc>
+template <bool ROWS, class V, class X, class Acc, bool COH = false>
 __device__ __forceinline__ void lane_entries(const int32_t* ib, const typename ValPair<V>::type* vb, int32_t off,
                                              int32_t eb, int32_t ee, const X* __restrict__ x, Acc& a0, Acc& a1) {
     for (int32_t e = eb; e < ee; e += 4) {
@@ -274,9 +282,10 @@ __device__ __forceinline__ void lane_entries(const int32_t* ib, const typename V
                 const int32_t j = ib[e + k - off];
                 pair_to_acc<Acc>(vb[e + k - off], v0[k], v1[k]);
                 if (ROWS) {
-                    g0[k] = vec_to_acc<Acc>(__ldg(x + j));
+                    g0[k] = vec_to_acc<Acc>(gather_load<COH>(x + j));
                 } else {
-                    const typename Two<X>::type g = __ldg(reinterpret_cast<const typename Two<X>::type*>(x) + j);
+                    const typename Two<X>::type g =
+                        gather_load<COH>(reinterpret_cast<const typename Two<X>::type*>(x) + j);
                     g0[k] = vec_to_acc<Acc>(g.x);
                     g1[k] = vec_to_acc<Acc>(g.y);
                 }
@@ -299,19 +308,19 @@ __device__ __forceinline__ void lane_entries(const int32_t* ib, const typename V
 // Summation policies of the staged traversal: how a lane gathers the vector for its entries
 // and accumulates its row (column).
 //   PlainSum: products and sums in Acc (FP64 for FP64 values, FP32 otherwise).
-template <bool ROWS, class V, class X, class Acc> struct PlainSum {
+template <bool ROWS, class V, class X, class Acc, bool COH = false> struct PlainSum {
     using acc_t = Acc;
     const X* x;
     __device__ __forceinline__ Acc zero() const { return Acc(0); }
     __device__ __forceinline__ void entries(const int32_t* ib, const typename ValPair<V>::type* vb, int32_t off,
                                             int32_t eb, int32_t ee, Acc& a0, Acc& a1) const {
-        lane_entries<ROWS, V, X, Acc>(ib, vb, off, eb, ee, x, a0, a1);
+        lane_entries<ROWS, V, X, Acc, COH>(ib, vb, off, eb, ee, x, a0, a1);
     }
     __device__ __forceinline__ Acc finish(Acc a) const { return a; }
 };
 
 // Forward declaration: the float-float policy (FFSum) is defined with the float-float kernels.
-template <bool ROWS, class V> struct FFSum;
+template <bool ROWS, class V, bool COH = false> struct FFSum;
 
 // row extents of this lane's row of tile t (0, 0 past the end)
 __device__ __forceinline__ void tile_extents(const int32_t* __restrict__ ptr, int64_t t, int64_t nrows, int32_t& rb,
@@ -524,7 +533,7 @@ namespace l1ls {
 // pair p is one float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} (both rows with one 16-byte load),
 // in plain storage one float2 {hi, lo} per row.
 
-template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
+template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, bool COH = false, class Pre, class Epi>
 __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, const int32_t* __restrict__ idx,
                                              const V* __restrict__ val, const float* __restrict__ xh,
                                              const float* __restrict__ xl, const void* __restrict__ rin, int64_t nrows,
@@ -569,10 +578,10 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
                     float hx = 0.f, lx = 0.f;
                     if (in) {
                         if (xl) {
-                            hx = __ldg(xh + ij[k]);
-                            lx = __ldg(xl + ij[k]);
+                            hx = gather_load<COH>(xh + ij[k]);
+                            lx = gather_load<COH>(xl + ij[k]);
                         } else {   // interleaved {hi, lo} pairs: one 8-byte gather
-                            const float2 g = __ldg(reinterpret_cast<const float2*>(xh) + ij[k]);
+                            const float2 g = gather_load<COH>(reinterpret_cast<const float2*>(xh) + ij[k]);
                             hx = g.x;
                             lx = g.y;
                         }
@@ -587,13 +596,13 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
                     }
                 } else if (PAIRED) {
                     // the two terms of a column entry, summed in turn below (as FFSum does)
-                    const float4 g = in ? __ldg(static_cast<const float4*>(rin) + ij[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 g = in ? gather_load<COH>(static_cast<const float4*>(rin) + ij[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
                     p0[k] = two_prod(v0, g.x);
                     p0[k].lo = __fmaf_rn(v0, g.z, p0[k].lo);
                     p1[k] = two_prod(v1, g.y);
                     p1[k].lo = __fmaf_rn(v1, g.w, p1[k].lo);
                 } else {
-                    const float2 g = in ? __ldg(static_cast<const float2*>(rin) + ij[k]) : make_float2(0.f, 0.f);
+                    const float2 g = in ? gather_load<COH>(static_cast<const float2*>(rin) + ij[k]) : make_float2(0.f, 0.f);
                     p0[k] = two_prod(v0, g.x);
                     p0[k].lo = __fmaf_rn(v0, g.y, p0[k].lo);
                     p1[k] = {0.f, 0.f};
@@ -636,18 +645,18 @@ __device__ __forceinline__ void tile_ff_body(int64_t t, int32_t rb, int32_t re, 
 }
 
 
-template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
+template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, bool COH = false, class Pre, class Epi>
 __device__ __forceinline__ void tile_ff(int64_t t, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                         const V* __restrict__ val, const float* __restrict__ xh,
                                         const float* __restrict__ xl, const void* __restrict__ rin, int64_t nrows,
                                         float* __restrict__ wbuf, Pre& pre, Epi& epi) {
     int32_t rb, re;
     tile_extents(ptr, t, nrows, rb, re);
-    tile_ff_body<ROWS, PAIRED, V, EPL>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
+    tile_ff_body<ROWS, PAIRED, V, EPL, COH>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
 }
 
 // tiles t0 .. t1-1 in order, each tile's row extents loaded before the previous tile's work
-template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, class Pre, class Epi>
+template <bool ROWS, bool PAIRED, class V, int EPL = kEPL, bool COH = false, class Pre, class Epi>
 __device__ __forceinline__ void tiles_ff(int64_t t0, int64_t t1, const int32_t* __restrict__ ptr,
                                          const int32_t* __restrict__ idx, const V* __restrict__ val,
                                          const float* __restrict__ xh, const float* __restrict__ xl,
@@ -659,7 +668,7 @@ __device__ __forceinline__ void tiles_ff(int64_t t0, int64_t t1, const int32_t* 
     for (int64_t t = t0; t < t1; ++t) {
         const int32_t rb = nb, re = ne;
         if (t + 1 < t1) tile_extents(ptr, t + 1, nrows, nb, ne);
-        tile_ff_body<ROWS, PAIRED, V, EPL>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
+        tile_ff_body<ROWS, PAIRED, V, EPL, COH>(t, rb, re, idx, val, xh, xl, rin, nrows, wbuf, pre, epi);
     }
 }
 
@@ -669,7 +678,7 @@ __device__ __forceinline__ void tiles_ff(int64_t t0, int64_t t1, const int32_t* 
 // one FP32 word), which is as accurate as a sum in twice the working precision; the row sum
 // is renormalised by TwoSum at the end.  ROWS gathers the float-float vector (xh, xl) at the
 // column index (xl NULL: xh holds interleaved {hi, lo} pairs); otherwise the residual float4 {hi(2p), hi(2p+1), lo(2p), lo(2p+1)} at the pair.
-template <bool ROWS, class V> struct FFSum {
+template <bool ROWS, class V, bool COH> struct FFSum {
     using acc_t = ff;
     const float* xh;
     const float* xl;
@@ -687,15 +696,15 @@ template <bool ROWS, class V> struct FFSum {
                     pair_to_acc<float>(vb[e + k - off], v0[k], v1[k]);
                     if (ROWS) {
                         if (xl) {
-                            g0[k] = __ldg(xh + j);
-                            h0[k] = __ldg(xl + j);
+                            g0[k] = gather_load<COH>(xh + j);
+                            h0[k] = gather_load<COH>(xl + j);
                         } else {   // interleaved {hi, lo} pairs: one 8-byte gather
-                            const float2 g = __ldg(reinterpret_cast<const float2*>(xh) + j);
+                            const float2 g = gather_load<COH>(reinterpret_cast<const float2*>(xh) + j);
                             g0[k] = g.x;
                             h0[k] = g.y;
                         }
                     } else {
-                        const float4 g = __ldg(r4 + j);
+                        const float4 g = gather_load<COH>(r4 + j);
                         g0[k] = g.x;
                         g1[k] = g.y;
                         h0[k] = g.z;

@@ -171,3 +171,22 @@ def test_fista_to_gap_several_tiles_per_warp(case):
     excess = max(f64 - ref.f_star, 0.0)
     smin = ref.sigma.min()
     assert float(np.sum((x - ref.xstar) ** 2)) <= 2.0 * excess / smin ** 2 + 1e-9 * float(ref.xstar @ ref.xstar)
+
+
+def test_pdncg_to_gap_phase_per_launch_path(case):
+    """pdNCG on the FP32 instance (n = 2^19, 2^20: above the size where the PCG runs in one
+    cooperative launch, so one launch per PCG phase): the oracle re-certifies the returned x on
+    the stored problem, and the oracle's pdNCG on that problem bounds the Newton count."""
+    log2n, ref, insts = case
+    params, inst = insts["f32"]
+    tol = W.C2_TOL
+    x, r = inst.solve_pdncg(tau=1.0, tol=tol, max_iter=200)
+    assert r["status"] == 0 and r["rel_gap"] <= tol
+    A = stored_values(ref.A, "f32")
+    b = ref.b.astype(np.float32).astype(np.float64)
+    P, D, gap, rel = solvers.certificate(A, b, 1.0, x)
+    assert rel <= 20 * tol
+    if log2n == 19:
+        o = solvers.pdncg(A, b, 1.0, tol)
+        assert o["status"] == 0
+        assert r["iters"] <= 2 * o["iters"] + 3, (r["iters"], o["iters"])
