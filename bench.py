@@ -29,6 +29,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving leg runs up to 16 slots on their own streams: 32 hardware work queues instead of
+# the default 8 keep the streams from sharing queues (read when CUDA initialises)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "Ax/ATy HBM GB/s (fused FISTA iteration)"
 UNIT = "GB/s"

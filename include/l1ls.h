@@ -328,7 +328,10 @@ l1ls_status l1ls_batch_free(l1ls_batch* batch);
  * overlap on the device.  A request's result does not depend on the other requests.
  *   l1ls_serve_config  optional, before the first l1ls_submit: slots (1..256; default 8) and
  *                      the capacity in bytes (0: the context budget not yet used).  EBUSY if
- *                      the loop is already running.
+ *                      the loop is already running.  With more than 8 slots, set the
+ *                      environment variable CUDA_DEVICE_MAX_CONNECTIONS to the slot count
+ *                      (up to 32) before the process initialises CUDA, so that the slots'
+ *                      streams do not share hardware work queues.
  *   l1ls_submit        queues a request; returns at once with its ticket.  o->tau < 0 means
  *                      |o->tau| * lambda_max of the generated instance.  EBUSY if its
  *                      footprint exceeds the whole capacity, EINVAL for bad options (bad

@@ -48,7 +48,7 @@ struct PdState {
     int32_t prev_full, stage_err;   // stage_err: kStageTimeout if a stage wait ran out
     double k1[2];
     double gnorm2, rz, rz0, alpha, beta;
-    int32_t cg_done, coop_err;   // coop_err: a grid barrier of the one-launch PCG ran out
+    int32_t cg_done, pad1;
     int64_t cg_it;
     double rAd, AdAd, step;
     int32_t ls_done, pad2;
@@ -428,185 +428,6 @@ __global__ void __launch_bounds__(kBlock) k_pd_cgupd(CV* __restrict__ d, typenam
     }
 }
 
-// ---- PCG in one cooperative launch (small instances) -----------------------------------
-// With n <= kCoopMaxN the PCG iterations of a Newton step run in one persistent launch: the
-// three phases of an iteration (the C1, C2 and C3 arithmetic above, entry for entry) are
-// separated by bounded grid barriers, and every block sums the per-block partials of each inner
-// product in the same fixed order, so every block takes the same decisions.  Launched one
-// kernel per phase, a small instance is bound by the rate at which the GPU starts kernels
-// (three per iteration), and so are concurrent requests of the serving loop.  Gathers of z and
-// A p use L2 loads: later phases read what earlier phases of the same launch wrote.
-#ifndef L1LS_COOP_MAX_LOG2N
-#define L1LS_COOP_MAX_LOG2N 17
-#endif
-constexpr int64_t kCoopMaxN = L1LS_COOP_MAX_LOG2N < 0 ? 0 : int64_t(1) << L1LS_COOP_MAX_LOG2N;
-constexpr int kCoopMaxBlocks = 64;
-#ifndef L1LS_COOP_TILES_PER_WARP
-#define L1LS_COOP_TILES_PER_WARP 2
-#endif
-#ifndef L1LS_COOP_SLEEP_NS
-#define L1LS_COOP_SLEEP_NS 64
-#endif
-constexpr uint32_t kCoopPolls = 1u << 24;
-
-template <class Vec> struct CoopArgs {
-    const int32_t *rptr, *ridx, *cptr, *cidx;
-    const void *rval, *cval;
-    Vec *z, *ap, *p, *hp, *d;
-    const Vec *hd, *minv;
-    typename CgRes<Vec>::type* rcg;
-    double *part_a, *part_b;    // per-block partials of p.Hp and res.z
-    unsigned *bar_count, *bar_gen;
-    int64_t m, n;
-    PdState* st;
-};
-
-// the sum of the gridDim.x partials in one fixed order (lane-strided, then a shuffle tree),
-// identical in every block; all threads of the block receive it
-__device__ __forceinline__ double coop_sum(const double* part, double* slot) {
-    if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(part + b);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) *slot = v;
-    }
-    __syncthreads();
-    const double r = *slot;
-    __syncthreads();
-    return r;
-}
-
-template <class V, class Vec, bool PAIRED>
-__global__ void __launch_bounds__(kBlock) k_pd_cg_coop(CoopArgs<Vec> a) {
-    using Acc = Vec;
-    __shared__ TraversalSmem<V, Acc, kBlock, PAIRED> sm;
-    __shared__ double red[32];
-    __shared__ double slot;
-    PdState* st = a.st;
-    if (halted(st)) return;
-    StageState ss{0, 0, false};
-    if constexpr (PAIRED) stage_init(sm, ss);
-    const V* rval = static_cast<const V*>(a.rval);
-    const V* cval = static_cast<const V*>(a.cval);
-    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
-    const int64_t m = a.m, n = a.n;
-    const int64_t nrow_units = PAIRED ? m / 2 : m;
-    const double rz0 = st->rz0, rtol = st->pcg_rtol;
-    const int64_t pcg_max = st->pcg_max;
-    double rz = st->rz;
-    Vec beta = Vec(0);
-    int64_t it = 0, counted = 0;
-    bool ok = true;
-    for (;;) {
-        // C1: A p = A z + beta A p_old
-        {
-            auto pre = [&](int64_t i, bool has) { return (has && beta != Vec(0)) ? a.ap[i] : Vec(0); };
-            auto epi = [&](int64_t i, Acc u, const Vec& old) { a.ap[i] = beta != Vec(0) ? u + beta * old : u; };
-            if constexpr (PAIRED)
-                staged_tiles<true, V, kBlock>(gw, nw, (nrow_units + 31) >> 5, a.rptr, a.ridx, rval, nrow_units, sm, ss,
-                                              &st->stage_err, PlainSum<true, V, Vec, Acc, true>{a.z}, pre, epi);
-            else
-                warp_csr<V, Vec, Acc, true>(a.rptr, a.ridx, rval, a.z, m, sm.warp_buf(), pre, epi);
-        }
-        if (!grid_sync(a.bar_count, a.bar_gen, &st->coop_err, kCoopPolls, 0u, L1LS_COOP_SLEEP_NS)) {
-            ok = false;
-            break;
-        }
-        // C2: p = z + beta p, Hp = h p + A^T A p, p.Hp
-        {
-            double q[1] = {0.0};
-            ff qf = {0.0f, 0.0f};
-            struct Ops {
-                Vec pj, h;
-            };
-            auto pre = [&](int64_t j, bool has) {
-                Ops o{Vec(0), Vec(0)};
-                if (has) {
-                    o.pj = beta != Vec(0) ? a.z[j] + beta * a.p[j] : a.z[j];
-                    o.h = a.hd[j];
-                }
-                return o;
-            };
-            auto epi = [&](int64_t j, Acc g, const Ops& o) {
-                const Vec h = o.h * o.pj + g;
-                a.p[j] = o.pj;
-                a.hp[j] = h;
-                if constexpr (sizeof(Vec) == 8) q[0] += o.pj * h;
-                else sum2_add(qf, two_prod(o.pj, h));
-            };
-            if constexpr (PAIRED)
-                staged_tiles<false, V, kBlock>(gw, nw, (n + 31) >> 5, a.cptr, a.cidx, cval, n, sm, ss, &st->stage_err,
-                                               PlainSum<false, V, Vec, Acc, true>{a.ap}, pre, epi);
-            else
-                warp_csr<V, Vec, Acc, true>(a.cptr, a.cidx, cval, a.ap, n, sm.warp_buf(), pre, epi);
-            if constexpr (sizeof(Vec) == 4) q[0] = ff_to_double(qf);
-            block_reduce<kBlock, 1>(q, 0u, red);
-            if (threadIdx.x == 0) a.part_a[blockIdx.x] = q[0];
-        }
-        if (!grid_sync(a.bar_count, a.bar_gen, &st->coop_err, kCoopPolls, 0u, L1LS_COOP_SLEEP_NS)) {
-            ok = false;
-            break;
-        }
-        const double pHp = coop_sum(a.part_a, &slot);
-        ++counted;
-        if (!(pHp > 0.0)) break;
-        // C3: d += alpha p, res -= alpha Hp, z = M^{-1} res, res.z
-        {
-            double q[1] = {0.0};
-            const double alpha = rz / pHp;
-            if constexpr (sizeof(Vec) == 8) {
-                for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-                    const double pj = a.p[j];
-                    a.d[j] += alpha * pj;
-                    const double rc = a.rcg[j] - alpha * a.hp[j];
-                    a.rcg[j] = rc;
-                    const double zj = a.minv[j] * rc;
-                    a.z[j] = zj;
-                    q[0] += rc * zj;
-                }
-            } else {
-                const ff al = ff_from_double(alpha);
-                ff rzf = {0.0f, 0.0f};
-                for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
-                    const float pj = a.p[j], hj = a.hp[j];
-                    a.d[j] = __fmaf_rn(al.hi, pj, a.d[j]);
-                    const float2 r2 = a.rcg[j];
-                    ff ah = two_prod(al.hi, hj);
-                    ah.lo = __fmaf_rn(al.lo, hj, ah.lo);
-                    const ff r = ff_sub(ff{r2.x, r2.y}, ah);
-                    a.rcg[j] = make_float2(r.hi, r.lo);
-                    const float zj = a.minv[j] * r.hi;
-                    a.z[j] = zj;
-                    ff t = two_prod(r.hi, zj);
-                    t.lo = __fmaf_rn(r.lo, zj, t.lo);
-                    sum2_add(rzf, t);
-                }
-                q[0] = ff_to_double(rzf);
-            }
-            block_reduce<kBlock, 1>(q, 0u, red);
-            if (threadIdx.x == 0) a.part_b[blockIdx.x] = q[0];
-        }
-        if (!grid_sync(a.bar_count, a.bar_gen, &st->coop_err, kCoopPolls, 0u, L1LS_COOP_SLEEP_NS)) {
-            ok = false;
-            break;
-        }
-        const double rzn = coop_sum(a.part_b, &slot);
-        ++it;
-        if (sqrt(rzn) <= rtol * sqrt(rz0) || it >= pcg_max) break;
-        beta = (Vec)(rzn / rz);
-        rz = rzn;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->cg_total += counted;
-        st->products += 2 * counted;
-        st->cg_it = it;
-        st->cg_done = 1;
-        if (!ok) st->coop_err = 1;
-    }
-}
-
 // ---- LT: Armijo trials on f_tau^mu of Eq. (prob2) -------------------------------------------------------------------
 // NT trials per pass: the first pass tries the full step alone (most Newton steps take it),
 // later passes four halvings each; every trial costs a square root and a division per entry
@@ -695,9 +516,6 @@ struct PdWork {
     PdState* st = nullptr;
     PdState* host = nullptr;
     int gm = 0, gn = 0, gv = 0, gmf = 0, gnf = 0;
-    int gc = 0;                                      // blocks of the one-launch PCG (0: graph chunks)
-    double *part_a = nullptr, *part_b = nullptr;     // its per-block partials
-    unsigned* bar = nullptr;                         // its grid barrier {count, generation}
     cudaGraphExec_t cg_exec = nullptr;
     int cg_chunk = 0;
     Ctx* pin_ctx = nullptr;   // host is a pinned slot of this context (else pageable)
@@ -768,22 +586,6 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         } else {
             w->host = new PdState();
         }
-        if (n <= kCoopMaxN) {
-            int per_sm = 0, coop = 0;
-            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, I->ctx->device);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pd_cg_coop<V, Vec, PAIRED>, kBlock, 0);
-            if (coop && per_sm >= 1) {
-                // about L1LS_COOP_TILES_PER_WARP tiles per warp in the larger of the two traversals
-                const int64_t tiles = std::max(((PAIRED ? m / 2 : m) + 31) / 32, (n + 31) / 32);
-                const int64_t cap = std::min<int64_t>(kCoopMaxBlocks, (int64_t)per_sm * I->ctx->num_sms);
-                constexpr int64_t per_block = L1LS_COOP_TILES_PER_WARP * (kBlock / 32);
-                w->gc = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (tiles + per_block - 1) / per_block));
-                L1LS_TRY(I->alloc_n(&w->part_a, kCoopMaxBlocks));
-                L1LS_TRY(I->alloc_n(&w->part_b, kCoopMaxBlocks));
-                L1LS_TRY(I->alloc_n(&w->bar, 2));
-                L1LS_CUDA(cudaMemsetAsync(w->bar, 0, 2 * sizeof(unsigned), s));
-            }
-        }
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
@@ -818,7 +620,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     const Vec* bvec = sizeof(Vec) == 8 ? (const Vec*)I->bhat : (const Vec*)I->bhat32;
     l1ls_status final_status = L1LS_OK;
     int chunk = o->check_every > 0 ? std::min(o->check_every, 16) : 8;
-    if (!w->gc && (!w->cg_exec || w->cg_chunk != chunk)) {
+    if (!w->cg_exec || w->cg_chunk != chunk) {
         if (w->cg_exec) {
             cudaGraphExecDestroy(w->cg_exec);
             w->cg_exec = nullptr;
@@ -858,10 +660,6 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         L1LS_CUDA(cudaGetLastError());
         L1LS_CUDA(cudaMemcpyAsync(w->host, w->st, sizeof(PdState), cudaMemcpyDeviceToHost, s));
         L1LS_CUDA(cudaStreamSynchronize(s));
-        if (w->host->coop_err) {
-            final_status = set_error(L1LS_ECUDA, "pdNCG: a grid barrier of the one-launch PCG ran out of polls");
-            break;
-        }
         if (w->host->stop) {
             final_status = (l1ls_status)w->host->status;
             break;
@@ -879,19 +677,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
                                                 (typename CgRes<Vec>::type*)w->rcg, (Vec*)w->z, (Vec*)w->d, n,
                                                 w->part, w->st);
         L1LS_CUDA(cudaGetLastError());
-        if (w->gc) {
-            // a barrier that ran out may have left its count set
-            L1LS_CUDA(cudaMemsetAsync(w->bar, 0, sizeof(unsigned), s));
-            CoopArgs<Vec> ca{R.ptr, R.idx, C.ptr, C.idx, R.val, C.val, (Vec*)w->z, (Vec*)w->ap, (Vec*)w->p,
-                             (Vec*)w->hp, (Vec*)w->d, (const Vec*)w->hd, (const Vec*)w->minv,
-                             (typename CgRes<Vec>::type*)w->rcg, w->part_a, w->part_b, w->bar, w->bar + 1, m, n,
-                             w->st};
-            void* params[] = {&ca};
-            L1LS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pd_cg_coop<V, Vec, PAIRED>, dim3(w->gc), dim3(kBlock),
-                                                  params, 0, s));
-        }
-        const int64_t max_cg_launches = w->gc ? 0 : o->pcg_max / chunk + 3;
-        for (int64_t launch = 0; !w->gc; ++launch) {
+        const int64_t max_cg_launches = o->pcg_max / chunk + 3;
+        for (int64_t launch = 0;; ++launch) {
             if (launch >= max_cg_launches) {
                 final_status = set_error(L1LS_ECUDA, "internal: PCG did not raise its stop flag");
                 break;

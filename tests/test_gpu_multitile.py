@@ -173,10 +173,10 @@ def test_fista_to_gap_several_tiles_per_warp(case):
     assert float(np.sum((x - ref.xstar) ** 2)) <= 2.0 * excess / smin ** 2 + 1e-9 * float(ref.xstar @ ref.xstar)
 
 
-def test_pdncg_to_gap_phase_per_launch_path(case):
-    """pdNCG on the FP32 instance (n = 2^19, 2^20: above the size where the PCG runs in one
-    cooperative launch, so one launch per PCG phase): the oracle re-certifies the returned x on
-    the stored problem, and the oracle's pdNCG on that problem bounds the Newton count."""
+def test_pdncg_to_gap_several_tiles_per_warp(case):
+    """pdNCG on the FP32 instance (its products traverse several tiles per warp): the oracle
+    re-certifies the returned x on the stored problem, and the oracle's pdNCG on that problem
+    bounds the Newton count."""
     log2n, ref, insts = case
     params, inst = insts["f32"]
     tol = W.C2_TOL
