@@ -123,7 +123,10 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
  * context may hold for instances and solver state (0 = 90% of the free memory at creation).
- * Errors: EINVAL (bad device), ECUDA. */
+ * The context also holds 512 KiB of pinned host memory (512 slots) into which the solvers
+ * read their per-step state back; pinned copies from concurrent threads do not queue behind
+ * each other as pageable ones do.  If that allocation fails, or all slots are taken, solvers
+ * fall back to pageable memory.  Errors: EINVAL (bad device), ECUDA. */
 l1ls_status l1ls_create(int device, size_t hbm_budget_bytes, l1ls_ctx** out);
 
 /* Destroy a context: waits for its serving thread, frees every instance it still owns. */
