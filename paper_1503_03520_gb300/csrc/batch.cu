@@ -234,10 +234,10 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
     };
     auto pre = [ax, bv](int64_t r, bool has) {
         Ops o{{0.f, 0.f}, 0.f};
-        if (has) {
-            const float2 v = ax[r];
+        if (has) {   // A x_{k-1} and b: last use in this step (evict-first, as in K1)
+            const float2 v = __ldcs(ax + r);
             o.axo = {v.x, v.y};
-            o.bb = bv[r];
+            o.bb = __ldcs(bv + r);
         }
         return o;
     };
@@ -245,7 +245,7 @@ __device__ __noinline__ void row_segment(const BDesc* __restrict__ dp, int cur, 
         // A y = A x_k + beta (A x_k - A x_{k-1}), r = b - A y (Sec. 8.1)
         const ff ay = ff_add(u, ff_mul(beta, ff_sub(u, o.axo)));
         const ff rr = ff_sub(ff_from_float(o.bb), ay);
-        ax[r] = make_float2(u.hi, u.lo);
+        __stcs(ax + r, make_float2(u.hi, u.lo));
         resf[4 * (r >> 1) + (r & 1)] = rr.hi;
         resf[4 * (r >> 1) + 2 + (r & 1)] = rr.lo;
         const ff dd = ff_sub(u, ff_from_float(o.bb));
@@ -286,8 +286,8 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
     };
     auto pre = [x1p, x0p](int64_t j, bool has) {
         Ops o{{0.f, 0.f}, {0.f, 0.f}};
-        if (has) {
-            const float2 a = x1p[j], b = x0p[j];
+        if (has) {   // both iterates: last use before x_{k-1} is overwritten (evict-first)
+            const float2 a = __ldcs(x1p + j), b = __ldcs(x0p + j);
             o.x1 = {a.x, a.y};
             o.x0 = {b.x, b.y};
         }
@@ -363,8 +363,11 @@ __global__ void __launch_bounds__(BLOCK, L1LS_BATCH_WARPS_PER_SM * 32 / BLOCK) k
         for (;;) {
             unsigned got = 0;
             if (lane == 0) got = atomicAdd(a.fetch + 1, 1u);
-            const int64_t sg = __shfl_sync(0xffffffffu, got, 0);
-            if (sg >= a.nseg2) break;
+            const int64_t g2 = __shfl_sync(0xffffffffu, got, 0);
+            if (g2 >= a.nseg2) break;
+            // in the reverse order of phase 1: the phase starts on the residuals phase 1 wrote
+            // last (still in L2), and the next phase 1 on the iterates this phase writes last
+            const int64_t sg = a.nseg2 - 1 - g2;
             const int i = a.sinst2[sg];
             if (__ldcg(&a.state[i].stop)) continue;
             const BDesc* dp = a.desc + i;

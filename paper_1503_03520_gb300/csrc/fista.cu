@@ -487,7 +487,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_fista_mf1(MfK1Args a) {
                 pk[k] = make_int2(INT32_MAX, INT32_MAX);
                 if (t < units) {
                     pk[k] = __ldcs(perm2 + t);
-                    axo[k] = ax2[t];
+                    axo[k] = __ldcs(ax2 + t);   // A x_{k-2}, b: streamed (evict-first), so that
+                                                // z and zt keep their place in L2
                     bb[k] = __ldcs(b2 + t);
                 }
             }
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_fista_mf1(MfK1Args a) {
                 const float u1 = __fmaf_rn(L.ct, z1[k], L.st * z0[k]);
                 const float r0 = epi(u0, axo[k].x, bb[k].x);
                 const float r1 = epi(u1, axo[k].y, bb[k].y);
-                ax2[t] = make_float2(u0, u1);
+                __stcs(ax2 + t, make_float2(u0, u1));
                 if (pk[k].x < L.n) a.zt[pk[k].x] = __fmaf_rn(L.ct, r0, L.st * r1);
                 if (pk[k].y < L.n) a.zt[pk[k].y] = __fmaf_rn(L.ct, r1, -L.st * r0);
             }
