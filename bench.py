@@ -303,22 +303,35 @@ def pcg_bytes_per_iteration(m, n, nnz):
     return c1 + c2 + c3
 
 
-def pcg_iteration_timing(inst, m, n, nnz, lo=16, hi=144):
+def mf_pcg_bytes_per_iteration(n):
+    """Algorithmic bytes of one PCG iteration of pdNCG on a matrix-free instance (FP32 vectors):
+    the product sweep (z, p_old, the curvature and sigma read, p and Hp written: 24n; A^T A p
+    = R Sigma^2 R^T p needs no m-vector) and the update (p, Hp, M^-1 read, d read and written,
+    the float-float residual read and written, z written: 40n)."""
+    return 24 * n + 40 * n
+
+
+def pcg_iteration_timing(inst, m, n, nnz, lo=16, hi=144, bytes_fn=None):
     """Time per PCG iteration of pdNCG: one Newton step from a point near x* with the relative
     residual target 1e-30 (PCG runs to its cap) at two caps; the difference of the two solve
     times over the difference of the iteration counts (whole CUDA-graph chunks of 16, so the
     host checks cancel)."""
     import numpy as np
+    import torch
     xs = inst.xstar()
     rng = np.random.default_rng(0)
-    x0 = xs * (1.0 + 0.01 * rng.standard_normal(xs.size)) + 1e-3 * rng.standard_normal(xs.size)
+    # x0 and x_out on the device: host copies of n doubles would add noise to both times
+    x0 = torch.tensor(xs * (1.0 + 0.01 * rng.standard_normal(xs.size)) + 1e-3 * rng.standard_normal(xs.size),
+                      device="cuda")
+    xo = torch.empty_like(x0)
     out = {}
     for k in (lo, hi):
         best = None
         for _ in range(3):
+            torch.cuda.synchronize()
             t = time.perf_counter()
-            _, r = inst.solve_pdncg(x0=x0, tau=1.0, tol=0.0, max_iter=1, pcg_max=k, pcg_rtol=1e-30, mu_start=1e-5,
-                                    check_every=16, allow=(4, 5))
+            _, r = inst.solve_pdncg(x0=x0, x_out=xo, tau=1.0, tol=0.0, max_iter=1, pcg_max=k, pcg_rtol=1e-30,
+                                    mu_start=1e-5, check_every=16, allow=(4, 5))
             el = time.perf_counter() - t
             best = el if best is None else min(best, el)
         out[k] = (best, r["cg_iters"])
@@ -326,7 +339,7 @@ def pcg_iteration_timing(inst, m, n, nnz, lo=16, hi=144):
     if iters <= 0:
         return None
     ms = (out[hi][0] - out[lo][0]) / iters * 1e3
-    b = pcg_bytes_per_iteration(m, n, nnz)
+    b = bytes_fn(n) if bytes_fn else pcg_bytes_per_iteration(m, n, nnz)
     peak, src = measured_hbm_peak()
     return {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak,
             "peak_source": src, "method": "(t(%d) - t(%d)) / %d PCG iterations of one Newton step" % (hi, lo, iters)}
@@ -491,6 +504,12 @@ def mf_form(l1, W, log2n, steps, warmup, solve_limit):
     _, r = inst.solve_fista(tau=1.0, tol=W.C2_TOL, max_iter=200000, time_limit_s=solve_limit, stream=stream,
                             allow=(4, 5))
     el = time.perf_counter() - t
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, rp = inst.solve_pdncg(tau=1.0, tol=W.C2_TOL, max_iter=200, time_limit_s=solve_limit, stream=stream,
+                             allow=(4, 5))
+    elp = time.perf_counter() - t
+    pcg = pcg_iteration_timing(inst, m, n, 0, bytes_fn=mf_pcg_bytes_per_iteration)
     out = {"workload": "c2 (m=2^%d, n=2^%d) with A not assembled: products by the stages of R, Sigma, "
                        "the permutation and the left rotations (FP32)" % (log2n + 1, log2n),
            "device_bytes": inst.info["device_bytes"], "iteration_ms": it_ms,
@@ -500,7 +519,13 @@ def mf_form(l1, W, log2n, steps, warmup, solve_limit):
            "gbs": (k1b + k2b) / (it_ms * 1e-3) / 1e9,
            "fista_to_gap": {"tol": W.C2_TOL, "seconds": el, "iters": r["iters"], "rel_gap": r["rel_gap"],
                             "status": r["status_name"],
-                            "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]}}
+                            "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"]},
+           "pdncg_to_gap": {"tol": W.C2_TOL, "seconds": elp, "iters": rp["iters"], "cg_iters": rp["cg_iters"],
+                            "rel_gap": rp["rel_gap"], "status": rp["status_name"],
+                            "rel_err_f": abs(rp["f"] - inst.info["f_star"]) / inst.info["f_star"],
+                            "pcg_iteration": pcg,
+                            "method": "gradient and certificate by an FP64 sweep (A^T b - R Sigma^2 R^T x), "
+                                      "PCG product by an FP32 sweep (A^T A = R Sigma^2 R^T)"}}
     inst.free()
     ctx.close()
     return out
@@ -513,21 +538,22 @@ def sec89_form(l1, W, log2n, newton_steps):
     import numpy as np
     ctx = l1.Context(0)
     rows = []
-    for dt in ("f64", "f32"):
-        inst = ctx.generate(W.sec89(log2n, dt))
+    for dt, mf in (("f64", 0), ("f32", 0), ("f32", 1)):
+        inst = ctx.generate(dict(W.sec89(log2n, dt), matrix_free=mf))
         xs = inst.xstar()
         acc = 0 if dt == "f64" else 1
+        tag = dt + (" matrix-free" if mf else "")
         for k in newton_steps:
             t = time.perf_counter()
             x, r = inst.solve_pdncg(tau=1.0, tol=0.0, max_iter=k, mu_min=1e-5, accum=acc, allow=(4, 5))
-            rows.append({"values": dt, "newton": r["iters"], "pcg": r["cg_iters"], "seconds": time.perf_counter() - t,
+            rows.append({"values": tag, "newton": r["iters"], "pcg": r["cg_iters"], "seconds": time.perf_counter() - t,
                          "rel_err_x": float(np.linalg.norm(x - xs) / np.linalg.norm(xs)),
                          "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"],
                          "rel_gap": r["rel_gap"]})
         for tol in (1e-4, 1e-6):   # to a certified gap with the defaults (continuation below mu allowed)
             t = time.perf_counter()
             x, r = inst.solve_pdncg(tau=1.0, tol=tol, max_iter=200, accum=acc, time_limit_s=30.0, allow=(4, 5))
-            rows.append({"values": dt, "tol": tol, "status": r["status_name"], "newton": r["iters"],
+            rows.append({"values": tag, "tol": tol, "status": r["status_name"], "newton": r["iters"],
                          "pcg": r["cg_iters"], "seconds": time.perf_counter() - t,
                          "rel_err_x": float(np.linalg.norm(x - xs) / np.linalg.norm(xs)),
                          "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"],
@@ -536,6 +562,44 @@ def sec89_form(l1, W, log2n, newton_steps):
     ctx.close()
     return {"workload": "sec. 8.9 shape at n=2^%d (m=2n, sigma 0.1/100, theta 2pi/3, x* n/2^10 nonzeros -1e4/0.1), "
                         "pdNCG with mu = 1e-5" % log2n, "runs": rows}
+
+
+def sec89_large_form(l1, W, log2n, newton_steps):
+    """Sec. 8.9's instance shape at the largest sizes one GPU holds, matrix-free (A = Sigma G^T
+    is never assembled; O(n) memory): pdNCG for the paper's 8 Newton steps and more, with the
+    paper's mu = 1e-5, the relative error of x against x* (Table 1's measure), device memory,
+    time per PCG iteration and its HBM fraction."""
+    import torch
+    ctx = l1.Context(0)
+    t = time.perf_counter()
+    inst = ctx.generate(dict(W.sec89(log2n, "f32"), matrix_free=1))
+    gen_s = time.perf_counter() - t
+    xs = torch.tensor(inst.xstar(), device="cuda")
+    x = torch.empty_like(xs)
+    n = inst.n
+    peak, src = measured_hbm_peak()
+    rows = []
+    for k in newton_steps:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, r = inst.solve_pdncg(x_out=x, tau=1.0, tol=0.0, max_iter=k, mu_min=1e-5, allow=(4, 5))
+        el = time.perf_counter() - t
+        pcg_ms = 1e3 * el / max(1, r["cg_iters"])   # whole solve over its PCG iterations (an upper bound)
+        rows.append({"newton": r["iters"], "pcg": r["cg_iters"], "seconds": el,
+                     "rel_err_x": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs)),
+                     "rel_err_f": abs(r["f"] - inst.info["f_star"]) / inst.info["f_star"], "rel_gap": r["rel_gap"],
+                     "ms_per_pcg_iteration_upper": pcg_ms,
+                     "pcg_frac_lower": mf_pcg_bytes_per_iteration(n) / (pcg_ms * 1e-3) / 1e9 / peak})
+    pcg = pcg_iteration_timing(inst, inst.m, n, 0, bytes_fn=mf_pcg_bytes_per_iteration)
+    out = {"workload": "sec. 8.9 shape at n=2^%d (m=2^%d), matrix-free, FP32 PCG, FP64 gradient" % (log2n, log2n + 1),
+           "generation_s": gen_s, "device_bytes": inst.info["device_bytes"], "pcg_iteration": pcg,
+           "pdncg_work_bytes": 76 * n, "runs": rows, "peak_source": src,
+           "x": "x0 = 0 and x_out on the device (the seconds include no host copy)",
+           "paper": "Table 1: n = 2^30 on 64 processors, 1,923 s; 8 Newton steps, about 100 PCG iterations each, "
+                    "relative error of order 1e-4"}
+    inst.free()
+    ctx.close()
+    return out
 
 
 def variants_form(l1, W, log2n, limit_s):
@@ -856,6 +920,10 @@ def run_ours(args):
     if rank == 0 and args.sec89:
         forms = forms or {}
         forms["sec89"] = sec89_form(l1, W, args.sec89_log2n, (8, 16, 32))
+    if rank == 0 and not args.no_forms and args.sec89_mf_log2n > 0:
+        forms = forms or {}
+        forms["sec89_matrix_free"] = sec89_large_form(l1, W, args.sec89_mf_log2n,
+                                                      tuple(int(k) for k in args.sec89_mf_newton.split(",")))
     if rank == 0 and not args.no_forms and not args.no_precision:
         forms = forms or {}
         forms["precision"] = precision_form(l1, W, args.precision_limit)
@@ -918,6 +986,9 @@ def main():
     ap.add_argument("--osgen3-limit", type=float, default=10.0, help="Sec. 8.5 leg: FISTA time limit (s)")
     ap.add_argument("--sec89", action="store_true", help="add the Sec. 8.9 pdNCG leg")
     ap.add_argument("--sec89-log2n", type=int, default=22)
+    ap.add_argument("--sec89-mf-log2n", type=int, default=26,
+                    help="Sec. 8.9 shape, matrix-free pdNCG at n = 2^k (0: skip; 29 is the largest, m = 2^30)")
+    ap.add_argument("--sec89-mf-newton", default="8,16", help="Newton steps of the matrix-free Sec. 8.9 runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

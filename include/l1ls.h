@@ -84,8 +84,8 @@ typedef enum { L1LS_F64 = 0, L1LS_F32 = 1, L1LS_BF16 = 2 } l1ls_dtype;
  *   matrix_free   1: A is not assembled; products apply its factors (Algorithms MvPA /
  *                 MvPAt of Sec. 4: the stages of R, Sigma, the permutation and the left
  *                 rotations), so the instance holds O(m + n) memory.  IGen (m >= n) with
- *                 FP32 value_dtype only; l1ls_matvec / l1ls_rmatvec and FISTA work on it
- *                 (pdNCG, batches and exports of A do not: EINVAL).
+ *                 FP32 value_dtype only; l1ls_matvec / l1ls_rmatvec, FISTA and pdNCG work
+ *                 on it (batches and exports of A do not: EINVAL).
  *   seed          all random draws are SplitMix64 streams of this seed.
  */
 typedef struct {
@@ -278,7 +278,12 @@ l1ls_status l1ls_fista_end(l1ls_inst* inst, double* x_out, l1ls_result* res, voi
  * smoothing (Eqs. pseudoHuber, prob2, bd4) with diagonal-preconditioned CG stopped at
  * relative residual pcg_rtol (in the preconditioner's norm), a halving Armijo line search of
  * at most ls_max trials, and mu-continuation as described with l1ls_solve_opts.  Certified
- * with the same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista. */
+ * with the same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista.
+ * Matrix-free instances: L in A = L Sigma R^T is orthogonal, so the gradient is A^T b (formed
+ * once per instance, FP64) - R Sigma^2 R^T x and the CG product A^T A p = R Sigma^2 R^T p:
+ * the gradient, the certificate and the line-search sums run in FP64 sweeps over the stages
+ * of R, the CG product in an FP32 sweep; o->accum is ignored.  The first solve on such an
+ * instance also forms diag(A^T A) and A^T b (n doubles each, kept with the instance). */
 l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
                              l1ls_result* res, void* stream);
 

@@ -1119,6 +1119,10 @@ l1ls_status generate_instance(Ctx* ctx, const l1ls_gen_params* p, cudaStream_t s
             I->mf_s = (float)g.s;
             I->mf_ct = (float)g.ct;
             I->mf_st = (float)g.st;
+            I->mf_c64 = g.c;
+            I->mf_s64 = g.s;
+            I->mf_ct64 = g.ct;
+            I->mf_st64 = g.st;
             I->f_star = p->tau * hred[0] + 0.5 * hred[1];
             I->lam_max = hred[2];
             I->lipschitz = sigma_max2(p);

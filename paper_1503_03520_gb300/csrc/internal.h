@@ -83,6 +83,7 @@ struct Inst {
     float* sigma32 = nullptr;   // Sigma in FP32 (padded to whole tiles)
     int32_t* mf_pperm = nullptr;   // per stored row pair, the two entries of P it rotates
     float mf_c = 0, mf_s = 0, mf_ct = 0, mf_st = 0;   // cos / sin of the right and left angles
+    double mf_c64 = 0, mf_s64 = 0, mf_ct64 = 0, mf_st64 = 0;   // the same in FP64 (pdNCG's gradient sweep)
     int dtype = L1LS_F64;
     // CSR of P1^T A (rows relabelled), m rows
     int32_t* csr_ptr = nullptr;

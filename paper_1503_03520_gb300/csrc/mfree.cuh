@@ -89,6 +89,31 @@ __device__ __forceinline__ void mf_stages(float* buf, int64_t g0, const MfRight&
     }
 }
 
+// The same stages on a buffer of LEN entries of type T (FP32 or FP64) with the rotation (c, s)
+// given in that type: the tile kernels of matrix-free pdNCG, whose buffers carry a halo of
+// 2 kMfHalo (R^T and R applied in one pass) and whose gradient sweep runs in FP64.
+template <bool TRANS, class T, int LEN>
+__device__ __forceinline__ void mf_stages_t(T* buf, int64_t g0, int64_t n, int w, T c, T s) {
+    for (int q = 0; q < w; ++q) {
+        const int k = TRANS ? w - q : q + 1;
+        const int first = (k - 1) & 1;
+        const int p0 = (int)(((first - g0) % 2 + 2) % 2);
+        for (int p = p0 + 2 * (int)threadIdx.x; p + 1 < LEN; p += 2 * kMfThreads) {
+            const int64_t i = g0 + p;
+            if (i < 0 || i + 1 >= n) continue;
+            const T a = buf[p], b = buf[p + 1];
+            if (TRANS) {
+                buf[p] = fma(c, a, s * b);
+                buf[p + 1] = fma(c, b, -s * a);
+            } else {
+                buf[p] = fma(c, a, -s * b);
+                buf[p + 1] = fma(c, b, s * a);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // y values of left row pair t (rows 2t, 2t+1) from z; L = I: row t alone (y1 unused)
 __device__ __forceinline__ void mf_left_rows(const MfLeft& L, const float* __restrict__ z, int64_t t, float& y0,
                                              float& y1) {

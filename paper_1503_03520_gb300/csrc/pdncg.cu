@@ -27,11 +27,15 @@
 // float-float arithmetic on the FP32 pipes: this GPU's FP64 pipe has a small fraction of the
 // FP32 rate, and FP64 arithmetic per entry (with the conversions to and from FP32) made the
 // vector update the slowest kernel of the iteration.
+// Matrix-free instances (A in factored form) run the same Newton loop with the passes of
+// run_mf below: the gradient and certificate in one FP64 sweep, the PCG product in one FP32
+// sweep (A^T A = R Sigma^2 R^T), the line search's sums in one FP64 sweep.
 #include <chrono>
 #include <cmath>
 #include <cstring>
 
 #include "internal.h"
+#include "mfree.cuh"
 #include "spmv.cuh"
 
 namespace l1ls {
@@ -57,6 +61,7 @@ struct PdState {
     int64_t iter, products, cg_total, ls_total;
     unsigned cnt[8];
     double f_target;   // stop once P(x) <= f_target (-inf: off)
+    double bb;         // ||b||^2 (matrix-free instances)
 };
 static_assert(sizeof(PdState) <= Ctx::kPinnedSlotBytes, "the state read-back fits a pinned slot");
 
@@ -377,11 +382,13 @@ __global__ void __launch_bounds__(kBlock) k_pd_hp(const int32_t* __restrict__ pt
 // ---- C3: d += alpha p, res -= alpha Hp, z = M^{-1} res ---------------------------------
 template <class CV>
 __global__ void __launch_bounds__(kBlock) k_pd_cgupd(CV* __restrict__ d, typename CgRes<CV>::type* __restrict__ rcg,
-                                                     const CV* __restrict__ p, const CV* __restrict__ hp,
+                                                     const CV* p0, const CV* p1, const CV* __restrict__ hp,
                                                      const CV* __restrict__ minv, CV* __restrict__ z, int64_t n,
                                                      double* partials, PdState* st) {
     __shared__ double red[2 * 32];
     if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
+    // p1 non-NULL: the search direction alternates between p0 and p1 by the CG iteration's parity
+    const CV* __restrict__ p = (p1 && (st->cg_it & 1)) ? p1 : p0;
     double q[2] = {0.0, 0.0};
     if constexpr (sizeof(CV) == 8) {
         const double alpha = st->alpha;
@@ -497,6 +504,271 @@ __global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, con
     }
 }
 
+// ---- matrix-free pdNCG (instances generated with matrix_free = 1) ---------------------------
+// A = L Sigma R^T with L orthogonal (the permutation and the left rotations, Eq. bd8), so
+// A^T A = R Sigma^2 R^T: the Hessian's product needs the stages of R and Sigma only, and the
+// left factor enters the gradient through c = A^T b alone, computed once per instance.  With
+// u = Sigma R^T x:  A^T r = c - R Sigma u,  ||r||^2 = ||b||^2 - 2 c.x + ||u||^2,  b.r = ||b||^2
+// - c.x (||A x|| = ||u||);  in the line search r.(A d) = (A^T r).d and ||A d|| = ||Sigma R^T d||.
+// Every pass is a sweep over tiles of kMfTile entries with a halo of 2 kMfHalo (R^T then R,
+// each widening the dependence by w <= kMfHalo entries); no m-vector is kept.  The gradient,
+// the certificate and the line-search sums run in FP64 once per Newton step; the PCG product
+// runs in FP32 like the stored-matrix path with FP32 values.
+constexpr int kPdHalo = 2 * kMfHalo;
+constexpr int kPdLen = kMfTile + 2 * kPdHalo;
+constexpr int kPdPer = (kPdLen + kMfThreads - 1) / kMfThreads;
+
+struct MfPd {
+    int64_t n;
+    int w;
+    float c, s;          // right angle (FP32: the PCG product)
+    double c64, s64;     // (FP64: gradient, line search, diagonal, A^T b)
+    const float* sigma32;
+    const double* sigma;
+};
+
+// buf[p] = v[g0 + p] for the tile's buffer (0 outside [0, n))
+template <class T, class S>
+__device__ __forceinline__ void mfpd_load(T* buf, const S* __restrict__ v, int64_t g0, int64_t n) {
+#pragma unroll
+    for (int u = 0; u < kPdPer; ++u) {
+        const int p = (int)threadIdx.x + u * kMfThreads;
+        const int64_t i = g0 + p;
+        if (p < kPdLen) buf[p] = (i >= 0 && i < n) ? (T)v[i] : T(0);
+    }
+    __syncthreads();
+}
+
+// buf[p] *= sigma[g0 + p]^POW
+template <int POW, class T>
+__device__ __forceinline__ void mfpd_scale(T* buf, const T* __restrict__ sigma, int64_t g0, int64_t n) {
+#pragma unroll
+    for (int u = 0; u < kPdPer; ++u) {
+        const int p = (int)threadIdx.x + u * kMfThreads;
+        const int64_t i = g0 + p;
+        if (p < kPdLen && i >= 0 && i < n) {
+            const T sg = sigma[i];
+            buf[p] *= POW == 2 ? sg * sg : sg;
+        }
+    }
+    __syncthreads();
+}
+
+// N1 + N2: A^T r at x (FP64), partials max |A^T r|, ||x||_1, c.x, ||u||^2; last CTA: the
+// certificate (pd_certify) from ||r||^2 and b.r formed as above (st->bb = ||b||^2)
+__global__ void __launch_bounds__(kMfThreads) k_mfpd_grad(MfPd P, const double* __restrict__ x,
+                                                          const double* __restrict__ c, double* __restrict__ atr,
+                                                          double* partials, PdState* st) {
+    __shared__ double buf[kPdLen];
+    __shared__ double red[4 * 32];
+    if (halted(st)) return;
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t ntiles = (P.n + kMfTile - 1) / kMfTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t a0 = tile * kMfTile, g0 = a0 - kPdHalo;
+        mfpd_load(buf, x, g0, P.n);
+        mf_stages_t<true, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+#pragma unroll
+        for (int u = 0; u < kPdPer; ++u) {   // u = Sigma R^T x; ||u||^2 over the tile's own entries
+            const int p = (int)threadIdx.x + u * kMfThreads;
+            const int64_t i = g0 + p;
+            if (p < kPdLen && i >= 0 && i < P.n) {
+                const double sg = P.sigma[i];
+                const double uv = buf[p] * sg;
+                if (p >= kPdHalo && p < kPdHalo + kMfTile) q[3] += uv * uv;
+                buf[p] = uv * sg;
+            }
+        }
+        __syncthreads();
+        mf_stages_t<false, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+        for (int p = kPdHalo + (int)threadIdx.x; p < kPdHalo + kMfTile; p += kMfThreads) {
+            const int64_t j = g0 + p;
+            if (j >= P.n) break;
+            const double cj = c[j], xj = x[j];
+            const double a = cj - buf[p];
+            atr[j] = a;
+            q[0] = fmax(q[0], fabs(a));
+            q[1] += fabs(xj);
+            q[2] += cj * xj;
+        }
+        __syncthreads();   // the buffer is reloaded next
+    }
+    block_reduce<kMfThreads, 4>(q, 1u, red);
+    double tot[4];
+    if (grid_reduce_last<kMfThreads, 4>(q, 1u, partials, &st->cnt[1], tot, red) && threadIdx.x == 0) {
+        st->k1[0] = st->bb - 2.0 * tot[2] + tot[3];   // ||b - A x||^2
+        st->k1[1] = st->bb - tot[2];                  // b.(b - A x)
+        const double t2[2] = {tot[0], tot[1]};
+        pd_certify(st, t2);
+    }
+}
+
+// C2 of the PCG iteration: p = z + beta p_old, Hp = h p + R Sigma^2 R^T p, alpha = rz / p.Hp
+// (FP32; p alternates between two buffers by the parity of the CG iteration, since the tiles
+// read their neighbours' p_old in the halo)
+__global__ void __launch_bounds__(kMfThreads) k_mfpd_hp(MfPd P, const float* __restrict__ z, float* p0, float* p1,
+                                                        const float* __restrict__ hd, float* __restrict__ hp,
+                                                        double* partials, PdState* st) {
+    __shared__ float buf[kPdLen];
+    __shared__ double red[32];
+    if (halted(st) || *(volatile int32_t*)&st->cg_done) return;
+    const bool odd = (st->cg_it & 1) != 0;
+    const float* pold = odd ? p0 : p1;
+    float* pnew = odd ? p1 : p0;
+    const float beta = (float)st->beta;
+    ff qf = {0.0f, 0.0f};
+    const int64_t ntiles = (P.n + kMfTile - 1) / kMfTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t a0 = tile * kMfTile, g0 = a0 - kPdHalo;
+        float pv[kPdPer], hv[kPdPer];
+#pragma unroll
+        for (int u = 0; u < kPdPer; ++u) {
+            const int p = (int)threadIdx.x + u * kMfThreads;
+            const int64_t i = g0 + p;
+            float v = 0.0f, h = 0.0f;
+            if (p < kPdLen && i >= 0 && i < P.n) {
+                v = z[i];
+                if (beta != 0.0f) v = __fmaf_rn(beta, pold[i], v);
+                if (p >= kPdHalo && p < kPdHalo + kMfTile) h = hd[i];
+            }
+            pv[u] = v;
+            hv[u] = h;
+            if (p < kPdLen) buf[p] = v;
+        }
+        __syncthreads();
+        mf_stages_t<true, float, kPdLen>(buf, g0, P.n, P.w, P.c, P.s);
+        mfpd_scale<2>(buf, P.sigma32, g0, P.n);
+        mf_stages_t<false, float, kPdLen>(buf, g0, P.n, P.w, P.c, P.s);
+#pragma unroll
+        for (int u = 0; u < kPdPer; ++u) {
+            const int p = (int)threadIdx.x + u * kMfThreads;
+            const int64_t j = g0 + p;
+            if (p < kPdHalo || p >= kPdHalo + kMfTile || j >= P.n) continue;
+            const float h = __fmaf_rn(hv[u], pv[u], buf[p]);
+            pnew[j] = pv[u];
+            hp[j] = h;
+            sum2_add(qf, two_prod(pv[u], h));
+        }
+        __syncthreads();
+    }
+    double q[1] = {ff_to_double(qf)};
+    block_reduce<kMfThreads, 1>(q, 0u, red);
+    double tot[1];
+    if (grid_reduce_last<kMfThreads, 1>(q, 0u, partials, &st->cnt[4], tot, red) && threadIdx.x == 0) {
+        st->products += 2;
+        st->cg_total += 1;
+        if (tot[0] <= 0.0) {
+            st->cg_done = 1;
+            st->alpha = 0.0;
+        } else {
+            st->alpha = st->rz / tot[0];
+        }
+    }
+}
+
+// L1: the line search's r.(A d) = (A^T r).d and ||A d||^2 = ||Sigma R^T d||^2 (FP64)
+__global__ void __launch_bounds__(kMfThreads) k_mfpd_ls(MfPd P, const float* __restrict__ d,
+                                                        const double* __restrict__ atr, double* partials,
+                                                        PdState* st) {
+    __shared__ double buf[kPdLen];
+    __shared__ double red[2 * 32];
+    if (halted(st)) return;
+    double q[2] = {0.0, 0.0};
+    const int64_t ntiles = (P.n + kMfTile - 1) / kMfTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t a0 = tile * kMfTile, g0 = a0 - kPdHalo;
+        mfpd_load(buf, d, g0, P.n);
+        mf_stages_t<true, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+        for (int p = kPdHalo + (int)threadIdx.x; p < kPdHalo + kMfTile; p += kMfThreads) {
+            const int64_t j = g0 + p;
+            if (j >= P.n) break;
+            const double v = buf[p] * P.sigma[j];
+            q[0] += atr[j] * (double)d[j];
+            q[1] += v * v;
+        }
+        __syncthreads();
+    }
+    block_reduce<kMfThreads, 2>(q, 0u, red);
+    double tot[2];
+    if (grid_reduce_last<kMfThreads, 2>(q, 0u, partials, &st->cnt[3], tot, red) && threadIdx.x == 0) {
+        st->rAd = tot[0];
+        st->AdAd = tot[1];
+        st->products += 1;
+        st->ls_done = 0;
+        st->ls_trial = 0;
+        st->step = 1.0;
+    }
+}
+
+// diag(A^T A) = diag(R Sigma^2 R^T) by probing (FP64): R has half-bandwidth w, so R Sigma^2 R^T
+// has at most 2w, and with K = 2w + 1 the product with the indicator of {i = q mod K} equals
+// the diagonal on those i.  Once per instance.
+__global__ void __launch_bounds__(kMfThreads) k_mfpd_diag(MfPd P, double* __restrict__ cn2) {
+    __shared__ double buf[kPdLen];
+    const int K = 2 * P.w + 1;
+    const int64_t ntiles = (P.n + kMfTile - 1) / kMfTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t a0 = tile * kMfTile, g0 = a0 - kPdHalo;
+        for (int q = 0; q < K; ++q) {
+            for (int p = threadIdx.x; p < kPdLen; p += kMfThreads) {
+                const int64_t i = g0 + p;
+                buf[p] = (i >= 0 && i < P.n && (int)(i % K) == q) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            mf_stages_t<true, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+            mfpd_scale<2>(buf, P.sigma, g0, P.n);
+            mf_stages_t<false, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+            for (int p = kPdHalo + (int)threadIdx.x; p < kPdHalo + kMfTile; p += kMfThreads) {
+                const int64_t j = g0 + p;
+                if (j < P.n && (int)(j % K) == q) cn2[j] = buf[p];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// A^T b in FP64 (once per instance): zs = the first n entries of P2^T G~^T b (b in the stored
+// row order), then c = R Sigma zs
+__global__ void k_mfpd_scatter(MfLeft L, double ct, double stt, const double* __restrict__ b, double* __restrict__ zs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L.left == 0) {
+        if (t < L.n) zs[t] = b[t];
+        return;
+    }
+    if (t >= L.m / 2) return;
+    const int32_t kx = L.perm[2 * t], ky = L.perm[2 * t + 1];
+    const double y0 = b[2 * t], y1 = b[2 * t + 1];
+    if (kx < L.n) zs[kx] = fma(ct, y0, stt * y1);
+    if (ky < L.n) zs[ky] = fma(ct, y1, -stt * y0);
+}
+
+__global__ void __launch_bounds__(kMfThreads) k_mfpd_rsig(MfPd P, const double* __restrict__ zs, double* __restrict__ c) {
+    __shared__ double buf[kPdLen];
+    const int64_t ntiles = (P.n + kMfTile - 1) / kMfTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t a0 = tile * kMfTile, g0 = a0 - kPdHalo;
+        mfpd_load(buf, zs, g0, P.n);
+        mfpd_scale<1>(buf, P.sigma, g0, P.n);
+        mf_stages_t<false, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+        for (int p = kPdHalo + (int)threadIdx.x; p < kPdHalo + kMfTile; p += kMfThreads) {
+            const int64_t j = g0 + p;
+            if (j < P.n) c[j] = buf[p];
+        }
+        __syncthreads();
+    }
+}
+
+// ||b||^2 into the state (FP64; once per solve, after the state is uploaded)
+__global__ void __launch_bounds__(kBlock) k_mfpd_bb(const double* __restrict__ b, int64_t m, double* partials,
+                                                    PdState* st) {
+    __shared__ double red[32];
+    double q[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock) q[0] += b[i] * b[i];
+    block_reduce<kBlock, 1>(q, 0u, red);
+    double tot[1];
+    if (grid_reduce_last<kBlock, 1>(q, 0u, partials, &st->cnt[7], tot, red) && threadIdx.x == 0) st->bb = tot[0];
+}
+
 template <class K>
 int grid_for(const Inst* I, K kernel, int64_t rows) {
     int per_sm = 0;
@@ -512,6 +784,8 @@ struct PdWork {
     void* rcg = nullptr;   // CG residual (CgRes)
     void *r = nullptr, *ap = nullptr, *ad = nullptr;
     float *xh = nullptr, *xl = nullptr, *rff = nullptr;   // compensated N1 / N2 (accum = 1)
+    double *cn2 = nullptr, *atb = nullptr;   // matrix-free: diag(A^T A), A^T b
+    void* p2 = nullptr;                      // matrix-free: the second search-direction buffer
     double* part = nullptr;
     PdState* st = nullptr;
     PdState* host = nullptr;
@@ -525,6 +799,39 @@ struct PdWork {
         else delete host;
     }
 };
+
+// the result of a solve (both loops): the iterate, the result record and the status
+l1ls_status pd_finish(Inst* I, PdWork* w, l1ls_status final_status, double* x_out, l1ls_result* res,
+                      std::chrono::steady_clock::time_point t0, cudaStream_t s) {
+    const int64_t n = I->n;
+    const PdState& f = *w->host;
+    if (f.stage_err && final_status == L1LS_OK)
+        final_status = set_error(L1LS_ECUDA, "a bulk-copy stage wait ran out of polls (sums read directly)");
+    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X, sizeof(double) * n, cudaMemcpyDefault, s));
+    L1LS_CUDA(cudaStreamSynchronize(s));
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->iters = f.iter;
+        res->products = f.products;
+        res->cg_iters = f.cg_total;
+        res->ls_trials = f.ls_total;
+        res->f = f.P;
+        res->dual = f.D;
+        res->gap = f.gap;
+        res->rel_gap = f.rel;
+        res->mu = f.mu;
+        res->status = final_status;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (final_status != L1LS_OK) {
+        const char* why = final_status == L1LS_ENOCONV ? "Newton iteration limit reached"
+                          : final_status == L1LS_ETIMEOUT ? "time limit reached"
+                          : final_status == L1LS_ECANCELLED ? "cancelled"
+                                                          : "NaN or Inf in the iteration";
+        return set_error(final_status, "pdNCG: %s (rel_gap %.3e)", why, f.rel);
+    }
+    return L1LS_OK;
+}
 
 // row and column orientation of the stored matrix (plain or paired)
 template <class V, bool PAIRED>
@@ -546,7 +853,7 @@ void enqueue_cg(Inst* I, PdWork* w, cudaStream_t s) {
                                                                  nullptr, I->m, w->part, w->st);
     k_pd_hp<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->ap, (const Vec*)w->hd,
                                                      (const Vec*)w->z, (Vec*)w->p, (Vec*)w->hp, I->n, w->part, w->st);
-    k_pd_cgupd<Vec><<<w->gv, kBlock, 0, s>>>((Vec*)w->d, (typename CgRes<Vec>::type*)w->rcg, (const Vec*)w->p,
+    k_pd_cgupd<Vec><<<w->gv, kBlock, 0, s>>>((Vec*)w->d, (typename CgRes<Vec>::type*)w->rcg, (const Vec*)w->p, nullptr,
                                              (const Vec*)w->hp,
                                              (const Vec*)w->minv, (Vec*)w->z, I->n, w->part, w->st);
 }
@@ -699,40 +1006,160 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
                                                  comp ? w->xl : nullptr, w->st);
         L1LS_CUDA(cudaGetLastError());
     }
-    const PdState& f = *w->host;
-    if (f.stage_err && final_status == L1LS_OK)
-        final_status = set_error(L1LS_ECUDA, "a bulk-copy stage wait ran out of polls (sums read directly)");
-    if (x_out) L1LS_CUDA(cudaMemcpyAsync(x_out, w->X, sizeof(double) * n, cudaMemcpyDefault, s));
-    L1LS_CUDA(cudaStreamSynchronize(s));
-    if (res) {
-        memset(res, 0, sizeof(*res));
-        res->iters = f.iter;
-        res->products = f.products;
-        res->cg_iters = f.cg_total;
-        res->ls_trials = f.ls_total;
-        res->f = f.P;
-        res->dual = f.D;
-        res->gap = f.gap;
-        res->rel_gap = f.rel;
-        res->mu = f.mu;
-        res->status = final_status;
-        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return pd_finish(I, w, final_status, x_out, res, t0, s);
+}
+
+MfPd mfpd_params(const Inst* I) {
+    return MfPd{I->n, I->p.right_stages, I->mf_c, I->mf_s, I->mf_c64, I->mf_s64, I->sigma32, I->sigma};
+}
+
+int mfpd_grid(const Inst* I, const void* kernel) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kMfThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ntiles = (I->n + kMfTile - 1) / kMfTile;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)I->ctx->num_sms * per_sm));
+}
+
+void enqueue_cg_mf(Inst* I, PdWork* w, cudaStream_t s) {
+    const MfPd P = mfpd_params(I);
+    k_mfpd_hp<<<w->gn, kMfThreads, 0, s>>>(P, (const float*)w->z, (float*)w->p, (float*)w->p2, (const float*)w->hd,
+                                           (float*)w->hp, w->part, w->st);
+    k_pd_cgupd<float><<<w->gv, kBlock, 0, s>>>((float*)w->d, (float2*)w->rcg, (const float*)w->p, (const float*)w->p2,
+                                               (const float*)w->hp, (const float*)w->minv, (float*)w->z, I->n, w->part,
+                                               w->st);
+}
+
+// pdNCG on a matrix-free instance: the Newton loop of run() with the passes above
+l1ls_status run_mf(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
+                   cudaStream_t s) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t m = I->m, n = I->n;
+    const MfPd P = mfpd_params(I);
+    PdWork* w = static_cast<PdWork*>(I->pd_work);
+    if (!w) {
+        w = new PdWork();
+        I->pd_work = w;
+        I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
+        for (double** v : {&w->X, &w->atr, &w->grad, &w->cn2, &w->atb}) L1LS_TRY(I->alloc_n(v, n));
+        L1LS_TRY(I->alloc(&w->rcg, sizeof(float2) * pad32(n)));
+        for (void** v : {&w->hd, &w->minv, &w->z, &w->p, &w->p2, &w->hp, &w->d})
+            L1LS_TRY(I->alloc(v, sizeof(float) * pad32(n)));
+        w->gn = mfpd_grid(I, (const void*)k_mfpd_hp);
+        w->gm = mfpd_grid(I, (const void*)k_mfpd_grad);
+        w->gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)I->ctx->num_sms * 8));
+        const int gmax = std::max(std::max(w->gm, w->gn), w->gv);
+        L1LS_TRY(I->alloc_n(&w->part, (int64_t)gmax * (kTrialsPerPass + 1)));
+        L1LS_TRY(I->alloc_n(&w->st, 1));
+        if (void* slot = I->ctx->pinned_get(sizeof(PdState))) {
+            w->host = new (slot) PdState();
+            w->pin_ctx = I->ctx;
+        } else {
+            w->host = new PdState();
+        }
+        // once per instance: diag(A^T A) and A^T b (grad serves as the scatter's scratch)
+        const MfLeft L{I->m, I->n, I->p.left_stages, I->mf_ct, I->mf_st, I->mf_pperm};
+        const int64_t units = std::max<int64_t>(n, m / 2);
+        k_mfpd_scatter<<<(unsigned)((units + 255) / 256), 256, 0, s>>>(L, I->mf_ct64, I->mf_st64, I->bhat, w->grad);
+        k_mfpd_rsig<<<w->gm, kMfThreads, 0, s>>>(P, w->grad, w->atb);
+        k_mfpd_diag<<<w->gm, kMfThreads, 0, s>>>(P, w->cn2);
+        L1LS_CUDA(cudaGetLastError());
     }
-    if (final_status != L1LS_OK) {
-        const char* why = final_status == L1LS_ENOCONV ? "Newton iteration limit reached"
-                          : final_status == L1LS_ETIMEOUT ? "time limit reached"
-                          : final_status == L1LS_ECANCELLED ? "cancelled"
-                                                          : "NaN or Inf in the iteration";
-        return set_error(final_status, "pdNCG: %s (rel_gap %.3e)", why, f.rel);
+    if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
+    else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
+    PdState h;
+    memset(&h, 0, sizeof(h));
+    h.tau = o->tau;
+    h.tol = o->rel_gap_tol;
+    h.f_target = o->f_target;
+    h.mu = o->mu_start > o->mu ? o->mu_start : o->mu;
+    h.mu_target = o->mu;
+    h.mu_min = o->mu_min;
+    h.pcg_rtol = o->pcg_rtol;
+    h.armijo = o->armijo;
+    h.stall = 0.5;
+    h.max_newton = o->max_iter;
+    h.pcg_max = o->pcg_max;
+    h.ls_max = o->ls_max;
+    h.prev_gap = INFINITY;
+    *w->host = h;
+    L1LS_CUDA(cudaMemcpyAsync(w->st, w->host, sizeof(PdState), cudaMemcpyHostToDevice, s));
+    k_mfpd_bb<<<w->gv, kBlock, 0, s>>>(I->bhat, m, w->part, w->st);
+    L1LS_CUDA(cudaGetLastError());
+    l1ls_status final_status = L1LS_OK;
+    // graphs of an even number of PCG iterations (the search direction alternates buffers)
+    int chunk = o->check_every > 0 ? std::min(o->check_every, 16) : 8;
+    chunk = std::max(2, chunk & ~1);
+    if (!w->cg_exec || w->cg_chunk != chunk) {
+        if (w->cg_exec) {
+            cudaGraphExecDestroy(w->cg_exec);
+            w->cg_exec = nullptr;
+        }
+        cudaStream_t cap;
+        L1LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        L1LS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < chunk; ++i) enqueue_cg_mf(I, w, cap);
+        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+        }
+        L1LS_CUDA(cudaGraphInstantiate(&w->cg_exec, graph, 0));
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        w->cg_chunk = chunk;
     }
-    return L1LS_OK;
+    const int ls_passes = (o->ls_max - 1 + kTrialsPerPass - 1) / kTrialsPerPass;
+    for (;;) {
+        k_mfpd_grad<<<w->gm, kMfThreads, 0, s>>>(P, w->X, w->atb, w->atr, w->part, w->st);
+        L1LS_CUDA(cudaGetLastError());
+        L1LS_CUDA(cudaMemcpyAsync(w->host, w->st, sizeof(PdState), cudaMemcpyDeviceToHost, s));
+        L1LS_CUDA(cudaStreamSynchronize(s));
+        if (w->host->stop) {
+            final_status = (l1ls_status)w->host->status;
+            break;
+        }
+        if (o->time_limit_s > 0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > o->time_limit_s) {
+            final_status = L1LS_ETIMEOUT;
+            break;
+        }
+        if (cancel_requested()) {
+            final_status = L1LS_ECANCELLED;
+            break;
+        }
+        k_pd_init<float><<<w->gv, kBlock, 0, s>>>(w->X, w->atr, w->cn2, w->grad, (float*)w->hd, (float*)w->minv,
+                                                  (float2*)w->rcg, (float*)w->z, (float*)w->d, n, w->part, w->st);
+        L1LS_CUDA(cudaGetLastError());
+        const int64_t max_cg_launches = o->pcg_max / chunk + 3;
+        for (int64_t launch = 0;; ++launch) {
+            if (launch >= max_cg_launches) {
+                final_status = set_error(L1LS_ECUDA, "internal: PCG did not raise its stop flag");
+                break;
+            }
+            L1LS_CUDA(cudaGraphLaunch(w->cg_exec, s));
+            L1LS_CUDA(cudaMemcpyAsync(&w->host->cg_done, &w->st->cg_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            L1LS_CUDA(cudaStreamSynchronize(s));
+            if (w->host->cg_done) break;
+        }
+        if (final_status != L1LS_OK) break;
+        k_mfpd_ls<<<w->gm, kMfThreads, 0, s>>>(P, (const float*)w->d, w->atr, w->part, w->st);
+        k_pd_trial<float, 1><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, w->grad, n, w->part, w->st);
+        for (int t = 0; t < ls_passes; ++t)
+            k_pd_trial<float, kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, w->grad, n, w->part,
+                                                                       w->st);
+        k_pd_apply<float><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, n, nullptr, nullptr, w->st);
+        L1LS_CUDA(cudaGetLastError());
+    }
+    return pd_finish(I, w, final_status, x_out, res, t0, s);
 }
 
 }  // namespace
 
 l1ls_status pdncg_solve(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_out, l1ls_result* res,
                         cudaStream_t st) {
-    if (I->matrix_free) return set_error(L1LS_EINVAL, "pdNCG needs the assembled matrix (matrix_free = 0)");
+    if (I->matrix_free) return run_mf(I, o, x0, x_out, res, st);
     if (I->paired) {
         switch (I->dtype) {
             case L1LS_F64: return run<double, double, true>(I, o, x0, x_out, res, st);

@@ -111,3 +111,16 @@ def test_pcg_iteration_bytes_counted_array_by_array():
     c3 = 4 * 4 * n + 8 * n + 2 * 4 * n + 8 * n
     assert bench.pcg_bytes_per_iteration(m, n, nnz) == mats + c1 + c2 + c3
     assert round(bench.pcg_bytes_per_iteration(m, n, nnz) / 1e9, 2) == 3.22
+
+
+def test_matrix_free_pcg_iteration_bytes_counted_array_by_array():
+    """One PCG iteration of matrix-free pdNCG (FP32 vectors), array by array: the product sweep
+    reads z, p_old, the curvature h and sigma and writes p and Hp (n floats each; the halo's
+    re-reads, 2 x 16 of every 2048 entries, are not counted); the update reads p, Hp and M^-1,
+    reads and writes d (n floats) and the float-float residual (n pairs), and writes z.  No
+    m-vector and no matrix."""
+    n = 2 ** 24
+    sweep = 4 * 4 * n + 2 * 4 * n
+    update = 3 * 4 * n + 2 * 4 * n + 2 * 8 * n + 4 * n
+    assert bench.mf_pcg_bytes_per_iteration(n) == sweep + update == 64 * n
+    assert round(bench.mf_pcg_bytes_per_iteration(n) / 1e9, 2) == 1.07

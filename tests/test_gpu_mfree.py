@@ -116,10 +116,100 @@ def test_matrix_free_rejections(ctx):
         assert e.value.status == 1
     inst = ctx.generate(W.params(m=512, n=256, value_dtype="f32", matrix_free=1))
     try:
-        for call in (lambda: inst.solve_pdncg(tau=1.0), lambda: inst.export(), lambda: inst.export_t(),
-                     lambda: inst.solve_fista(tau=1.0, accum=1)):
+        for call in (lambda: inst.export(), lambda: inst.export_t(), lambda: inst.solve_fista(tau=1.0, accum=1)):
             with pytest.raises(l1.L1LSError) as e:
                 call()
             assert e.value.status == 1
     finally:
         inst.free()
+
+
+# ---- pdNCG on matrix-free instances ---------------------------------------------------------
+# Gradient and certificate by one FP64 sweep (A^T r = A^T b - R Sigma^2 R^T x), the PCG product
+# by one FP32 sweep (A^T A = R Sigma^2 R^T), the line search's sums by one FP64 sweep.
+
+
+@pytest.mark.parametrize("left,w", [(1, 2), (0, 2), (1, 5), (0, 8)])
+def test_pdncg_matrix_free_certificate_at_x0(ctx, left, w):
+    """max_iter = 0 returns the first certificate at x0: P and D against the oracle's at the same
+    x0 on the FP64 A (A^T b, ||b||^2, ||Sigma R^T x||^2 and max |A^T r| all enter them).  Two
+    tiles with a ragged second one (n = 3001)."""
+    n = 3001
+    params = W.params(m=2 * n + 2, n=n, right_stages=w, left_stages=left, kappa=1e3, seed=11, xstar_frac=0.02,
+                      value_dtype="f32")
+    ref = oracle_instance(params)
+    inst = ctx.generate(dict(params, matrix_free=1))
+    try:
+        for seed, tau in ((4, 1.0), (5, 0.3 * ref.lam_max)):
+            x0 = ref.xstar + 0.1 * W.random_vector(n, seed)
+            x, r = inst.solve_pdncg(x0=x0.copy(), tau=tau, tol=1e-12, max_iter=0, allow=(4, 5))
+            P, D, gap, rel = solvers.certificate(ref.A, ref.b, tau, x0)
+            assert r["iters"] == 0 and np.array_equal(x, x0)
+            assert r["f"] == pytest.approx(P, rel=1e-11)
+            assert r["dual"] == pytest.approx(D, rel=1e-10, abs=1e-10 * abs(P))
+    finally:
+        inst.free()
+
+
+@pytest.mark.parametrize("left", [1, 0])
+def test_pdncg_matrix_free_matches_oracle(ctx, left):
+    """pdNCG to 1e-6 on a matrix-free instance: the oracle re-certifies the returned x on the FP64
+    A, f is compared with f*, and the oracle's pdNCG bounds the Newton count."""
+    n = 3000
+    params = W.params(m=2 * n, n=n, right_stages=2, left_stages=left, kappa=1e3, seed=9, xstar_frac=0.02,
+                      value_dtype="f32")
+    ref = oracle_instance(params)
+    inst = ctx.generate(dict(params, matrix_free=1))
+    try:
+        x, r = inst.solve_pdncg(tau=1.0, tol=1e-6, max_iter=200)
+        assert r["status"] == 0 and r["rel_gap"] <= 1e-6
+        P, D, gap, rel = solvers.certificate(ref.A, ref.b, 1.0, x)
+        assert rel <= 1.01e-6 and P == pytest.approx(r["f"], rel=1e-11)
+        assert abs(P - ref.f_star) <= 2e-6 * ref.f_star
+        o = solvers.pdncg(ref.A, ref.b, 1.0, 1e-6)
+        assert o["status"] == 0
+        assert r["iters"] <= 2 * o["iters"] + 3, (r["iters"], o["iters"])
+    finally:
+        inst.free()
+
+
+def test_pdncg_matrix_free_sec89_shape(ctx):
+    """Sec. 8.9's instance shape (A = Sigma G^T, L = I, sigma 0.1 / 100, x* entries -1e4 and 0.1)
+    at n = 2^12: matrix-free pdNCG to 1e-6 against the stored FP32 instance (float-float
+    gradient) and the oracle's x*."""
+    params = W.sec89(12, "f32")
+    ref = oracle_instance(params)
+    a = ctx.generate(dict(params, matrix_free=1))
+    b = ctx.generate(params)
+    try:
+        xa, ra = a.solve_pdncg(tau=1.0, tol=1e-6, max_iter=200)
+        xb, rb = b.solve_pdncg(tau=1.0, tol=1e-6, max_iter=200, accum=1)
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert solvers.certificate(ref.A, ref.b, 1.0, xa)[3] <= 1.01e-6
+        assert np.linalg.norm(xa - ref.xstar) <= 1e-6 * np.linalg.norm(ref.xstar)
+        assert abs(ra["iters"] - rb["iters"]) <= max(3, rb["iters"] // 4), (ra["iters"], rb["iters"])
+    finally:
+        a.free()
+        b.free()
+
+
+def test_pdncg_matrix_free_several_tiles_per_block(ctx):
+    """C2 recipe at n = 2^22 (2048 tiles, more than one block's share on this grid): the
+    certificate at x* is the one of the exact minimiser, and pdNCG to 1e-6 takes about the
+    Newton steps of the stored FP32 instance."""
+    params = W.c2_scaled(22)
+    a = ctx.generate(dict(params, matrix_free=1))
+    b = ctx.generate(params)
+    try:
+        xs = a.xstar()
+        _, r0 = a.solve_pdncg(x0=xs.copy(), tau=1.0, tol=1e-12, max_iter=0, allow=(4, 5))
+        assert abs(r0["f"] - a.info["f_star"]) <= 1e-12 * a.info["f_star"]
+        assert r0["rel_gap"] <= 1e-10
+        xa, ra = a.solve_pdncg(tau=1.0, tol=W.C2_TOL, max_iter=200)
+        xb, rb = b.solve_pdncg(tau=1.0, tol=W.C2_TOL, max_iter=200, accum=1)
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert abs(ra["f"] - a.info["f_star"]) <= 2 * W.C2_TOL * a.info["f_star"]
+        assert abs(ra["iters"] - rb["iters"]) <= max(3, rb["iters"] // 4), (ra["iters"], rb["iters"])
+    finally:
+        a.free()
+        b.free()
