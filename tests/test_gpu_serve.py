@@ -22,6 +22,11 @@ REQS = [
           n_nnz_per_col=4), "fista", 1.0),
     (dict(m=16384, n=8192, kappa=1e2, seed=7, right_stages=2, left_stages=1, value_dtype="bf16"), "fista", 0.5),
     (dict(m=512, n=256, kappa=10.0, seed=8, right_stages=1, left_stages=1, value_dtype="f64"), "pdncg", 0.8),
+    # A by its factors (Algorithms MvPA / MvPAt): pdNCG and FISTA on matrix-free instances
+    (dict(m=6000, n=3000, kappa=1e3, seed=9, right_stages=2, left_stages=1, value_dtype="f32", matrix_free=1),
+     "pdncg", 0.1),
+    (dict(m=5000, n=2500, kappa=1e2, seed=10, right_stages=2, left_stages=0, value_dtype="f32", matrix_free=1),
+     "fista", 0.3),
 ]
 OPTS = dict(tol=1e-6, max_iter=20000, restart=1)
 
@@ -62,7 +67,7 @@ def test_results_alone_equal_results_in_the_mix():
         assert st["peak_running"] >= 2                     # requests overlapped
         assert st["peak_reserved_bytes"] <= st["capacity_bytes"]
         for (p, m, frac), (status, res, x) in zip(REQS, served):
-            if m == "fista" or p["value_dtype"] == "f64":
+            if m == "fista" or p["value_dtype"] == "f64" or p.get("matrix_free"):
                 assert status == 0 and res["rel_gap"] <= 1e-6, (p, res)
             assert res["latency_s"] >= res["queue_s"] >= 0.0
             xa, ra, tau = _solve_alone(l1, ctx, _params(p), m, frac)
