@@ -194,6 +194,24 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
     return fast_two_sum(p.hi, p.lo);
 }
+// Square root and quotient of double-word numbers (Dekker 1971, "A floating-point technique for
+// extending the available precision": sqrt2 and div2): the FP32 root (quotient) plus one
+// correction from the exact remainder, which TwoProduct gives; relative error a few units of
+// 2^-46.  For v > 0 (v = 0 gives 0) and b != 0 within the FP32 range.
+__device__ __forceinline__ ff ff_sqrt(ff v) {
+    const float s = __fsqrt_rn(v.hi);
+    if (s == 0.0f) return {0.0f, 0.0f};
+    const ff s2 = two_prod(s, s);
+    const float e = __fadd_rn(__fsub_rn(__fsub_rn(v.hi, s2.hi), s2.lo), v.lo);   // v - s^2 (first difference exact)
+    return fast_two_sum(s, __fmul_rn(e, __fmul_rn(0.5f, __frcp_rn(s))));
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    const float r = __frcp_rn(b.hi);
+    const float c = __fmul_rn(a.hi, r);
+    const ff u = two_prod(c, b.hi);
+    const float cc = __fmul_rn(__fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, u.hi), u.lo), a.lo), __fmul_rn(c, b.lo)), r);
+    return fast_two_sum(c, cc);
+}
 __device__ __forceinline__ ff ff_from_float(float a) { return {a, 0.0f}; }
 __device__ __forceinline__ ff ff_from_double(double d) {   // FP64 pipe: use outside hot loops
     const float hi = __double2float_rn(d);

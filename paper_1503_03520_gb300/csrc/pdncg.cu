@@ -62,6 +62,7 @@ struct PdState {
     unsigned cnt[8];
     double f_target;   // stop once P(x) <= f_target (-inf: off)
     double bb;         // ||b||^2 (matrix-free instances)
+    double slope;      // grad.d of the current line search (float-float trials)
 };
 static_assert(sizeof(PdState) <= Ctx::kPinnedSlotBytes, "the state read-back fits a pinned slot");
 
@@ -483,6 +484,77 @@ __global__ void __launch_bounds__(kBlock) k_pd_trial(const double* __restrict__ 
     }
 }
 
+// The same trials for FP32 CG vectors, in float-float on the FP32 pipes: x as its (hi, lo)
+// pair, each per-coordinate difference with Dekker's double-word square root and quotient
+// (relative error a few units of 2^-46, against 2^-53 in FP64; the Armijo test compares sums of
+// these terms with c a slope, far above that error), so a trial costs FP32 operations
+// instead of an FP64 square root and division per entry.  The trial steps are powers of two,
+// so a d_j is exact in FP32.  Entries beyond the FP32 range (|x| or |x + a d| >= 1e18) take the
+// FP64 formula.  The slope grad.d is summed in the first pass only.
+template <int NT>
+__global__ void __launch_bounds__(kBlock) k_pd_trial_ff(const float* __restrict__ xh, const float* __restrict__ xl,
+                                                        const float* __restrict__ d, const double* __restrict__ grad,
+                                                        int64_t n, double* partials, PdState* st) {
+    __shared__ double red[(NT + 1) * 32];
+    if (halted(st) || *(volatile int32_t*)&st->ls_done) return;
+    const double mu = st->mu, step0 = st->step;
+    const bool first = st->ls_trial == 0;
+    const ff mu2 = ff_from_double(mu * mu);
+    ff q[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) q[t] = {0.0f, 0.0f};
+    double slope = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
+        const ff x = {xh[j], xl[j]};
+        const float dj = d[j];
+        if (first) slope += grad[j] * (double)dj;
+        const ff w0 = ff_sqrt(ff_add(mu2, ff_mul(x, x)));
+        float a = (float)step0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const float ad = a * dj;
+            const ff xt = ff_add(x, ff_from_float(ad));
+            ff term;
+            if (fabsf(x.hi) < 1e18f && fabsf(xt.hi) < 1e18f) {
+                const ff den = ff_add(ff_sqrt(ff_add(mu2, ff_mul(xt, xt))), w0);
+                const ff s2 = ff_add(x, xt);
+                ff num = two_prod(s2.hi, ad);
+                num.lo = __fmaf_rn(s2.lo, ad, num.lo);
+                term = den.hi > 0.0f ? ff_div(num, den) : ff{0.0f, 0.0f};
+            } else {
+                const double xd = ff_to_double(x), xtd = xd + (double)ad;
+                term = ff_from_double((double)ad * (xd + xtd) / (sqrt(mu * mu + xtd * xtd) + sqrt(mu * mu + xd * xd)));
+            }
+            sum2_add(q[t], term);
+            a *= 0.5f;
+        }
+    }
+    double p[NT + 1];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) p[t] = ff_to_double(q[t]);
+    p[NT] = slope;
+    block_reduce<kBlock, NT + 1>(p, 0u, red);
+    double tot[NT + 1];
+    if (grid_reduce_last<kBlock, NT + 1>(p, 0u, partials, &st->cnt[6], tot, red) && threadIdx.x == 0) {
+        if (first) st->slope = tot[NT];
+        const double sl = st->slope;
+        double a = step0;
+        for (int t = 0; t < NT; ++t) {
+            const int64_t trial = st->ls_trial + t;
+            const double df = st->tau * tot[t] - a * st->rAd + 0.5 * a * a * st->AdAd;
+            if (df <= st->armijo * a * sl || trial >= st->ls_max - 1) {
+                st->step = a;
+                st->ls_done = 1;
+                st->ls_total += trial + 1;
+                return;
+            }
+            a *= 0.5;
+        }
+        st->step = a;
+        st->ls_trial += NT;
+    }
+}
+
 // ---- L3: x += step d (the dual estimate is recomputed from A^T r at the next N3) ----------
 template <class CV>
 __global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, const CV* __restrict__ d, int64_t n,
@@ -492,7 +564,7 @@ __global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, con
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
         const double v = x[j] + step * (double)d[j];
         x[j] = v;
-        if (xh) {   // the float-float copy that the compensated N1 gathers
+        if (xh) {   // the float-float copy that the compensated N1 gathers and the trials read
             const ff f = ff_from_double(v);
             xh[j] = f.hi;
             xl[j] = f.lo;
@@ -896,14 +968,15 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
-    // accum = 1 with FP32 / BF16 values: the gradient's products N1 / N2 in float-float
+    // accum = 1 with FP32 / BF16 values: the gradient's products N1 / N2 in float-float.  With
+    // FP32 CG vectors the iterate is also kept as a float-float pair for the line search.
     const bool comp = sizeof(Vec) == 4 && o->accum == 1;
-    if (comp) {
+    if constexpr (sizeof(Vec) == 4) {
         if (!w->xh) {
             L1LS_TRY(I->alloc_n(&w->xh, pad32(n)));
             L1LS_TRY(I->alloc_n(&w->xl, pad32(n)));
-            L1LS_TRY(I->alloc_n(&w->rff, 2 * pad32(m)));
         }
+        if (comp && !w->rff) L1LS_TRY(I->alloc_n(&w->rff, 2 * pad32(m)));
         k_pd_split<<<w->gv, kBlock, 0, s>>>(w->X, w->xh, w->xl, n);
         L1LS_CUDA(cudaGetLastError());
     }
@@ -998,12 +1071,18 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         if (final_status != L1LS_OK) break;
         k_pd_ax<V, Vec, Vec, true, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, (const Vec*)w->d,
                                                                     (Vec*)w->ad, (const Vec*)w->r, m, w->part, w->st);
-        k_pd_trial<Vec, 1><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n, w->part, w->st);
-        for (int t = 0; t < ls_passes; ++t)
-            k_pd_trial<Vec, kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n, w->part,
-                                                                     w->st);
-        k_pd_apply<Vec><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, n, comp ? w->xh : nullptr,
-                                                 comp ? w->xl : nullptr, w->st);
+        if constexpr (sizeof(Vec) == 4) {
+            k_pd_trial_ff<1><<<w->gv, kBlock, 0, s>>>(w->xh, w->xl, (const float*)w->d, w->grad, n, w->part, w->st);
+            for (int t = 0; t < ls_passes; ++t)
+                k_pd_trial_ff<kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->xh, w->xl, (const float*)w->d, w->grad, n,
+                                                                       w->part, w->st);
+        } else {
+            k_pd_trial<Vec, 1><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n, w->part, w->st);
+            for (int t = 0; t < ls_passes; ++t)
+                k_pd_trial<Vec, kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, w->grad, n,
+                                                                         w->part, w->st);
+        }
+        k_pd_apply<Vec><<<w->gv, kBlock, 0, s>>>(w->X, (const Vec*)w->d, n, w->xh, w->xl, w->st);
         L1LS_CUDA(cudaGetLastError());
     }
     return pd_finish(I, w, final_status, x_out, res, t0, s);
@@ -1045,6 +1124,8 @@ l1ls_status run_mf(Inst* I, const l1ls_solve_opts* o, const double* x0, double* 
         L1LS_TRY(I->alloc(&w->rcg, sizeof(float2) * pad32(n)));
         for (void** v : {&w->hd, &w->minv, &w->z, &w->p, &w->p2, &w->hp, &w->d})
             L1LS_TRY(I->alloc(v, sizeof(float) * pad32(n)));
+        L1LS_TRY(I->alloc_n(&w->xh, pad32(n)));
+        L1LS_TRY(I->alloc_n(&w->xl, pad32(n)));
         w->gn = mfpd_grid(I, (const void*)k_mfpd_hp);
         w->gm = mfpd_grid(I, (const void*)k_mfpd_grad);
         w->gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)I->ctx->num_sms * 8));
@@ -1067,6 +1148,7 @@ l1ls_status run_mf(Inst* I, const l1ls_solve_opts* o, const double* x0, double* 
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
+    k_pd_split<<<w->gv, kBlock, 0, s>>>(w->X, w->xh, w->xl, n);
     PdState h;
     memset(&h, 0, sizeof(h));
     h.tau = o->tau;
@@ -1145,11 +1227,11 @@ l1ls_status run_mf(Inst* I, const l1ls_solve_opts* o, const double* x0, double* 
         }
         if (final_status != L1LS_OK) break;
         k_mfpd_ls<<<w->gm, kMfThreads, 0, s>>>(P, (const float*)w->d, w->atr, w->part, w->st);
-        k_pd_trial<float, 1><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, w->grad, n, w->part, w->st);
+        k_pd_trial_ff<1><<<w->gv, kBlock, 0, s>>>(w->xh, w->xl, (const float*)w->d, w->grad, n, w->part, w->st);
         for (int t = 0; t < ls_passes; ++t)
-            k_pd_trial<float, kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, w->grad, n, w->part,
-                                                                       w->st);
-        k_pd_apply<float><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, n, nullptr, nullptr, w->st);
+            k_pd_trial_ff<kTrialsPerPass><<<w->gv, kBlock, 0, s>>>(w->xh, w->xl, (const float*)w->d, w->grad, n,
+                                                                   w->part, w->st);
+        k_pd_apply<float><<<w->gv, kBlock, 0, s>>>(w->X, (const float*)w->d, n, w->xh, w->xl, w->st);
         L1LS_CUDA(cudaGetLastError());
     }
     return pd_finish(I, w, final_status, x_out, res, t0, s);
