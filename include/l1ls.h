@@ -281,8 +281,8 @@ l1ls_status l1ls_fista_end(l1ls_inst* inst, double* x_out, l1ls_result* res, voi
  * with the same gap as FISTA at the current iterate.  Arguments as for l1ls_solve_fista.
  * Matrix-free instances: L in A = L Sigma R^T is orthogonal, so the gradient is A^T b (formed
  * once per instance, FP64) - R Sigma^2 R^T x and the CG product A^T A p = R Sigma^2 R^T p:
- * the gradient, the certificate and the line-search sums run in FP64 sweeps over the stages
- * of R, the CG product in an FP32 sweep; o->accum is ignored.  The first solve on such an
+ * the gradient and the certificate run in an FP64 sweep over the stages of R, the CG product
+ * and the line search's ||A d|| in FP32 sweeps; o->accum is ignored.  The first solve on such an
  * instance also forms diag(A^T A) and A^T b (n doubles each, kept with the instance). */
 l1ls_status l1ls_solve_pdncg(l1ls_inst* inst, const l1ls_solve_opts* o, const double* x0, double* x_out,
                              l1ls_result* res, void* stream);

@@ -29,7 +29,7 @@
 // vector update the slowest kernel of the iteration.
 // Matrix-free instances (A in factored form) run the same Newton loop with the passes of
 // run_mf below: the gradient and certificate in one FP64 sweep, the PCG product in one FP32
-// sweep (A^T A = R Sigma^2 R^T), the line search's sums in one FP64 sweep.
+// sweep (A^T A = R Sigma^2 R^T), the line search's ||A d|| in one FP32 sweep.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -583,9 +583,9 @@ __global__ void __launch_bounds__(kBlock) k_pd_apply(double* __restrict__ x, con
 // u = Sigma R^T x:  A^T r = c - R Sigma u,  ||r||^2 = ||b||^2 - 2 c.x + ||u||^2,  b.r = ||b||^2
 // - c.x (||A x|| = ||u||);  in the line search r.(A d) = (A^T r).d and ||A d|| = ||Sigma R^T d||.
 // Every pass is a sweep over tiles of kMfTile entries with a halo of 2 kMfHalo (R^T then R,
-// each widening the dependence by w <= kMfHalo entries); no m-vector is kept.  The gradient,
-// the certificate and the line-search sums run in FP64 once per Newton step; the PCG product
-// runs in FP32 like the stored-matrix path with FP32 values.
+// each widening the dependence by w <= kMfHalo entries); no m-vector is kept.  The gradient
+// and the certificate run in FP64 once per Newton step; the PCG product and the line search's
+// ||A d|| run in FP32 like the stored-matrix path with FP32 values.
 constexpr int kPdHalo = 2 * kMfHalo;
 constexpr int kPdLen = kMfTile + 2 * kPdHalo;
 constexpr int kPdPer = (kPdLen + kMfThreads - 1) / kMfThreads;
@@ -738,28 +738,32 @@ __global__ void __launch_bounds__(kMfThreads) k_mfpd_hp(MfPd P, const float* __r
     }
 }
 
-// L1: the line search's r.(A d) = (A^T r).d and ||A d||^2 = ||Sigma R^T d||^2 (FP64)
+// L1: the line search's r.(A d) = (A^T r).d (FP64) and ||A d||^2 = ||Sigma R^T d||^2 (an FP32
+// sweep like the stored path's FP32 A d, its squares summed in float-float: the Armijo test
+// needs ||A d||^2 to a relative 1e-7 at most, since it weighs against armijo * slope)
 __global__ void __launch_bounds__(kMfThreads) k_mfpd_ls(MfPd P, const float* __restrict__ d,
                                                         const double* __restrict__ atr, double* partials,
                                                         PdState* st) {
-    __shared__ double buf[kPdLen];
+    __shared__ float buf[kPdLen];
     __shared__ double red[2 * 32];
     if (halted(st)) return;
     double q[2] = {0.0, 0.0};
+    ff vv = {0.0f, 0.0f};
     const int64_t ntiles = (P.n + kMfTile - 1) / kMfTile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t a0 = tile * kMfTile, g0 = a0 - kPdHalo;
         mfpd_load(buf, d, g0, P.n);
-        mf_stages_t<true, double, kPdLen>(buf, g0, P.n, P.w, P.c64, P.s64);
+        mf_stages_t<true, float, kPdLen>(buf, g0, P.n, P.w, P.c, P.s);
         for (int p = kPdHalo + (int)threadIdx.x; p < kPdHalo + kMfTile; p += kMfThreads) {
             const int64_t j = g0 + p;
             if (j >= P.n) break;
-            const double v = buf[p] * P.sigma[j];
+            const float v = buf[p] * P.sigma32[j];
             q[0] += atr[j] * (double)d[j];
-            q[1] += v * v;
+            sum2_add(vv, two_prod(v, v));
         }
         __syncthreads();
     }
+    q[1] = ff_to_double(vv);
     block_reduce<kMfThreads, 2>(q, 0u, red);
     double tot[2];
     if (grid_reduce_last<kMfThreads, 2>(q, 0u, partials, &st->cnt[3], tot, red) && threadIdx.x == 0) {
