@@ -908,34 +908,43 @@ def run_ours(args):
             solves["pdncg"]["pcg_iteration"] = pcg_iteration_timing(inst, m, n, nnz)
 
     inst.free()
+    default_forms = {"batch", "matrix_free", "serve", "fista_variants", "c1", "sec89_matrix_free", "precision"}
+    if args.forms is not None:
+        chosen = set(f for f in args.forms.split(",") if f)
+    else:
+        chosen = set() if args.no_forms else set(default_forms)
+        if args.no_precision:
+            chosen.discard("precision")
+        if args.sec89_mf_log2n <= 0:
+            chosen.discard("sec89_matrix_free")
+        chosen |= {f for f, on in (("size_sweep", args.sweep), ("osgen3", args.osgen3), ("sec89", args.sec89)) if on}
     forms = None
-    if rank == 0 and not args.no_forms:
-        forms = {"batch": batch_form(l1, W, ctx, args.batch_iters)}
+    if rank == 0 and chosen:
+        forms = {}
+        if "batch" in chosen:
+            forms["batch"] = batch_form(l1, W, ctx, args.batch_iters)
     ctx.close()
-    if rank == 0 and not args.no_forms:
-        forms["matrix_free"] = mf_form(l1, W, args.log2n, args.steps, args.warmup, args.solve_limit)
-    if rank == 0 and not args.no_forms:
-        rates = SERVE_RATES if args.serve_rate is None else (args.serve_rate,)
-        forms["serve"] = serve_form(l1, W, args.serve_count, rates, args.serve_log2n, args.serve_slots)
-    if rank == 0 and not args.no_forms:
-        forms["fista_variants"] = variants_form(l1, W, args.variants_log2n, args.solve_limit)
-        forms["c1"] = c1_form(l1, W)
-    if rank == 0 and args.sweep:
-        forms = forms or {}
-        forms["size_sweep"] = sweep_form(l1, W, range(20, 28), range(24, 30), 20, 3)
-    if rank == 0 and args.osgen3:
-        forms = forms or {}
-        forms["osgen3"] = osgen3_form(l1, W, args.osgen3_log2n, args.osgen3_limit)
-    if rank == 0 and args.sec89:
-        forms = forms or {}
-        forms["sec89"] = sec89_form(l1, W, args.sec89_log2n, (8, 16, 32))
-    if rank == 0 and not args.no_forms and args.sec89_mf_log2n > 0:
-        forms = forms or {}
-        forms["sec89_matrix_free"] = sec89_large_form(l1, W, args.sec89_mf_log2n,
-                                                      tuple(int(k) for k in args.sec89_mf_newton.split(",")))
-    if rank == 0 and not args.no_forms and not args.no_precision:
-        forms = forms or {}
-        forms["precision"] = precision_form(l1, W, args.precision_limit)
+    if rank == 0 and chosen:
+        if "matrix_free" in chosen:
+            forms["matrix_free"] = mf_form(l1, W, args.log2n, args.steps, args.warmup, args.solve_limit)
+        if "serve" in chosen:
+            rates = SERVE_RATES if args.serve_rate is None else (args.serve_rate,)
+            forms["serve"] = serve_form(l1, W, args.serve_count, rates, args.serve_log2n, args.serve_slots)
+        if "fista_variants" in chosen:
+            forms["fista_variants"] = variants_form(l1, W, args.variants_log2n, args.solve_limit)
+        if "c1" in chosen:
+            forms["c1"] = c1_form(l1, W)
+        if "size_sweep" in chosen:
+            forms["size_sweep"] = sweep_form(l1, W, range(20, 28), range(24, 30), 20, 3)
+        if "osgen3" in chosen:
+            forms["osgen3"] = osgen3_form(l1, W, args.osgen3_log2n, args.osgen3_limit)
+        if "sec89" in chosen:
+            forms["sec89"] = sec89_form(l1, W, args.sec89_log2n, (8, 16, 32))
+        if "sec89_matrix_free" in chosen:
+            forms["sec89_matrix_free"] = sec89_large_form(l1, W, args.sec89_mf_log2n,
+                                                          tuple(int(k) for k in args.sec89_mf_newton.split(",")))
+        if "precision" in chosen:
+            forms["precision"] = precision_form(l1, W, args.precision_limit)
 
     if rank == 0:
         cpu = None
@@ -976,7 +985,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--solve-limit", type=float, default=30.0)
-    ap.add_argument("--no-forms", action="store_true", help="skip the batched (c4) and serving (c5) legs")
+    ap.add_argument("--no-forms", action="store_true", help="skip every form (the legs beside the metric)")
+    ap.add_argument("--forms", default=None,
+                    help="run exactly these forms (comma list of batch, matrix_free, serve, fista_variants, c1, "
+                         "sec89_matrix_free, precision, size_sweep, osgen3, sec89); default: all but the last three")
     ap.add_argument("--batch-iters", type=int, default=300, help="c4: FISTA iterations per tau at most")
     ap.add_argument("--serve-count", type=int, default=48, help="c5: requests per arrival rate")
     ap.add_argument("--serve-rate", type=float, default=None, help="c5: one arrival rate (default: the sweep "
