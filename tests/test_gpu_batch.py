@@ -118,7 +118,7 @@ def test_bounded_barrier_expires_and_the_context_survives(setup):
 
 
 def test_batch_with_more_segments_than_warps():
-    """Six C2-recipe instances at n = 2^18: 6 x 1024 segments of 8 tiles per phase against at
+    """Six C2-recipe instances at n = 2^19: 6 x 1024 segments of 16 tiles per phase against at
     most 152 SMs x 24 warps = 3648 warps, so warps draw several segments from the phase counters
     and run the staged traversal over several tiles each.  Both sides run at most 30 FISTA
     iterations at each of two tau (the caps end every tau) from x = 0 with the same warm start;
@@ -128,7 +128,7 @@ def test_batch_with_more_segments_than_warps():
     ctx = l1.Context(0)
     insts = []
     try:
-        params = [W.c2_scaled(18, seed=70 + k, kappa=10.0 ** (2 + 0.5 * k)) for k in range(6)]
+        params = [W.c2_scaled(19, seed=70 + k, kappa=10.0 ** (2 + 0.5 * k)) for k in range(6)]
         refs = [oracle_instance(p) for p in params]
         insts = [ctx.generate(p) for p in params]
         # at these tau 30 iterations leave gaps far above the tolerance, so the caps end both
