@@ -123,7 +123,13 @@ def test_batch_with_more_segments_than_warps():
     and run the staged traversal over several tiles each.  Both sides run at most 30 FISTA
     iterations at each of two tau (the caps end every tau) from x = 0 with the same warm start;
     the batch's float-float products (about 44 bits) against the oracle's FP64 FISTA on the
-    stored FP32 problem.  One instance alone equals itself in the batch bit for bit."""
+    stored FP32 problem.  The device's FP32 values of A may differ from the oracle's rounding of
+    its FP64 values by one unit (the generator's value parity), so x, whose components along the
+    weak singular directions move by up to about kappa times such a perturbation, is compared
+    within 1e-6 max|x| for kappa <= 1e3 and kappa / 1e3 times that above; f, insensitive to it,
+    within 1e-9.  (Measured at n = 2^19: 4e-12 at kappa 1e2, 7e-5 at kappa 1e4 with
+    max|x| = 51; the same x with segments of 8 or 16 tiles.)  One instance alone equals itself in
+    the batch bit for bit."""
     import paper_1503_03520_gb300 as l1
     ctx = l1.Context(0)
     insts = []
@@ -149,7 +155,8 @@ def test_batch_with_more_segments_than_warps():
                 assert r["status"] == 5 and r["iters"] == 30, (k, j, r)
                 assert abs(r["f"] - o["P"]) <= 1e-9 * o["P"], (k, j, r["f"], o["P"])
                 x0 = o["x_next"]
-            assert np.abs(xs[k] - o["x"]).max() <= 1e-6 * max(1.0, np.abs(o["x"]).max()), k
+            kappa = params[k]["kappa"]
+            assert np.abs(xs[k] - o["x"]).max() <= 1e-6 * max(1.0, kappa / 1e3) * max(1.0, np.abs(o["x"]).max()), k
         alone = l1.Batch(ctx, [insts[4]])
         x_alone = [np.zeros(insts[4].n)]
         res_alone = alone.solve_path(taus[4:5], x_out=x_alone, tol=1e-12, max_iter=30, restart=0)
