@@ -319,10 +319,11 @@ __device__ __noinline__ void col_segment(const BDesc* __restrict__ dp, int cur, 
 
 // EPL = 0: the staged stream (each lane sums its own row from shared memory); 4 or 8: lane
 // runs of EPL entries summed through a warp buffer.  Registers are sized for
-// L1LS_BATCH_WARPS_PER_SM resident warps (a build parameter: 16 needs no spills, 24 caps a
-// thread at 80 registers with about 100 bytes of spills and measured 4% faster on C4).
+// L1LS_BATCH_WARPS_PER_SM resident warps (a build parameter; with 128-thread blocks 20 allows
+// 96 registers with about 40 bytes of spills, 24 allows 80 with about 110 and 32 allows 64:
+// on a shortened C4 run 0.610, 0.647 and 0.871 ms per step).
 #ifndef L1LS_BATCH_WARPS_PER_SM
-#define L1LS_BATCH_WARPS_PER_SM 24
+#define L1LS_BATCH_WARPS_PER_SM 20
 #endif
 // The tau path of Sec. 8.8 for a batch of instances: FISTA (Sec. 8.1) with warm starts along
 // each path, all instances in one persistent kernel.
