@@ -180,9 +180,9 @@ l1ls_status l1ls_rmatvec(const l1ls_inst* inst, const void* y, l1ls_dtype vec_dt
  *   library: 2^20 doubles (8 MiB) held by every GPU that loads the library until the process
  *   exits.  Instances with m > 2^20 are rejected with L1LS_EINVAL.
  *   No cudaMalloc, cudaFree or other allocating call is made.  The first call on a device
- *   looks up the array's device address (cudaGetSymbolAddress) with that device current;
- *   make that first call before any stream capture.  The address is kept for the life of the
- *   process, which assumes the device's primary context is never reset (cudaDeviceReset).
+ *   looks up the array's device address (cudaGetSymbolAddress) with that device current.
+ *   The address is kept for the life of the process, which assumes the device's primary
+ *   context is never reset (cudaDeviceReset).
  *   All calls share the array and it keeps the last call's contents (every entry used is
  *   written before it is read, so nothing needs clearing).  Calls whose work overlaps on the
  *   GPU (different streams, or different threads) race on the array: order them.
