@@ -18,6 +18,7 @@
 // the FP32 rate; FP64 per row in these epilogues bounded both kernels before.)
 #include <chrono>
 #include <cmath>
+#include <memory>
 
 #include "internal.h"
 #include <cstring>
@@ -834,9 +835,10 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
     if (o->accum != 0 && o->accum != 1) return set_error(L1LS_EINVAL, "accum must be 0 or 1");
     FistaWork* w = static_cast<FistaWork*>(I->fista_work);
     if (!w) {
-        w = new FistaWork();
-        I->fista_work = w;
-        I->fista_work_free = [](void* p) { delete static_cast<FistaWork*>(p); };
+        // the work space is attached to the instance only once complete: a failed allocation
+        // leaves no partial work space for the next solve to use
+        std::unique_ptr<FistaWork> fresh(new FistaWork());
+        w = fresh.get();
         if (sizeof(Vec) == 8) {
             L1LS_TRY(I->alloc_n(&w->X[0], pad32(n)));
             L1LS_TRY(I->alloc_n(&w->X[1], pad32(n)));
@@ -886,10 +888,12 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
             L1LS_CUDA(cudaEventCreate(&w->ev[k][1]));
             L1LS_CUDA(cudaEventCreate(&w->ev[k][2]));
         }
+        I->fista_work = fresh.release();
+        I->fista_work_free = [](void* p) { delete static_cast<FistaWork*>(p); };
     }
     if constexpr (sizeof(Vec) == 4) {
-        if (o->accum == 1 && !w->ax_ff) {
-            L1LS_TRY(I->alloc_n(&w->ax_ff, pad32(m)));
+        if (o->accum == 1 && !w->res_ff) {   // res_ff last: set only when both exist
+            if (!w->ax_ff) L1LS_TRY(I->alloc_n(&w->ax_ff, pad32(m)));
             L1LS_TRY(I->alloc_n(&w->res_ff, 2 * pad32(m)));
             if (I->paired) {
                 w->grid1c = grid_of(I, k_fista_k1c<V, true>, m / 2);

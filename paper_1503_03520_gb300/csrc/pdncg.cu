@@ -33,6 +33,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 #include "internal.h"
 #include "mfree.cuh"
@@ -942,9 +943,9 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     const int64_t m = I->m, n = I->n;
     PdWork* w = static_cast<PdWork*>(I->pd_work);
     if (!w) {
-        w = new PdWork();
-        I->pd_work = w;
-        I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
+        // attached to the instance only once complete (a failed allocation leaves none behind)
+        std::unique_ptr<PdWork> fresh(new PdWork());
+        w = fresh.get();
         for (double** v : {&w->X, &w->atr, &w->grad}) L1LS_TRY(I->alloc_n(v, n));
         L1LS_TRY(I->alloc(&w->rcg, sizeof(typename CgRes<Vec>::type) * pad32(n)));
         for (void** v : {&w->hd, &w->minv, &w->z, &w->p, &w->hp, &w->d}) L1LS_TRY(I->alloc(v, sizeof(Vec) * pad32(n)));
@@ -969,6 +970,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         } else {
             w->host = new PdState();
         }
+        I->pd_work = fresh.release();
+        I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
@@ -976,8 +979,8 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     // FP32 CG vectors the iterate is also kept as a float-float pair for the line search.
     const bool comp = sizeof(Vec) == 4 && o->accum == 1;
     if constexpr (sizeof(Vec) == 4) {
-        if (!w->xh) {
-            L1LS_TRY(I->alloc_n(&w->xh, pad32(n)));
+        if (!w->xl) {   // xl last: set only when both exist
+            if (!w->xh) L1LS_TRY(I->alloc_n(&w->xh, pad32(n)));
             L1LS_TRY(I->alloc_n(&w->xl, pad32(n)));
         }
         if (comp && !w->rff) L1LS_TRY(I->alloc_n(&w->rff, 2 * pad32(m)));
@@ -1121,9 +1124,8 @@ l1ls_status run_mf(Inst* I, const l1ls_solve_opts* o, const double* x0, double* 
     const MfPd P = mfpd_params(I);
     PdWork* w = static_cast<PdWork*>(I->pd_work);
     if (!w) {
-        w = new PdWork();
-        I->pd_work = w;
-        I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
+        std::unique_ptr<PdWork> fresh(new PdWork());
+        w = fresh.get();
         for (double** v : {&w->X, &w->atr, &w->grad, &w->cn2, &w->atb}) L1LS_TRY(I->alloc_n(v, n));
         L1LS_TRY(I->alloc(&w->rcg, sizeof(float2) * pad32(n)));
         for (void** v : {&w->hd, &w->minv, &w->z, &w->p, &w->p2, &w->hp, &w->d})
@@ -1149,6 +1151,8 @@ l1ls_status run_mf(Inst* I, const l1ls_solve_opts* o, const double* x0, double* 
         k_mfpd_rsig<<<w->gm, kMfThreads, 0, s>>>(P, w->grad, w->atb);
         k_mfpd_diag<<<w->gm, kMfThreads, 0, s>>>(P, w->cn2);
         L1LS_CUDA(cudaGetLastError());
+        I->pd_work = fresh.release();
+        I->pd_work_free = [](void* q) { delete static_cast<PdWork*>(q); };
     }
     if (x0) L1LS_CUDA(cudaMemcpyAsync(w->X, x0, sizeof(double) * n, cudaMemcpyDefault, s));
     else L1LS_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n, s));
