@@ -351,6 +351,19 @@ def rank_workload(log2n, rank):
     return W.c2_scaled(log2n, seed=rank)
 
 
+def batch_bytes_per_step(m, n, nnz):
+    """Algorithmic bytes of one step of the batched kernel for one instance (FP32 values in
+    paired storage, float-float vectors as interleaved {hi, lo} pairs).  Row phase: row-pair
+    pointers, indices and values, the iterate gathered as one pair per column (8n), A x_{k-1}
+    read and A x_k written as pairs (16m), b (4m), the residual's {hi, lo} written (8m).
+    Column phase: column pointers, indices and values, the residual gathered (8m), both iterates
+    read and the new one written (24n)."""
+    mat = 4 * (nnz // 2) + 4 * nnz
+    rows = mat + 4 * (m // 2 + 1) + 8 * n + 16 * m + 4 * m + 8 * m
+    cols = mat + 4 * (n + 1) + 8 * m + 24 * n
+    return rows + cols
+
+
 def batch_form(l1, W, ctx, iters_per_tau):
     """C4: 256 instances along 16-tau paths in the batched kernel, against the same paths
     solved one instance at a time with FP64 values (a 1-in-16 subsample), equal tolerance and
@@ -367,6 +380,16 @@ def batch_form(l1, W, ctx, iters_per_tau):
     el = time.perf_counter() - t
     st = b.stats()
     sched = b.schedule()
+    # the kernel's bandwidth: algorithmic bytes of every instance-iteration run over the device
+    # time of all steps; once for the whole path, once for 64 iterations at the last (smallest)
+    # tau, where no instance certifies so early (the schedule is already chosen: no probes)
+    ib = [batch_bytes_per_step(i.m, i.n, i.nnz) for i in insts]
+    path_bytes = sum(ib[k] * r["iters"] for k, rr in enumerate(res) for r in rr)
+    res_all = b.solve_path(taus[:, -1:], tol=1e-300, max_iter=64, restart=1, allow=(4, 5))
+    st_all = b.stats()
+    all_bytes = sum(ib[k] * rr[0]["iters"] for k, rr in enumerate(res_all))
+    all_iters = sum(rr[0]["iters"] for rr in res_all)
+    peak, src = measured_hbm_peak()
     b.free()
     it = sum(r["iters"] for rr in res for r in rr)
     ok = sum(r["status"] == 0 for rr in res for r in rr)
@@ -396,6 +419,16 @@ def batch_form(l1, W, ctx, iters_per_tau):
                         "certified_by_tau_index": ok_by_tau, "steps": st["steps"],
                         "ms_per_step": st["device_ms"] / max(1, st["steps"]), "schedule": sched,
                         "values": "FP32, float-float products and iterates"},
+            "bandwidth": {"path": {"algorithmic_bytes": path_bytes, "device_ms": st["device_ms"],
+                                   "gbs": path_bytes / (st["device_ms"] * 1e-3) / 1e9,
+                                   "frac": path_bytes / (st["device_ms"] * 1e-3) / 1e9 / peak},
+                          "last_tau_64_iterations": {"instance_iterations": all_iters, "steps": st_all["steps"],
+                                                     "algorithmic_bytes": all_bytes, "device_ms": st_all["device_ms"],
+                                                     "gbs": all_bytes / (st_all["device_ms"] * 1e-3) / 1e9,
+                                                     "frac": all_bytes / (st_all["device_ms"] * 1e-3) / 1e9 / peak},
+                          "peak_source": src,
+                          "bytes": "batch_bytes_per_step of each instance times its iterations (includes the "
+                                   "autotuner's probe steps in the path's device time)"},
             "one_at_a_time_fp64": {"seconds": t_one, "instances": len(sub), "instance_iterations": it_one,
                                    "instance_iterations_per_s": rate_one, "certified": ok_one,
                                    "of": len(sub) * 16, "certified_per_s": cert_rate_one,

@@ -128,3 +128,16 @@ def test_matrix_free_pcg_iteration_bytes_counted_array_by_array():
     update = 3 * 4 * n + 2 * 4 * n + 2 * 8 * n + 4 * n
     assert bench.mf_pcg_bytes_per_iteration(n) == sweep + update == 64 * n
     assert round(bench.mf_pcg_bytes_per_iteration(n) / 1e9, 2) == 1.07
+
+
+def test_batch_step_bytes_counted_array_by_array():
+    """One step of the batched kernel for one instance (FP32 values, paired storage, float-float
+    vectors as {hi, lo} pairs), array by array: both orientations of the matrix with their
+    pointers; the row phase gathers the iterate pair (8n), reads and writes A x as pairs (16m),
+    reads b (4m) and writes the residual pair (8m); the column phase gathers the residual
+    (8m), reads both iterates and writes the new one (24n)."""
+    m, n, nnz = 2 ** 19, 2 ** 18, 8 * 2 ** 18 - 8
+    mats = 2 * (4 * (nnz // 2) + 4 * nnz) + 4 * (m // 2 + 1) + 4 * (n + 1)
+    rows = 8 * n + 16 * m + 4 * m + 8 * m
+    cols = 8 * m + 24 * n
+    assert bench.batch_bytes_per_step(m, n, nnz) == mats + rows + cols == 12 * nnz + 38 * m + 36 * n + 8
