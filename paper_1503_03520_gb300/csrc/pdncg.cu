@@ -952,7 +952,10 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
         L1LS_TRY(I->alloc(&w->r, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->ap, sizeof(Vec) * pad32(m)));
         L1LS_TRY(I->alloc(&w->ad, sizeof(Vec) * pad32(m)));
-        w->gm = grid_for(I, k_pd_resid<V, Vec, double, PAIRED>, PAIRED ? m / 2 : m);
+        // N1 gathers x in the product precision: the FP64 iterate, or with FP32 CG vectors
+        // its FP32 rounding, the high word of the float-float copy (the same values the
+        // FP32 sums would convert it to, at half the gathered bytes)
+        w->gm = grid_for(I, k_pd_resid<V, Vec, Vec, PAIRED>, PAIRED ? m / 2 : m);
         w->gn = grid_for(I, k_pd_atr<V, Vec, PAIRED>, n);
         w->gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)I->ctx->num_sms * 8));
         int gmax = std::max(w->gm, std::max(w->gn, w->gv));
@@ -1029,7 +1032,7 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
     }
     const int ls_passes = (o->ls_max - 1 + kTrialsPerPass - 1) / kTrialsPerPass;   // after the full-step pass
     for (;;) {
-        // N1 gathers the FP64 iterate (once per Newton step), or its float-float copy
+        // N1 gathers the iterate (FP64, or its FP32 word with FP32 CG vectors), or its float-float copy
         if constexpr (sizeof(Vec) == 4) {
             if (comp) {
                 k_pd_resid_ff<V, PAIRED><<<w->gmf, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->xh, w->xl, I->bhat32, w->rff,
@@ -1039,8 +1042,9 @@ l1ls_status run(Inst* I, const l1ls_solve_opts* o, const double* x0, double* x_o
             }
         }
         if (!comp) {
-            k_pd_resid<V, Vec, double, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, w->X, bvec, (Vec*)w->r, m,
-                                                                        w->part, w->st);
+            const Vec* xg = sizeof(Vec) == 8 ? (const Vec*)w->X : (const Vec*)w->xh;
+            k_pd_resid<V, Vec, Vec, PAIRED><<<w->gm, kBlock, 0, s>>>(R.ptr, R.idx, R.val, xg, bvec, (Vec*)w->r, m,
+                                                                     w->part, w->st);
             k_pd_atr<V, Vec, PAIRED><<<w->gn, kBlock, 0, s>>>(C.ptr, C.idx, C.val, (const Vec*)w->r, w->X, w->atr, n,
                                                               w->part, w->st);
         }
