@@ -52,7 +52,7 @@ struct PdState {
     double P, D, gap, rel, prev_gap;
     int32_t prev_full, stage_err;   // stage_err: kStageTimeout if a stage wait ran out
     double k1[2];
-    double gnorm2, rz, rz0, alpha, beta;
+    double rz, rz0, alpha, beta;
     int32_t cg_done, pad1;
     int64_t cg_it;
     double rAd, AdAd, step;
@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x
                                                     CV* __restrict__ minv, typename CgRes<CV>::type* __restrict__ rcg,
                                                     CV* __restrict__ z, CV* __restrict__ d,
                                                     int64_t n, double* partials, PdState* st) {
-    __shared__ double red[2 * 32];
+    __shared__ double red[32];
     if (halted(st)) return;
     const double mu = st->mu, tau = st->tau, itau = 1.0 / tau;
-    double q[2] = {0.0, 0.0};
+    double q[1] = {0.0};
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < n; j += (int64_t)gridDim.x * kBlock) {
         const double xj = x[j], aj = atr[j];
         // one reciprocal square root instead of a square root and three divisions (FP64 pipe)
@@ -278,15 +278,13 @@ __global__ void __launch_bounds__(kBlock) k_pd_init(const double* __restrict__ x
         }
         z[j] = zj;
         d[j] = CV(0);
-        q[0] += gr * gr;
-        q[1] += rc * (double)zj;
+        q[0] += rc * (double)zj;
     }
-    block_reduce<kBlock, 2>(q, 0u, red);
-    double tot[2];
-    if (grid_reduce_last<kBlock, 2>(q, 0u, partials, &st->cnt[2], tot, red) && threadIdx.x == 0) {
-        st->gnorm2 = tot[0];
-        st->rz = tot[1];
-        st->rz0 = tot[1];
+    block_reduce<kBlock, 1>(q, 0u, red);
+    double tot[1];
+    if (grid_reduce_last<kBlock, 1>(q, 0u, partials, &st->cnt[2], tot, red) && threadIdx.x == 0) {
+        st->rz = tot[0];
+        st->rz0 = tot[0];
         st->beta = 0.0;
         st->cg_done = 0;
         st->cg_it = 0;
