@@ -308,8 +308,7 @@ struct K1CArgs {
     const int32_t* ptr;
     const int32_t* col;
     const V* val;
-    const float* xh;     // x_{k-1}, float-float
-    const float* xl;
+    const float2* x;     // x_{k-1}, float-float {hi, lo} pairs (one 8-byte gather per entry)
     float2* ax;          // in: A x_{k-2}; out: A x_{k-1} (float-float)
     float* res;          // out: r_k (layout above)
     const float* b;
@@ -324,10 +323,8 @@ struct K2CArgs {
     const int32_t* pair;     // pair index (paired) or row index (plain) per entry
     const V* val;
     const float* res;
-    const float* xch;
-    const float* xcl;
-    float* xoh;
-    float* xol;
+    const float2* x1;    // x_{k-1} as {hi, lo} pairs
+    float2* x0;          // in: x_{k-2}; out: x_k
     double* partials;
     FistaState* st;
     int64_t n;
@@ -373,12 +370,13 @@ __global__ void __launch_bounds__(kBlock, L1LS_K1C_MIN_BLOCKS) k_fista_k1c(K1CAr
     };
     const int64_t nrows = PAIRED ? a.m / 2 : a.m;
     if constexpr (PAIRED) {
-        warp_pcsr<true, V>(a.ptr, a.col, a.val, nrows, sm, &a.st->stage_err, FFSum<true, V>{a.xh, a.xl, nullptr}, pre,
-                           epi);
+        warp_pcsr<true, V>(a.ptr, a.col, a.val, nrows, sm, &a.st->stage_err,
+                           FFSum<true, V>{reinterpret_cast<const float*>(a.x), nullptr, nullptr}, pre, epi);
     } else {
         const int64_t nw = (int64_t)gridDim.x * (kBlock / 32), ntiles = (nrows + 31) >> 5;
         for (int64_t t = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < ntiles; t += nw)
-            tile_ff<true, false, V>(t, a.ptr, a.col, a.val, a.xh, a.xl, nullptr, nrows, sm.warp_buf(), pre, epi);
+            tile_ff<true, false, V>(t, a.ptr, a.col, a.val, reinterpret_cast<const float*>(a.x), nullptr, nullptr,
+                                    nrows, sm.warp_buf(), pre, epi);
     }
     double p[3] = {ff_to_double(q[0]), ff_to_double(q[1]), ff_to_double(q[2])};
     block_reduce<kBlock, 3>(p, 0u, red);
@@ -406,15 +404,15 @@ __global__ void __launch_bounds__(kBlock, L1LS_K2C_MIN_BLOCKS) k_fista_k2c(K2CAr
     auto pre = [&](int64_t j, bool has) {
         Ops o{{0.f, 0.f}, {0.f, 0.f}};
         if (has) {   // read once in this iteration (evict-first, as in K2)
-            o.x1 = {__ldcs(a.xch + j), __ldcs(a.xcl + j)};
-            o.x0 = {__ldcs(a.xoh + j), __ldcs(a.xol + j)};
+            const float2 v1 = __ldcs(a.x1 + j), v0 = __ldcs(a.x0 + j);
+            o.x1 = {v1.x, v1.y};
+            o.x0 = {v0.x, v0.y};
         }
         return o;
     };
     auto epi = [&](int64_t j, ff g, const Ops& o) {
         const FfStep f = ff_fista_step(o.x1, o.x0, g, beta_f, invL_f, thr_f);
-        a.xoh[j] = f.x.hi;
-        a.xol[j] = f.x.lo;
+        a.x0[j] = make_float2(f.x.hi, f.x.lo);
         gmax = fmaxf(gmax, fabsf(g.hi));
         sum2_add(l1, f.mag);
         if (rs) sum2_add(rt, ff_mul(ff_sub(f.y, f.x), ff_sub(f.x, o.x1)));
@@ -632,6 +630,19 @@ __global__ void k_ff2d(const float* __restrict__ hi, const float* __restrict__ l
     if (i < n) out[i] = ff_to_double({hi[i], lo[i]});
 }
 
+// the same for the {hi, lo} pairs of the float-float kernels
+__global__ void k_d2ff2(const double* __restrict__ in, int64_t n, float2* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ff v = ff_from_double(in[i]);
+    out[i] = make_float2(v.hi, v.lo);
+}
+
+__global__ void k_ff22d(const float2* __restrict__ x, int64_t n, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ff_to_double({x[i].x, x[i].y});
+}
+
 template <class K>
 int grid_of(const Inst* I, K kernel, int64_t rows) {
     int per_sm = 0;
@@ -654,6 +665,7 @@ struct FistaWork {
     float* zt = nullptr;
     float2* ax_ff = nullptr;             // compensated kernels: A x and the residual (2m floats)
     float* res_ff = nullptr;
+    float2* X2[2] = {nullptr, nullptr};  // compensated kernels: the iterates as {hi, lo} pairs
     int grid1c = 0, grid2c = 0;
     bool comp = false;                   // this run uses the compensated kernels
     bool restart = false;                // this run uses the gradient restart
@@ -744,8 +756,7 @@ void enqueue_k1c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a.ptr = I->paired ? I->prow_ptr : I->csr_ptr;
     a.col = I->paired ? I->prow_col : I->csr_col;
     a.val = static_cast<const V*>(I->paired ? I->prow_val : I->csr_val);
-    a.xh = w->Xh[parity];
-    a.xl = w->Xl[parity];
+    a.x = w->X2[parity];
     a.ax = w->ax_ff;
     a.res = w->res_ff;
     a.b = I->bhat32;
@@ -764,10 +775,8 @@ void enqueue_k2c(Inst* I, FistaWork* w, int parity, cudaStream_t st) {
     a.pair = I->paired ? I->pcol_pair : I->csc_row;
     a.val = static_cast<const V*>(I->paired ? I->pcol_val : I->csc_val);
     a.res = w->res_ff;
-    a.xch = w->Xh[c];
-    a.xcl = w->Xl[c];
-    a.xoh = w->Xh[o];
-    a.xol = w->Xl[o];
+    a.x1 = w->X2[c];
+    a.x0 = w->X2[o];
     a.partials = w->part2;
     a.st = w->st;
     a.n = I->n;
@@ -892,7 +901,9 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         I->fista_work_free = [](void* p) { delete static_cast<FistaWork*>(p); };
     }
     if constexpr (sizeof(Vec) == 4) {
-        if (o->accum == 1 && !w->res_ff) {   // res_ff last: set only when both exist
+        if (o->accum == 1 && !w->res_ff) {   // res_ff last: set only when all exist
+            for (int k = 0; k < 2; ++k)
+                if (!w->X2[k]) L1LS_TRY(I->alloc_n(&w->X2[k], pad32(n)));
             if (!w->ax_ff) L1LS_TRY(I->alloc_n(&w->ax_ff, pad32(m)));
             L1LS_TRY(I->alloc_n(&w->res_ff, 2 * pad32(m)));
             if (I->paired) {
@@ -931,6 +942,9 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         if (sizeof(Vec) == 8) {
             L1LS_CUDA(cudaMemcpyAsync(w->X[0], w->tmp64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             L1LS_CUDA(cudaMemcpyAsync(w->X[1], w->tmp64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        } else if (w->comp) {
+            k_d2ff2<<<nb, 256, 0, st>>>(w->tmp64, n, w->X2[0]);
+            k_d2ff2<<<nb, 256, 0, st>>>(w->tmp64, n, w->X2[1]);
         } else {
             k_d2ff<<<nb, 256, 0, st>>>(w->tmp64, n, w->Xh[0], w->Xl[0]);
             k_d2ff<<<nb, 256, 0, st>>>(w->tmp64, n, w->Xh[1], w->Xl[1]);
@@ -955,6 +969,8 @@ l1ls_status begin(Inst* I, const l1ls_solve_opts* o, const double* x0, cudaStrea
         if (sizeof(Vec) == 8) {
             L1LS_CUDA(cudaMemsetAsync(w->X[0], 0, sizeof(double) * n, st));
             L1LS_CUDA(cudaMemsetAsync(w->X[1], 0, sizeof(double) * n, st));
+        } else if (w->comp) {
+            for (int k = 0; k < 2; ++k) L1LS_CUDA(cudaMemsetAsync(w->X2[k], 0, sizeof(float2) * n, st));
         } else {
             for (int k = 0; k < 2; ++k) {
                 L1LS_CUDA(cudaMemsetAsync(w->Xh[k], 0, sizeof(float) * n, st));
@@ -1035,6 +1051,10 @@ l1ls_status end(Inst* I, double* x_out, l1ls_result* res, l1ls_status final_stat
         const int c = (int)(f.cert_iter & 1);
         if (w->X[c]) {
             L1LS_CUDA(cudaMemcpyAsync(x_out, w->X[c], sizeof(double) * I->n, cudaMemcpyDefault, st));
+        } else if (w->comp) {
+            k_ff22d<<<(unsigned)((I->n + 255) / 256), 256, 0, st>>>(w->X2[c], I->n, w->tmp64);
+            L1LS_CUDA(cudaGetLastError());
+            L1LS_CUDA(cudaMemcpyAsync(x_out, w->tmp64, sizeof(double) * I->n, cudaMemcpyDefault, st));
         } else {
             k_ff2d<<<(unsigned)((I->n + 255) / 256), 256, 0, st>>>(w->Xh[c], w->Xl[c], I->n, w->tmp64);
             L1LS_CUDA(cudaGetLastError());
